@@ -1,0 +1,134 @@
+"""Seeded synthetic inputs for TR-ALS-Sampled, shared by the tests, the oracle checks and
+the benchmark.
+
+This module only draws random numbers and lays them out; it holds no step of the sampled
+ALS method. Random cores are returned in the paper's shape ``(R_{k-1}, I_k, R_k)``
+(Sec. 2.1); ``slice_major`` converts them to the library's ``[I_k][Rl][Rr]`` layout.
+
+Workload recipes (the paper's datasets are not available; these synthetic tensors stand
+in for its synthetic experiment of Sec. 4.1.1 and its image-stack workloads):
+  * ``tr_plus_noise``: X = TR(cores) + Gaussian noise, cores i.i.d. N(0, 1), noise
+    standard deviation ``rel * ||TR||_F / sqrt(prod I)`` so that the total noise norm is
+    ``rel * ||TR||_F``.
+  * ``cosine_sum``: X = sum over 20 terms of products over modes of
+    cos(2 pi f i_k / I_k + phi), f ~ U[0, 4), phi ~ U[0, 2 pi), plus uniform noise
+    U[-a, a] with a = 5 % of max |X|.
+"""
+
+from __future__ import annotations
+
+import math
+from typing import List, Sequence
+
+import torch
+
+
+def _gen(seed: int) -> torch.Generator:
+    g = torch.Generator(device="cpu")
+    g.manual_seed(int(seed))
+    return g
+
+
+def random_cores(dims: Sequence[int], ranks: Sequence[int], seed: int,
+                 dtype=torch.float64) -> List[torch.Tensor]:
+    """N(0, 1) cores; core k has shape (ranks[k-1], dims[k], ranks[k])."""
+    g = _gen(seed)
+    N = len(dims)
+    out = []
+    for k in range(N):
+        shape = (int(ranks[(k - 1) % N]), int(dims[k]), int(ranks[k]))
+        out.append(torch.randn(shape, generator=g, dtype=torch.float64).to(dtype))
+    return out
+
+
+def slice_major(core: torch.Tensor) -> torch.Tensor:
+    """(Rl, I, Rr) -> contiguous (I, Rl, Rr): each lateral slice G(:, i, :) contiguous."""
+    return core.permute(1, 0, 2).contiguous()
+
+
+def paper_layout(core_slice_major: torch.Tensor) -> torch.Tensor:
+    """(I, Rl, Rr) -> (Rl, I, Rr)."""
+    return core_slice_major.permute(1, 0, 2).contiguous()
+
+
+def _ring_tensor(cores: Sequence[torch.Tensor], device, dtype) -> torch.Tensor:
+    """Dense tensor of a ring of cores, merged left to right and closed by a trace."""
+    dims = [int(c.shape[1]) for c in cores]
+    T = cores[0].to(device=device, dtype=dtype)
+    for G in cores[1:-1]:
+        G = G.to(device=device, dtype=dtype)
+        Ra, M, Rb = T.shape
+        T = torch.einsum("amb,bic->amic", T, G).reshape(Ra, M * G.shape[1], G.shape[2])
+    last = cores[-1].to(device=device, dtype=dtype)
+    Ra, M, Rb = T.shape
+    # X[m, i] = sum_{a,b} T[a, m, b] * last[b, i, a]  -> one matmul
+    lhs = T.permute(1, 0, 2).reshape(M, Ra * Rb)                    # [m, a*Rb + b]
+    rhs = last.permute(2, 0, 1).reshape(Ra * Rb, last.shape[1])     # [a*Rb + b, i]
+    return (lhs @ rhs).reshape(dims)
+
+
+def tr_plus_noise(dims, ranks, seed: int, rel_noise: float, device="cpu",
+                  dtype=torch.float32):
+    """X = TR(cores) + noise of total norm rel_noise * ||TR||_F. Returns (X, cores)."""
+    cores = random_cores(dims, ranks, seed)
+    X = _ring_tensor(cores, device, torch.float64 if dtype == torch.float64 else torch.float32)
+    if rel_noise > 0:
+        sigma = rel_noise * float(torch.linalg.vector_norm(X, dtype=torch.float64)) \
+            / math.sqrt(X.numel())
+        g = torch.Generator(device=X.device)
+        g.manual_seed(int(seed) + 7919)
+        X.add_(torch.randn(X.shape, generator=g, device=X.device, dtype=X.dtype), alpha=sigma)
+    return X.to(dtype), cores
+
+
+def cosine_sum(dims, seed: int, terms: int = 20, noise_amp: float = 0.05, device="cpu",
+               dtype=torch.float32) -> torch.Tensor:
+    """Sum of ``terms`` separable products of low-frequency cosines plus uniform noise."""
+    g = _gen(seed)
+    factors = []
+    for I in dims:
+        f = torch.rand(terms, generator=g, dtype=torch.float64) * 4.0
+        phi = torch.rand(terms, generator=g, dtype=torch.float64) * (2 * math.pi)
+        i = torch.arange(I, dtype=torch.float64)[:, None]
+        factors.append(torch.cos(2 * math.pi * f[None, :] * i / I + phi[None, :]))
+    # Khatri-Rao of the leading half of the modes times that of the trailing half.
+    h = len(dims) // 2
+
+    def khatri_rao(mats):
+        out = mats[0]
+        for Mx in mats[1:]:
+            out = (out[:, None, :] * Mx[None, :, :]).reshape(-1, terms)
+        return out
+
+    left = khatri_rao(factors[:h]).to(device=device, dtype=torch.float32)
+    right = khatri_rao(factors[h:]).to(device=device, dtype=torch.float32)
+    X = (left @ right.T).reshape([int(d) for d in dims])
+    a = noise_amp * float(X.abs().max())
+    gd = torch.Generator(device=X.device)
+    gd.manual_seed(int(seed) + 104729)
+    X.add_(torch.rand(X.shape, generator=gd, device=X.device, dtype=X.dtype).mul_(2 * a).sub_(a))
+    return X.to(dtype)
+
+
+def random_distribution(I: int, seed: int, zero_frac: float = 0.0) -> torch.Tensor:
+    """A probability vector on [I] (FP64); a fraction of entries set exactly to zero."""
+    g = _gen(seed)
+    p = torch.rand(I, generator=g, dtype=torch.float64) + 0.05
+    if zero_frac > 0:
+        z = torch.rand(I, generator=g, dtype=torch.float64) < zero_frac
+        z[0] = False
+        p[z] = 0.0
+    return p / p.sum()
+
+
+# Workloads: (dims, ranks, J, sweeps, relative noise, X dtype).
+WORKLOADS = {
+    # 3-way 100^3 FP64 TR of rank 5 + 1e-3 noise, J = 2000, 10 sweeps (FP64 path).
+    "tr3_100_r5_fp64": dict(dims=(100, 100, 100), ranks=(5, 5, 5), J=2000, sweeps=10,
+                           rel_noise=1e-3, dtype=torch.float64, seed=0, init_seed=0,
+                           sample_seed=0),
+    # 3-way 500^3 FP32 TR of rank 10 + 1e-2 noise, J = 4000, 10 sweeps (mixed path).
+    "tr3_500_r10_fp32": dict(dims=(500, 500, 500), ranks=(10, 10, 10), J=4000, sweeps=10,
+                            rel_noise=1e-2, dtype=torch.float32, seed=1, init_seed=1,
+                            sample_seed=2),
+}
