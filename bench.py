@@ -1,0 +1,474 @@
+"""Benchmark: ALS sweeps/s of TR-ALS-Sampled on the 500x500x500 FP32 rank-10 workload.
+
+One step = one whole decomposition through the C ABI (tr_als_sampled: initial leverage
+scores + 10 sweeps of Alg. 2, J = 4000, mixed precision) with X resident in HBM. The
+metric is sweeps/s = sweeps per step * steps / time. Besides it the JSON line carries the
+end-to-end number through the host-memory entry point, the roofline of the dominant
+kernel, the plain FP64 GPU form (the metric's comparator) and the FP64 CPU oracle on a
+bounded sample.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun), every rank decomposes its own tensor (replicas, weak scaling).
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2010_08581_gb300 import inputs  # noqa: E402
+
+WORKLOAD = "tr3_500_r10_fp32"
+METRIC = "ALS sweeps/s at fixed rel. fit vs plain FP64 GPU; p50/p99 decomposition latency"
+FALLBACK_HBM_GBS = 6800.0
+FALLBACK_BF16_TFLOPS = 1900.0
+NOMINAL_FP64_TFLOPS = 1.25
+
+
+def workload_config(wl):
+    return {
+        "workload": f"{WORKLOAD}: 500x500x500 FP32 X = TR(rank-10 N(0,1) cores) + 1e-2 rel. "
+                    f"Gaussian noise; target ranks 10, J={wl['J']}, {wl['sweeps']} sweeps per "
+                    "step (one whole decomposition), mixed precision (FP32 rows/fibres/"
+                    "contractions, FP64 Cholesky + refinement + leverage)",
+        "dims": list(wl["dims"]), "ranks": list(wl["ranks"]), "J": wl["J"],
+        "sweeps_per_step": wl["sweeps"],
+        "l2": "inputs larger than L2: X is 500 MB (> 129 MB L2); samples are redrawn every "
+              "step (seed + step)",
+    }
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def allreduce_max(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# --------------------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        self.t0 = time.time()
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            out["reasons"] = ["nvidia-smi unavailable"]
+            return out
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if sm:
+            out.update(sm_mhz=statistics.median(sm), sm_max_mhz=max(mx), samples=len(sm))
+        out["reasons"] = sorted(reasons)
+        return out
+
+
+# --------------------------------------------------------------------------------------
+# roofline of the dominant kernel
+# --------------------------------------------------------------------------------------
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+    except Exception:
+        return None
+    return d
+
+
+def _peak_hbm(peaks):
+    if peaks:
+        for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+            if k in peaks and isinstance(peaks[k], (int, float)):
+                return float(peaks[k]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def algorithmic_cost(kernel, wl):
+    """(kind, per-launch algorithmic bytes or flops) of one launch on this workload.
+
+    Per core update n (I = I_n, L = R^2, J samples, s = 4 bytes in the mixed path):
+      gather        : J*I*s read + J*I*s written
+      normal_eq     : 2*J*L*(L + I) flops (SIMT FP32)
+      subchain      : J*(N-1)*L*8 slice bytes read + J*L*s written
+      cholesky_*    : L^3/3 FP64 flops
+      solve_rhs     : (4 + 2) * L^2 * I FP64 flops (two solves, refinement residual)
+      gram_f64      : I*L^2 FP64 flops (upper tiles, counted as full products)
+    """
+    dims, ranks, J = wl["dims"], wl["ranks"], wl["J"]
+    N = len(dims)
+    I = sum(dims) / N
+    L = ranks[0] * ranks[1]
+    s = 4
+    table = {
+        "gather": ("hbm", 2.0 * J * I * s),
+        "normal_eq": ("flops_f32", 2.0 * J * L * (L + I)),
+        "subchain": ("hbm", J * (N - 1) * L * 8.0 + J * L * s),
+        "cholesky_solve": ("flops_f64", L ** 3 / 3.0),
+        "cholesky_leverage": ("flops_f64", L ** 3 / 3.0),
+        "solve_rhs": ("flops_f64", 6.0 * L * L * I),
+        "gram_f64": ("flops_f64", 2.0 * I * L * L),
+        "leverage_rows": ("flops_f64", I * L * L),
+        "sample": ("hbm", J * (N - 1) * (4 + 8 * math.log2(max(I, 2))) + J * 8),
+        "reduce_B": ("hbm", L * I * 8.0),
+        "reduce_M": ("hbm", L * L * 8.0),
+        "reduce_gram": ("hbm", L * L * 8.0),
+        "cdf": ("hbm", I * 8.0 * 3),
+        "init_normal": ("hbm", I * L * 8.0),
+    }
+    return table.get(kernel)
+
+
+def traffic_for(kernel):
+    """Per-launch DRAM bytes from the committed ncu summary, if its source is unchanged."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(path))
+    except Exception:
+        return None
+    e = d.get(kernel)
+    if not e:
+        return None
+    src = os.path.join(ROOT, "paper_2010_08581_gb300", "csrc", e.get("source", ""))
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except Exception:
+        return None
+    return e.get("bytes_per_launch") if h == e.get("source_sha") else None
+
+
+def roofline(prof, wl, peaks):
+    ranked = sorted(prof.items(), key=lambda kv: -kv[1][0])
+    for name, (ms, n) in ranked:
+        cost = algorithmic_cost(name, wl)
+        if cost is None:
+            continue
+        kind, amount = cost
+        avg_s = ms / 1e3 / n
+        if kind == "hbm":
+            peak, src = _peak_hbm(peaks)
+            ach = amount / avg_s / 1e9
+            return {"kernel": name, "bound": "hbm", "achieved": round(ach, 3), "peak": peak,
+                    "unit": "GB/s", "frac": round(ach / peak, 5),
+                    "traffic": traffic_for(name), "peak_source": f"{src} HBM copy",
+                    "avg_launch_us": round(avg_s * 1e6, 3), "launches": n,
+                    "share_of_timed": None}
+        if kind == "flops_f64":
+            # FP64 ALU bound: nominal GB300 FP64 rate (no measured FP64 peak is provided).
+            peak = NOMINAL_FP64_TFLOPS
+            ach = amount / avg_s / 1e12
+            return {"kernel": name, "bound": "alu", "achieved": round(ach, 6), "peak": peak,
+                    "unit": "TFLOP/s", "frac": round(ach / peak, 5),
+                    "traffic": traffic_for(name),
+                    "peak_source": "nominal FP64 1.25 TFLOP/s (152 SMs x clock x FP64 units)",
+                    "avg_launch_us": round(avg_s * 1e6, 3), "launches": n,
+                    "share_of_timed": None}
+        if kind == "flops_f32":
+            # SIMT FP32: 152 SMs * 128 FMA/clk * 2 flop * 2.07 GHz
+            peak = 152 * 128 * 2 * 2.07e9 / 1e12
+            ach = amount / avg_s / 1e12
+            return {"kernel": name, "bound": "alu", "achieved": round(ach, 4), "peak": round(peak, 2),
+                    "unit": "TFLOP/s", "frac": round(ach / peak, 5),
+                    "traffic": traffic_for(name),
+                    "peak_source": "FP32 SIMT: 152 SMs x 128 FMA/clk x 2 x 2.07 GHz",
+                    "avg_launch_us": round(avg_s * 1e6, 3), "launches": n,
+                    "share_of_timed": None}
+    return None
+
+
+# --------------------------------------------------------------------------------------
+# CPU oracle on a bounded sample
+# --------------------------------------------------------------------------------------
+def oracle_sample(X_np, init_paper, wl, budget_s=15.0, max_sweeps=50):
+    """Time the FP64 NumPy oracle (as it stands) doing whole sweeps of the same workload
+    until about budget_s seconds of CPU work."""
+    import oracle as orc
+    N = len(wl["dims"])
+    cores = [np.array(c, dtype=np.float64) for c in init_paper]
+    ps, cdfs = [None] * N, [None] * N
+    t0 = time.perf_counter()
+    for k in range(1, N):
+        ps[k], cdfs[k] = orc.core_distribution(cores[k])
+    sweeps = 0
+    while sweeps < max_sweeps:
+        for n in range(N):
+            cores[n], _, _ = orc.sampled_core_update(X_np, cores, ps, cdfs, n, wl["J"],
+                                                     wl["sample_seed"], sweeps * N + n)
+            ps[n], cdfs[n] = orc.core_distribution(cores[n])
+        sweeps += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    try:
+        ncores = len(os.sched_getaffinity(0))
+    except Exception:
+        ncores = os.cpu_count()
+    return sweeps, dt, ncores
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    wl = inputs.WORKLOADS[WORKLOAD]
+    X, _ = inputs.tr_plus_noise(wl["dims"], wl["ranks"], seed=wl["seed"],
+                                rel_noise=wl["rel_noise"], dtype=torch.float32)
+    Xn = X.numpy()
+    init = [c.numpy() for c in inputs.random_cores(wl["dims"], wl["ranks"], wl["init_seed"])]
+    per_step = []
+    total_sweeps = 0
+    for k in range(args.warmup + args.steps):
+        sw, dt, ncores = oracle_sample(Xn, init, wl, budget_s=4.0, max_sweeps=wl["sweeps"])
+        if k >= args.warmup:
+            per_step.append(dt)
+            total_sweeps += sw
+    T = sum(per_step)
+    value = total_sweeps / T
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "sweeps/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * T / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(wl),
+        "cpu_baseline": {"value": round(value, 4), "unit": "sweeps/s", "cores": ncores,
+                         "kind": "oracle",
+                         "sample": f"each step: the NumPy FP64 oracle runs whole sweeps of the "
+                                   f"same workload (up to {wl['sweeps']}, about 4 s of CPU work)"},
+        "e2e": {"value": round(value, 4), "unit": "sweeps/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# --------------------------------------------------------------------------------------
+# our path
+# --------------------------------------------------------------------------------------
+def run_ours(args):
+    from paper_2010_08581_gb300 import plain_fp64
+    from paper_2010_08581_gb300 import trals as T
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    wl = inputs.WORKLOADS[WORKLOAD]
+    dims, ranks, J, sweeps = wl["dims"], wl["ranks"], wl["J"], wl["sweeps"]
+    N = len(dims)
+
+    # CPU oracle sample first (rank 0, N = 1 only), before any GPU work.
+    cpu = None
+    X_cpu = None
+    init_paper = [c for c in inputs.random_cores(dims, ranks, wl["init_seed"])]
+    if rank == 0 and world == 1 and not args.skip_cpu:
+        X_cpu, _ = inputs.tr_plus_noise(dims, ranks, seed=wl["seed"], rel_noise=wl["rel_noise"],
+                                        dtype=torch.float32)
+        sw, dt, ncores = oracle_sample(X_cpu.numpy(), [c.numpy() for c in init_paper], wl,
+                                       budget_s=args.cpu_seconds)
+        cpu = {"value": round(sw / dt, 4), "unit": "sweeps/s", "cores": ncores, "kind": "oracle",
+               "sample": f"{sw} whole sweeps of the same workload by the NumPy FP64 oracle "
+                         f"(paper's QR solve), {dt:.1f} s on the host; cores = visible CPUs "
+                         "(NumPy's BLAS default thread count)"}
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    X, _ = inputs.tr_plus_noise(dims, ranks, seed=wl["seed"] + rank, rel_noise=wl["rel_noise"],
+                                device=dev, dtype=torch.float32)
+    init_dev = [inputs.slice_major(c).to(dev) for c in init_paper]
+    ctx = T.Context(local)
+    cores = T.empty_cores(dims, ranks, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(i):
+        T.tr_als_sampled(ctx, X, ranks, J, sweeps, wl["sample_seed"] + i, T.TR_PREC_MIXED, cores,
+                         init_cores=init_dev)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    T.tr_profile_begin(ctx)
+    for i in range(args.steps):
+        evs[i][0].record(stream)
+        step(args.warmup + i)
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    prof = T.tr_profile_end(ctx)
+    barrier(world)
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_s = allreduce_max(sum(step_ms) / 1e3, world)
+    value = world * sweeps * args.steps / total_s
+    fit = T.tr_rel_error(ctx, X, ranks, cores)
+
+    # end to end through the host entry point: H2D of X and the initial cores, D2H of the
+    # resulting cores, every step.
+    Xh = X.cpu().pin_memory()
+    init_h = [c.cpu().pin_memory() for c in init_dev]
+    out_h = [torch.empty(c.shape, dtype=torch.float64).pin_memory() for c in cores]
+    e2e_steps = max(1, min(args.steps, 5))
+    T.tr_als_sampled_host(ctx, Xh, ranks, J, sweeps, 1, T.TR_PREC_MIXED, out_h, init_h)
+    torch.cuda.synchronize()
+    barrier(world)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    e0.record(stream)
+    for i in range(e2e_steps):
+        T.tr_als_sampled_host(ctx, Xh, ranks, J, sweeps, 100 + i, T.TR_PREC_MIXED, out_h, init_h)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_s = allreduce_max(max(e0.elapsed_time(e1) / 1e3, time.perf_counter() - t0), world)
+    e2e_value = world * sweeps * e2e_steps / e2e_s
+    h2d = Xh.numel() * 4 + sum(c.numel() * 8 for c in init_h[1:])
+    d2h = sum(c.numel() * 8 for c in out_h)
+
+    # plain FP64 GPU form at the same workload (comparator of the metric)
+    fp64 = None
+    if not args.skip_fp64:
+        init_pl = [c.to(dev) for c in init_paper]
+        plain_fp64.als_sampled(X, init_pl, J, 1, 0)       # warm-up
+        torch.cuda.synchronize()
+        reps = 2
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for r in range(reps):
+            res = plain_fp64.als_sampled(X, init_pl, J, sweeps, 1 + r)
+        b.record(stream)
+        torch.cuda.synchronize()
+        sec = a.elapsed_time(b) / 1e3
+        fp64_fit = plain_fp64.rel_error(X, res)
+        fp64 = {"value": round(sweeps * reps / sec, 3), "unit": "sweeps/s",
+                "final_rel_err": fp64_fit,
+                "speedup": round(value / world / (sweeps * reps / sec), 2),
+                "equal_fit": abs(fit - fp64_fit) <= 0.01 * fp64_fit}
+
+    peaks = measured_peaks()
+    roof = roofline(prof, wl, peaks)
+    tot_ms = sum(v[0] for v in prof.values())
+    if roof:
+        roof["share_of_timed"] = round(prof[roof["kernel"]][0] / max(tot_ms, 1e-9), 4)
+    launches = int(sum(v[1] for v in prof.values()))
+    lat = sorted(step_ms)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": "sweeps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(total_s * 1e3 / args.steps, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": workload_config(wl),
+            "final_rel_err": fit,
+            "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 4),
+                           "p99": round(float(np.percentile(lat, 99)), 4),
+                           "what": "one whole decomposition (10 sweeps) per step"},
+            "e2e": {"value": round(e2e_value, 3), "unit": "sweeps/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "steps": e2e_steps},
+            "gpu_launches": launches,
+            "roofline": roof,
+            "kernels_ms": {k: [round(v[0], 4), v[1]] for k, v in
+                           sorted(prof.items(), key=lambda kv: -kv[1][0])},
+            "fp64_gpu_form": fp64,
+            "cpu_baseline": cpu,
+            "clocks": clk,
+        }
+        print(json.dumps(line))
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-fp64", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

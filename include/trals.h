@@ -1,0 +1,180 @@
+/*
+ * trals.h -- C ABI of libtrals.so, a GB300 (sm_103a) implementation of the hot path of
+ * TR-ALS-Sampled (Malik & Becker, "A Sampling-Based Method for Tensor Ring
+ * Decomposition", ICML 2021, Alg. 2 with Alg. 3 and Alg. 4).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Modes are 0-based: k = 0..N-1. ranks[k] is the paper's R_{k+1}; core k has left rank
+ *    Rl_k = ranks[(k-1+N) % N] and right rank Rr_k = ranks[k] (the paper's
+ *    G^(k+1) in R^{R_k x I_{k+1} x R_{k+1}}, Sec. 2.1, eq. 1).
+ *  - Cores are FP64, slice-major: core_k[i][a][b] at offset (i*Rl_k + a)*Rr_k + b, so the
+ *    lateral slice G(:, i, :) is one contiguous Rl_k x Rr_k row-major block.
+ *  - X is dense, row-major (last mode fastest), FP32 or FP64.
+ *  - Sampled multi-indices idx[J][N-1] (int32) are in ring order: position m holds the
+ *    index of mode (k+1+m) % N (Def. 3.1 / Alg. 3).
+ *  - Design rows: row j, column c = a + Rl_k*b holds the (b, a) entry of the Rr_k x Rl_k
+ *    slice product of Alg. 4 (the paper's column overline{r_{k-1} r_k}).
+ *  - All tensor arguments are DEVICE pointers owned by the caller unless stated; arrays of
+ *    per-mode pointers (cores, p, cdf) and dims/ranks are HOST arrays.
+ *  - Every call is asynchronous on `stream` (a cudaStream_t; NULL = legacy default
+ *    stream) and returns a status; nothing aborts or traps. Argument errors are reported
+ *    before any launch. Errors found on the device (a non-positive Cholesky pivot, an
+ *    out-of-range caller index) are recorded in the context and returned by the next
+ *    tr_status_sync() (or by the synchronous tr_als_sampled / tr_rel_error).
+ *  - A context owns only its device workspace (grown on demand, capped by the HBM budget
+ *    given at creation). Calls that share a context must not overlap in time: issue them
+ *    on one stream.
+ */
+#ifndef TRALS_H
+#define TRALS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum tr_status {
+  TR_OK = 0,
+  TR_ERR_INVALID_ARG = 1,  /* bad sizes, null pointers, unsupported rank/mode count     */
+  TR_ERR_OOM = 2,          /* device allocation failed                                  */
+  TR_ERR_BUDGET = 3,       /* workspace would exceed the context's HBM budget          */
+  TR_ERR_SINGULAR = 4,     /* non-positive pivot in the normal equations, or zero core */
+  TR_ERR_TIMEOUT = 5,      /* reserved for bounded device waits                         */
+  TR_ERR_CUDA = 6,         /* a CUDA runtime call failed (see tr_last_error)            */
+  TR_ERR_NOT_CONVERGED = 7 /* reserved                                                  */
+} tr_status;
+
+typedef enum tr_dtype { TR_F32 = 0, TR_F64 = 1 } tr_dtype;
+
+/* Arithmetic of the least-squares step (rows a3-a6).
+ * TR_PREC_FP64 : design rows, fibres, contractions, Cholesky and solves in FP64.
+ * TR_PREC_MIXED: design rows and fibres in FP32, contractions with FP32 accumulation,
+ *                FP64 Cholesky of the normal matrix, FP64 solve and one step of
+ *                iterative refinement against the FP32-accurate normal-equation residual. */
+typedef enum tr_precision { TR_PREC_FP64 = 0, TR_PREC_MIXED = 1 } tr_precision;
+
+typedef struct tr_ctx tr_ctx;
+typedef void* tr_stream;
+
+#define TR_MAX_MODES 16   /* largest N                                   */
+#define TR_MAX_RANK_PRODUCT 256 /* largest Rl_k * Rr_k (LS unknowns per row) */
+
+/* Create a context on CUDA device `device`. hbm_budget_bytes caps the workspace the
+ * context may allocate (0 = no cap). *ctx receives the handle (NULL on failure). */
+tr_status tr_create(tr_ctx** ctx, int device, size_t hbm_budget_bytes);
+
+/* Free the context and its workspace (synchronises the device first). NULL is a no-op. */
+void tr_destroy(tr_ctx* ctx);
+
+/* Text of the last error reported by a call on this context ("" if none). */
+const char* tr_last_error(const tr_ctx* ctx);
+
+/* Wait for `stream`, then return and clear the device-side error record of the context
+ * (TR_ERR_SINGULAR, TR_ERR_INVALID_ARG for out-of-range sample indices, or TR_OK). */
+tr_status tr_status_sync(tr_ctx* ctx, tr_stream stream);
+
+/* Row a1 -- sampling distribution of one core (Def. 3.3; eq. for p^(n); Alg. 2, "compute
+ * distributions" and "update n-th distribution").
+ * core  : FP64 [I][Rl][Rr]; the matrix G_(2) is I x (Rl*Rr).
+ * p     : FP64 [I] out, p[i] = ell_i(G_(2)) / sum_i ell_i(G_(2)).
+ * cdf   : FP64 [I] out, inclusive prefix sum of p in index order.
+ * Leverage scores come from a Cholesky-based thin QR of G_(2) (or of G_(2)^T when
+ * I < Rl*Rr) in FP64, with dependent columns dropped at pivot <= max(I,L)*eps*max diag.
+ * A zero core records TR_ERR_SINGULAR and yields the uniform distribution. */
+tr_status tr_leverage(tr_ctx* ctx, const double* core, int64_t I, int Rl, int Rr,
+                      double* p, double* cdf, tr_stream stream);
+
+/* Row a2 -- J i.i.d. draws from q^{!=k} = prod_{j!=k} p^(j) (Alg. 3; Def. 3.4).
+ * p, cdf   : host arrays of N device pointers (entry k unused), FP64 [dims[j]].
+ * seed, update_id : Philox4x32-10 key and counter words: the uniform for sample j at ring
+ *            position m comes from counter (j, m/2, update_id lo, update_id hi), words
+ *            (2(m%2), 2(m%2)+1) as (hi, lo), u = top 53 bits * 2^-53.
+ * idx      : int32 [J][N-1] out (ring order); index = smallest i with u < cdf[i], or
+ *            the largest i with p[i] > 0 when u >= cdf[last].
+ * w        : FP64 [J] out, w_j = 1 / sqrt(J * prod_m p(idx[j][m])) (product in ring
+ *            order). */
+tr_status tr_sample(tr_ctx* ctx, int N, int k, const int64_t* dims,
+                    const double* const* p, const double* const* cdf, int64_t J,
+                    uint64_t seed, uint64_t update_id, int32_t* idx, double* w,
+                    tr_stream stream);
+
+/* Row a3 -- sampled subchain S G_[2]^{!=k} (Alg. 4; Def. 3.2).
+ * cores : host array of N device pointers (entry k unused), FP64 slice-major.
+ * idx   : int32 [J][N-1] ring order; w: FP64 [J] row scales (NULL = 1).
+ * A     : [J][Rl_k*Rr_k] out in A_dtype (TR_F32: products in FP32; TR_F64: in FP64).
+ * Out-of-range indices record TR_ERR_INVALID_ARG and give zero rows. */
+tr_status tr_subchain(tr_ctx* ctx, int N, int k, const int64_t* dims, const int* ranks,
+                      const double* const* cores, const int32_t* idx, const double* w,
+                      int64_t J, void* A, tr_dtype A_dtype, tr_stream stream);
+
+/* Row a4 -- sampled fibres S X_[k]^T (Alg. 2, "compute X~"; Def. 3.1).
+ * X : dense row-major [dims[0]]...[dims[N-1]] in X_dtype.
+ * Y : [J][dims[k]] out in Y_dtype, Y[j][i] = w_j * X(.., i at mode k, ..).
+ * w : FP64 [J] (NULL = 1). Out-of-range indices record TR_ERR_INVALID_ARG, zero rows. */
+tr_status tr_gather(tr_ctx* ctx, const void* X, tr_dtype X_dtype, int N,
+                    const int64_t* dims, int k, const int32_t* idx, const double* w,
+                    int64_t J, void* Y, tr_dtype Y_dtype, tr_stream stream);
+
+/* Rows a5 + a6 -- solve the sampled LS argmin_Z || A Z - Y ||_F (Alg. 2, LS step) through
+ * the normal equations M = A^T A, B = A^T Y, FP64 Cholesky M = L L^T, Z = M^-1 B (and, in
+ * TR_PREC_MIXED, one refinement Z += M^-1 (B - M Z)), then write the new core
+ * core_out[i][a][b] = Z[a + Rl*b][i].
+ * A : [J][Rl*Rr], Y : [J][I], both in `dtype` (TR_F32 for TR_PREC_MIXED, TR_F64 for
+ * TR_PREC_FP64). A pivot <= L*eps*max diag(M) records TR_ERR_SINGULAR and leaves
+ * core_out unchanged. */
+tr_status tr_solve(tr_ctx* ctx, const void* A, const void* Y, tr_dtype dtype, int64_t J,
+                   int Rl, int Rr, int64_t I, tr_precision prec, double* core_out,
+                   tr_stream stream);
+
+/* The whole method (Alg. 2) with a fixed number of sweeps, synchronous.
+ * X          : device, row-major, X_dtype.
+ * init_cores : host array of N device pointers with the initial cores (entry 0 unused),
+ *              or NULL: cores 1..N-1 are drawn i.i.d. N(0,1) on the device from `seed`.
+ * cores      : host array of N device pointers, FP64 slice-major, receive the result.
+ * Sweep s, core n draws its samples with update_id = s*N + n.
+ * prec       : TR_PREC_MIXED expects X in FP32 or FP64; TR_PREC_FP64 any.
+ * Returns TR_ERR_SINGULAR if any update met a singular normal matrix (that core kept). */
+tr_status tr_als_sampled(tr_ctx* ctx, const void* X, tr_dtype X_dtype, int N,
+                         const int64_t* dims, const int* ranks, int64_t J, int sweeps,
+                         uint64_t seed, tr_precision prec, const double* const* init_cores,
+                         double* const* cores, tr_stream stream);
+
+/* Same as tr_als_sampled with X and the cores in HOST memory: X is copied to the device,
+ * the method runs, and the cores are copied back into the host arrays cores_host[k]
+ * (FP64 slice-major). init_cores_host may be NULL. Pinned host memory is fastest. */
+tr_status tr_als_sampled_host(tr_ctx* ctx, const void* X_host, tr_dtype X_dtype, int N,
+                              const int64_t* dims, const int* ranks, int64_t J, int sweeps,
+                              uint64_t seed, tr_precision prec,
+                              const double* const* init_cores_host,
+                              double* const* cores_host, tr_stream stream);
+
+/* Relative error ||TR(cores) - X||_F / ||X||_F (Sec. 4.1), synchronous; *rel_err is a
+ * host double. Reconstruction runs in X's precision with FP64 sums of squares. */
+tr_status tr_rel_error(tr_ctx* ctx, const void* X, tr_dtype X_dtype, int N,
+                       const int64_t* dims, const int* ranks, const double* const* cores,
+                       double* rel_err, tr_stream stream);
+
+/* Draw cores i.i.d. N(0,1) (Philox4x32-10 + Box-Muller) into the device buffers cores[k],
+ * k in [k_begin, N). Used by tr_als_sampled when init_cores is NULL. */
+tr_status tr_init_cores(tr_ctx* ctx, int N, const int64_t* dims, const int* ranks,
+                        uint64_t seed, int k_begin, double* const* cores, tr_stream stream);
+
+/* Per-kernel timing. Between tr_profile_begin and tr_profile_end every kernel the context
+ * launches is bracketed by a pair of CUDA events recorded on the launching stream.
+ * tr_profile_end waits for `stream` and folds the event pairs into per-kernel totals
+ * (milliseconds and launch counts) that tr_profile_entry reads by index
+ * (0 <= i < tr_profile_count). tr_profile_begin clears earlier totals. */
+tr_status tr_profile_begin(tr_ctx* ctx);
+tr_status tr_profile_end(tr_ctx* ctx, tr_stream stream);
+int tr_profile_count(const tr_ctx* ctx);
+tr_status tr_profile_entry(const tr_ctx* ctx, int i, const char** name, double* total_ms,
+                           int64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TRALS_H */

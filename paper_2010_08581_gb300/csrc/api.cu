@@ -1,0 +1,752 @@
+// C ABI of libtrals.so: argument checks, workspace, and the Alg. 2 driver. Every step of
+// the hot path runs in the kernels of this library; this file only validates, carves the
+// workspace and issues launches on the caller's stream.
+#include <cmath>
+#include <cstdarg>
+#include <map>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+struct tr_ctx {
+  int device = 0;
+  size_t budget = 0;
+  char* arena = nullptr;
+  size_t arena_bytes = 0;
+  char* host_stage = nullptr;      // device buffers of tr_als_sampled_host
+  size_t host_stage_bytes = 0;
+  unsigned* d_err = nullptr;
+  std::string last_error;
+  // per-kernel profiler
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<std::pair<const char*, size_t>> prof_marks;  // (kernel, first event index)
+  std::vector<std::string> prof_names;
+  std::vector<double> prof_ms;
+  std::vector<int64_t> prof_count;
+};
+
+namespace {
+
+using namespace trk;
+
+tr_status fail(tr_ctx* ctx, tr_status s, const char* fmt, ...) {
+  if (ctx) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    ctx->last_error = buf;
+  }
+  return s;
+}
+
+#define TR_CUDA(expr)                                                                   \
+  do {                                                                                  \
+    cudaError_t e_ = (expr);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return fail(ctx, TR_ERR_CUDA, "%s failed: %s", #expr, cudaGetErrorString(e_));   \
+  } while (0)
+
+#define TR_TRY(expr)                       \
+  do {                                     \
+    tr_status s_ = (expr);                 \
+    if (s_ != TR_OK) return s_;            \
+  } while (0)
+
+// Makes ctx->device current for the duration of a call and restores the caller's device.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    int cur;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+// Bump allocator over the context arena. With base == nullptr it only measures.
+struct Carver {
+  char* base;
+  size_t off = 0;
+  explicit Carver(char* b, size_t start = 0) : base(b), off(start) {}
+  template <typename T>
+  T* take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+tr_status ensure_ws(tr_ctx* ctx, size_t bytes) {
+  if (bytes <= ctx->arena_bytes) return TR_OK;
+  size_t want = bytes + bytes / 4;
+  want = (want + (2u << 20) - 1) & ~size_t((2u << 20) - 1);
+  if (ctx->budget && want + ctx->host_stage_bytes > ctx->budget) {
+    want = bytes;
+    if (want + ctx->host_stage_bytes > ctx->budget)
+      return fail(ctx, TR_ERR_BUDGET, "workspace of %zu bytes exceeds the HBM budget of %zu",
+                  bytes, ctx->budget);
+  }
+  // The old arena may still be read by queued work on any stream of this context.
+  TR_CUDA(cudaDeviceSynchronize());
+  if (ctx->arena) cudaFree(ctx->arena);
+  ctx->arena = nullptr;
+  ctx->arena_bytes = 0;
+  if (cudaMalloc(&ctx->arena, want) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->arena = nullptr;
+    return fail(ctx, TR_ERR_OOM, "cudaMalloc of %zu workspace bytes failed", want);
+  }
+  ctx->arena_bytes = want;
+  return TR_OK;
+}
+
+cudaStream_t S(tr_stream s) { return static_cast<cudaStream_t>(s); }
+
+// Records an event pair around one launch when profiling is on.
+struct Prof {
+  tr_ctx* ctx;
+  const char* name;
+  cudaStream_t st;
+  size_t first = 0;
+  bool on;
+  Prof(tr_ctx* c, const char* n, cudaStream_t s) : ctx(c), name(n), st(s), on(c->prof) {
+    if (!on) return;
+    if (ctx->ev_used + 2 > ctx->ev_pool.size()) {
+      for (int i = 0; i < 256; ++i) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) { on = false; return; }
+        ctx->ev_pool.push_back(e);
+      }
+    }
+    first = ctx->ev_used;
+    ctx->ev_used += 2;
+    cudaEventRecord(ctx->ev_pool[first], st);
+  }
+  ~Prof() {
+    if (!on) return;
+    cudaEventRecord(ctx->ev_pool[first + 1], st);
+    ctx->prof_marks.emplace_back(name, first);
+  }
+};
+
+#define TR_LAUNCH(name, expr)                     \
+  do {                                            \
+    Prof prof_(ctx, name, st);                    \
+    TR_CUDA(expr);                                \
+  } while (0)
+
+// ------------------------------------------------------------------------------------
+// Row a1: leverage-score distribution of one core.
+// ------------------------------------------------------------------------------------
+struct LevPass {  // one Cholesky-QR pass over an m x n row-major matrix (n = Gram size)
+  double* partial; double* G; double* Lrow; double* Lcol; double* invdiag; int* keep; int* info;
+  int splits;
+};
+
+LevPass carve_pass(Carver& c, int64_t rows, int cols, bool trans) {
+  LevPass p{};
+  const int n = trans ? static_cast<int>(rows) : cols;
+  gram_workspace(rows, cols, trans, &p.splits);
+  p.partial = c.take<double>(static_cast<size_t>(p.splits) * n * n);
+  p.G = c.take<double>(static_cast<size_t>(n) * n);
+  p.Lrow = c.take<double>(static_cast<size_t>(n) * n);
+  p.Lcol = c.take<double>(static_cast<size_t>(n) * n);
+  p.invdiag = c.take<double>(n);
+  p.keep = c.take<int>(n);
+  p.info = c.take<int>(1);
+  return p;
+}
+
+tr_status run_pass(tr_ctx* ctx, const LevPass& p, const double* A, int64_t rows, int cols,
+                   int64_t lda, bool trans, double tol_scale, cudaStream_t st) {
+  const int n = trans ? static_cast<int>(rows) : cols;
+  TR_LAUNCH("gram_f64", launch_gram(A, rows, cols, lda, trans, p.partial, p.splits, st));
+  TR_LAUNCH("reduce_gram", launch_reduce(p.partial, false, p.splits, static_cast<int64_t>(n) * n,
+                                         n, 0, n, 0, n, p.G, n, false, st));
+  TR_LAUNCH("cholesky_leverage", launch_cholesky(p.G, n, 1, tol_scale, p.Lrow, p.Lcol,
+                                                   p.invdiag, p.keep, p.info, ctx->d_err, st));
+  return TR_OK;
+}
+
+size_t leverage_plan(Carver& c, int64_t I, int L, LevPass* p1, LevPass* p2, double** ell) {
+  if (I >= L) {
+    *p1 = carve_pass(c, I, L, false);
+  } else {
+    *p1 = carve_pass(c, I, L, true);                // K = A A^T (I x I) -> factor C
+    *p2 = carve_pass(c, I, static_cast<int>(I), false);  // Gram of C (I x I)
+  }
+  *ell = c.take<double>(I);
+  return c.off;
+}
+
+size_t leverage_bytes(int64_t I, int L) {
+  Carver c(nullptr);
+  LevPass a, b;
+  double* e;
+  return leverage_plan(c, I, L, &a, &b, &e);
+}
+
+tr_status leverage_run(tr_ctx* ctx, char* ws, const double* core, int64_t I, int Rl, int Rr,
+                       double* p, double* cdf, cudaStream_t st) {
+  const int L = Rl * Rr;
+  Carver c(ws);
+  LevPass p1{}, p2{};
+  double* ell;
+  leverage_plan(c, I, L, &p1, &p2, &ell);
+  const double eps = 2.220446049250313e-16;
+  const double tol = static_cast<double>(I > L ? I : L) * eps;
+  if (I >= L) {
+    TR_TRY(run_pass(ctx, p1, core, I, L, L, false, tol, st));
+    TR_LAUNCH("leverage_rows", launch_leverage_rows(core, I, L, L, p1.Lcol, p1.invdiag, p1.keep,
+                                                    ell, st));
+  } else {
+    // Wide G_(2): the range of A is that of C with A A^T = C C^T; ell(A) = ell(C).
+    const int n = static_cast<int>(I);
+    TR_TRY(run_pass(ctx, p1, core, I, L, L, true, tol, st));
+    TR_TRY(run_pass(ctx, p2, p1.Lrow, I, n, n, false, tol, st));
+    TR_LAUNCH("leverage_rows", launch_leverage_rows(p1.Lrow, I, n, n, p2.Lcol, p2.invdiag,
+                                                    p2.keep, ell, st));
+  }
+  TR_LAUNCH("cdf", launch_cdf(ell, I, p, cdf, ctx->d_err, st));
+  return TR_OK;
+}
+
+// ------------------------------------------------------------------------------------
+// Rows a5 + a6: normal equations, Cholesky, solve, refinement.
+// ------------------------------------------------------------------------------------
+struct SolvePlan {
+  void* partial; double* M; double* BT; double* Lrow; double* Lcol; double* invdiag;
+  int* keep; int* info; int splits;
+};
+
+size_t solve_plan(Carver& c, int64_t J, int L, int64_t I, bool f64, SolvePlan* s) {
+  const size_t pbytes = normal_eq_workspace(J, L, I, f64, &s->splits);
+  s->partial = c.take<char>(pbytes);
+  s->M = c.take<double>(static_cast<size_t>(L) * L);
+  s->BT = c.take<double>(static_cast<size_t>(I) * L);
+  s->Lrow = c.take<double>(static_cast<size_t>(L) * L);
+  s->Lcol = c.take<double>(static_cast<size_t>(L) * L);
+  s->invdiag = c.take<double>(L);
+  s->keep = c.take<int>(L);
+  s->info = c.take<int>(1);
+  return c.off;
+}
+
+size_t solve_bytes(int64_t J, int L, int64_t I, bool f64) {
+  Carver c(nullptr);
+  SolvePlan s;
+  return solve_plan(c, J, L, I, f64, &s);
+}
+
+tr_status solve_run(tr_ctx* ctx, char* ws, const void* A, const void* Y, bool f64, int64_t J,
+                    int Rl, int Rr, int64_t I, bool refine, double* core_out, cudaStream_t st) {
+  const int L = Rl * Rr;
+  Carver c(ws);
+  SolvePlan s;
+  solve_plan(c, J, L, I, f64, &s);
+  const int64_t ld = L + I;
+  TR_LAUNCH("normal_eq", launch_normal_eq(A, Y, f64, J, L, I, s.partial, s.splits, st));
+  TR_LAUNCH("reduce_M", launch_reduce(s.partial, !f64, s.splits, L * ld, ld, 0, L, 0, L, s.M, L,
+                                      false, st));
+  TR_LAUNCH("reduce_B", launch_reduce(s.partial, !f64, s.splits, L * ld, ld, 0, L, L, I, s.BT, L,
+                                      true, st));
+  const double eps = 2.220446049250313e-16;
+  TR_LAUNCH("cholesky_solve", launch_cholesky(s.M, L, 0, static_cast<double>(L) * eps, s.Lrow,
+                                               s.Lcol, s.invdiag, s.keep, s.info, ctx->d_err,
+                                               st));
+  TR_LAUNCH("solve_rhs", launch_solve_rhs(s.BT, s.M, L, Rl, Rr, I, s.Lrow, s.Lcol, s.invdiag,
+                                          refine, s.info, core_out, st));
+  return TR_OK;
+}
+
+// ------------------------------------------------------------------------------------
+// Validation helpers.
+// ------------------------------------------------------------------------------------
+tr_status check_ctx(tr_ctx* ctx) {
+  return ctx ? TR_OK : TR_ERR_INVALID_ARG;
+}
+
+tr_status check_shape(tr_ctx* ctx, int N, const int64_t* dims, const int* ranks) {
+  if (N < 2 || N > kMaxModes) return fail(ctx, TR_ERR_INVALID_ARG, "N=%d outside [2, %d]", N, kMaxModes);
+  if (!dims) return fail(ctx, TR_ERR_INVALID_ARG, "dims is NULL");
+  for (int k = 0; k < N; ++k)
+    if (dims[k] < 1 || dims[k] > INT32_MAX)
+      return fail(ctx, TR_ERR_INVALID_ARG, "dims[%d]=%lld outside [1, 2^31-1]", k,
+                  static_cast<long long>(dims[k]));
+  if (ranks) {
+    for (int k = 0; k < N; ++k)
+      if (ranks[k] < 1 || ranks[k] > 16)
+        return fail(ctx, TR_ERR_INVALID_ARG, "ranks[%d]=%d outside [1, 16]", k, ranks[k]);
+  }
+  return TR_OK;
+}
+
+int rl_of(const int* ranks, int N, int k) { return ranks[(k - 1 + N) % N]; }
+
+void row_major_strides(int N, const int64_t* dims, int64_t* stride) {
+  int64_t s = 1;
+  for (int k = N - 1; k >= 0; --k) { stride[k] = s; s *= dims[k]; }
+}
+
+tr_status read_device_error(tr_ctx* ctx, cudaStream_t st) {
+  unsigned h = 0;
+  TR_CUDA(cudaStreamSynchronize(st));
+  TR_CUDA(cudaMemcpy(&h, ctx->d_err, sizeof h, cudaMemcpyDeviceToHost));
+  TR_CUDA(cudaMemset(ctx->d_err, 0, sizeof(unsigned)));
+  if (h & kErrBadIndex) return fail(ctx, TR_ERR_INVALID_ARG, "a sample index was out of range");
+  if (h & kErrSingular)
+    return fail(ctx, TR_ERR_SINGULAR, "non-positive pivot in the normal equations or a zero core");
+  return TR_OK;
+}
+
+// The Alg. 2 driver on device buffers (no synchronisation).
+tr_status als_sampled_async(tr_ctx* ctx, const void* X, tr_dtype xdt, int N, const int64_t* dims,
+                            const int* ranks, int64_t J, int sweeps, uint64_t seed,
+                            tr_precision prec, const double* const* init_cores,
+                            double* const* cores, cudaStream_t st) {
+  const bool f64 = prec == TR_PREC_FP64;
+  const size_t es = f64 ? 8 : 4;
+  int64_t Imax = 0, Isum = 0;
+  int Lmax = 0;
+  for (int k = 0; k < N; ++k) {
+    Imax = dims[k] > Imax ? dims[k] : Imax;
+    Isum += dims[k];
+    const int L = rl_of(ranks, N, k) * ranks[k];
+    Lmax = L > Lmax ? L : Lmax;
+  }
+  // Persistent region, then a stage region reused by every step.
+  auto carve_persist = [&](Carver& c, double** pbase, double** cbase, int32_t** idx, double** w,
+                           void** A, void** Y) {
+    *pbase = c.take<double>(Isum);
+    *cbase = c.take<double>(Isum);
+    *idx = c.take<int32_t>(static_cast<size_t>(J) * (N - 1));
+    *w = c.take<double>(J);
+    *A = c.take<char>(static_cast<size_t>(J) * Lmax * es);
+    *Y = c.take<char>(static_cast<size_t>(J) * Imax * es);
+  };
+  double *pbase, *cbase, *w;
+  int32_t* idx;
+  void *A, *Y;
+  Carver dry(nullptr);
+  carve_persist(dry, &pbase, &cbase, &idx, &w, &A, &Y);
+  const size_t persist = (dry.off + 255) & ~size_t(255);
+  size_t stage = 0;
+  for (int k = 0; k < N; ++k) {
+    const int L = rl_of(ranks, N, k) * ranks[k];
+    const size_t a = leverage_bytes(dims[k], L), b = solve_bytes(J, L, dims[k], f64);
+    stage = a > stage ? a : stage;
+    stage = b > stage ? b : stage;
+  }
+  TR_TRY(ensure_ws(ctx, persist + stage));
+  Carver c(ctx->arena);
+  carve_persist(c, &pbase, &cbase, &idx, &w, &A, &Y);
+  char* ws = ctx->arena + persist;
+
+  std::vector<double*> p(N), cdf(N);
+  {
+    int64_t off = 0;
+    for (int k = 0; k < N; ++k) { p[k] = pbase + off; cdf[k] = cbase + off; off += dims[k]; }
+  }
+  // Initial cores G^(2..N) (paper numbering).
+  for (int k = 1; k < N; ++k) {
+    const size_t count = static_cast<size_t>(dims[k]) * rl_of(ranks, N, k) * ranks[k];
+    if (init_cores) {
+      if (!init_cores[k]) return fail(ctx, TR_ERR_INVALID_ARG, "init_cores[%d] is NULL", k);
+      TR_CUDA(cudaMemcpyAsync(cores[k], init_cores[k], count * sizeof(double),
+                              cudaMemcpyDeviceToDevice, st));
+    } else {
+      TR_LAUNCH("init_normal", launch_init_normal(cores[k], static_cast<int64_t>(count), seed,
+                                                  static_cast<uint32_t>(k), st));
+    }
+  }
+  for (int k = 1; k < N; ++k)
+    TR_TRY(leverage_run(ctx, ws, cores[k], dims[k], rl_of(ranks, N, k), ranks[k], p[k], cdf[k], st));
+
+  int64_t stride[kMaxModes];
+  row_major_strides(N, dims, stride);
+  const bool x64 = xdt == TR_F64;
+  for (int s = 0; s < sweeps; ++s) {
+    for (int n = 0; n < N; ++n) {
+      SampleArgs sa{};
+      ChainArgs ca{};
+      GatherArgs ga{};
+      sa.npos = ca.npos = ga.npos = N - 1;
+      for (int m = 0; m < N - 1; ++m) {
+        const int mode = (n + 1 + m) % N;
+        sa.p[m] = p[mode];
+        sa.cdf[m] = cdf[mode];
+        sa.I[m] = ca.I[m] = ga.I[m] = dims[mode];
+        ca.core[m] = cores[mode];
+        ca.rl[m] = rl_of(ranks, N, mode);
+        ca.rr[m] = ranks[mode];
+        ga.stride[m] = stride[mode];
+      }
+      ga.In = dims[n];
+      ga.stride_n = stride[n];
+      const uint64_t uid = static_cast<uint64_t>(s) * N + n;
+      TR_LAUNCH("sample", launch_sample(sa, J, seed, uid, idx, w, st));
+      TR_LAUNCH("subchain", launch_subchain(ca, idx, w, J, A, f64, ctx->d_err, st));
+      TR_LAUNCH("gather", launch_gather(ga, X, x64, idx, w, J, Y, f64, ctx->d_err, st));
+      const int Rl = rl_of(ranks, N, n), Rr = ranks[n];
+      TR_TRY(solve_run(ctx, ws, A, Y, f64, J, Rl, Rr, dims[n], !f64, cores[n], st));
+      TR_TRY(leverage_run(ctx, ws, cores[n], dims[n], Rl, Rr, p[n], cdf[n], st));
+    }
+  }
+  return TR_OK;
+}
+
+}  // namespace
+
+// ======================================================================================
+// Public entry points
+// ======================================================================================
+extern "C" {
+
+tr_status tr_create(tr_ctx** out, int device, size_t hbm_budget_bytes) {
+  if (!out) return TR_ERR_INVALID_ARG;
+  *out = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+    cudaGetLastError();
+    return TR_ERR_INVALID_ARG;
+  }
+  tr_ctx* ctx = new tr_ctx;
+  ctx->device = device;
+  ctx->budget = hbm_budget_bytes;
+  DeviceGuard g(device);
+  if (!g.ok || cudaMalloc(&ctx->d_err, 256) != cudaSuccess ||
+      cudaMemset(ctx->d_err, 0, 256) != cudaSuccess) {
+    cudaGetLastError();
+    if (ctx->d_err) cudaFree(ctx->d_err);
+    delete ctx;
+    return TR_ERR_CUDA;
+  }
+  *out = ctx;
+  return TR_OK;
+}
+
+void tr_destroy(tr_ctx* ctx) {
+  if (!ctx) return;
+  DeviceGuard g(ctx->device);
+  cudaDeviceSynchronize();
+  if (ctx->arena) cudaFree(ctx->arena);
+  if (ctx->host_stage) cudaFree(ctx->host_stage);
+  if (ctx->d_err) cudaFree(ctx->d_err);
+  for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+  delete ctx;
+}
+
+const char* tr_last_error(const tr_ctx* ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+
+tr_status tr_status_sync(tr_ctx* ctx, tr_stream stream) {
+  TR_TRY(check_ctx(ctx));
+  DeviceGuard g(ctx->device);
+  return read_device_error(ctx, S(stream));
+}
+
+tr_status tr_leverage(tr_ctx* ctx, const double* core, int64_t I, int Rl, int Rr, double* p,
+                      double* cdf, tr_stream stream) {
+  TR_TRY(check_ctx(ctx));
+  if (!core || !p || !cdf) return fail(ctx, TR_ERR_INVALID_ARG, "null pointer");
+  if (I < 1 || Rl < 1 || Rr < 1 || Rl * Rr > kMaxL)
+    return fail(ctx, TR_ERR_INVALID_ARG, "bad core shape I=%lld Rl=%d Rr=%d",
+                static_cast<long long>(I), Rl, Rr);
+  DeviceGuard g(ctx->device);
+  TR_TRY(ensure_ws(ctx, leverage_bytes(I, Rl * Rr)));
+  return leverage_run(ctx, ctx->arena, core, I, Rl, Rr, p, cdf, S(stream));
+}
+
+tr_status tr_sample(tr_ctx* ctx, int N, int k, const int64_t* dims, const double* const* p,
+                    const double* const* cdf, int64_t J, uint64_t seed, uint64_t update_id,
+                    int32_t* idx, double* w, tr_stream stream) {
+  TR_TRY(check_ctx(ctx));
+  TR_TRY(check_shape(ctx, N, dims, nullptr));
+  if (k < 0 || k >= N) return fail(ctx, TR_ERR_INVALID_ARG, "k=%d outside [0, N)", k);
+  if (J < 1 || J > INT32_MAX) return fail(ctx, TR_ERR_INVALID_ARG, "J=%lld", static_cast<long long>(J));
+  if (!p || !cdf || !idx || !w) return fail(ctx, TR_ERR_INVALID_ARG, "null pointer");
+  SampleArgs sa{};
+  sa.npos = N - 1;
+  for (int m = 0; m < N - 1; ++m) {
+    const int mode = (k + 1 + m) % N;
+    if (!p[mode] || !cdf[mode]) return fail(ctx, TR_ERR_INVALID_ARG, "p/cdf[%d] is NULL", mode);
+    sa.p[m] = p[mode];
+    sa.cdf[m] = cdf[mode];
+    sa.I[m] = dims[mode];
+  }
+  DeviceGuard g(ctx->device);
+  cudaStream_t st = S(stream);
+  TR_LAUNCH("sample", launch_sample(sa, J, seed, update_id, idx, w, st));
+  return TR_OK;
+}
+
+tr_status tr_subchain(tr_ctx* ctx, int N, int k, const int64_t* dims, const int* ranks,
+                      const double* const* cores, const int32_t* idx, const double* w,
+                      int64_t J, void* A, tr_dtype A_dtype, tr_stream stream) {
+  TR_TRY(check_ctx(ctx));
+  TR_TRY(check_shape(ctx, N, dims, ranks));
+  if (!ranks) return fail(ctx, TR_ERR_INVALID_ARG, "ranks is NULL");
+  if (k < 0 || k >= N) return fail(ctx, TR_ERR_INVALID_ARG, "k=%d outside [0, N)", k);
+  if (J < 1) return fail(ctx, TR_ERR_INVALID_ARG, "J=%lld", static_cast<long long>(J));
+  if (!cores || !idx || !A) return fail(ctx, TR_ERR_INVALID_ARG, "null pointer");
+  if (A_dtype != TR_F32 && A_dtype != TR_F64) return fail(ctx, TR_ERR_INVALID_ARG, "bad dtype");
+  ChainArgs ca{};
+  ca.npos = N - 1;
+  for (int m = 0; m < N - 1; ++m) {
+    const int mode = (k + 1 + m) % N;
+    if (!cores[mode]) return fail(ctx, TR_ERR_INVALID_ARG, "cores[%d] is NULL", mode);
+    ca.core[m] = cores[mode];
+    ca.I[m] = dims[mode];
+    ca.rl[m] = rl_of(ranks, N, mode);
+    ca.rr[m] = ranks[mode];
+  }
+  DeviceGuard g(ctx->device);
+  cudaStream_t st = S(stream);
+  TR_LAUNCH("subchain", launch_subchain(ca, idx, w, J, A, A_dtype == TR_F64, ctx->d_err, st));
+  return TR_OK;
+}
+
+tr_status tr_gather(tr_ctx* ctx, const void* X, tr_dtype X_dtype, int N, const int64_t* dims,
+                    int k, const int32_t* idx, const double* w, int64_t J, void* Y,
+                    tr_dtype Y_dtype, tr_stream stream) {
+  TR_TRY(check_ctx(ctx));
+  TR_TRY(check_shape(ctx, N, dims, nullptr));
+  if (k < 0 || k >= N) return fail(ctx, TR_ERR_INVALID_ARG, "k=%d outside [0, N)", k);
+  if (J < 1) return fail(ctx, TR_ERR_INVALID_ARG, "J=%lld", static_cast<long long>(J));
+  if (!X || !idx || !Y) return fail(ctx, TR_ERR_INVALID_ARG, "null pointer");
+  if ((X_dtype != TR_F32 && X_dtype != TR_F64) || (Y_dtype != TR_F32 && Y_dtype != TR_F64))
+    return fail(ctx, TR_ERR_INVALID_ARG, "bad dtype");
+  int64_t stride[kMaxModes];
+  row_major_strides(N, dims, stride);
+  GatherArgs ga{};
+  ga.npos = N - 1;
+  for (int m = 0; m < N - 1; ++m) {
+    const int mode = (k + 1 + m) % N;
+    ga.I[m] = dims[mode];
+    ga.stride[m] = stride[mode];
+  }
+  ga.In = dims[k];
+  ga.stride_n = stride[k];
+  DeviceGuard g(ctx->device);
+  cudaStream_t st = S(stream);
+  TR_LAUNCH("gather", launch_gather(ga, X, X_dtype == TR_F64, idx, w, J, Y, Y_dtype == TR_F64,
+                                    ctx->d_err, st));
+  return TR_OK;
+}
+
+tr_status tr_solve(tr_ctx* ctx, const void* A, const void* Y, tr_dtype dtype, int64_t J, int Rl,
+                   int Rr, int64_t I, tr_precision prec, double* core_out, tr_stream stream) {
+  TR_TRY(check_ctx(ctx));
+  if (!A || !Y || !core_out) return fail(ctx, TR_ERR_INVALID_ARG, "null pointer");
+  if (J < 1 || I < 1 || Rl < 1 || Rr < 1 || Rl * Rr > kMaxL)
+    return fail(ctx, TR_ERR_INVALID_ARG, "bad sizes J=%lld L=%d I=%lld",
+                static_cast<long long>(J), Rl * Rr, static_cast<long long>(I));
+  if (prec == TR_PREC_FP64 && dtype != TR_F64)
+    return fail(ctx, TR_ERR_INVALID_ARG, "TR_PREC_FP64 needs FP64 A and Y");
+  if (prec == TR_PREC_MIXED && dtype != TR_F32)
+    return fail(ctx, TR_ERR_INVALID_ARG, "TR_PREC_MIXED needs FP32 A and Y");
+  if (prec != TR_PREC_FP64 && prec != TR_PREC_MIXED)
+    return fail(ctx, TR_ERR_INVALID_ARG, "bad precision");
+  const bool f64 = prec == TR_PREC_FP64;
+  DeviceGuard g(ctx->device);
+  TR_TRY(ensure_ws(ctx, solve_bytes(J, Rl * Rr, I, f64)));
+  return solve_run(ctx, ctx->arena, A, Y, f64, J, Rl, Rr, I, !f64, core_out, S(stream));
+}
+
+tr_status tr_init_cores(tr_ctx* ctx, int N, const int64_t* dims, const int* ranks, uint64_t seed,
+                        int k_begin, double* const* cores, tr_stream stream) {
+  TR_TRY(check_ctx(ctx));
+  TR_TRY(check_shape(ctx, N, dims, ranks));
+  if (!ranks || !cores) return fail(ctx, TR_ERR_INVALID_ARG, "null pointer");
+  DeviceGuard g(ctx->device);
+  cudaStream_t st = S(stream);
+  for (int k = k_begin < 0 ? 0 : k_begin; k < N; ++k) {
+    if (!cores[k]) return fail(ctx, TR_ERR_INVALID_ARG, "cores[%d] is NULL", k);
+    const int64_t count = dims[k] * rl_of(ranks, N, k) * ranks[k];
+    TR_LAUNCH("init_normal", launch_init_normal(cores[k], count, seed, static_cast<uint32_t>(k),
+                                                st));
+  }
+  return TR_OK;
+}
+
+static tr_status check_als(tr_ctx* ctx, const void* X, tr_dtype xdt, int N, const int64_t* dims,
+                           const int* ranks, int64_t J, int sweeps, tr_precision prec,
+                           double* const* cores) {
+  TR_TRY(check_shape(ctx, N, dims, ranks));
+  if (!ranks) return fail(ctx, TR_ERR_INVALID_ARG, "ranks is NULL");
+  if (!X || !cores) return fail(ctx, TR_ERR_INVALID_ARG, "null pointer");
+  for (int k = 0; k < N; ++k)
+    if (!cores[k]) return fail(ctx, TR_ERR_INVALID_ARG, "cores[%d] is NULL", k);
+  if (J < 1 || J > INT32_MAX) return fail(ctx, TR_ERR_INVALID_ARG, "J=%lld", static_cast<long long>(J));
+  if (sweeps < 0) return fail(ctx, TR_ERR_INVALID_ARG, "sweeps=%d", sweeps);
+  if (xdt != TR_F32 && xdt != TR_F64) return fail(ctx, TR_ERR_INVALID_ARG, "bad X dtype");
+  if (prec != TR_PREC_FP64 && prec != TR_PREC_MIXED)
+    return fail(ctx, TR_ERR_INVALID_ARG, "bad precision");
+  return TR_OK;
+}
+
+tr_status tr_als_sampled(tr_ctx* ctx, const void* X, tr_dtype X_dtype, int N, const int64_t* dims,
+                         const int* ranks, int64_t J, int sweeps, uint64_t seed,
+                         tr_precision prec, const double* const* init_cores,
+                         double* const* cores, tr_stream stream) {
+  TR_TRY(check_ctx(ctx));
+  TR_TRY(check_als(ctx, X, X_dtype, N, dims, ranks, J, sweeps, prec, cores));
+  DeviceGuard g(ctx->device);
+  TR_TRY(als_sampled_async(ctx, X, X_dtype, N, dims, ranks, J, sweeps, seed, prec, init_cores,
+                           cores, S(stream)));
+  return read_device_error(ctx, S(stream));
+}
+
+tr_status tr_als_sampled_host(tr_ctx* ctx, const void* X_host, tr_dtype X_dtype, int N,
+                              const int64_t* dims, const int* ranks, int64_t J, int sweeps,
+                              uint64_t seed, tr_precision prec,
+                              const double* const* init_cores_host, double* const* cores_host,
+                              tr_stream stream) {
+  TR_TRY(check_ctx(ctx));
+  TR_TRY(check_als(ctx, X_host, X_dtype, N, dims, ranks, J, sweeps, prec, cores_host));
+  DeviceGuard g(ctx->device);
+  cudaStream_t st = S(stream);
+  int64_t numel = 1;
+  for (int k = 0; k < N; ++k) numel *= dims[k];
+  const size_t xbytes = static_cast<size_t>(numel) * (X_dtype == TR_F64 ? 8 : 4);
+  std::vector<size_t> cbytes(N);
+  size_t total = (xbytes + 255) & ~size_t(255);
+  for (int k = 0; k < N; ++k) {
+    cbytes[k] = static_cast<size_t>(dims[k]) * rl_of(ranks, N, k) * ranks[k] * sizeof(double);
+    total += 2 * ((cbytes[k] + 255) & ~size_t(255));
+  }
+  if (total > ctx->host_stage_bytes) {
+    if (ctx->budget && total + ctx->arena_bytes > ctx->budget)
+      return fail(ctx, TR_ERR_BUDGET, "host staging of %zu bytes exceeds the HBM budget", total);
+    TR_CUDA(cudaDeviceSynchronize());
+    if (ctx->host_stage) cudaFree(ctx->host_stage);
+    ctx->host_stage = nullptr;
+    ctx->host_stage_bytes = 0;
+    if (cudaMalloc(&ctx->host_stage, total) != cudaSuccess) {
+      cudaGetLastError();
+      ctx->host_stage = nullptr;
+      return fail(ctx, TR_ERR_OOM, "cudaMalloc of %zu staging bytes failed", total);
+    }
+    ctx->host_stage_bytes = total;
+  }
+  char* base = ctx->host_stage;
+  void* dX = base;
+  size_t off = (xbytes + 255) & ~size_t(255);
+  std::vector<double*> dcores(N), dinit(N, nullptr);
+  for (int k = 0; k < N; ++k) {
+    dcores[k] = reinterpret_cast<double*>(base + off);
+    off += (cbytes[k] + 255) & ~size_t(255);
+    dinit[k] = reinterpret_cast<double*>(base + off);
+    off += (cbytes[k] + 255) & ~size_t(255);
+  }
+  TR_CUDA(cudaMemcpyAsync(dX, X_host, xbytes, cudaMemcpyHostToDevice, st));
+  if (init_cores_host) {
+    for (int k = 1; k < N; ++k) {
+      if (!init_cores_host[k]) return fail(ctx, TR_ERR_INVALID_ARG, "init_cores[%d] is NULL", k);
+      TR_CUDA(cudaMemcpyAsync(dinit[k], init_cores_host[k], cbytes[k], cudaMemcpyHostToDevice, st));
+    }
+  }
+  TR_TRY(als_sampled_async(ctx, dX, X_dtype, N, dims, ranks, J, sweeps, seed, prec,
+                           init_cores_host ? dinit.data() : nullptr, dcores.data(), st));
+  for (int k = 0; k < N; ++k)
+    TR_CUDA(cudaMemcpyAsync(cores_host[k], dcores[k], cbytes[k], cudaMemcpyDeviceToHost, st));
+  return read_device_error(ctx, st);
+}
+
+tr_status tr_rel_error(tr_ctx* ctx, const void* X, tr_dtype X_dtype, int N, const int64_t* dims,
+                       const int* ranks, const double* const* cores, double* rel_err,
+                       tr_stream stream) {
+  TR_TRY(check_ctx(ctx));
+  TR_TRY(check_shape(ctx, N, dims, ranks));
+  if (!ranks || !X || !cores || !rel_err) return fail(ctx, TR_ERR_INVALID_ARG, "null pointer");
+  if (X_dtype != TR_F32 && X_dtype != TR_F64) return fail(ctx, TR_ERR_INVALID_ARG, "bad dtype");
+  FitArgs fa{};
+  fa.N = N;
+  for (int k = 0; k < N; ++k) {
+    if (!cores[k]) return fail(ctx, TR_ERR_INVALID_ARG, "cores[%d] is NULL", k);
+    fa.core[k] = cores[k];
+    fa.dims[k] = dims[k];
+    fa.ranks[k] = ranks[k];
+  }
+  DeviceGuard g(ctx->device);
+  int blocks;
+  const size_t bytes = fit_workspace(fa, &blocks);
+  TR_TRY(ensure_ws(ctx, bytes));
+  double* partial = reinterpret_cast<double*>(ctx->arena);
+  cudaStream_t st = S(stream);
+  TR_LAUNCH("fit", launch_fit(fa, X, X_dtype == TR_F64, partial, blocks, st));
+  std::vector<double> h(2 * static_cast<size_t>(blocks));
+  TR_CUDA(cudaMemcpyAsync(h.data(), partial, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  TR_CUDA(cudaStreamSynchronize(st));
+  double se = 0.0, sx = 0.0;
+  for (int b = 0; b < blocks; ++b) { se += h[b]; sx += h[blocks + b]; }
+  *rel_err = sx > 0.0 ? std::sqrt(se / sx) : (se > 0.0 ? INFINITY : 0.0);
+  return TR_OK;
+}
+
+tr_status tr_profile_begin(tr_ctx* ctx) {
+  TR_TRY(check_ctx(ctx));
+  ctx->prof = true;
+  ctx->ev_used = 0;
+  ctx->prof_marks.clear();
+  ctx->prof_names.clear();
+  ctx->prof_ms.clear();
+  ctx->prof_count.clear();
+  return TR_OK;
+}
+
+tr_status tr_profile_end(tr_ctx* ctx, tr_stream stream) {
+  TR_TRY(check_ctx(ctx));
+  DeviceGuard g(ctx->device);
+  ctx->prof = false;
+  TR_CUDA(cudaStreamSynchronize(S(stream)));
+  TR_CUDA(cudaDeviceSynchronize());
+  std::map<std::string, size_t> slot;
+  for (size_t i = 0; i < ctx->prof_names.size(); ++i) slot[ctx->prof_names[i]] = i;
+  for (const auto& m : ctx->prof_marks) {
+    float ms = 0.f;
+    TR_CUDA(cudaEventElapsedTime(&ms, ctx->ev_pool[m.second], ctx->ev_pool[m.second + 1]));
+    auto it = slot.find(m.first);
+    size_t k;
+    if (it == slot.end()) {
+      k = ctx->prof_names.size();
+      slot[m.first] = k;
+      ctx->prof_names.emplace_back(m.first);
+      ctx->prof_ms.push_back(0.0);
+      ctx->prof_count.push_back(0);
+    } else {
+      k = it->second;
+    }
+    ctx->prof_ms[k] += ms;
+    ctx->prof_count[k] += 1;
+  }
+  ctx->prof_marks.clear();
+  ctx->ev_used = 0;
+  return TR_OK;
+}
+
+int tr_profile_count(const tr_ctx* ctx) {
+  return ctx ? static_cast<int>(ctx->prof_names.size()) : 0;
+}
+
+tr_status tr_profile_entry(const tr_ctx* ctx, int i, const char** name, double* total_ms,
+                           int64_t* launches) {
+  if (!ctx || i < 0 || i >= static_cast<int>(ctx->prof_names.size()))
+    return TR_ERR_INVALID_ARG;
+  if (name) *name = ctx->prof_names[i].c_str();
+  if (total_ms) *total_ms = ctx->prof_ms[i];
+  if (launches) *launches = ctx->prof_count[i];
+  return TR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,143 @@
+// Internal declarations shared by the CUDA translation units of libtrals.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/trals.h"
+
+namespace trk {
+
+// Bits of the device-side error record (one uint32 per context).
+enum : unsigned {
+  kErrSingular = 1u,    // non-positive pivot or zero core
+  kErrBadIndex = 2u,    // a caller-provided sample index out of range
+};
+
+constexpr int kMaxModes = TR_MAX_MODES;
+constexpr int kMaxL = TR_MAX_RANK_PRODUCT;
+
+// ------------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of
+//   (c0,c1,c2,c3) -> (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1, lo(M0 c0))
+// with the key bumped by the Weyl increments (W0, W1) between rounds.
+// ------------------------------------------------------------------------------------
+struct u32x4 { uint32_t x, y, z, w; };
+
+__device__ __forceinline__ u32x4 philox4x32_10(u32x4 c, uint32_t k0, uint32_t k1) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) { k0 += W0; k1 += W1; }
+    const uint32_t hi0 = __umulhi(M0, c.x), lo0 = M0 * c.x;
+    const uint32_t hi1 = __umulhi(M1, c.z), lo1 = M1 * c.z;
+    c = u32x4{hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
+  }
+  return c;
+}
+
+// 53-bit uniform in [0, 1) from a (hi, lo) word pair.
+__device__ __forceinline__ double u53(uint32_t hi, uint32_t lo) {
+  const uint64_t bits = ((static_cast<uint64_t>(hi) << 32) | lo) >> 11;
+  return static_cast<double>(bits) * 0x1.0p-53;
+}
+
+// ------------------------------------------------------------------------------------
+// Launchers (defined in the .cu files; all asynchronous on `st`).
+// ------------------------------------------------------------------------------------
+struct SampleArgs {
+  const double* p[kMaxModes];    // per ring position m
+  const double* cdf[kMaxModes];
+  int64_t I[kMaxModes];
+  int npos;                      // N - 1
+};
+cudaError_t launch_sample(const SampleArgs& a, int64_t J, uint64_t seed, uint64_t update_id,
+                          int32_t* idx, double* w, cudaStream_t st);
+
+struct ChainArgs {
+  const double* core[kMaxModes]; // per ring position m, slice-major
+  int64_t I[kMaxModes];
+  int rl[kMaxModes], rr[kMaxModes];
+  int npos;
+};
+cudaError_t launch_subchain(const ChainArgs& a, const int32_t* idx, const double* w,
+                            int64_t J, void* A, bool f64, unsigned* err, cudaStream_t st);
+
+struct GatherArgs {
+  int64_t stride[kMaxModes];     // element stride of the mode at ring position m
+  int64_t I[kMaxModes];
+  int npos;
+  int64_t In;                    // length of the gathered mode
+  int64_t stride_n;              // its stride
+};
+cudaError_t launch_gather(const GatherArgs& a, const void* X, bool x_f64, const int32_t* idx,
+                          const double* w, int64_t J, void* Y, bool y_f64, unsigned* err,
+                          cudaStream_t st);
+
+// Normal-equation contraction: partial[s][r][c] = sum over the s-th chunk of rows j of
+// A[j][r] * [A | Y][j][c], r < L, c < L + I. Returns the number of chunks in *splits.
+size_t normal_eq_workspace(int64_t J, int L, int64_t I, bool f64, int* splits);
+cudaError_t launch_normal_eq(const void* A, const void* Y, bool f64, int64_t J, int L,
+                             int64_t I, void* partial, int splits, cudaStream_t st);
+
+// Gram of a row-major matrix: trans=false: G = A^T A (cols x cols); trans=true:
+// G = A A^T (rows x rows). Partials [splits][n][n] FP64; only tiles on or above the
+// diagonal are written (entry (p, q) with p <= q is valid).
+size_t gram_workspace(int64_t rows, int cols, bool trans, int* splits);
+cudaError_t launch_gram(const double* A, int64_t rows, int cols, int64_t lda, bool trans,
+                        double* partial, int splits, cudaStream_t st);
+
+// out = sum over s (in order s = 0..splits-1) of the nrows x ncols block of partial[s]
+// starting at (row0, col0); partial row stride pld, split stride pstride, FP32 or FP64.
+// transpose=false: out[r*ldo + c]; transpose=true: out[c*ldo + r]. FP64 output.
+cudaError_t launch_reduce(const void* partial, bool partial_f32, int splits, int64_t pstride,
+                          int64_t pld, int64_t row0, int64_t nrows, int64_t col0,
+                          int64_t ncols, double* out, int64_t ldo, bool transpose,
+                          cudaStream_t st);
+
+// Cholesky G = L L^T of the n x n FP64 matrix G (row-major, ld n; only the upper triangle
+// G[j][i], j <= i, is read), one CTA. A pivot <= tol_scale * max diag is
+//   mode 0 (solve): fatal -> *info = column + 1 and the singular error bit;
+//   mode 1 (leverage): the column is dropped (keep = 0) and the factorisation continues.
+// Outputs: Lrow (n x n row-major lower factor), Lcol (its transpose), invdiag[n] (1/L_cc,
+// 0 for dropped columns), keep[n], *info (0 = success).
+cudaError_t launch_cholesky(const double* G, int n, int mode, double tol_scale, double* Lrow,
+                            double* Lcol, double* invdiag, int* keep, int* info,
+                            unsigned* err, cudaStream_t st);
+
+// Right-hand sides of the normal equations: BT is I x L (row i = column i of B). For each
+// i, z = M^-1 b via the factor; if refine, z += M^-1 (b - M z) with M the full symmetric
+// FP64 matrix. Writes core_out[i][a][b] = z[a + Rl*b]; nothing if *info != 0.
+cudaError_t launch_solve_rhs(const double* BT, const double* M, int L, int Rl, int Rr,
+                             int64_t I, const double* Lrow, const double* Lcol,
+                             const double* invdiag, bool refine, const int* info,
+                             double* core_out, cudaStream_t st);
+
+// Leverage rows: ell[i] = || L^-1 a_i ||^2 over kept columns, a_i = row i of A (rows x n,
+// row-major, lda).
+cudaError_t launch_leverage_rows(const double* A, int64_t rows, int n, int64_t lda,
+                                 const double* Lcol, const double* invdiag, const int* keep,
+                                 double* ell, cudaStream_t st);
+
+// p = ell / sum(ell), cdf = inclusive prefix sum (fixed order), one CTA. All-zero ell ->
+// uniform p and the singular bit.
+cudaError_t launch_cdf(const double* ell, int64_t I, double* p, double* cdf, unsigned* err,
+                       cudaStream_t st);
+
+// Core initialisation N(0,1) by Philox + Box-Muller.
+cudaError_t launch_init_normal(double* out, int64_t count, uint64_t seed, uint32_t stream_id,
+                               cudaStream_t st);
+
+// Fit: partial sums of squares of (X - TR) and X over blocks; FP64 outputs [2][blocks].
+struct FitArgs {
+  const double* core[kMaxModes];  // slice-major, natural mode order
+  int64_t dims[kMaxModes];
+  int ranks[kMaxModes];
+  int N;
+};
+size_t fit_workspace(const FitArgs& a, int* blocks);
+cudaError_t launch_fit(const FitArgs& a, const void* X, bool x_f64, double* partial,
+                       int blocks, cudaStream_t st);
+
+}  // namespace trk

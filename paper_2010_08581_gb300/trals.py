@@ -1,0 +1,275 @@
+"""Thin ctypes binding of ``libtrals.so`` (declared in ``include/trals.h``).
+
+Functions keep the C names and only marshal arguments: torch tensors become device
+pointers, per-mode lists become host pointer arrays, and the current torch CUDA stream is
+passed as the stream. Every step of the method runs in the library's CUDA kernels; there
+is no CPU fallback: loading fails loudly if the library has not been built.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import List, Optional, Sequence
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtrals.so")
+
+TR_OK, TR_ERR_INVALID_ARG, TR_ERR_OOM, TR_ERR_BUDGET, TR_ERR_SINGULAR, TR_ERR_TIMEOUT, \
+    TR_ERR_CUDA, TR_ERR_NOT_CONVERGED = range(8)
+TR_F32, TR_F64 = 0, 1
+TR_PREC_FP64, TR_PREC_MIXED = 0, 1
+
+_STATUS_NAMES = ["TR_OK", "TR_ERR_INVALID_ARG", "TR_ERR_OOM", "TR_ERR_BUDGET",
+                 "TR_ERR_SINGULAR", "TR_ERR_TIMEOUT", "TR_ERR_CUDA", "TR_ERR_NOT_CONVERGED"]
+
+_lib = None
+
+c_int, c_i64, c_u64, c_dbl, c_vp, c_sz = (ctypes.c_int, ctypes.c_int64, ctypes.c_uint64,
+                                          ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t)
+PP = ctypes.POINTER(c_vp)
+P64 = ctypes.POINTER(c_i64)
+PI = ctypes.POINTER(c_int)
+
+# name -> (restype, argtypes); mirrors include/trals.h
+SIGNATURES = {
+    "tr_create": (c_int, [ctypes.POINTER(c_vp), c_int, c_sz]),
+    "tr_destroy": (None, [c_vp]),
+    "tr_last_error": (ctypes.c_char_p, [c_vp]),
+    "tr_status_sync": (c_int, [c_vp, c_vp]),
+    "tr_leverage": (c_int, [c_vp, c_vp, c_i64, c_int, c_int, c_vp, c_vp, c_vp]),
+    "tr_sample": (c_int, [c_vp, c_int, c_int, P64, PP, PP, c_i64, c_u64, c_u64, c_vp, c_vp,
+                          c_vp]),
+    "tr_subchain": (c_int, [c_vp, c_int, c_int, P64, PI, PP, c_vp, c_vp, c_i64, c_vp, c_int,
+                            c_vp]),
+    "tr_gather": (c_int, [c_vp, c_vp, c_int, c_int, P64, c_int, c_vp, c_vp, c_i64, c_vp, c_int,
+                          c_vp]),
+    "tr_solve": (c_int, [c_vp, c_vp, c_vp, c_int, c_i64, c_int, c_int, c_i64, c_int, c_vp,
+                         c_vp]),
+    "tr_als_sampled": (c_int, [c_vp, c_vp, c_int, c_int, P64, PI, c_i64, c_int, c_u64, c_int,
+                               PP, PP, c_vp]),
+    "tr_als_sampled_host": (c_int, [c_vp, c_vp, c_int, c_int, P64, PI, c_i64, c_int, c_u64,
+                                    c_int, PP, PP, c_vp]),
+    "tr_rel_error": (c_int, [c_vp, c_vp, c_int, c_int, P64, PI, PP, ctypes.POINTER(c_dbl),
+                             c_vp]),
+    "tr_init_cores": (c_int, [c_vp, c_int, P64, PI, c_u64, c_int, PP, c_vp]),
+    "tr_profile_begin": (c_int, [c_vp]),
+    "tr_profile_end": (c_int, [c_vp, c_vp]),
+    "tr_profile_count": (c_int, [c_vp]),
+    "tr_profile_entry": (c_int, [c_vp, c_int, ctypes.POINTER(ctypes.c_char_p),
+                                 ctypes.POINTER(c_dbl), ctypes.POINTER(c_i64)]),
+}
+
+
+def load():
+    """Load libtrals.so (raises if it is missing; nothing falls back to the CPU)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(
+            f"{LIB_PATH} is not built; run `python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class TrError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        self.status = status
+
+
+class Context:
+    """Owns a ``tr_ctx`` (device workspace) on one CUDA device."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0):
+        lib = load()
+        h = c_vp()
+        st = lib.tr_create(ctypes.byref(h), int(device), int(hbm_budget_bytes))
+        if st != TR_OK:
+            raise TrError(st, "tr_create failed")
+        self.handle = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().tr_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def check(self, st: int):
+        if st != TR_OK:
+            raise TrError(st, load().tr_last_error(self.handle).decode())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return c_vp(s.cuda_stream)
+
+
+def _dt(t: torch.Tensor) -> int:
+    if t.dtype == torch.float32:
+        return TR_F32
+    if t.dtype == torch.float64:
+        return TR_F64
+    raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    if t is None:
+        return c_vp(None)
+    if t.is_cuda and not t.is_contiguous():
+        raise ValueError("tensors must be contiguous")
+    return c_vp(t.data_ptr())
+
+
+def _ptrs(ts: Sequence[Optional[torch.Tensor]]):
+    arr = (c_vp * len(ts))()
+    for i, t in enumerate(ts):
+        arr[i] = t.data_ptr() if t is not None else None
+    return ctypes.cast(arr, PP), arr
+
+
+def _i64s(v):
+    arr = (c_i64 * len(v))(*[int(x) for x in v])
+    return ctypes.cast(arr, P64), arr
+
+
+def _ints(v):
+    arr = (c_int * len(v))(*[int(x) for x in v])
+    return ctypes.cast(arr, PI), arr
+
+
+def tr_status_sync(ctx: Context, stream=None):
+    ctx.check(load().tr_status_sync(ctx.handle, _stream(stream)))
+
+
+def tr_leverage(ctx: Context, core: torch.Tensor, p: torch.Tensor, cdf: torch.Tensor, stream=None):
+    """core: float64 (I, Rl, Rr) slice-major on the device; p, cdf: float64 (I,)."""
+    I, Rl, Rr = core.shape
+    ctx.check(load().tr_leverage(ctx.handle, _ptr(core), I, Rl, Rr, _ptr(p), _ptr(cdf),
+                                 _stream(stream)))
+
+
+def tr_sample(ctx: Context, k: int, dims, ps: List[torch.Tensor], cdfs: List[torch.Tensor],
+              J: int, seed: int, update_id: int, idx: torch.Tensor, w: torch.Tensor, stream=None):
+    N = len(dims)
+    d, _d = _i64s(dims)
+    pp, _p = _ptrs(ps)
+    cp, _c = _ptrs(cdfs)
+    ctx.check(load().tr_sample(ctx.handle, N, k, d, pp, cp, J, seed, update_id, _ptr(idx),
+                               _ptr(w), _stream(stream)))
+
+
+def tr_subchain(ctx: Context, k: int, dims, ranks, cores: List[torch.Tensor], idx: torch.Tensor,
+                w: Optional[torch.Tensor], A: torch.Tensor, stream=None):
+    N = len(dims)
+    d, _d = _i64s(dims)
+    r, _r = _ints(ranks)
+    cp, _c = _ptrs(cores)
+    ctx.check(load().tr_subchain(ctx.handle, N, k, d, r, cp, _ptr(idx), _ptr(w), idx.shape[0],
+                                 _ptr(A), _dt(A), _stream(stream)))
+
+
+def tr_gather(ctx: Context, X: torch.Tensor, k: int, idx: torch.Tensor, w: Optional[torch.Tensor],
+              Y: torch.Tensor, stream=None):
+    dims = list(X.shape)
+    d, _d = _i64s(dims)
+    ctx.check(load().tr_gather(ctx.handle, _ptr(X), _dt(X), len(dims), d, k, _ptr(idx), _ptr(w),
+                               idx.shape[0], _ptr(Y), _dt(Y), _stream(stream)))
+
+
+def tr_solve(ctx: Context, A: torch.Tensor, Y: torch.Tensor, Rl: int, Rr: int, prec: int,
+             core_out: torch.Tensor, stream=None):
+    J, L = A.shape
+    I = Y.shape[1]
+    ctx.check(load().tr_solve(ctx.handle, _ptr(A), _ptr(Y), _dt(A), J, Rl, Rr, I, prec,
+                              _ptr(core_out), _stream(stream)))
+
+
+def tr_init_cores(ctx: Context, dims, ranks, seed: int, k_begin: int, cores, stream=None):
+    d, _d = _i64s(dims)
+    r, _r = _ints(ranks)
+    cp, _c = _ptrs(cores)
+    ctx.check(load().tr_init_cores(ctx.handle, len(dims), d, r, seed, k_begin, cp,
+                                   _stream(stream)))
+
+
+def tr_als_sampled(ctx: Context, X: torch.Tensor, ranks, J: int, sweeps: int, seed: int,
+                   prec: int, cores: List[torch.Tensor],
+                   init_cores: Optional[List[Optional[torch.Tensor]]] = None, stream=None):
+    dims = list(X.shape)
+    d, _d = _i64s(dims)
+    r, _r = _ints(ranks)
+    cp, _c = _ptrs(cores)
+    if init_cores is not None:
+        ip, _i = _ptrs(init_cores)
+    else:
+        ip = ctypes.cast(c_vp(None), PP)
+    ctx.check(load().tr_als_sampled(ctx.handle, _ptr(X), _dt(X), len(dims), d, r, J, sweeps,
+                                    seed, prec, ip, cp, _stream(stream)))
+
+
+def tr_als_sampled_host(ctx: Context, X_host: torch.Tensor, ranks, J: int, sweeps: int,
+                        seed: int, prec: int, cores_host: List[torch.Tensor],
+                        init_cores_host: Optional[List[Optional[torch.Tensor]]] = None,
+                        stream=None):
+    """X_host and cores_host are CPU tensors (pinned for speed)."""
+    dims = list(X_host.shape)
+    d, _d = _i64s(dims)
+    r, _r = _ints(ranks)
+    cp, _c = _ptrs(cores_host)
+    if init_cores_host is not None:
+        ip, _i = _ptrs(init_cores_host)
+    else:
+        ip = ctypes.cast(c_vp(None), PP)
+    ctx.check(load().tr_als_sampled_host(ctx.handle, c_vp(X_host.data_ptr()), _dt(X_host),
+                                         len(dims), d, r, J, sweeps, seed, prec, ip, cp,
+                                         _stream(stream)))
+
+
+def tr_rel_error(ctx: Context, X: torch.Tensor, ranks, cores: List[torch.Tensor], stream=None):
+    dims = list(X.shape)
+    d, _d = _i64s(dims)
+    r, _r = _ints(ranks)
+    cp, _c = _ptrs(cores)
+    out = c_dbl(0.0)
+    ctx.check(load().tr_rel_error(ctx.handle, _ptr(X), _dt(X), len(dims), d, r, cp,
+                                  ctypes.byref(out), _stream(stream)))
+    return out.value
+
+
+def tr_profile_begin(ctx: Context):
+    ctx.check(load().tr_profile_begin(ctx.handle))
+
+
+def tr_profile_end(ctx: Context, stream=None):
+    """Stop recording; returns {kernel: (total_ms, launches)}."""
+    lib = load()
+    ctx.check(lib.tr_profile_end(ctx.handle, _stream(stream)))
+    out = {}
+    for i in range(lib.tr_profile_count(ctx.handle)):
+        name, ms, n = ctypes.c_char_p(), c_dbl(), c_i64()
+        ctx.check(lib.tr_profile_entry(ctx.handle, i, ctypes.byref(name), ctypes.byref(ms),
+                                       ctypes.byref(n)))
+        out[name.value.decode()] = (ms.value, n.value)
+    return out
+
+
+def empty_cores(dims, ranks, device="cuda"):
+    """Device buffers for the cores, FP64 slice-major (I_k, Rl_k, Rr_k)."""
+    N = len(dims)
+    return [torch.empty((dims[k], ranks[(k - 1) % N], ranks[k]), dtype=torch.float64,
+                        device=device) for k in range(N)]
