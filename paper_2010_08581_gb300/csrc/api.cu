@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <map>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -25,9 +26,17 @@ struct tr_ctx {
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
   std::vector<std::pair<const char*, size_t>> prof_marks;  // (kernel, first event index)
-  std::vector<std::string> prof_names;
-  std::vector<double> prof_ms;
-  std::vector<int64_t> prof_count;
+  std::map<std::string, std::pair<double, int64_t>> prof_tot;
+  std::vector<std::pair<std::string, std::pair<double, int64_t>>> prof_snapshot;
+  // CUDA graph of the last tr_als_sampled signature
+  cudaStream_t cap = nullptr;       // internal stream, used only for capture
+  uint64_t* d_seed = nullptr;       // Philox key read by the captured kernels
+  bool capturing = false;
+  struct Mark { const char* name; cudaEvent_t a, b; };
+  std::vector<Mark> graph_marks;    // profiler events captured into the graph
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<uint64_t> gkey;
+  bool gprof = false;
 };
 
 namespace {
@@ -113,15 +122,25 @@ tr_status ensure_ws(tr_ctx* ctx, size_t bytes) {
 
 cudaStream_t S(tr_stream s) { return static_cast<cudaStream_t>(s); }
 
-// Records an event pair around one launch when profiling is on.
+// Records an event pair around one launch when profiling is on. While a graph is being
+// captured the events become nodes of that graph and belong to it.
 struct Prof {
   tr_ctx* ctx;
   const char* name;
   cudaStream_t st;
   size_t first = 0;
+  cudaEvent_t ga = nullptr, gb = nullptr;
   bool on;
   Prof(tr_ctx* c, const char* n, cudaStream_t s) : ctx(c), name(n), st(s), on(c->prof) {
     if (!on) return;
+    if (ctx->capturing) {
+      if (cudaEventCreate(&ga) != cudaSuccess || cudaEventCreate(&gb) != cudaSuccess) {
+        on = false;
+        return;
+      }
+      cudaEventRecord(ga, st);
+      return;
+    }
     if (ctx->ev_used + 2 > ctx->ev_pool.size()) {
       for (int i = 0; i < 256; ++i) {
         cudaEvent_t e;
@@ -135,10 +154,29 @@ struct Prof {
   }
   ~Prof() {
     if (!on) return;
+    if (ctx->capturing) {
+      cudaEventRecord(gb, st);
+      ctx->graph_marks.push_back({name, ga, gb});
+      return;
+    }
     cudaEventRecord(ctx->ev_pool[first + 1], st);
     ctx->prof_marks.emplace_back(name, first);
   }
 };
+
+void add_prof(tr_ctx* ctx, const char* name, float ms) {
+  auto& t = ctx->prof_tot[name];
+  t.first += ms;
+  t.second += 1;
+}
+
+void drop_graph(tr_ctx* ctx) {
+  if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+  ctx->gexec = nullptr;
+  for (auto& m : ctx->graph_marks) { cudaEventDestroy(m.a); cudaEventDestroy(m.b); }
+  ctx->graph_marks.clear();
+  ctx->gkey.clear();
+}
 
 #define TR_LAUNCH(name, expr)                     \
   do {                                            \
@@ -173,7 +211,7 @@ tr_status run_pass(tr_ctx* ctx, const LevPass& p, const double* A, int64_t rows,
   const int n = trans ? static_cast<int>(rows) : cols;
   TR_LAUNCH("gram_f64", launch_gram(A, rows, cols, lda, trans, p.partial, p.splits, st));
   TR_LAUNCH("reduce_gram", launch_reduce(p.partial, false, p.splits, static_cast<int64_t>(n) * n,
-                                         n, 0, n, 0, n, p.G, n, false, st));
+                                         n, n, n, n, p.G, n, nullptr, 0, st));
   TR_LAUNCH("cholesky_leverage", launch_cholesky(p.G, n, 1, tol_scale, p.Lrow, p.Lcol,
                                                    p.invdiag, p.keep, p.info, ctx->d_err, st));
   return TR_OK;
@@ -208,15 +246,15 @@ tr_status leverage_run(tr_ctx* ctx, char* ws, const double* core, int64_t I, int
   const double tol = static_cast<double>(I > L ? I : L) * eps;
   if (I >= L) {
     TR_TRY(run_pass(ctx, p1, core, I, L, L, false, tol, st));
-    TR_LAUNCH("leverage_rows", launch_leverage_rows(core, I, L, L, p1.Lcol, p1.invdiag, p1.keep,
-                                                    ell, st));
+    TR_LAUNCH("leverage_rows", launch_trsm(0, false, L, p1.Lrow, p1.Lcol, p1.invdiag, nullptr, I,
+                                           core, L, nullptr, 1, 1, nullptr, ell, st));
   } else {
     // Wide G_(2): the range of A is that of C with A A^T = C C^T; ell(A) = ell(C).
     const int n = static_cast<int>(I);
     TR_TRY(run_pass(ctx, p1, core, I, L, L, true, tol, st));
     TR_TRY(run_pass(ctx, p2, p1.Lrow, I, n, n, false, tol, st));
-    TR_LAUNCH("leverage_rows", launch_leverage_rows(p1.Lrow, I, n, n, p2.Lcol, p2.invdiag,
-                                                    p2.keep, ell, st));
+    TR_LAUNCH("leverage_rows", launch_trsm(0, false, n, p2.Lrow, p2.Lcol, p2.invdiag, nullptr, I,
+                                           p1.Lrow, n, nullptr, 1, 1, nullptr, ell, st));
   }
   TR_LAUNCH("cdf", launch_cdf(ell, I, p, cdf, ctx->d_err, st));
   return TR_OK;
@@ -257,16 +295,14 @@ tr_status solve_run(tr_ctx* ctx, char* ws, const void* A, const void* Y, bool f6
   solve_plan(c, J, L, I, f64, &s);
   const int64_t ld = L + I;
   TR_LAUNCH("normal_eq", launch_normal_eq(A, Y, f64, J, L, I, s.partial, s.splits, st));
-  TR_LAUNCH("reduce_M", launch_reduce(s.partial, !f64, s.splits, L * ld, ld, 0, L, 0, L, s.M, L,
-                                      false, st));
-  TR_LAUNCH("reduce_B", launch_reduce(s.partial, !f64, s.splits, L * ld, ld, 0, L, L, I, s.BT, L,
-                                      true, st));
+  TR_LAUNCH("reduce_MB", launch_reduce(s.partial, !f64, s.splits, L * ld, ld, L, ld, L, s.M, L,
+                                       s.BT, L, st));
   const double eps = 2.220446049250313e-16;
   TR_LAUNCH("cholesky_solve", launch_cholesky(s.M, L, 0, static_cast<double>(L) * eps, s.Lrow,
                                                s.Lcol, s.invdiag, s.keep, s.info, ctx->d_err,
                                                st));
-  TR_LAUNCH("solve_rhs", launch_solve_rhs(s.BT, s.M, L, Rl, Rr, I, s.Lrow, s.Lcol, s.invdiag,
-                                          refine, s.info, core_out, st));
+  TR_LAUNCH("solve_rhs", launch_trsm(refine ? 2 : 1, refine, L, s.Lrow, s.Lcol, s.invdiag, s.info,
+                                      I, s.BT, L, s.M, Rl, Rr, core_out, nullptr, st));
   return TR_OK;
 }
 
@@ -310,84 +346,92 @@ tr_status read_device_error(tr_ctx* ctx, cudaStream_t st) {
   return TR_OK;
 }
 
-// The Alg. 2 driver on device buffers (no synchronisation).
-tr_status als_sampled_async(tr_ctx* ctx, const void* X, tr_dtype xdt, int N, const int64_t* dims,
-                            const int* ranks, int64_t J, int sweeps, uint64_t seed,
-                            tr_precision prec, const double* const* init_cores,
-                            double* const* cores, cudaStream_t st) {
-  const bool f64 = prec == TR_PREC_FP64;
+// The Alg. 2 driver on device buffers: plan the workspace (outside any capture), then issue
+// every launch of one call on a stream.
+struct AlsPlan {
+  const void* X; tr_dtype xdt; int N; const int64_t* dims; const int* ranks; int64_t J;
+  int sweeps; tr_precision prec; const double* const* init; double* const* cores;
+  std::vector<double*> p, cdf;
+  int32_t* idx; double* w; void* A; void* Y; char* ws;
+};
+
+tr_status als_plan(tr_ctx* ctx, AlsPlan& P) {
+  const int N = P.N;
+  const bool f64 = P.prec == TR_PREC_FP64;
   const size_t es = f64 ? 8 : 4;
   int64_t Imax = 0, Isum = 0;
   int Lmax = 0;
   for (int k = 0; k < N; ++k) {
-    Imax = dims[k] > Imax ? dims[k] : Imax;
-    Isum += dims[k];
-    const int L = rl_of(ranks, N, k) * ranks[k];
+    Imax = P.dims[k] > Imax ? P.dims[k] : Imax;
+    Isum += P.dims[k];
+    const int L = rl_of(P.ranks, N, k) * P.ranks[k];
     Lmax = L > Lmax ? L : Lmax;
   }
-  // Persistent region, then a stage region reused by every step.
-  auto carve_persist = [&](Carver& c, double** pbase, double** cbase, int32_t** idx, double** w,
-                           void** A, void** Y) {
-    *pbase = c.take<double>(Isum);
-    *cbase = c.take<double>(Isum);
-    *idx = c.take<int32_t>(static_cast<size_t>(J) * (N - 1));
-    *w = c.take<double>(J);
-    *A = c.take<char>(static_cast<size_t>(J) * Lmax * es);
-    *Y = c.take<char>(static_cast<size_t>(J) * Imax * es);
+  auto carve = [&](Carver& c, double** pb, double** cb) {
+    *pb = c.take<double>(Isum);
+    *cb = c.take<double>(Isum);
+    P.idx = c.take<int32_t>(static_cast<size_t>(P.J) * (N - 1));
+    P.w = c.take<double>(P.J);
+    P.A = c.take<char>(static_cast<size_t>(P.J) * Lmax * es);
+    P.Y = c.take<char>(static_cast<size_t>(P.J) * Imax * es);
   };
-  double *pbase, *cbase, *w;
-  int32_t* idx;
-  void *A, *Y;
+  double *pb, *cb;
   Carver dry(nullptr);
-  carve_persist(dry, &pbase, &cbase, &idx, &w, &A, &Y);
+  carve(dry, &pb, &cb);
   const size_t persist = (dry.off + 255) & ~size_t(255);
   size_t stage = 0;
   for (int k = 0; k < N; ++k) {
-    const int L = rl_of(ranks, N, k) * ranks[k];
-    const size_t a = leverage_bytes(dims[k], L), b = solve_bytes(J, L, dims[k], f64);
+    const int L = rl_of(P.ranks, N, k) * P.ranks[k];
+    const size_t a = leverage_bytes(P.dims[k], L), b = solve_bytes(P.J, L, P.dims[k], f64);
     stage = a > stage ? a : stage;
     stage = b > stage ? b : stage;
   }
   TR_TRY(ensure_ws(ctx, persist + stage));
   Carver c(ctx->arena);
-  carve_persist(c, &pbase, &cbase, &idx, &w, &A, &Y);
-  char* ws = ctx->arena + persist;
+  carve(c, &pb, &cb);
+  P.ws = ctx->arena + persist;
+  P.p.resize(N);
+  P.cdf.resize(N);
+  int64_t off = 0;
+  for (int k = 0; k < N; ++k) { P.p[k] = pb + off; P.cdf[k] = cb + off; off += P.dims[k]; }
+  return TR_OK;
+}
 
-  std::vector<double*> p(N), cdf(N);
-  {
-    int64_t off = 0;
-    for (int k = 0; k < N; ++k) { p[k] = pbase + off; cdf[k] = cbase + off; off += dims[k]; }
-  }
-  // Initial cores G^(2..N) (paper numbering).
+tr_status als_issue(tr_ctx* ctx, const AlsPlan& P, uint64_t seed, const uint64_t* seed_dev,
+                    cudaStream_t st) {
+  const int N = P.N;
+  const bool f64 = P.prec == TR_PREC_FP64;
+  const int64_t* dims = P.dims;
+  const int* ranks = P.ranks;
   for (int k = 1; k < N; ++k) {
     const size_t count = static_cast<size_t>(dims[k]) * rl_of(ranks, N, k) * ranks[k];
-    if (init_cores) {
-      if (!init_cores[k]) return fail(ctx, TR_ERR_INVALID_ARG, "init_cores[%d] is NULL", k);
-      TR_CUDA(cudaMemcpyAsync(cores[k], init_cores[k], count * sizeof(double),
+    if (P.init) {
+      TR_CUDA(cudaMemcpyAsync(P.cores[k], P.init[k], count * sizeof(double),
                               cudaMemcpyDeviceToDevice, st));
     } else {
-      TR_LAUNCH("init_normal", launch_init_normal(cores[k], static_cast<int64_t>(count), seed,
-                                                  static_cast<uint32_t>(k), st));
+      TR_LAUNCH("init_normal", launch_init_normal(P.cores[k], static_cast<int64_t>(count), seed,
+                                                  static_cast<uint32_t>(k), seed_dev, st));
     }
   }
   for (int k = 1; k < N; ++k)
-    TR_TRY(leverage_run(ctx, ws, cores[k], dims[k], rl_of(ranks, N, k), ranks[k], p[k], cdf[k], st));
-
+    TR_TRY(leverage_run(ctx, P.ws, P.cores[k], dims[k], rl_of(ranks, N, k), ranks[k], P.p[k],
+                        P.cdf[k], st));
   int64_t stride[kMaxModes];
   row_major_strides(N, dims, stride);
-  const bool x64 = xdt == TR_F64;
-  for (int s = 0; s < sweeps; ++s) {
+  const bool x64 = P.xdt == TR_F64;
+  for (int s = 0; s < P.sweeps; ++s) {
     for (int n = 0; n < N; ++n) {
       SampleArgs sa{};
       ChainArgs ca{};
       GatherArgs ga{};
       sa.npos = ca.npos = ga.npos = N - 1;
+      sa.seed_dev = seed_dev;
       for (int m = 0; m < N - 1; ++m) {
         const int mode = (n + 1 + m) % N;
-        sa.p[m] = p[mode];
-        sa.cdf[m] = cdf[mode];
+        sa.p[m] = P.p[mode];
+        sa.cdf[m] = P.cdf[mode];
         sa.I[m] = ca.I[m] = ga.I[m] = dims[mode];
-        ca.core[m] = cores[mode];
+        ca.core[m] = P.cores[mode];
         ca.rl[m] = rl_of(ranks, N, mode);
         ca.rr[m] = ranks[mode];
         ga.stride[m] = stride[mode];
@@ -395,13 +439,87 @@ tr_status als_sampled_async(tr_ctx* ctx, const void* X, tr_dtype xdt, int N, con
       ga.In = dims[n];
       ga.stride_n = stride[n];
       const uint64_t uid = static_cast<uint64_t>(s) * N + n;
-      TR_LAUNCH("sample", launch_sample(sa, J, seed, uid, idx, w, st));
-      TR_LAUNCH("subchain", launch_subchain(ca, idx, w, J, A, f64, ctx->d_err, st));
-      TR_LAUNCH("gather", launch_gather(ga, X, x64, idx, w, J, Y, f64, ctx->d_err, st));
+      TR_LAUNCH("sample", launch_sample(sa, P.J, seed, uid, P.idx, P.w, st));
+      TR_LAUNCH("subchain", launch_subchain(ca, P.idx, P.w, P.J, P.A, f64, ctx->d_err, st));
+      TR_LAUNCH("gather", launch_gather(ga, P.X, x64, P.idx, P.w, P.J, P.Y, f64, ctx->d_err, st));
       const int Rl = rl_of(ranks, N, n), Rr = ranks[n];
-      TR_TRY(solve_run(ctx, ws, A, Y, f64, J, Rl, Rr, dims[n], !f64, cores[n], st));
-      TR_TRY(leverage_run(ctx, ws, cores[n], dims[n], Rl, Rr, p[n], cdf[n], st));
+      TR_TRY(solve_run(ctx, P.ws, P.A, P.Y, f64, P.J, Rl, Rr, dims[n], !f64, P.cores[n], st));
+      TR_TRY(leverage_run(ctx, P.ws, P.cores[n], dims[n], Rl, Rr, P.p[n], P.cdf[n], st));
     }
+  }
+  return TR_OK;
+}
+
+std::vector<uint64_t> als_key(const tr_ctx* ctx, const AlsPlan& P) {
+  std::vector<uint64_t> k;
+  auto u = [&](uint64_t v) { k.push_back(v); };
+  u(reinterpret_cast<uintptr_t>(P.X));
+  u(P.xdt);
+  u(P.N);
+  for (int i = 0; i < P.N; ++i) {
+    u(static_cast<uint64_t>(P.dims[i]));
+    u(static_cast<uint64_t>(P.ranks[i]));
+    u(reinterpret_cast<uintptr_t>(P.cores[i]));
+    u(P.init ? reinterpret_cast<uintptr_t>(P.init[i]) : 0);
+  }
+  u(static_cast<uint64_t>(P.J));
+  u(static_cast<uint64_t>(P.sweeps));
+  u(P.prec);
+  u(P.init ? 1 : 0);
+  u(reinterpret_cast<uintptr_t>(ctx->arena));
+  u(ctx->arena_bytes);
+  return k;
+}
+
+bool graphs_enabled() {
+  const char* e = getenv("TRALS_NO_GRAPH");
+  return !(e && e[0] == '1');
+}
+
+// One whole call: plan, then either issue directly or (re)capture and launch the graph.
+tr_status als_run(tr_ctx* ctx, AlsPlan& P, uint64_t seed, cudaStream_t st) {
+  TR_TRY(als_plan(ctx, P));
+  if (!graphs_enabled()) return als_issue(ctx, P, seed, nullptr, st);
+  std::vector<uint64_t> key = als_key(ctx, P);
+  if (!ctx->gexec || key != ctx->gkey || ctx->gprof != ctx->prof) {
+    drop_graph(ctx);
+    cudaGraph_t g = nullptr;
+    ctx->capturing = true;
+    TR_CUDA(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
+    tr_status s = als_issue(ctx, P, 0, ctx->d_seed, ctx->cap);
+    cudaError_t e = cudaStreamEndCapture(ctx->cap, &g);
+    ctx->capturing = false;
+    if (s != TR_OK) {
+      if (g) cudaGraphDestroy(g);
+      drop_graph(ctx);
+      return s;
+    }
+    if (e != cudaSuccess) {
+      drop_graph(ctx);
+      return fail(ctx, TR_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+    }
+    e = cudaGraphInstantiate(&ctx->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      ctx->gexec = nullptr;
+      drop_graph(ctx);
+      return fail(ctx, TR_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+    }
+    ctx->gkey = key;
+    ctx->gprof = ctx->prof;
+  }
+  TR_CUDA(cudaMemcpyAsync(ctx->d_seed, &seed, sizeof seed, cudaMemcpyHostToDevice, st));
+  TR_CUDA(cudaGraphLaunch(ctx->gexec, st));
+  return TR_OK;
+}
+
+// After a synchronised graph launch, fold its captured profiler events into the totals.
+tr_status fold_graph_marks(tr_ctx* ctx) {
+  if (!ctx->gexec || !ctx->gprof || !graphs_enabled()) return TR_OK;
+  for (const auto& m : ctx->graph_marks) {
+    float ms = 0.f;
+    TR_CUDA(cudaEventElapsedTime(&ms, m.a, m.b));
+    add_prof(ctx, m.name, ms);
   }
   return TR_OK;
 }
@@ -426,12 +544,16 @@ tr_status tr_create(tr_ctx** out, int device, size_t hbm_budget_bytes) {
   ctx->budget = hbm_budget_bytes;
   DeviceGuard g(device);
   if (!g.ok || cudaMalloc(&ctx->d_err, 256) != cudaSuccess ||
-      cudaMemset(ctx->d_err, 0, 256) != cudaSuccess) {
+      cudaMemset(ctx->d_err, 0, 256) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking) != cudaSuccess ||
+      init_kernel_attributes() != cudaSuccess) {
     cudaGetLastError();
     if (ctx->d_err) cudaFree(ctx->d_err);
+    if (ctx->cap) cudaStreamDestroy(ctx->cap);
     delete ctx;
     return TR_ERR_CUDA;
   }
+  ctx->d_seed = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(ctx->d_err) + 128);
   *out = ctx;
   return TR_OK;
 }
@@ -442,6 +564,8 @@ void tr_destroy(tr_ctx* ctx) {
   cudaDeviceSynchronize();
   if (ctx->arena) cudaFree(ctx->arena);
   if (ctx->host_stage) cudaFree(ctx->host_stage);
+  drop_graph(ctx);
+  if (ctx->cap) cudaStreamDestroy(ctx->cap);
   if (ctx->d_err) cudaFree(ctx->d_err);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   delete ctx;
@@ -574,14 +698,14 @@ tr_status tr_init_cores(tr_ctx* ctx, int N, const int64_t* dims, const int* rank
     if (!cores[k]) return fail(ctx, TR_ERR_INVALID_ARG, "cores[%d] is NULL", k);
     const int64_t count = dims[k] * rl_of(ranks, N, k) * ranks[k];
     TR_LAUNCH("init_normal", launch_init_normal(cores[k], count, seed, static_cast<uint32_t>(k),
-                                                st));
+                                                nullptr, st));
   }
   return TR_OK;
 }
 
 static tr_status check_als(tr_ctx* ctx, const void* X, tr_dtype xdt, int N, const int64_t* dims,
                            const int* ranks, int64_t J, int sweeps, tr_precision prec,
-                           double* const* cores) {
+                           double* const* cores, const double* const* init) {
   TR_TRY(check_shape(ctx, N, dims, ranks));
   if (!ranks) return fail(ctx, TR_ERR_INVALID_ARG, "ranks is NULL");
   if (!X || !cores) return fail(ctx, TR_ERR_INVALID_ARG, "null pointer");
@@ -592,6 +716,9 @@ static tr_status check_als(tr_ctx* ctx, const void* X, tr_dtype xdt, int N, cons
   if (xdt != TR_F32 && xdt != TR_F64) return fail(ctx, TR_ERR_INVALID_ARG, "bad X dtype");
   if (prec != TR_PREC_FP64 && prec != TR_PREC_MIXED)
     return fail(ctx, TR_ERR_INVALID_ARG, "bad precision");
+  if (init)
+    for (int k = 1; k < N; ++k)
+      if (!init[k]) return fail(ctx, TR_ERR_INVALID_ARG, "init_cores[%d] is NULL", k);
   return TR_OK;
 }
 
@@ -600,11 +727,13 @@ tr_status tr_als_sampled(tr_ctx* ctx, const void* X, tr_dtype X_dtype, int N, co
                          tr_precision prec, const double* const* init_cores,
                          double* const* cores, tr_stream stream) {
   TR_TRY(check_ctx(ctx));
-  TR_TRY(check_als(ctx, X, X_dtype, N, dims, ranks, J, sweeps, prec, cores));
+  TR_TRY(check_als(ctx, X, X_dtype, N, dims, ranks, J, sweeps, prec, cores, init_cores));
   DeviceGuard g(ctx->device);
-  TR_TRY(als_sampled_async(ctx, X, X_dtype, N, dims, ranks, J, sweeps, seed, prec, init_cores,
-                           cores, S(stream)));
-  return read_device_error(ctx, S(stream));
+  AlsPlan P{X, X_dtype, N, dims, ranks, J, sweeps, prec, init_cores, cores};
+  TR_TRY(als_run(ctx, P, seed, S(stream)));
+  tr_status s = read_device_error(ctx, S(stream));
+  TR_TRY(fold_graph_marks(ctx));
+  return s;
 }
 
 tr_status tr_als_sampled_host(tr_ctx* ctx, const void* X_host, tr_dtype X_dtype, int N,
@@ -613,7 +742,8 @@ tr_status tr_als_sampled_host(tr_ctx* ctx, const void* X_host, tr_dtype X_dtype,
                               const double* const* init_cores_host, double* const* cores_host,
                               tr_stream stream) {
   TR_TRY(check_ctx(ctx));
-  TR_TRY(check_als(ctx, X_host, X_dtype, N, dims, ranks, J, sweeps, prec, cores_host));
+  TR_TRY(check_als(ctx, X_host, X_dtype, N, dims, ranks, J, sweeps, prec, cores_host,
+                   init_cores_host));
   DeviceGuard g(ctx->device);
   cudaStream_t st = S(stream);
   int64_t numel = 1;
@@ -656,11 +786,14 @@ tr_status tr_als_sampled_host(tr_ctx* ctx, const void* X_host, tr_dtype X_dtype,
       TR_CUDA(cudaMemcpyAsync(dinit[k], init_cores_host[k], cbytes[k], cudaMemcpyHostToDevice, st));
     }
   }
-  TR_TRY(als_sampled_async(ctx, dX, X_dtype, N, dims, ranks, J, sweeps, seed, prec,
-                           init_cores_host ? dinit.data() : nullptr, dcores.data(), st));
+  AlsPlan P{dX, X_dtype, N, dims, ranks, J, sweeps, prec,
+            init_cores_host ? dinit.data() : nullptr, dcores.data()};
+  TR_TRY(als_run(ctx, P, seed, st));
   for (int k = 0; k < N; ++k)
     TR_CUDA(cudaMemcpyAsync(cores_host[k], dcores[k], cbytes[k], cudaMemcpyDeviceToHost, st));
-  return read_device_error(ctx, st);
+  tr_status s = read_device_error(ctx, st);
+  TR_TRY(fold_graph_marks(ctx));
+  return s;
 }
 
 tr_status tr_rel_error(tr_ctx* ctx, const void* X, tr_dtype X_dtype, int N, const int64_t* dims,
@@ -699,9 +832,8 @@ tr_status tr_profile_begin(tr_ctx* ctx) {
   ctx->prof = true;
   ctx->ev_used = 0;
   ctx->prof_marks.clear();
-  ctx->prof_names.clear();
-  ctx->prof_ms.clear();
-  ctx->prof_count.clear();
+  ctx->prof_tot.clear();
+  ctx->prof_snapshot.clear();
   return TR_OK;
 }
 
@@ -711,41 +843,29 @@ tr_status tr_profile_end(tr_ctx* ctx, tr_stream stream) {
   ctx->prof = false;
   TR_CUDA(cudaStreamSynchronize(S(stream)));
   TR_CUDA(cudaDeviceSynchronize());
-  std::map<std::string, size_t> slot;
-  for (size_t i = 0; i < ctx->prof_names.size(); ++i) slot[ctx->prof_names[i]] = i;
   for (const auto& m : ctx->prof_marks) {
     float ms = 0.f;
     TR_CUDA(cudaEventElapsedTime(&ms, ctx->ev_pool[m.second], ctx->ev_pool[m.second + 1]));
-    auto it = slot.find(m.first);
-    size_t k;
-    if (it == slot.end()) {
-      k = ctx->prof_names.size();
-      slot[m.first] = k;
-      ctx->prof_names.emplace_back(m.first);
-      ctx->prof_ms.push_back(0.0);
-      ctx->prof_count.push_back(0);
-    } else {
-      k = it->second;
-    }
-    ctx->prof_ms[k] += ms;
-    ctx->prof_count[k] += 1;
+    add_prof(ctx, m.first, ms);
   }
   ctx->prof_marks.clear();
   ctx->ev_used = 0;
+  ctx->prof_snapshot.assign(ctx->prof_tot.begin(), ctx->prof_tot.end());
   return TR_OK;
 }
 
 int tr_profile_count(const tr_ctx* ctx) {
-  return ctx ? static_cast<int>(ctx->prof_names.size()) : 0;
+  return ctx ? static_cast<int>(ctx->prof_snapshot.size()) : 0;
 }
 
 tr_status tr_profile_entry(const tr_ctx* ctx, int i, const char** name, double* total_ms,
                            int64_t* launches) {
-  if (!ctx || i < 0 || i >= static_cast<int>(ctx->prof_names.size()))
+  if (!ctx || i < 0 || i >= static_cast<int>(ctx->prof_snapshot.size()))
     return TR_ERR_INVALID_ARG;
-  if (name) *name = ctx->prof_names[i].c_str();
-  if (total_ms) *total_ms = ctx->prof_ms[i];
-  if (launches) *launches = ctx->prof_count[i];
+  const auto& e = ctx->prof_snapshot[i];
+  if (name) *name = e.first.c_str();
+  if (total_ms) *total_ms = e.second.first;
+  if (launches) *launches = e.second.second;
   return TR_OK;
 }
 

@@ -51,6 +51,7 @@ struct SampleArgs {
   const double* cdf[kMaxModes];
   int64_t I[kMaxModes];
   int npos;                      // N - 1
+  const uint64_t* seed_dev;      // if non-null, the Philox key is read from here
 };
 cudaError_t launch_sample(const SampleArgs& a, int64_t J, uint64_t seed, uint64_t update_id,
                           int32_t* idx, double* w, cudaStream_t st);
@@ -88,12 +89,12 @@ size_t gram_workspace(int64_t rows, int cols, bool trans, int* splits);
 cudaError_t launch_gram(const double* A, int64_t rows, int cols, int64_t lda, bool trans,
                         double* partial, int splits, cudaStream_t st);
 
-// out = sum over s (in order s = 0..splits-1) of the nrows x ncols block of partial[s]
-// starting at (row0, col0); partial row stride pld, split stride pstride, FP32 or FP64.
-// transpose=false: out[r*ldo + c]; transpose=true: out[c*ldo + r]. FP64 output.
+// Fixed-order reduction over splits s = 0..splits-1 of an nrows x ncols block of partials
+// (row stride pld, split stride pstride; FP32 or FP64) into FP64. Columns c < c_split go
+// to out1[r*ld1 + c]; columns c >= c_split go transposed to out2[(c - c_split)*ld2 + r].
 cudaError_t launch_reduce(const void* partial, bool partial_f32, int splits, int64_t pstride,
-                          int64_t pld, int64_t row0, int64_t nrows, int64_t col0,
-                          int64_t ncols, double* out, int64_t ldo, bool transpose,
+                          int64_t pld, int64_t nrows, int64_t ncols, int64_t c_split,
+                          double* out1, int64_t ld1, double* out2, int64_t ld2,
                           cudaStream_t st);
 
 // Cholesky G = L L^T of the n x n FP64 matrix G (row-major, ld n; only the upper triangle
@@ -106,19 +107,17 @@ cudaError_t launch_cholesky(const double* G, int n, int mode, double tol_scale, 
                             double* Lcol, double* invdiag, int* keep, int* info,
                             unsigned* err, cudaStream_t st);
 
-// Right-hand sides of the normal equations: BT is I x L (row i = column i of B). For each
-// i, z = M^-1 b via the factor; if refine, z += M^-1 (b - M z) with M the full symmetric
-// FP64 matrix. Writes core_out[i][a][b] = z[a + Rl*b]; nothing if *info != 0.
-cudaError_t launch_solve_rhs(const double* BT, const double* M, int L, int Rl, int Rr,
-                             int64_t I, const double* Lrow, const double* Lcol,
-                             const double* invdiag, bool refine, const int* info,
-                             double* core_out, cudaStream_t st);
-
-// Leverage rows: ell[i] = || L^-1 a_i ||^2 over kept columns, a_i = row i of A (rows x n,
-// row-major, lda).
-cudaError_t launch_leverage_rows(const double* A, int64_t rows, int n, int64_t lda,
-                                 const double* Lcol, const double* invdiag, const int* keep,
-                                 double* ell, cudaStream_t st);
+// Triangular solves with the factor of launch_cholesky for nvec vectors (row v of rhs,
+// leading dimension ld, length n):
+//   mode 0: ell[v] = || L^-1 rhs_v ||^2 (leverage rows);
+//   mode 1: z = L^-T L^-1 rhs_v written to core_out[v][a][b] = z[a + Rl*b];
+//   mode 2: as mode 1 plus one refinement step z += M^-1 (rhs_v - M z), M (n x n FP64).
+// f32 selects FP32 arithmetic (factor and M rounded to FP32), else FP64. Nothing is done
+// when *info != 0 (info may be NULL).
+cudaError_t launch_trsm(int mode, bool f32, int n, const double* Lrow, const double* Lcol,
+                        const double* invdiag, const int* info, int64_t nvec, const double* rhs,
+                        int64_t ld, const double* M, int Rl, int Rr, double* core_out,
+                        double* ell, cudaStream_t st);
 
 // p = ell / sum(ell), cdf = inclusive prefix sum (fixed order), one CTA. All-zero ell ->
 // uniform p and the singular bit.
@@ -127,7 +126,10 @@ cudaError_t launch_cdf(const double* ell, int64_t I, double* p, double* cdf, uns
 
 // Core initialisation N(0,1) by Philox + Box-Muller.
 cudaError_t launch_init_normal(double* out, int64_t count, uint64_t seed, uint32_t stream_id,
-                               cudaStream_t st);
+                               const uint64_t* seed_dev, cudaStream_t st);
+
+// Raise the dynamic shared-memory limit of the kernels that need it (once per device).
+cudaError_t init_kernel_attributes();
 
 // Fit: partial sums of squares of (X - TR) and X over blocks; FP64 outputs [2][blocks].
 struct FitArgs {

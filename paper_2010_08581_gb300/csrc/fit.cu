@@ -138,22 +138,33 @@ cudaError_t launch_fit(const FitArgs& a, const void* X, bool x_f64, double* part
   for (int m = 0; m < a.N - 1; ++m) lead *= a.dims[m];
   if (x_f64) {
     const size_t dyn = static_cast<size_t>(FL + FI) * a.ranks[a.N - 2] * a.ranks[a.N - 1] * sizeof(double);
-    cudaError_t e = cudaFuncSetAttribute(k_fit<double>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(dyn));
-    if (e != cudaSuccess) return e;
     k_fit<double><<<blocks, FNT, dyn, st>>>(a, static_cast<const double*>(X), lead, partial,
                                             blocks);
   } else {
     const size_t dyn = static_cast<size_t>(FL + FI) * a.ranks[a.N - 2] * a.ranks[a.N - 1] * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(k_fit<float>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(dyn));
-    if (e != cudaSuccess) return e;
     k_fit<float><<<blocks, FNT, dyn, st>>>(a, static_cast<const float*>(X), lead, partial,
                                            blocks);
   }
   return cudaGetLastError();
+}
+
+cudaError_t fit_attributes() {
+  cudaError_t e = cudaFuncSetAttribute(k_fit<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       200 * 1024);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_fit<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              200 * 1024);
+}
+
+cudaError_t cholesky_attributes();
+cudaError_t trsm_attributes();
+
+cudaError_t init_kernel_attributes() {
+  cudaError_t e = cholesky_attributes();
+  if (e != cudaSuccess) return e;
+  e = trsm_attributes();
+  if (e != cudaSuccess) return e;
+  return fit_attributes();
 }
 
 }  // namespace trk

@@ -1,0 +1,149 @@
+// Gram matrices for the Cholesky-based thin QR behind the leverage scores (row a1:
+// Def. 3.3, eq. for p^(n)), and the fixed-order reduction of split partials used by the
+// Gram and by the normal-equation contraction (rows a1, a5).
+#include "common.cuh"
+
+namespace trk {
+namespace {
+
+// ------------------------------------------------------------------------------------
+// Gram: partial[s][p][q] = sum_{t in chunk s} X(t, p) X(t, q), tiles with tp <= tq only.
+// X(t, p) = A[t*lda + p] (trans = false) or A[p*lda + t] (trans = true).
+// ------------------------------------------------------------------------------------
+constexpr int GT = 32, GK = 32, GNT = 256;
+
+__global__ void __launch_bounds__(GNT) k_gram(const double* __restrict__ A, int64_t K, int n,
+                                              int64_t lda, bool trans, int64_t chunk,
+                                              double* __restrict__ partial) {
+  __shared__ double P[GK][GT + 1];
+  __shared__ double Q[GK][GT + 1];
+  const int nt = (n + GT - 1) / GT;
+  int tp = 0, rem = blockIdx.x;
+  while (rem >= nt - tp) { rem -= nt - tp; ++tp; }
+  const int tq = tp + rem;
+  const int p0 = tp * GT, q0 = tq * GT;
+  const int64_t k0 = static_cast<int64_t>(blockIdx.y) * chunk;
+  const int64_t k1 = (k0 + chunk < K) ? k0 + chunk : K;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  double acc[4] = {0, 0, 0, 0};
+  for (int64_t kb = k0; kb < k1; kb += GK) {
+#pragma unroll
+    for (int r = 0; r < (GK * GT) / GNT; ++r) {
+      const int e = threadIdx.x + r * GNT;
+      int kk, col;
+      if (!trans) { kk = e / GT; col = e % GT; } else { col = e / GK; kk = e % GK; }
+      const int64_t t = kb + kk;
+      const int p = p0 + col, q = q0 + col;
+      double vp = 0.0, vq = 0.0;
+      if (t < k1) {
+        if (p < n) vp = trans ? A[p * lda + t] : A[t * lda + p];
+        if (q < n) vq = trans ? A[q * lda + t] : A[t * lda + q];
+      }
+      P[kk][col] = vp;
+      Q[kk][col] = vq;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < GK; ++kk) {
+      const double b = Q[kk][tx];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc[u] += P[kk][ty + 8 * u] * b;
+    }
+    __syncthreads();
+  }
+  double* out = partial + static_cast<int64_t>(blockIdx.y) * n * n;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int p = p0 + ty + 8 * u, q = q0 + tx;
+    if (p < n && q < n) out[static_cast<int64_t>(p) * n + q] = acc[u];
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// Fixed-order reduction of split partials (s = 0, 1, ..., splits-1) into FP64.
+// Columns c < c_split go to out1[r*ld1 + c]; columns c >= c_split go transposed to
+// out2[(c - c_split)*ld2 + r]. One element per thread, loads coalesced along c.
+// ------------------------------------------------------------------------------------
+template <typename TP>
+__global__ void __launch_bounds__(256) k_reduce(const TP* __restrict__ partial, int splits,
+                                                int64_t pstride, int64_t pld, int64_t nrows,
+                                                int64_t ncols, int64_t c_split,
+                                                double* __restrict__ out1, int64_t ld1,
+                                                double* __restrict__ out2, int64_t ld2) {
+  const int64_t total = nrows * ncols;
+  for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t r = e / ncols, c = e - (e / ncols) * ncols;
+    const TP* src = partial + r * pld + c;
+    double s = 0.0;
+    int q = 0;
+    for (; q + 8 <= splits; q += 8) {
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = static_cast<double>(src[(q + u) * pstride]);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) s += v[u];
+    }
+    for (; q < splits; ++q) s += static_cast<double>(src[q * pstride]);
+    if (c < c_split) out1[r * ld1 + c] = s;
+    else out2[(c - c_split) * ld2 + r] = s;
+  }
+}
+
+int plan_splits(int64_t K, int tiles, int min_chunk, int64_t* chunk) {
+  int64_t s = (2 * 152 + tiles - 1) / tiles;
+  const int64_t maxs = (K + min_chunk - 1) / min_chunk;
+  if (s > maxs) s = maxs;
+  if (s < 1) s = 1;
+  int64_t c = (K + s - 1) / s;
+  c = (c + GK - 1) / GK * GK;
+  s = (K + c - 1) / c;
+  if (s < 1) s = 1;
+  *chunk = c;
+  return static_cast<int>(s);
+}
+
+}  // namespace
+
+size_t gram_workspace(int64_t rows, int cols, bool trans, int* splits) {
+  const int64_t K = trans ? cols : rows;
+  const int n = trans ? static_cast<int>(rows) : cols;
+  const int nt = (n + GT - 1) / GT;
+  int64_t chunk;
+  *splits = plan_splits(K, nt * (nt + 1) / 2, GK, &chunk);
+  return static_cast<size_t>(*splits) * n * n * sizeof(double);
+}
+
+cudaError_t launch_gram(const double* A, int64_t rows, int cols, int64_t lda, bool trans,
+                        double* partial, int splits, cudaStream_t st) {
+  const int64_t K = trans ? cols : rows;
+  const int n = trans ? static_cast<int>(rows) : cols;
+  const int nt = (n + GT - 1) / GT;
+  int64_t chunk;
+  const int s = plan_splits(K, nt * (nt + 1) / 2, GK, &chunk);
+  if (s != splits) return cudaErrorInvalidValue;
+  dim3 grid(nt * (nt + 1) / 2, s);
+  k_gram<<<grid, GNT, 0, st>>>(A, K, n, lda, trans, chunk, partial);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce(const void* partial, bool partial_f32, int splits, int64_t pstride,
+                          int64_t pld, int64_t nrows, int64_t ncols, int64_t c_split,
+                          double* out1, int64_t ld1, double* out2, int64_t ld2,
+                          cudaStream_t st) {
+  const int64_t total = nrows * ncols;
+  if (total <= 0) return cudaSuccess;
+  int64_t blocks = (total + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (partial_f32)
+    k_reduce<float><<<static_cast<unsigned>(blocks), 256, 0, st>>>(
+        static_cast<const float*>(partial), splits, pstride, pld, nrows, ncols, c_split, out1,
+        ld1, out2, ld2);
+  else
+    k_reduce<double><<<static_cast<unsigned>(blocks), 256, 0, st>>>(
+        static_cast<const double*>(partial), splits, pstride, pld, nrows, ncols, c_split, out1,
+        ld1, out2, ld2);
+  return cudaGetLastError();
+}
+
+}  // namespace trk

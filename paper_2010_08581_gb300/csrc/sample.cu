@@ -12,6 +12,11 @@ __global__ void __launch_bounds__(256) k_sample(SampleArgs a, int64_t J, uint32_
                                                 double* __restrict__ w) {
   const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (j >= J) return;
+  if (a.seed_dev) {
+    const uint64_t s = *a.seed_dev;
+    key0 = static_cast<uint32_t>(s);
+    key1 = static_cast<uint32_t>(s >> 32);
+  }
   double q = 1.0;
   u32x4 r{0, 0, 0, 0};
   for (int m = 0; m < a.npos; ++m) {
