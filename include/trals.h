@@ -69,7 +69,8 @@ tr_status tr_create(tr_ctx** ctx, int device, size_t hbm_budget_bytes);
 /* Free the context and its workspace (synchronises the device first). NULL is a no-op. */
 void tr_destroy(tr_ctx* ctx);
 
-/* Text of the last error reported by a call on this context ("" if none). */
+/* Text of the last error reported by a call on this context ("" if none); with ctx NULL,
+ * the reason of the last failed tr_create. */
 const char* tr_last_error(const tr_ctx* ctx);
 
 /* Wait for `stream`, then return and clear the device-side error record of the context

@@ -268,8 +268,15 @@ struct SolvePlan {
   int* keep; int* info; int splits;
 };
 
+bool use_tensor_cores(bool f64) {
+  if (f64) return false;
+  const char* e = getenv("TRALS_SIMT_CONTRACT");
+  return !(e && e[0] == '1');
+}
+
 size_t solve_plan(Carver& c, int64_t J, int L, int64_t I, bool f64, SolvePlan* s) {
-  const size_t pbytes = normal_eq_workspace(J, L, I, f64, &s->splits);
+  const size_t pbytes = use_tensor_cores(f64) ? normal_eq_tc_workspace(J, L, I, &s->splits)
+                                              : normal_eq_workspace(J, L, I, f64, &s->splits);
   s->partial = c.take<char>(pbytes);
   s->M = c.take<double>(static_cast<size_t>(L) * L);
   s->BT = c.take<double>(static_cast<size_t>(I) * L);
@@ -294,7 +301,14 @@ tr_status solve_run(tr_ctx* ctx, char* ws, const void* A, const void* Y, bool f6
   SolvePlan s;
   solve_plan(c, J, L, I, f64, &s);
   const int64_t ld = L + I;
-  TR_LAUNCH("normal_eq", launch_normal_eq(A, Y, f64, J, L, I, s.partial, s.splits, st));
+  if (use_tensor_cores(f64)) {
+    TR_LAUNCH("normal_eq_tc", launch_normal_eq_tc(static_cast<const float*>(A),
+                                                  static_cast<const float*>(Y), J, L, I,
+                                                  static_cast<float*>(s.partial), s.splits,
+                                                  ctx->d_err, st));
+  } else {
+    TR_LAUNCH("normal_eq", launch_normal_eq(A, Y, f64, J, L, I, s.partial, s.splits, st));
+  }
   TR_LAUNCH("reduce_MB", launch_reduce(s.partial, !f64, s.splits, L * ld, ld, L, ld, L, s.M, L,
                                        s.BT, L, st));
   const double eps = 2.220446049250313e-16;
@@ -340,6 +354,7 @@ tr_status read_device_error(tr_ctx* ctx, cudaStream_t st) {
   TR_CUDA(cudaStreamSynchronize(st));
   TR_CUDA(cudaMemcpy(&h, ctx->d_err, sizeof h, cudaMemcpyDeviceToHost));
   TR_CUDA(cudaMemset(ctx->d_err, 0, sizeof(unsigned)));
+  if (h & kErrTimeout) return fail(ctx, TR_ERR_TIMEOUT, "a bounded device wait expired");
   if (h & kErrBadIndex) return fail(ctx, TR_ERR_INVALID_ARG, "a sample index was out of range");
   if (h & kErrSingular)
     return fail(ctx, TR_ERR_SINGULAR, "non-positive pivot in the normal equations or a zero core");
@@ -531,11 +546,16 @@ tr_status fold_graph_marks(tr_ctx* ctx) {
 // ======================================================================================
 extern "C" {
 
+static std::string g_create_error;  // message of the last failed tr_create
+
 tr_status tr_create(tr_ctx** out, int device, size_t hbm_budget_bytes) {
   if (!out) return TR_ERR_INVALID_ARG;
   *out = nullptr;
   int count = 0;
-  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+  cudaError_t e = cudaGetDeviceCount(&count);
+  if (e != cudaSuccess || device < 0 || device >= count) {
+    g_create_error = std::string("no CUDA device ") + std::to_string(device) + ": " +
+                     (e != cudaSuccess ? cudaGetErrorString(e) : "index out of range");
     cudaGetLastError();
     return TR_ERR_INVALID_ARG;
   }
@@ -543,10 +563,18 @@ tr_status tr_create(tr_ctx** out, int device, size_t hbm_budget_bytes) {
   ctx->device = device;
   ctx->budget = hbm_budget_bytes;
   DeviceGuard g(device);
-  if (!g.ok || cudaMalloc(&ctx->d_err, 256) != cudaSuccess ||
-      cudaMemset(ctx->d_err, 0, 256) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking) != cudaSuccess ||
-      init_kernel_attributes() != cudaSuccess) {
+  const char* step = "cudaSetDevice";
+  const char* which = "";
+  e = g.ok ? cudaSuccess : cudaErrorInvalidDevice;
+  if (e == cudaSuccess) { step = "cudaMalloc(status)"; e = cudaMalloc(&ctx->d_err, 256); }
+  if (e == cudaSuccess) { step = "cudaMemset(status)"; e = cudaMemset(ctx->d_err, 0, 256); }
+  if (e == cudaSuccess) {
+    step = "cudaStreamCreate";
+    e = cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking);
+  }
+  if (e == cudaSuccess) { step = "cudaFuncSetAttribute"; e = init_kernel_attributes(&which); }
+  if (e != cudaSuccess) {
+    g_create_error = std::string(step) + " " + which + ": " + cudaGetErrorString(e);
     cudaGetLastError();
     if (ctx->d_err) cudaFree(ctx->d_err);
     if (ctx->cap) cudaStreamDestroy(ctx->cap);
@@ -571,7 +599,9 @@ void tr_destroy(tr_ctx* ctx) {
   delete ctx;
 }
 
-const char* tr_last_error(const tr_ctx* ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+const char* tr_last_error(const tr_ctx* ctx) {
+  return ctx ? ctx->last_error.c_str() : g_create_error.c_str();
+}
 
 tr_status tr_status_sync(tr_ctx* ctx, tr_stream stream) {
   TR_TRY(check_ctx(ctx));

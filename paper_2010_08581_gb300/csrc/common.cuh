@@ -12,6 +12,7 @@ namespace trk {
 enum : unsigned {
   kErrSingular = 1u,    // non-positive pivot or zero core
   kErrBadIndex = 2u,    // a caller-provided sample index out of range
+  kErrTimeout = 4u,     // a bounded device wait expired
 };
 
 constexpr int kMaxModes = TR_MAX_MODES;
@@ -79,6 +80,12 @@ cudaError_t launch_gather(const GatherArgs& a, const void* X, bool x_f64, const 
 // Normal-equation contraction: partial[s][r][c] = sum over the s-th chunk of rows j of
 // A[j][r] * [A | Y][j][c], r < L, c < L + I. Returns the number of chunks in *splits.
 size_t normal_eq_workspace(int64_t J, int L, int64_t I, bool f64, int* splits);
+
+// The same contraction on the tensor cores (tcgen05, TF32 split into hi + lo, FP32
+// accumulation in TMEM) for FP32 inputs; FP32 partials [splits][L][L + I].
+size_t normal_eq_tc_workspace(int64_t J, int L, int64_t I, int* splits);
+cudaError_t launch_normal_eq_tc(const float* A, const float* Y, int64_t J, int L, int64_t I,
+                                float* partial, int splits, unsigned* err, cudaStream_t st);
 cudaError_t launch_normal_eq(const void* A, const void* Y, bool f64, int64_t J, int L,
                              int64_t I, void* partial, int splits, cudaStream_t st);
 
@@ -128,8 +135,9 @@ cudaError_t launch_cdf(const double* ell, int64_t I, double* p, double* cdf, uns
 cudaError_t launch_init_normal(double* out, int64_t count, uint64_t seed, uint32_t stream_id,
                                const uint64_t* seed_dev, cudaStream_t st);
 
-// Raise the dynamic shared-memory limit of the kernels that need it (once per device).
-cudaError_t init_kernel_attributes();
+// Raise the dynamic shared-memory limit of the kernels that need it (once per device);
+// on failure *which names the kernel.
+cudaError_t init_kernel_attributes(const char** which);
 
 // Fit: partial sums of squares of (X - TR) and X over blocks; FP64 outputs [2][blocks].
 struct FitArgs {

@@ -148,23 +148,29 @@ cudaError_t launch_fit(const FitArgs& a, const void* X, bool x_f64, double* part
   return cudaGetLastError();
 }
 
+// The largest dynamic request of k_fit is (FL + FI) * kMaxL elements.
 cudaError_t fit_attributes() {
   cudaError_t e = cudaFuncSetAttribute(k_fit<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       200 * 1024);
+                                       (FL + FI) * kMaxL * static_cast<int>(sizeof(double)));
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_fit<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              200 * 1024);
+                              (FL + FI) * kMaxL * static_cast<int>(sizeof(float)));
 }
 
 cudaError_t cholesky_attributes();
 cudaError_t trsm_attributes();
+cudaError_t normal_eq_tc_attributes();
 
-cudaError_t init_kernel_attributes() {
+cudaError_t init_kernel_attributes(const char** which) {
   cudaError_t e = cholesky_attributes();
-  if (e != cudaSuccess) return e;
+  if (e != cudaSuccess) { *which = "cholesky"; return e; }
   e = trsm_attributes();
-  if (e != cudaSuccess) return e;
-  return fit_attributes();
+  if (e != cudaSuccess) { *which = "trsm"; return e; }
+  e = normal_eq_tc_attributes();
+  if (e != cudaSuccess) { *which = "normal_eq_tc"; return e; }
+  e = fit_attributes();
+  if (e != cudaSuccess) *which = "fit";
+  return e;
 }
 
 }  // namespace trk

@@ -1,0 +1,284 @@
+// Row a5 on the 5th-generation tensor cores: C = A~^T [A~ | Y~] (M = A~^T A~ and B = A~^T Y~
+// of the sampled LS, Alg. 2 LS step) with tcgen05.mma kind::tf32 and FP32 accumulation in
+// tensor memory.
+//
+// Each FP32 operand x is split into TF32 parts hi = rna_tf32(x), lo = rna_tf32(x - hi), and
+// every k-step issues hi*hi + hi*lo + lo*hi into the same accumulator, which recovers
+// close to FP32 accuracy (Markidis et al., "NVIDIA Tensor Core Programmability,
+// Performance & Precision", 2018; Ootomo & Yokota, 2022).
+//
+// One CTA = one 128 x BN output tile over one chunk of the J samples (split-K, partials
+// reduced downstream in a fixed order). All 256 threads load the chunk from global memory
+// (coalesced along the feature / fibre index), split it and store it into K-major,
+// 128-byte-swizzled shared-memory tiles; one elected thread issues the MMAs and commits
+// them to an mbarrier per pipeline stage; TMEM is read back with tcgen05.ld. Every
+// mbarrier wait is bounded: on expiry the CTA records an error, waits (bounded) for its
+// outstanding MMAs, frees its TMEM and returns.
+#include "common.cuh"
+
+namespace trk {
+namespace {
+
+constexpr int TM = 128;          // UMMA M
+constexpr int TN = 128;          // UMMA N (output columns per CTA)
+constexpr int TK = 32;           // samples per pipeline stage (one 128-byte swizzle row)
+constexpr int NT = 256;
+constexpr int STAGES = 2;
+constexpr int A_BYTES = TM * TK * 4;   // 16 KB
+constexpr int B_BYTES = TN * TK * 4;   // 16 KB
+constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;  // hi and lo of both operands
+constexpr uint32_t TMEM_COLS = TN;     // FP32 accumulator: 128 lanes x TN columns
+constexpr long long kSpinLimit = 1ll << 26;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// Byte offset of element (row, k) in a K-major SW128 tile of 32-bit elements (8-row atoms
+// of 8 x 128 B; the 16-byte chunk index is XORed with the row inside the atom).
+__device__ __forceinline__ uint32_t sw128_offset(int row, int k) {
+  return static_cast<uint32_t>((row >> 3) * 1024 + (row & 7) * 128 +
+                               ((((k >> 2) ^ (row & 7)) & 7) << 4) + ((k & 3) << 2));
+}
+
+// tcgen05 shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B
+// apart (stride byte offset), version 1.
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((saddr >> 4) & 0x3FFFu);          // start address
+  d |= static_cast<uint64_t>(1u) << 16;                        // leading byte offset (unused)
+  d |= static_cast<uint64_t>(1024u >> 4) << 32;                // stride byte offset
+  d |= static_cast<uint64_t>(1u) << 46;                        // descriptor version
+  d |= static_cast<uint64_t>(2u) << 61;                        // SWIZZLE_128B
+  return d;
+}
+
+// Instruction descriptor: D = F32, A = B = TF32, both K-major, M = 128, N = TN.
+constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) |
+                            (static_cast<uint32_t>(TN >> 3) << 17) |
+                            (static_cast<uint32_t>(TM >> 4) << 24);
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+      :: "r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+               :: "r"(mbar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(mbar), "r"(count) : "memory");
+}
+
+// Bounded wait for the given phase parity; returns false if the limit expired.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+  for (long long it = 0; it < kSpinLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tmem_load32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+        "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__global__ void __launch_bounds__(NT, 1) k_normal_eq_tc(const float* __restrict__ A,
+                                                        const float* __restrict__ Y, int64_t J,
+                                                        int L, int64_t I, int64_t chunk,
+                                                        float* __restrict__ partial,
+                                                        unsigned* err) {
+  extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
+  // 1024-byte alignment of the tiles (required by the 128-byte swizzle atoms)
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ __align__(8) uint64_t mbar[STAGES];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int s_abort;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t ldc = L + I;
+  const int m0 = blockIdx.y * TM;
+  const int64_t n0 = static_cast<int64_t>(blockIdx.x) * TN;
+  const int64_t j0 = static_cast<int64_t>(blockIdx.z) * chunk;
+  const int64_t j1 = (j0 + chunk < J) ? j0 + chunk : J;
+  const int nchunks = static_cast<int>((j1 - j0 + TK - 1) / TK);
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 :: "r"(smem_u32(&tmem_slot)), "r"(TMEM_COLS) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    for (int s = 0; s < STAGES; ++s) mbar_init(smem_u32(&mbar[s]), 1);
+    s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem_d = tmem_slot;
+
+  // Element loaders: thread t covers row (t % 128) of the tile and samples k = t/128 + 2r.
+  const int row = tid & 127;
+  const int k_first = tid >> 7;
+  const int am = m0 + row;                    // feature index of the A operand
+  const int64_t bn = n0 + row;                // output column of the B operand
+  int issued = 0;                             // commits issued (thread 0)
+
+  for (int c = 0; c < nchunks; ++c) {
+    const int s = c % STAGES;
+    unsigned char* st = base + s * STAGE_BYTES;
+    if (c >= STAGES) {   // wait until the MMAs that read this stage have finished
+      const bool ok = mbar_wait(smem_u32(&mbar[s]), ((c / STAGES) - 1) & 1);
+      if (!ok) atomicExch(&s_abort, 1);
+    }
+    __syncthreads();
+    if (s_abort) break;
+    const int64_t jb = j0 + static_cast<int64_t>(c) * TK;
+#pragma unroll 4
+    for (int r = 0; r < TK / 2; ++r) {
+      const int k = k_first + 2 * r;
+      const int64_t j = jb + k;
+      float a = 0.f, b = 0.f;
+      if (j < j1) {
+        if (am < L) a = A[j * L + am];
+        if (bn < L) b = A[j * L + bn];
+        else if (bn < ldc) b = Y[j * I + (bn - L)];
+      }
+      const float ah = tf32_rna(a), bh = tf32_rna(b);
+      const float al = tf32_rna(a - ah), bl = tf32_rna(b - bh);
+      const uint32_t oa = sw128_offset(row, k);
+      *reinterpret_cast<float*>(st + oa) = ah;
+      *reinterpret_cast<float*>(st + A_BYTES + oa) = al;
+      *reinterpret_cast<float*>(st + 2 * A_BYTES + oa) = bh;
+      *reinterpret_cast<float*>(st + 2 * A_BYTES + B_BYTES + oa) = bl;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a_hi = smem_u32(st), a_lo = a_hi + A_BYTES;
+      const uint32_t b_hi = a_hi + 2 * A_BYTES, b_lo = b_hi + B_BYTES;
+#pragma unroll
+      for (int ks = 0; ks < TK / 8; ++ks) {
+        const uint32_t koff = ks * 32;   // 8 TF32 = 32 bytes along K inside the swizzle row
+        const uint32_t acc0 = (c > 0 || ks > 0) ? 1u : 0u;
+        mma_tf32(tmem_d, make_desc(a_hi + koff), make_desc(b_hi + koff), acc0);
+        mma_tf32(tmem_d, make_desc(a_hi + koff), make_desc(b_lo + koff), 1u);
+        mma_tf32(tmem_d, make_desc(a_lo + koff), make_desc(b_hi + koff), 1u);
+      }
+      mma_commit(smem_u32(&mbar[s]));
+      ++issued;
+    }
+  }
+  __syncthreads();
+  const int aborted = s_abort;
+  // Wait for the last commit of each stage that was used (bounded).
+  bool ok = true;
+  if (nchunks > 0) {
+    const int last = nchunks - 1;
+    ok = mbar_wait(smem_u32(&mbar[last % STAGES]), (last / STAGES) & 1);
+    if (nchunks > 1) {
+      const int prev = nchunks - 2;
+      ok = mbar_wait(smem_u32(&mbar[prev % STAGES]), (prev / STAGES) & 1) && ok;
+    }
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (!ok || aborted) {
+    if (tid == 0) atomicOr(err, kErrTimeout);
+  } else if (nchunks > 0) {
+    // Epilogue: warp w reads TMEM lanes 32*(w%4).. (rows) and column half w/4.
+    const int quad = warp & 3, half = warp >> 2;
+    const int m = m0 + quad * 32 + lane;
+#pragma unroll
+    for (int cc = 0; cc < TN / 64; ++cc) {
+      const int col = half * (TN / 2) + cc * 32;
+      float v[32];
+      tmem_load32(tmem_d + (static_cast<uint32_t>(quad * 32) << 16) + col, v);
+      if (m < L) {
+        float* out = partial + (static_cast<int64_t>(blockIdx.z) * L + m) * ldc + n0 + col;
+#pragma unroll
+        for (int i = 0; i < 32; ++i)
+          if (n0 + col + i < ldc) out[i] = v[i];
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
+                 :: "r"(tmem_d), "r"(TMEM_COLS) : "memory");
+  (void)issued;
+}
+
+void plan_tc(int64_t J, int L, int64_t I, int* splits, int64_t* chunk) {
+  const int64_t tiles = ((L + TM - 1) / TM) * ((L + I + TN - 1) / TN);
+  int64_t s = (148 + tiles - 1) / tiles;
+  const int64_t maxs = (J + 4 * TK - 1) / (4 * TK);   // at least 4 stages per CTA
+  if (s > maxs) s = maxs;
+  if (s < 1) s = 1;
+  int64_t c = (J + s - 1) / s;
+  c = (c + TK - 1) / TK * TK;
+  s = (J + c - 1) / c;
+  *splits = static_cast<int>(s);
+  *chunk = c;
+}
+
+}  // namespace
+
+size_t normal_eq_tc_workspace(int64_t J, int L, int64_t I, int* splits) {
+  int64_t chunk;
+  plan_tc(J, L, I, splits, &chunk);
+  return static_cast<size_t>(*splits) * L * (L + I) * sizeof(float);
+}
+
+cudaError_t launch_normal_eq_tc(const float* A, const float* Y, int64_t J, int L, int64_t I,
+                                float* partial, int splits, unsigned* err, cudaStream_t st) {
+  int s;
+  int64_t chunk;
+  plan_tc(J, L, I, &s, &chunk);
+  if (s != splits) return cudaErrorInvalidValue;
+  dim3 grid(static_cast<unsigned>((L + I + TN - 1) / TN), (L + TM - 1) / TM, s);
+  const size_t dyn = STAGES * STAGE_BYTES + 1024;
+  k_normal_eq_tc<<<grid, NT, dyn, st>>>(A, Y, J, L, I, chunk, partial, err);
+  return cudaGetLastError();
+}
+
+cudaError_t normal_eq_tc_attributes() {
+  return cudaFuncSetAttribute(k_normal_eq_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              STAGES * STAGE_BYTES + 1024);
+}
+
+}  // namespace trk

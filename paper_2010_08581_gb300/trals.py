@@ -94,7 +94,7 @@ class Context:
         h = c_vp()
         st = lib.tr_create(ctypes.byref(h), int(device), int(hbm_budget_bytes))
         if st != TR_OK:
-            raise TrError(st, "tr_create failed")
+            raise TrError(st, "tr_create failed: " + (lib.tr_last_error(None) or b"").decode())
         self.handle = h
         self.device = device
 
