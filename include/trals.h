@@ -70,7 +70,7 @@ tr_status tr_create(tr_ctx** ctx, int device, size_t hbm_budget_bytes);
 void tr_destroy(tr_ctx* ctx);
 
 /* Text of the last error reported by a call on this context ("" if none); with ctx NULL,
- * the reason of the last failed tr_create. */
+ * the reason of the last failed tr_create or tr_solve_noalloc. */
 const char* tr_last_error(const tr_ctx* ctx);
 
 /* Wait for `stream`, then return and clear the device-side error record of the context
@@ -162,6 +162,36 @@ tr_status tr_rel_error(tr_ctx* ctx, const void* X, tr_dtype X_dtype, int N,
  * k in [k_begin, N). Used by tr_als_sampled when init_cores is NULL. */
 tr_status tr_init_cores(tr_ctx* ctx, int N, const int64_t* dims, const int* ranks,
                         uint64_t seed, int k_begin, double* const* cores, tr_stream stream);
+
+/* Least-squares step without any device allocation (the paper has no counterpart; this
+ * is a deployment variant of tr_solve).
+ *
+ * Some callers cannot call cudaMalloc: code that issues work while a CUDA graph is being
+ * captured in global mode (allocation is not allowed there), latency-critical serving
+ * loops where cudaMalloc/cudaFree would synchronise the device, and hosts that have
+ * partitioned all device memory up front. tr_solve_noalloc computes exactly what
+ * tr_solve computes (same kernels, same arguments, same results) but takes its scratch
+ * from one fixed 16 MiB array that the library keeps in device memory; it calls no
+ * cudaMalloc, cudaFree or allocating library routine, and needs no context.
+ *
+ * - Every GPU on which the library is loaded holds the 16 MiB array until the process
+ *   exits.
+ * - A problem whose scratch (the split partials of the L x (L+I) contraction plus the
+ *   L x I right-hand sides and the factor) exceeds 16 MiB is rejected with
+ *   TR_ERR_INVALID_ARG and a message (tr_last_error(NULL)); nothing is launched. For
+ *   J = 4000, L = 100, I = 500 about 7 MiB are used.
+ * - All calls share the array and it keeps the previous call's contents, so calls that
+ *   overlap on the GPU (on different streams, or on several host threads) race and give
+ *   wrong results: serialise them on one stream.
+ * - The first call on each device (with that device current) resolves the array's
+ *   device address and sets kernel attributes; make that first call before any stream
+ *   capture begins.
+ * - info (device int32, may be NULL) receives 0, or column+1 of the first non-positive
+ *   pivot, in which case core_out is left unchanged.
+ * Arguments otherwise as tr_solve; the current device must be the one holding the data. */
+tr_status tr_solve_noalloc(const void* A, const void* Y, tr_dtype dtype, int64_t J, int Rl,
+                           int Rr, int64_t I, tr_precision prec, double* core_out,
+                           int32_t* info, tr_stream stream);
 
 /* Per-kernel timing. Between tr_profile_begin and tr_profile_end every kernel the context
  * launches is bracketed by a pair of CUDA events recorded on the launching stream.

@@ -547,7 +547,7 @@ tr_status fold_graph_marks(tr_ctx* ctx) {
 // ======================================================================================
 extern "C" {
 
-static std::string g_create_error;  // message of the last failed tr_create
+static std::string g_create_error;  // message of the last failed tr_create / tr_solve_noalloc
 
 tr_status tr_create(tr_ctx** out, int device, size_t hbm_budget_bytes) {
   if (!out) return TR_ERR_INVALID_ARG;
@@ -901,3 +901,7 @@ tr_status tr_profile_entry(const tr_ctx* ctx, int i, const char** name, double* 
 }
 
 }  // extern "C"
+
+namespace trk {
+void set_global_error(const std::string& msg) { g_create_error = msg; }
+}  // namespace trk

@@ -55,6 +55,8 @@ SIGNATURES = {
     "tr_rel_error": (c_int, [c_vp, c_vp, c_int, c_int, P64, PI, PP, ctypes.POINTER(c_dbl),
                              c_vp]),
     "tr_init_cores": (c_int, [c_vp, c_int, P64, PI, c_u64, c_int, PP, c_vp]),
+    "tr_solve_noalloc": (c_int, [c_vp, c_vp, c_int, c_i64, c_int, c_int, c_i64, c_int, c_vp,
+                                 c_vp, c_vp]),
     "tr_profile_begin": (c_int, [c_vp]),
     "tr_profile_end": (c_int, [c_vp, c_vp]),
     "tr_profile_count": (c_int, [c_vp]),
@@ -197,6 +199,18 @@ def tr_solve(ctx: Context, A: torch.Tensor, Y: torch.Tensor, Rl: int, Rr: int, p
     I = Y.shape[1]
     ctx.check(load().tr_solve(ctx.handle, _ptr(A), _ptr(Y), _dt(A), J, Rl, Rr, I, prec,
                               _ptr(core_out), _stream(stream)))
+
+
+def tr_solve_noalloc(A: torch.Tensor, Y: torch.Tensor, Rl: int, Rr: int, prec: int,
+                     core_out: torch.Tensor, info: Optional[torch.Tensor] = None, stream=None):
+    """tr_solve without any device allocation (fixed 16 MiB library scratch; no context)."""
+    lib = load()
+    J, L = A.shape
+    I = Y.shape[1]
+    st = lib.tr_solve_noalloc(_ptr(A), _ptr(Y), _dt(A), J, Rl, Rr, I, prec, _ptr(core_out),
+                              _ptr(info), _stream(stream))
+    if st != TR_OK:
+        raise TrError(st, (lib.tr_last_error(None) or b"").decode())
 
 
 def tr_init_cores(ctx: Context, dims, ranks, seed: int, k_begin: int, cores, stream=None):
