@@ -30,6 +30,8 @@ struct tr_ctx {
   std::vector<std::pair<std::string, std::pair<double, int64_t>>> prof_snapshot;
   // CUDA graph of the last tr_als_sampled signature
   cudaStream_t cap = nullptr;       // internal stream, used only for capture
+  cudaStream_t side = nullptr;      // second branch of each core update
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   uint64_t* d_seed = nullptr;       // Philox key read by the captured kernels
   bool capturing = false;
   struct Mark { const char* name; cudaEvent_t a, b; };
@@ -189,6 +191,7 @@ void drop_graph(tr_ctx* ctx) {
 // ------------------------------------------------------------------------------------
 struct LevPass {  // one Cholesky-QR pass over an m x n row-major matrix (n = Gram size)
   double* partial; double* G; double* Lrow; double* Lcol; double* invdiag; int* keep; int* info;
+  double* img;     // padded FP64 image of the factor for the row solves
   int splits;
 };
 
@@ -203,6 +206,7 @@ LevPass carve_pass(Carver& c, int64_t rows, int cols, bool trans) {
   p.invdiag = c.take<double>(n);
   p.keep = c.take<int>(n);
   p.info = c.take<int>(1);
+  p.img = reinterpret_cast<double*>(c.take<char>(trsm_image_bytes(n, false)));
   return p;
 }
 
@@ -213,7 +217,8 @@ tr_status run_pass(tr_ctx* ctx, const LevPass& p, const double* A, int64_t rows,
   TR_LAUNCH("reduce_gram", launch_reduce(p.partial, false, p.splits, static_cast<int64_t>(n) * n,
                                          n, n, n, n, p.G, n, nullptr, 0, st));
   TR_LAUNCH("cholesky_leverage", launch_cholesky(p.G, n, 1, tol_scale, p.Lrow, p.Lcol,
-                                                   p.invdiag, p.keep, p.info, ctx->d_err, st));
+                                                   p.invdiag, p.keep, p.info, ctx->d_err, st,
+                                                   p.img));
   return TR_OK;
 }
 
@@ -235,9 +240,10 @@ size_t leverage_bytes(int64_t I, int L) {
   return leverage_plan(c, I, L, &a, &b, &e);
 }
 
-tr_status leverage_run(tr_ctx* ctx, char* ws, const double* core, int64_t I, int Rl, int Rr,
-                       double* p, double* cdf, cudaStream_t st) {
-  const int L = Rl * Rr;
+// Leverage scores of the rows of the I x L row-major matrix `mat` (a core's G_(2), or any
+// matrix with the same column space) into ell.
+tr_status leverage_ell(tr_ctx* ctx, char* ws, const double* mat, int64_t I, int L, double** ell_out,
+                       cudaStream_t st) {
   Carver c(ws);
   LevPass p1{}, p2{};
   double* ell;
@@ -245,17 +251,25 @@ tr_status leverage_run(tr_ctx* ctx, char* ws, const double* core, int64_t I, int
   const double eps = 2.220446049250313e-16;
   const double tol = static_cast<double>(I > L ? I : L) * eps;
   if (I >= L) {
-    TR_TRY(run_pass(ctx, p1, core, I, L, L, false, tol, st));
+    TR_TRY(run_pass(ctx, p1, mat, I, L, L, false, tol, st));
     TR_LAUNCH("leverage_rows", launch_trsm(0, false, L, p1.Lrow, p1.Lcol, p1.invdiag, nullptr, I,
-                                           core, L, nullptr, 1, 1, nullptr, ell, st));
+                                           mat, L, nullptr, 1, 1, nullptr, ell, st, p1.img));
   } else {
     // Wide G_(2): the range of A is that of C with A A^T = C C^T; ell(A) = ell(C).
     const int n = static_cast<int>(I);
-    TR_TRY(run_pass(ctx, p1, core, I, L, L, true, tol, st));
+    TR_TRY(run_pass(ctx, p1, mat, I, L, L, true, tol, st));
     TR_TRY(run_pass(ctx, p2, p1.Lrow, I, n, n, false, tol, st));
     TR_LAUNCH("leverage_rows", launch_trsm(0, false, n, p2.Lrow, p2.Lcol, p2.invdiag, nullptr, I,
-                                           p1.Lrow, n, nullptr, 1, 1, nullptr, ell, st));
+                                           p1.Lrow, n, nullptr, 1, 1, nullptr, ell, st, p2.img));
   }
+  *ell_out = ell;
+  return TR_OK;
+}
+
+tr_status leverage_run(tr_ctx* ctx, char* ws, const double* core, int64_t I, int Rl, int Rr,
+                       double* p, double* cdf, cudaStream_t st) {
+  double* ell;
+  TR_TRY(leverage_ell(ctx, ws, core, I, Rl * Rr, &ell, st));
   TR_LAUNCH("cdf", launch_cdf(ell, I, p, cdf, ctx->d_err, st));
   return TR_OK;
 }
@@ -265,7 +279,7 @@ tr_status leverage_run(tr_ctx* ctx, char* ws, const double* core, int64_t I, int
 // ------------------------------------------------------------------------------------
 struct SolvePlan {
   void* partial; double* M; double* BT; double* Lrow; double* Lcol; double* invdiag;
-  int* keep; int* info; int splits;
+  int* keep; int* info; void* limg; float* mimg; int splits;
 };
 
 bool use_tensor_cores(bool f64) {
@@ -285,6 +299,8 @@ size_t solve_plan(Carver& c, int64_t J, int L, int64_t I, bool f64, SolvePlan* s
   s->invdiag = c.take<double>(L);
   s->keep = c.take<int>(L);
   s->info = c.take<int>(1);
+  s->limg = c.take<char>(trsm_image_bytes(L, !f64));
+  s->mimg = f64 ? nullptr : reinterpret_cast<float*>(c.take<char>(trsm_image_bytes(L, true)));
   return c.off;
 }
 
@@ -294,12 +310,8 @@ size_t solve_bytes(int64_t J, int L, int64_t I, bool f64) {
   return solve_plan(c, J, L, I, f64, &s);
 }
 
-tr_status solve_run(tr_ctx* ctx, char* ws, const void* A, const void* Y, bool f64, int64_t J,
-                    int Rl, int Rr, int64_t I, bool refine, double* core_out, cudaStream_t st) {
-  const int L = Rl * Rr;
-  Carver c(ws);
-  SolvePlan s;
-  solve_plan(c, J, L, I, f64, &s);
+tr_status solve_contract(tr_ctx* ctx, const SolvePlan& s, const void* A, const void* Y,
+                         bool f64, int64_t J, int L, int64_t I, cudaStream_t st) {
   const int64_t ld = L + I;
   if (use_tensor_cores(f64)) {
     TR_LAUNCH("normal_eq_tc", launch_normal_eq_tc(static_cast<const float*>(A),
@@ -311,12 +323,59 @@ tr_status solve_run(tr_ctx* ctx, char* ws, const void* A, const void* Y, bool f6
   }
   TR_LAUNCH("reduce_MB", launch_reduce(s.partial, !f64, s.splits, L * ld, ld, L, ld, L, s.M, L,
                                        s.BT, L, st));
+  return TR_OK;
+}
+
+tr_status solve_factor(tr_ctx* ctx, const SolvePlan& s, bool f64, int Rl, int Rr, int64_t I,
+                       bool refine, double* core_out, cudaStream_t st) {
+  const int L = Rl * Rr;
   const double eps = 2.220446049250313e-16;
-  TR_LAUNCH("cholesky_solve", launch_cholesky(s.M, L, 0, static_cast<double>(L) * eps, s.Lrow,
-                                               s.Lcol, s.invdiag, s.keep, s.info, ctx->d_err,
-                                               st));
+  TR_LAUNCH("cholesky_solve",
+            launch_cholesky(s.M, L, 0, static_cast<double>(L) * eps, s.Lrow, s.Lcol, s.invdiag,
+                            s.keep, s.info, ctx->d_err, st,
+                            f64 ? static_cast<double*>(s.limg) : nullptr,
+                            f64 ? nullptr : static_cast<float*>(s.limg), s.mimg));
   TR_LAUNCH("solve_rhs", launch_trsm(refine ? 2 : 1, refine, L, s.Lrow, s.Lcol, s.invdiag, s.info,
-                                      I, s.BT, L, s.M, Rl, Rr, core_out, nullptr, st));
+                                      I, s.BT, L, s.M, Rl, Rr, core_out, nullptr, st, s.limg,
+                                      s.mimg));
+  return TR_OK;
+}
+
+tr_status solve_run(tr_ctx* ctx, char* ws, const void* A, const void* Y, bool f64, int64_t J,
+                    int Rl, int Rr, int64_t I, bool refine, double* core_out, cudaStream_t st) {
+  const int L = Rl * Rr;
+  Carver c(ws);
+  SolvePlan s;
+  solve_plan(c, J, L, I, f64, &s);
+  TR_TRY(solve_contract(ctx, s, A, Y, f64, J, L, I, st));
+  return solve_factor(ctx, s, f64, Rl, Rr, I, refine, core_out, st);
+}
+
+// One core update's LS step and distribution update as two concurrent branches. Since
+// M = A~^T A~ is nonsingular whenever the solve succeeds, the new core's G_(2) = Z^T =
+// B^T M^-1 has the column space of B^T, so p^(n) is computed from B^T on the side stream
+// while the main stream factors M and solves. The CDF step joins both and keeps the old
+// distribution if the solve reported a singular system (the core is then unchanged).
+tr_status update_run(tr_ctx* ctx, char* ws, size_t solve_ws, const void* A, const void* Y,
+                     bool f64, int64_t J, int Rl, int Rr, int64_t I, double* core_out, double* p,
+                     double* cdf, cudaStream_t st, cudaStream_t side) {
+  const int L = Rl * Rr;
+  Carver c(ws);
+  SolvePlan s;
+  solve_plan(c, J, L, I, f64, &s);
+  TR_TRY(solve_contract(ctx, s, A, Y, f64, J, L, I, st));
+  TR_CUDA(cudaEventRecord(ctx->ev_fork, st));
+  TR_CUDA(cudaStreamWaitEvent(side, ctx->ev_fork, 0));
+  double* ell;
+  TR_TRY(leverage_ell(ctx, ws + solve_ws, s.BT, I, L, &ell, side));
+  TR_TRY(solve_factor(ctx, s, f64, Rl, Rr, I, !f64, core_out, st));
+  TR_CUDA(cudaEventRecord(ctx->ev_join, side));
+  TR_CUDA(cudaStreamWaitEvent(st, ctx->ev_join, 0));
+  {
+    cudaStream_t st_cdf = st;
+    Prof prof_(ctx, "cdf", st_cdf);
+    TR_CUDA(launch_cdf(ell, I, p, cdf, ctx->d_err, st_cdf, s.info));
+  }
   return TR_OK;
 }
 
@@ -368,6 +427,7 @@ struct AlsPlan {
   int sweeps; tr_precision prec; const double* const* init; double* const* cores;
   std::vector<double*> p, cdf;
   int32_t* idx; double* w; void* A; void* Y; char* ws;
+  size_t solve_ws;   // bytes of the stage region used by the LS step; leverage follows it
 };
 
 tr_status als_plan(tr_ctx* ctx, AlsPlan& P) {
@@ -394,13 +454,18 @@ tr_status als_plan(tr_ctx* ctx, AlsPlan& P) {
   Carver dry(nullptr);
   carve(dry, &pb, &cb);
   const size_t persist = (dry.off + 255) & ~size_t(255);
-  size_t stage = 0;
+  size_t stage = 0, solve_max = 0;
   for (int k = 0; k < N; ++k) {
     const int L = rl_of(P.ranks, N, k) * P.ranks[k];
-    const size_t a = leverage_bytes(P.dims[k], L), b = solve_bytes(P.J, L, P.dims[k], f64);
-    stage = a > stage ? a : stage;
-    stage = b > stage ? b : stage;
+    const size_t b = (solve_bytes(P.J, L, P.dims[k], f64) + 255) & ~size_t(255);
+    solve_max = b > solve_max ? b : solve_max;
   }
+  for (int k = 0; k < N; ++k) {
+    const int L = rl_of(P.ranks, N, k) * P.ranks[k];
+    const size_t a = leverage_bytes(P.dims[k], L);
+    stage = solve_max + a > stage ? solve_max + a : stage;
+  }
+  P.solve_ws = solve_max;
   TR_TRY(ensure_ws(ctx, persist + stage));
   Carver c(ctx->arena);
   carve(c, &pb, &cb);
@@ -413,7 +478,7 @@ tr_status als_plan(tr_ctx* ctx, AlsPlan& P) {
 }
 
 tr_status als_issue(tr_ctx* ctx, const AlsPlan& P, uint64_t seed, const uint64_t* seed_dev,
-                    cudaStream_t st) {
+                    cudaStream_t st, cudaStream_t side) {
   const int N = P.N;
   const bool f64 = P.prec == TR_PREC_FP64;
   const int64_t* dims = P.dims;
@@ -458,8 +523,8 @@ tr_status als_issue(tr_ctx* ctx, const AlsPlan& P, uint64_t seed, const uint64_t
       TR_LAUNCH("subchain", launch_subchain(ca, P.idx, P.w, P.J, P.A, f64, ctx->d_err, st));
       TR_LAUNCH("gather", launch_gather(ga, P.X, x64, P.idx, P.w, P.J, P.Y, f64, ctx->d_err, st));
       const int Rl = rl_of(ranks, N, n), Rr = ranks[n];
-      TR_TRY(solve_run(ctx, P.ws, P.A, P.Y, f64, P.J, Rl, Rr, dims[n], !f64, P.cores[n], st));
-      TR_TRY(leverage_run(ctx, P.ws, P.cores[n], dims[n], Rl, Rr, P.p[n], P.cdf[n], st));
+      TR_TRY(update_run(ctx, P.ws, P.solve_ws, P.A, P.Y, f64, P.J, Rl, Rr, dims[n], P.cores[n],
+                        P.p[n], P.cdf[n], st, side));
     }
   }
   return TR_OK;
@@ -494,14 +559,14 @@ bool graphs_enabled() {
 // One whole call: plan, then either issue directly or (re)capture and launch the graph.
 tr_status als_run(tr_ctx* ctx, AlsPlan& P, uint64_t seed, cudaStream_t st) {
   TR_TRY(als_plan(ctx, P));
-  if (!graphs_enabled()) return als_issue(ctx, P, seed, nullptr, st);
+  if (!graphs_enabled()) return als_issue(ctx, P, seed, nullptr, st, ctx->side);
   std::vector<uint64_t> key = als_key(ctx, P);
   if (!ctx->gexec || key != ctx->gkey || ctx->gprof != ctx->prof) {
     drop_graph(ctx);
     cudaGraph_t g = nullptr;
     ctx->capturing = true;
     TR_CUDA(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
-    tr_status s = als_issue(ctx, P, 0, ctx->d_seed, ctx->cap);
+    tr_status s = als_issue(ctx, P, 0, ctx->d_seed, ctx->cap, ctx->side);
     cudaError_t e = cudaStreamEndCapture(ctx->cap, &g);
     ctx->capturing = false;
     if (s != TR_OK) {
@@ -572,6 +637,12 @@ tr_status tr_create(tr_ctx** out, int device, size_t hbm_budget_bytes) {
   if (e == cudaSuccess) {
     step = "cudaStreamCreate";
     e = cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking);
+  }
+  if (e == cudaSuccess) {
+    step = "cudaEventCreate";
+    e = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming);
   }
   if (e == cudaSuccess) { step = "cudaFuncSetAttribute"; e = init_kernel_attributes(&which); }
   if (e != cudaSuccess) {
@@ -579,6 +650,9 @@ tr_status tr_create(tr_ctx** out, int device, size_t hbm_budget_bytes) {
     cudaGetLastError();
     if (ctx->d_err) cudaFree(ctx->d_err);
     if (ctx->cap) cudaStreamDestroy(ctx->cap);
+    if (ctx->side) cudaStreamDestroy(ctx->side);
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
     delete ctx;
     return TR_ERR_CUDA;
   }
@@ -595,6 +669,9 @@ void tr_destroy(tr_ctx* ctx) {
   if (ctx->host_stage) cudaFree(ctx->host_stage);
   drop_graph(ctx);
   if (ctx->cap) cudaStreamDestroy(ctx->cap);
+  if (ctx->side) cudaStreamDestroy(ctx->side);
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   if (ctx->d_err) cudaFree(ctx->d_err);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   delete ctx;

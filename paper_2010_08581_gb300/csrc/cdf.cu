@@ -35,7 +35,8 @@ __device__ __forceinline__ double block_exclusive_scan(double v, double* warp_to
 
 __global__ void __launch_bounds__(PNT) k_cdf(const double* __restrict__ ell, int64_t I,
                                              double* __restrict__ p, double* __restrict__ cdf,
-                                             unsigned* err) {
+                                             unsigned* err, const int* __restrict__ skip) {
+  if (skip && *skip) return;  // the core was not updated: keep its distribution
   __shared__ double warp_tot[PNT / 32];
   __shared__ double s_total;
   const int t = threadIdx.x;
@@ -94,8 +95,8 @@ __global__ void k_init_normal(double* __restrict__ out, int64_t count, uint32_t 
 }  // namespace
 
 cudaError_t launch_cdf(const double* ell, int64_t I, double* p, double* cdf, unsigned* err,
-                       cudaStream_t st) {
-  k_cdf<<<1, PNT, 0, st>>>(ell, I, p, cdf, err);
+                       cudaStream_t st, const int* skip) {
+  k_cdf<<<1, PNT, 0, st>>>(ell, I, p, cdf, err, skip);
   return cudaGetLastError();
 }
 

@@ -109,10 +109,13 @@ cudaError_t launch_reduce(const void* partial, bool partial_f32, int splits, int
 //   mode 0 (solve): fatal -> *info = column + 1 and the singular error bit;
 //   mode 1 (leverage): the column is dropped (keep = 0) and the factorisation continues.
 // Outputs: Lrow (n x n row-major lower factor), Lcol (its transpose), invdiag[n] (1/L_cc,
-// 0 for dropped columns), keep[n], *info (0 = success).
+// 0 for dropped columns), keep[n], *info (0 = success); optionally the padded images read
+// by launch_trsm: img64/img32[c*(n+1) + r] = L[r][c] and gimg32[c*(n+1) + r] = G[r][c]
+// (buffers of trsm_image_bytes(n, ...) bytes).
 cudaError_t launch_cholesky(const double* G, int n, int mode, double tol_scale, double* Lrow,
                             double* Lcol, double* invdiag, int* keep, int* info,
-                            unsigned* err, cudaStream_t st);
+                            unsigned* err, cudaStream_t st, double* img64 = nullptr,
+                            float* img32 = nullptr, float* gimg32 = nullptr);
 
 // Triangular solves with the factor of launch_cholesky for nvec vectors (row v of rhs,
 // leading dimension ld, length n):
@@ -121,15 +124,19 @@ cudaError_t launch_cholesky(const double* G, int n, int mode, double tol_scale, 
 //   mode 2: as mode 1 plus one refinement step z += M^-1 (rhs_v - M z), M (n x n FP64).
 // f32 selects FP32 arithmetic (factor and M rounded to FP32), else FP64. Nothing is done
 // when *info != 0 (info may be NULL).
+// Limg: padded factor image in the arithmetic type (FP32 when f32, else FP64), Mimg: FP32
+// image of M (mode 2, f32); both optional (NULL: converted from Lcol / M instead).
 cudaError_t launch_trsm(int mode, bool f32, int n, const double* Lrow, const double* Lcol,
                         const double* invdiag, const int* info, int64_t nvec, const double* rhs,
                         int64_t ld, const double* M, int Rl, int Rr, double* core_out,
-                        double* ell, cudaStream_t st);
+                        double* ell, cudaStream_t st, const void* Limg = nullptr,
+                        const float* Mimg = nullptr);
+size_t trsm_image_bytes(int n, bool f32);
 
 // p = ell / sum(ell), cdf = inclusive prefix sum (fixed order), one CTA. All-zero ell ->
-// uniform p and the singular bit.
+// uniform p and the singular bit. Nothing is written when skip && *skip != 0.
 cudaError_t launch_cdf(const double* ell, int64_t I, double* p, double* cdf, unsigned* err,
-                       cudaStream_t st);
+                       cudaStream_t st, const int* skip = nullptr);
 
 // Core initialisation N(0,1) by Philox + Box-Muller.
 cudaError_t launch_init_normal(double* out, int64_t count, uint64_t seed, uint32_t stream_id,

@@ -155,28 +155,39 @@ __global__ void __launch_bounds__(NT, 1) k_normal_eq_tc(const float* __restrict_
   const int k_first = tid >> 7;
   const int am = m0 + row;                    // feature index of the A operand
   const int64_t bn = n0 + row;                // output column of the B operand
-  int issued = 0;                             // commits issued (thread 0)
+  // Raw FP32 values of one chunk for this thread: samples k_first + 2r, r < TK/2.
+  auto load_chunk = [&](int c, float (&ra)[TK / 2], float (&rb)[TK / 2]) {
+    const int64_t jb = j0 + static_cast<int64_t>(c) * TK;
+#pragma unroll
+    for (int r = 0; r < TK / 2; ++r) {
+      const int64_t j = jb + k_first + 2 * r;
+      float a = 0.f, b = 0.f;
+      if (j < j1) {
+        if (am < L) a = __ldg(A + j * L + am);
+        if (bn < L) b = __ldg(A + j * L + bn);
+        else if (bn < ldc) b = __ldg(Y + j * I + (bn - L));
+      }
+      ra[r] = a;
+      rb[r] = b;
+    }
+  };
+  float ca[TK / 2], cb[TK / 2], na[TK / 2], nb[TK / 2];
+  if (nchunks > 0) load_chunk(0, ca, cb);
 
   for (int c = 0; c < nchunks; ++c) {
     const int s = c % STAGES;
     unsigned char* st = base + s * STAGE_BYTES;
+    if (c + 1 < nchunks) load_chunk(c + 1, na, nb);   // in flight while this chunk is stored
     if (c >= STAGES) {   // wait until the MMAs that read this stage have finished
       const bool ok = mbar_wait(smem_u32(&mbar[s]), ((c / STAGES) - 1) & 1);
       if (!ok) atomicExch(&s_abort, 1);
     }
     __syncthreads();
     if (s_abort) break;
-    const int64_t jb = j0 + static_cast<int64_t>(c) * TK;
-#pragma unroll 4
+#pragma unroll
     for (int r = 0; r < TK / 2; ++r) {
       const int k = k_first + 2 * r;
-      const int64_t j = jb + k;
-      float a = 0.f, b = 0.f;
-      if (j < j1) {
-        if (am < L) a = A[j * L + am];
-        if (bn < L) b = A[j * L + bn];
-        else if (bn < ldc) b = Y[j * I + (bn - L)];
-      }
+      const float a = ca[r], b = cb[r];
       const float ah = tf32_rna(a), bh = tf32_rna(b);
       const float al = tf32_rna(a - ah), bl = tf32_rna(b - bh);
       const uint32_t oa = sw128_offset(row, k);
@@ -200,8 +211,9 @@ __global__ void __launch_bounds__(NT, 1) k_normal_eq_tc(const float* __restrict_
         mma_tf32(tmem_d, make_desc(a_lo + koff), make_desc(b_hi + koff), 1u);
       }
       mma_commit(smem_u32(&mbar[s]));
-      ++issued;
     }
+#pragma unroll
+    for (int r = 0; r < TK / 2; ++r) { ca[r] = na[r]; cb[r] = nb[r]; }
   }
   __syncthreads();
   const int aborted = s_abort;
@@ -240,7 +252,6 @@ __global__ void __launch_bounds__(NT, 1) k_normal_eq_tc(const float* __restrict_
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
                  :: "r"(tmem_d), "r"(TMEM_COLS) : "memory");
-  (void)issued;
 }
 
 void plan_tc(int64_t J, int L, int64_t I, int* splits, int64_t* chunk) {

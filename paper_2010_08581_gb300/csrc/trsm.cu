@@ -4,49 +4,52 @@
 //   mode 1 (LS solve, row a6):      z_v = L^-T L^-1 b_v, written into the new core;
 //   mode 2 (LS solve + one refinement step, row a6):
 //           z = L^-T L^-1 b;  r = b - M z;  z += L^-T L^-1 r.
-// One warp owns NB vectors; lane l holds rows l, l+32, ... of each in registers, so a
+// One warp owns NB vectors; lane l holds rows l, l+32, ... (QN registers per vector), so a
 // substitution step is one shuffle broadcast plus independent FMAs. The factor (and M) are
-// staged in shared memory in the compute type T with a padded row stride when they fit.
+// staged in shared memory with a padded row stride (n+1): from the padded images written
+// by the Cholesky kernel (cp.async, 16 bytes per request) when given, else converted from
+// the FP64 column-major factor.
 #include "common.cuh"
 
 namespace trk {
 namespace {
 
-constexpr int QMAX = kMaxL / 32;  // 8 register rows per lane
-constexpr int TW = 4;             // warps per CTA
+constexpr int TW = 4;   // warps per CTA
 
-template <typename T>
+template <typename T, bool SMEM>
 struct Factor {
-  const T* s;            // shared: s[c*(n+1) + r] = L[r][c]   (may be null)
+  const T* s;            // shared: s[c*(n+1) + r] = L[r][c]
   const double* Lcol;    // global: Lcol[c*n + r] = L[r][c]
   const double* Lrow;    // global: Lrow[c*n + r] = L[c][r]
   int n;
   __device__ __forceinline__ T col(int c, int r) const {   // L[r][c]
-    return s ? s[c * (n + 1) + r] : static_cast<T>(Lcol[c * n + r]);
+    if constexpr (SMEM) return s[c * (n + 1) + r];
+    else return static_cast<T>(Lcol[c * n + r]);
   }
   __device__ __forceinline__ T row(int c, int r) const {   // L[c][r]
-    return s ? s[r * (n + 1) + c] : static_cast<T>(Lrow[c * n + r]);
+    if constexpr (SMEM) return s[r * (n + 1) + c];
+    else return static_cast<T>(Lrow[c * n + r]);
   }
 };
 
-template <typename T, int NB>
-__device__ __forceinline__ T pick(const T (&x)[QMAX][NB], int q, int v) {
+template <typename T, int QN, int NB>
+__device__ __forceinline__ T pick(const T (&x)[QN][NB], int q, int v) {
   T s = x[0][v];
 #pragma unroll
-  for (int u = 1; u < QMAX; ++u) s = (u == q) ? x[u][v] : s;
+  for (int u = 1; u < QN; ++u) s = (u == q) ? x[u][v] : s;
   return s;
 }
 
-template <typename T, int NB>
-__device__ __forceinline__ void put(T (&x)[QMAX][NB], int q, int v, T val) {
+template <typename T, int QN, int NB>
+__device__ __forceinline__ void put(T (&x)[QN][NB], int q, int v, T val) {
 #pragma unroll
-  for (int u = 0; u < QMAX; ++u)
+  for (int u = 0; u < QN; ++u)
     if (u == q) x[u][v] = val;
 }
 
 // x <- L^-1 x
-template <typename T, int NB>
-__device__ __forceinline__ void forward(T (&x)[QMAX][NB], const Factor<T>& F, const T* inv,
+template <typename T, int QN, int NB, bool SMEM>
+__device__ __forceinline__ void forward(T (&x)[QN][NB], const Factor<T, SMEM>& F, const T* inv,
                                         int lane) {
   const int n = F.n;
   for (int c = 0; c < n; ++c) {
@@ -59,7 +62,7 @@ __device__ __forceinline__ void forward(T (&x)[QMAX][NB], const Factor<T>& F, co
       if (lane == lc) put(x, qc, v, xc[v]);
     }
 #pragma unroll
-    for (int q = 0; q < QMAX; ++q) {
+    for (int q = 0; q < QN; ++q) {
       const int r = lane + 32 * q;
       if (q >= qc && r > c && r < n) {
         const T l = F.col(c, r);
@@ -71,8 +74,8 @@ __device__ __forceinline__ void forward(T (&x)[QMAX][NB], const Factor<T>& F, co
 }
 
 // x <- L^-T x
-template <typename T, int NB>
-__device__ __forceinline__ void backward(T (&x)[QMAX][NB], const Factor<T>& F, const T* inv,
+template <typename T, int QN, int NB, bool SMEM>
+__device__ __forceinline__ void backward(T (&x)[QN][NB], const Factor<T, SMEM>& F, const T* inv,
                                          int lane) {
   const int n = F.n;
   for (int c = n - 1; c >= 0; --c) {
@@ -85,7 +88,7 @@ __device__ __forceinline__ void backward(T (&x)[QMAX][NB], const Factor<T>& F, c
       if (lane == lc) put(x, qc, v, zc[v]);
     }
 #pragma unroll
-    for (int q = 0; q < QMAX; ++q) {
+    for (int q = 0; q < QN; ++q) {
       const int r = lane + 32 * q;
       if (q <= qc && r < c) {
         const T l = F.row(c, r);
@@ -96,36 +99,59 @@ __device__ __forceinline__ void backward(T (&x)[QMAX][NB], const Factor<T>& F, c
   }
 }
 
-template <typename T, int NB>
+// Copy `bytes` (multiple of 16) from global to shared memory with cp.async, all threads.
+__device__ __forceinline__ void stage_async(void* dst, const void* src, int bytes) {
+  const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+  const char* s = static_cast<const char*>(src);
+  for (int o = threadIdx.x * 16; o < bytes; o += blockDim.x * 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(d + o), "l"(s + o) : "memory");
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
+template <typename T, int QN, int NB, bool SMEM>
 __global__ void __launch_bounds__(TW * 32) k_trsm(int n, const double* __restrict__ Lrow,
                                                   const double* __restrict__ Lcol,
                                                   const double* __restrict__ invdiag,
                                                   const int* __restrict__ info, int64_t nvec,
                                                   const double* __restrict__ rhs, int64_t ld,
                                                   int mode, const double* __restrict__ M,
-                                                  int Rl, int Rr, double* __restrict__ core_out,
-                                                  double* __restrict__ ell, int use_smem) {
+                                                  const T* __restrict__ Limg,
+                                                  const float* __restrict__ Mimg, int Rl, int Rr,
+                                                  double* __restrict__ core_out,
+                                                  double* __restrict__ ell) {
   extern __shared__ __align__(16) unsigned char trsm_smem[];
   if (info && *info) return;
-  T* inv = reinterpret_cast<T*>(trsm_smem);                       // n (padded to kMaxL)
-  T* Ls = inv + kMaxL;                                            // n*(n+1) if staged
-  T* Ms = Ls + (use_smem ? n * (n + 1) : 0);                      // n*(n+1) if staged, mode 2
+  const int np = n + 1;
+  const int img_elems = ((n * np * static_cast<int>(sizeof(T)) + 15) / 16) * 16 /
+                        static_cast<int>(sizeof(T));
+  T* inv = reinterpret_cast<T*>(trsm_smem);                  // kMaxL entries
+  T* Ls = inv + kMaxL;                                       // n*(n+1) (padded to 16 B)
+  T* Ms = Ls + (SMEM ? img_elems : 0);                       // mode 2
   for (int c = threadIdx.x; c < n; c += blockDim.x) inv[c] = static_cast<T>(invdiag[c]);
-  if (use_smem) {
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-      const int c = e / n, r = e - (e / n) * n;
-      Ls[c * (n + 1) + r] = static_cast<T>(Lcol[e]);
-      if (mode == 2) Ms[c * (n + 1) + r] = static_cast<T>(M[e]);
+  if constexpr (SMEM) {
+    if (Limg) {
+      stage_async(Ls, Limg, img_elems * static_cast<int>(sizeof(T)));
+    } else {
+      for (int c = threadIdx.x >> 5; c < n; c += TW)
+        for (int r = threadIdx.x & 31; r < n; r += 32) Ls[c * np + r] = static_cast<T>(Lcol[c * n + r]);
+    }
+    if (mode == 2) {
+      if (Mimg && sizeof(T) == 4) {
+        stage_async(Ms, Mimg, img_elems * static_cast<int>(sizeof(T)));
+      } else {
+        for (int c = threadIdx.x >> 5; c < n; c += TW)
+          for (int r = threadIdx.x & 31; r < n; r += 32) Ms[c * np + r] = static_cast<T>(M[c * n + r]);
+      }
     }
   }
   __syncthreads();
-  Factor<T> F{use_smem ? Ls : nullptr, Lcol, Lrow, n};
+  Factor<T, SMEM> F{Ls, Lcol, Lrow, n};
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t v0 = (static_cast<int64_t>(blockIdx.x) * TW + warp) * NB;
   if (v0 >= nvec) return;
-  T x[QMAX][NB];
+  T x[QN][NB];
 #pragma unroll
-  for (int q = 0; q < QMAX; ++q) {
+  for (int q = 0; q < QN; ++q) {
     const int r = lane + 32 * q;
 #pragma unroll
     for (int v = 0; v < NB; ++v)
@@ -137,7 +163,7 @@ __global__ void __launch_bounds__(TW * 32) k_trsm(int n, const double* __restric
     for (int v = 0; v < NB; ++v) {
       T s = T(0);
 #pragma unroll
-      for (int q = 0; q < QMAX; ++q) s += x[q][v] * x[q][v];
+      for (int q = 0; q < QN; ++q) s += x[q][v] * x[q][v];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
       if (lane == 0 && v0 + v < nvec) ell[v0 + v] = static_cast<double>(s);
@@ -147,9 +173,9 @@ __global__ void __launch_bounds__(TW * 32) k_trsm(int n, const double* __restric
   backward(x, F, inv, lane);
   if (mode == 2) {
     // residual r = b - M z (M symmetric: column t of M = row t)
-    T res[QMAX][NB];
+    T res[QN][NB];
 #pragma unroll
-    for (int q = 0; q < QMAX; ++q) {
+    for (int q = 0; q < QN; ++q) {
       const int r = lane + 32 * q;
 #pragma unroll
       for (int v = 0; v < NB; ++v)
@@ -161,10 +187,12 @@ __global__ void __launch_bounds__(TW * 32) k_trsm(int n, const double* __restric
 #pragma unroll
       for (int v = 0; v < NB; ++v) zt[v] = __shfl_sync(0xffffffffu, pick(x, qt, v), lt);
 #pragma unroll
-      for (int q = 0; q < QMAX; ++q) {
+      for (int q = 0; q < QN; ++q) {
         const int r = lane + 32 * q;
         if (r < n) {
-          const T m = use_smem ? Ms[t * (n + 1) + r] : static_cast<T>(M[t * n + r]);
+          T m;
+          if constexpr (SMEM) m = Ms[t * np + r];
+          else m = static_cast<T>(M[t * n + r]);
 #pragma unroll
           for (int v = 0; v < NB; ++v) res[q][v] -= m * zt[v];
         }
@@ -173,13 +201,13 @@ __global__ void __launch_bounds__(TW * 32) k_trsm(int n, const double* __restric
     forward(res, F, inv, lane);
     backward(res, F, inv, lane);
 #pragma unroll
-    for (int q = 0; q < QMAX; ++q)
+    for (int q = 0; q < QN; ++q)
 #pragma unroll
       for (int v = 0; v < NB; ++v) x[q][v] += res[q][v];
   }
   // new core: core[i][a][b] = z[a + Rl*b]
 #pragma unroll
-  for (int q = 0; q < QMAX; ++q) {
+  for (int q = 0; q < QN; ++q) {
     const int r = lane + 32 * q;
     if (r >= n) continue;
     const int a = r % Rl, b = r / Rl;
@@ -189,19 +217,67 @@ __global__ void __launch_bounds__(TW * 32) k_trsm(int n, const double* __restric
   }
 }
 
+template <typename T>
+size_t staged_bytes(int n, int mode) {
+  const size_t img = ((static_cast<size_t>(n) * (n + 1) * sizeof(T) + 15) / 16) * 16;
+  return kMaxL * sizeof(T) + (mode == 2 ? 2 : 1) * img;
+}
+
+template <typename T, int QN, int NB>
+cudaError_t run_q(int n, const double* Lrow, const double* Lcol, const double* invdiag,
+                  const int* info, int64_t nvec, const double* rhs, int64_t ld, int mode,
+                  const double* M, const T* Limg, const float* Mimg, int Rl, int Rr,
+                  double* core_out, double* ell, cudaStream_t st) {
+  const size_t staged = staged_bytes<T>(n, mode);
+  const int64_t per_cta = static_cast<int64_t>(TW) * NB;
+  const unsigned blocks = static_cast<unsigned>((nvec + per_cta - 1) / per_cta);
+  if (staged <= 200 * 1024) {
+    k_trsm<T, QN, NB, true><<<blocks, TW * 32, staged, st>>>(
+        n, Lrow, Lcol, invdiag, info, nvec, rhs, ld, mode, M, Limg, Mimg, Rl, Rr, core_out, ell);
+  } else {
+    k_trsm<T, QN, NB, false><<<blocks, TW * 32, kMaxL * sizeof(T), st>>>(
+        n, Lrow, Lcol, invdiag, info, nvec, rhs, ld, mode, M, Limg, Mimg, Rl, Rr, core_out, ell);
+  }
+  return cudaGetLastError();
+}
+
 template <typename T, int NB>
 cudaError_t run(int n, const double* Lrow, const double* Lcol, const double* invdiag,
                 const int* info, int64_t nvec, const double* rhs, int64_t ld, int mode,
-                const double* M, int Rl, int Rr, double* core_out, double* ell, cudaStream_t st) {
-  const size_t mats = (mode == 2) ? 2 : 1;
-  const size_t staged = (kMaxL + mats * n * (n + 1)) * sizeof(T);
-  const int use_smem = staged <= 200 * 1024 ? 1 : 0;
-  const size_t dyn = use_smem ? staged : kMaxL * sizeof(T);
-  const int64_t per_cta = static_cast<int64_t>(TW) * NB;
-  const int64_t blocks = (nvec + per_cta - 1) / per_cta;
-  k_trsm<T, NB><<<static_cast<unsigned>(blocks), TW * 32, dyn, st>>>(
-      n, Lrow, Lcol, invdiag, info, nvec, rhs, ld, mode, M, Rl, Rr, core_out, ell, use_smem);
-  return cudaGetLastError();
+                const double* M, const T* Limg, const float* Mimg, int Rl, int Rr,
+                double* core_out, double* ell, cudaStream_t st) {
+  switch ((n + 31) / 32) {
+#define TRSM_CASE(q)                                                                        \
+  case q:                                                                                   \
+    return run_q<T, q, NB>(n, Lrow, Lcol, invdiag, info, nvec, rhs, ld, mode, M, Limg, Mimg, \
+                           Rl, Rr, core_out, ell, st);
+    TRSM_CASE(1) TRSM_CASE(2) TRSM_CASE(3) TRSM_CASE(4)
+    TRSM_CASE(5) TRSM_CASE(6) TRSM_CASE(7) TRSM_CASE(8)
+#undef TRSM_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename T, int QN, int NB>
+cudaError_t attr_q() {
+  cudaError_t e = cudaFuncSetAttribute(k_trsm<T, QN, NB, true>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_trsm<T, QN, NB, false>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}
+
+template <typename T, int NB>
+cudaError_t attr() {
+  cudaError_t e;
+  if ((e = attr_q<T, 1, NB>()) != cudaSuccess) return e;
+  if ((e = attr_q<T, 2, NB>()) != cudaSuccess) return e;
+  if ((e = attr_q<T, 3, NB>()) != cudaSuccess) return e;
+  if ((e = attr_q<T, 4, NB>()) != cudaSuccess) return e;
+  if ((e = attr_q<T, 5, NB>()) != cudaSuccess) return e;
+  if ((e = attr_q<T, 6, NB>()) != cudaSuccess) return e;
+  if ((e = attr_q<T, 7, NB>()) != cudaSuccess) return e;
+  return attr_q<T, 8, NB>();
 }
 
 }  // namespace
@@ -209,21 +285,23 @@ cudaError_t run(int n, const double* Lrow, const double* Lcol, const double* inv
 cudaError_t launch_trsm(int mode, bool f32, int n, const double* Lrow, const double* Lcol,
                         const double* invdiag, const int* info, int64_t nvec, const double* rhs,
                         int64_t ld, const double* M, int Rl, int Rr, double* core_out,
-                        double* ell, cudaStream_t st) {
+                        double* ell, cudaStream_t st, const void* Limg, const float* Mimg) {
   if (nvec <= 0) return cudaSuccess;
   if (f32)
-    return run<float, 2>(n, Lrow, Lcol, invdiag, info, nvec, rhs, ld, mode, M, Rl, Rr,
-                         core_out, ell, st);
-  return run<double, 1>(n, Lrow, Lcol, invdiag, info, nvec, rhs, ld, mode, M, Rl, Rr, core_out,
-                        ell, st);
+    return run<float, 2>(n, Lrow, Lcol, invdiag, info, nvec, rhs, ld, mode, M,
+                         static_cast<const float*>(Limg), Mimg, Rl, Rr, core_out, ell, st);
+  return run<double, 1>(n, Lrow, Lcol, invdiag, info, nvec, rhs, ld, mode, M,
+                        static_cast<const double*>(Limg), Mimg, Rl, Rr, core_out, ell, st);
+}
+
+size_t trsm_image_bytes(int n, bool f32) {
+  return ((static_cast<size_t>(n) * (n + 1) * (f32 ? 4 : 8) + 15) / 16) * 16;
 }
 
 cudaError_t trsm_attributes() {
-  cudaError_t e = cudaFuncSetAttribute(k_trsm<float, 2>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaError_t e = attr<float, 2>();
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_trsm<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              200 * 1024);
+  return attr<double, 1>();
 }
 
 }  // namespace trk
