@@ -47,55 +47,84 @@ __device__ __forceinline__ void put(T (&x)[QN][NB], int q, int v, T val) {
     if (u == q) x[u][v] = val;
 }
 
-// x <- L^-1 x
+// x <- L^-1 x. Rows are processed in blocks of 32 (register slot qb of every lane); inside a
+// block the pivot row's lane is a compile-time constant and the block's values live in one
+// register per vector, so one step is a shuffle, a multiply and independent FMAs.
 template <typename T, int QN, int NB, bool SMEM>
 __device__ __forceinline__ void forward(T (&x)[QN][NB], const Factor<T, SMEM>& F, const T* inv,
                                         int lane) {
   const int n = F.n;
-  for (int c = 0; c < n; ++c) {
-    const int qc = c >> 5, lc = c & 31;
-    const T ic = inv[c];
-    T xc[NB];
+  for (int qb = 0; qb < QN; ++qb) {
+    T xb[NB];
 #pragma unroll
-    for (int v = 0; v < NB; ++v) {
-      xc[v] = __shfl_sync(0xffffffffu, pick(x, qc, v), lc) * ic;
-      if (lane == lc) put(x, qc, v, xc[v]);
-    }
+    for (int v = 0; v < NB; ++v) xb[v] = pick(x, qb, v);
 #pragma unroll
-    for (int q = 0; q < QN; ++q) {
-      const int r = lane + 32 * q;
-      if (q >= qc && r > c && r < n) {
-        const T l = F.col(c, r);
+    for (int lc = 0; lc < 32; ++lc) {
+      const int c = qb * 32 + lc;
+      if (c >= n) break;
+      const T ic = inv[c];
+      T xc[NB];
 #pragma unroll
-        for (int v = 0; v < NB; ++v) x[q][v] -= l * xc[v];
+      for (int v = 0; v < NB; ++v) {
+        xc[v] = __shfl_sync(0xffffffffu, xb[v], lc) * ic;
+        if (lane == lc) xb[v] = xc[v];
+      }
+      if (lane > lc && qb * 32 + lane < n) {
+        const T l = F.col(c, qb * 32 + lane);
+#pragma unroll
+        for (int v = 0; v < NB; ++v) xb[v] -= l * xc[v];
+      }
+#pragma unroll
+      for (int q = 0; q < QN; ++q) {
+        if (q > qb) {
+          const int r = lane + 32 * q;
+          const T l = (r < n) ? F.col(c, r) : T(0);
+#pragma unroll
+          for (int v = 0; v < NB; ++v) x[q][v] -= l * xc[v];
+        }
       }
     }
+#pragma unroll
+    for (int v = 0; v < NB; ++v) put(x, qb, v, xb[v]);
   }
 }
 
-// x <- L^-T x
+// x <- L^-T x, blocks in reverse order.
 template <typename T, int QN, int NB, bool SMEM>
 __device__ __forceinline__ void backward(T (&x)[QN][NB], const Factor<T, SMEM>& F, const T* inv,
                                          int lane) {
   const int n = F.n;
-  for (int c = n - 1; c >= 0; --c) {
-    const int qc = c >> 5, lc = c & 31;
-    const T ic = inv[c];
-    T zc[NB];
+  for (int qb = QN - 1; qb >= 0; --qb) {
+    T xb[NB];
 #pragma unroll
-    for (int v = 0; v < NB; ++v) {
-      zc[v] = __shfl_sync(0xffffffffu, pick(x, qc, v), lc) * ic;
-      if (lane == lc) put(x, qc, v, zc[v]);
-    }
+    for (int v = 0; v < NB; ++v) xb[v] = pick(x, qb, v);
 #pragma unroll
-    for (int q = 0; q < QN; ++q) {
-      const int r = lane + 32 * q;
-      if (q <= qc && r < c) {
-        const T l = F.row(c, r);
+    for (int lc = 31; lc >= 0; --lc) {
+      const int c = qb * 32 + lc;
+      if (c >= n) continue;
+      const T ic = inv[c];
+      T zc[NB];
 #pragma unroll
-        for (int v = 0; v < NB; ++v) x[q][v] -= l * zc[v];
+      for (int v = 0; v < NB; ++v) {
+        zc[v] = __shfl_sync(0xffffffffu, xb[v], lc) * ic;
+        if (lane == lc) xb[v] = zc[v];
+      }
+      if (lane < lc) {
+        const T l = F.row(c, qb * 32 + lane);
+#pragma unroll
+        for (int v = 0; v < NB; ++v) xb[v] -= l * zc[v];
+      }
+#pragma unroll
+      for (int q = 0; q < QN; ++q) {
+        if (q < qb) {
+          const T l = F.row(c, lane + 32 * q);
+#pragma unroll
+          for (int v = 0; v < NB; ++v) x[q][v] -= l * zc[v];
+        }
       }
     }
+#pragma unroll
+    for (int v = 0; v < NB; ++v) put(x, qb, v, xb[v]);
   }
 }
 
@@ -163,7 +192,8 @@ __global__ void __launch_bounds__(TW * 32) k_trsm(int n, const double* __restric
     for (int v = 0; v < NB; ++v) {
       T s = T(0);
 #pragma unroll
-      for (int q = 0; q < QN; ++q) s += x[q][v] * x[q][v];
+      for (int q = 0; q < QN; ++q)
+        if (lane + 32 * q < n) s += x[q][v] * x[q][v];   // rows >= n hold no data
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
       if (lane == 0 && v0 + v < nvec) ell[v0 + v] = static_cast<double>(s);
@@ -181,20 +211,27 @@ __global__ void __launch_bounds__(TW * 32) k_trsm(int n, const double* __restric
       for (int v = 0; v < NB; ++v)
         res[q][v] = (r < n && v0 + v < nvec) ? static_cast<T>(rhs[(v0 + v) * ld + r]) : T(0);
     }
-    for (int t = 0; t < n; ++t) {
-      const int qt = t >> 5, lt = t & 31;
-      T zt[NB];
+    for (int qt = 0; qt < QN; ++qt) {
+      T xt[NB];
 #pragma unroll
-      for (int v = 0; v < NB; ++v) zt[v] = __shfl_sync(0xffffffffu, pick(x, qt, v), lt);
+      for (int v = 0; v < NB; ++v) xt[v] = pick(x, qt, v);
+#pragma unroll 8
+      for (int lt = 0; lt < 32; ++lt) {
+        const int t = qt * 32 + lt;
+        if (t >= n) break;
+        T zt[NB];
 #pragma unroll
-      for (int q = 0; q < QN; ++q) {
-        const int r = lane + 32 * q;
-        if (r < n) {
-          T m;
-          if constexpr (SMEM) m = Ms[t * np + r];
-          else m = static_cast<T>(M[t * n + r]);
+        for (int v = 0; v < NB; ++v) zt[v] = __shfl_sync(0xffffffffu, xt[v], lt);
 #pragma unroll
-          for (int v = 0; v < NB; ++v) res[q][v] -= m * zt[v];
+        for (int q = 0; q < QN; ++q) {
+          const int r = lane + 32 * q;
+          if (r < n) {
+            T m;
+            if constexpr (SMEM) m = Ms[t * np + r];
+            else m = static_cast<T>(M[t * n + r]);
+#pragma unroll
+            for (int v = 0; v < NB; ++v) res[q][v] -= m * zt[v];
+          }
         }
       }
     }
