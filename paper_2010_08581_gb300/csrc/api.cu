@@ -31,7 +31,7 @@ struct tr_ctx {
   // CUDA graph of the last tr_als_sampled signature
   cudaStream_t cap = nullptr;       // internal stream, used only for capture
   cudaStream_t side = nullptr;      // second branch of each core update
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_info = nullptr;
   uint64_t* d_seed = nullptr;       // Philox key read by the captured kernels
   bool capturing = false;
   struct Mark { const char* name; cudaEvent_t a, b; };
@@ -230,6 +230,7 @@ size_t leverage_plan(Carver& c, int64_t I, int L, LevPass* p1, LevPass* p2, doub
     *p2 = carve_pass(c, I, static_cast<int>(I), false);  // Gram of C (I x I)
   }
   *ell = c.take<double>(I);
+  c.take<unsigned>(1);   // completion counter of the fused CDF step
   return c.off;
 }
 
@@ -241,37 +242,42 @@ size_t leverage_bytes(int64_t I, int L) {
 }
 
 // Leverage scores of the rows of the I x L row-major matrix `mat` (a core's G_(2), or any
-// matrix with the same column space) into ell.
-tr_status leverage_ell(tr_ctx* ctx, char* ws, const double* mat, int64_t I, int L, double** ell_out,
-                       cudaStream_t st) {
+// matrix with the same column space) and, from them, p and the CDF (unless *skip != 0).
+tr_status leverage_dist(tr_ctx* ctx, char* ws, const double* mat, int64_t I, int L, double* p,
+                        double* cdf, const int* skip, cudaStream_t st,
+                        cudaEvent_t wait_before_rows = nullptr) {
   Carver c(ws);
   LevPass p1{}, p2{};
   double* ell;
   leverage_plan(c, I, L, &p1, &p2, &ell);
+  unsigned* counter = reinterpret_cast<unsigned*>(reinterpret_cast<char*>(ell) +
+                                                  ((I * sizeof(double) + 255) & ~size_t(255)));
   const double eps = 2.220446049250313e-16;
   const double tol = static_cast<double>(I > L ? I : L) * eps;
+  TR_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned), st));
+  const CdfEpilogue ep{counter, p, cdf, skip, ctx->d_err};
   if (I >= L) {
     TR_TRY(run_pass(ctx, p1, mat, I, L, L, false, tol, st));
+    if (wait_before_rows) TR_CUDA(cudaStreamWaitEvent(st, wait_before_rows, 0));
     TR_LAUNCH("leverage_rows", launch_trsm(0, false, L, p1.Lrow, p1.Lcol, p1.invdiag, nullptr, I,
-                                           mat, L, nullptr, 1, 1, nullptr, ell, st, p1.img));
+                                           mat, L, nullptr, 1, 1, nullptr, ell, st, p1.img,
+                                           nullptr, &ep));
   } else {
     // Wide G_(2): the range of A is that of C with A A^T = C C^T; ell(A) = ell(C).
     const int n = static_cast<int>(I);
     TR_TRY(run_pass(ctx, p1, mat, I, L, L, true, tol, st));
     TR_TRY(run_pass(ctx, p2, p1.Lrow, I, n, n, false, tol, st));
+    if (wait_before_rows) TR_CUDA(cudaStreamWaitEvent(st, wait_before_rows, 0));
     TR_LAUNCH("leverage_rows", launch_trsm(0, false, n, p2.Lrow, p2.Lcol, p2.invdiag, nullptr, I,
-                                           p1.Lrow, n, nullptr, 1, 1, nullptr, ell, st, p2.img));
+                                           p1.Lrow, n, nullptr, 1, 1, nullptr, ell, st, p2.img,
+                                           nullptr, &ep));
   }
-  *ell_out = ell;
   return TR_OK;
 }
 
 tr_status leverage_run(tr_ctx* ctx, char* ws, const double* core, int64_t I, int Rl, int Rr,
                        double* p, double* cdf, cudaStream_t st) {
-  double* ell;
-  TR_TRY(leverage_ell(ctx, ws, core, I, Rl * Rr, &ell, st));
-  TR_LAUNCH("cdf", launch_cdf(ell, I, p, cdf, ctx->d_err, st));
-  return TR_OK;
+  return leverage_dist(ctx, ws, core, I, Rl * Rr, p, cdf, nullptr, st);
 }
 
 // ------------------------------------------------------------------------------------
@@ -326,19 +332,29 @@ tr_status solve_contract(tr_ctx* ctx, const SolvePlan& s, const void* A, const v
   return TR_OK;
 }
 
-tr_status solve_factor(tr_ctx* ctx, const SolvePlan& s, bool f64, int Rl, int Rr, int64_t I,
-                       bool refine, double* core_out, cudaStream_t st) {
-  const int L = Rl * Rr;
+tr_status solve_cholesky(tr_ctx* ctx, const SolvePlan& s, bool f64, int L, cudaStream_t st) {
   const double eps = 2.220446049250313e-16;
   TR_LAUNCH("cholesky_solve",
             launch_cholesky(s.M, L, 0, static_cast<double>(L) * eps, s.Lrow, s.Lcol, s.invdiag,
                             s.keep, s.info, ctx->d_err, st,
                             f64 ? static_cast<double*>(s.limg) : nullptr,
                             f64 ? nullptr : static_cast<float*>(s.limg), s.mimg));
+  return TR_OK;
+}
+
+tr_status solve_rhs(tr_ctx* ctx, const SolvePlan& s, int Rl, int Rr, int64_t I, bool refine,
+                    double* core_out, cudaStream_t st) {
+  const int L = Rl * Rr;
   TR_LAUNCH("solve_rhs", launch_trsm(refine ? 2 : 1, refine, L, s.Lrow, s.Lcol, s.invdiag, s.info,
                                       I, s.BT, L, s.M, Rl, Rr, core_out, nullptr, st, s.limg,
                                       s.mimg));
   return TR_OK;
+}
+
+tr_status solve_factor(tr_ctx* ctx, const SolvePlan& s, bool f64, int Rl, int Rr, int64_t I,
+                       bool refine, double* core_out, cudaStream_t st) {
+  TR_TRY(solve_cholesky(ctx, s, f64, Rl * Rr, st));
+  return solve_rhs(ctx, s, Rl, Rr, I, refine, core_out, st);
 }
 
 tr_status solve_run(tr_ctx* ctx, char* ws, const void* A, const void* Y, bool f64, int64_t J,
@@ -366,16 +382,14 @@ tr_status update_run(tr_ctx* ctx, char* ws, size_t solve_ws, const void* A, cons
   TR_TRY(solve_contract(ctx, s, A, Y, f64, J, L, I, st));
   TR_CUDA(cudaEventRecord(ctx->ev_fork, st));
   TR_CUDA(cudaStreamWaitEvent(side, ctx->ev_fork, 0));
-  double* ell;
-  TR_TRY(leverage_ell(ctx, ws + solve_ws, s.BT, I, L, &ell, side));
-  TR_TRY(solve_factor(ctx, s, f64, Rl, Rr, I, !f64, core_out, st));
+  TR_TRY(solve_cholesky(ctx, s, f64, L, st));
+  // The side branch needs the solve's Cholesky status (info) only in its last kernel, to
+  // keep the old distribution when the core was not updated.
+  TR_CUDA(cudaEventRecord(ctx->ev_info, st));
+  TR_TRY(solve_rhs(ctx, s, Rl, Rr, I, !f64, core_out, st));
+  TR_TRY(leverage_dist(ctx, ws + solve_ws, s.BT, I, L, p, cdf, s.info, side, ctx->ev_info));
   TR_CUDA(cudaEventRecord(ctx->ev_join, side));
   TR_CUDA(cudaStreamWaitEvent(st, ctx->ev_join, 0));
-  {
-    cudaStream_t st_cdf = st;
-    Prof prof_(ctx, "cdf", st_cdf);
-    TR_CUDA(launch_cdf(ell, I, p, cdf, ctx->d_err, st_cdf, s.info));
-  }
   return TR_OK;
 }
 
@@ -519,8 +533,8 @@ tr_status als_issue(tr_ctx* ctx, const AlsPlan& P, uint64_t seed, const uint64_t
       ga.In = dims[n];
       ga.stride_n = stride[n];
       const uint64_t uid = static_cast<uint64_t>(s) * N + n;
-      TR_LAUNCH("sample", launch_sample(sa, P.J, seed, uid, P.idx, P.w, st));
-      TR_LAUNCH("subchain", launch_subchain(ca, P.idx, P.w, P.J, P.A, f64, ctx->d_err, st));
+      TR_LAUNCH("sample_chain", launch_sample_chain(sa, ca, P.J, seed, uid, P.idx, P.w, P.A, f64,
+                                                    st));
       TR_LAUNCH("gather", launch_gather(ga, P.X, x64, P.idx, P.w, P.J, P.Y, f64, ctx->d_err, st));
       const int Rl = rl_of(ranks, N, n), Rr = ranks[n];
       TR_TRY(update_run(ctx, P.ws, P.solve_ws, P.A, P.Y, f64, P.J, Rl, Rr, dims[n], P.cores[n],
@@ -643,6 +657,7 @@ tr_status tr_create(tr_ctx** out, int device, size_t hbm_budget_bytes) {
     step = "cudaEventCreate";
     e = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_info, cudaEventDisableTiming);
   }
   if (e == cudaSuccess) { step = "cudaFuncSetAttribute"; e = init_kernel_attributes(&which); }
   if (e != cudaSuccess) {
@@ -653,6 +668,7 @@ tr_status tr_create(tr_ctx** out, int device, size_t hbm_budget_bytes) {
     if (ctx->side) cudaStreamDestroy(ctx->side);
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+    if (ctx->ev_info) cudaEventDestroy(ctx->ev_info);
     delete ctx;
     return TR_ERR_CUDA;
   }
@@ -672,6 +688,7 @@ void tr_destroy(tr_ctx* ctx) {
   if (ctx->side) cudaStreamDestroy(ctx->side);
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+  if (ctx->ev_info) cudaEventDestroy(ctx->ev_info);
   if (ctx->d_err) cudaFree(ctx->d_err);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   delete ctx;

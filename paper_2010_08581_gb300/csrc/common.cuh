@@ -66,6 +66,12 @@ struct ChainArgs {
 cudaError_t launch_subchain(const ChainArgs& a, const int32_t* idx, const double* w,
                             int64_t J, void* A, bool f64, unsigned* err, cudaStream_t st);
 
+// Fused sampler + subchain (driver): the same draws as launch_sample and the same rows as
+// launch_subchain, in one launch; p and the CDFs are staged in shared memory when they fit.
+cudaError_t launch_sample_chain(const SampleArgs& sa, const ChainArgs& ca, int64_t J,
+                                uint64_t seed, uint64_t update_id, int32_t* idx, double* w,
+                                void* A, bool f64, cudaStream_t st);
+
 struct GatherArgs {
   int64_t stride[kMaxModes];     // element stride of the mode at ring position m
   int64_t I[kMaxModes];
@@ -126,17 +132,22 @@ cudaError_t launch_cholesky(const double* G, int n, int mode, double tol_scale, 
 // when *info != 0 (info may be NULL).
 // Limg: padded factor image in the arithmetic type (FP32 when f32, else FP64), Mimg: FP32
 // image of M (mode 2, f32); both optional (NULL: converted from Lcol / M instead).
+// cdf (mode 0, optional): the CTA that finishes last forms p = ell / sum(ell) and the CDF
+// (fixed-order scan); *counter must be 0 before the launch and is 0 again after it; when
+// skip && *skip != 0 p and the CDF are left unchanged.
+struct CdfEpilogue {
+  unsigned* counter;
+  double* p;
+  double* cdf;
+  const int* skip;
+  unsigned* err;
+};
 cudaError_t launch_trsm(int mode, bool f32, int n, const double* Lrow, const double* Lcol,
                         const double* invdiag, const int* info, int64_t nvec, const double* rhs,
                         int64_t ld, const double* M, int Rl, int Rr, double* core_out,
                         double* ell, cudaStream_t st, const void* Limg = nullptr,
-                        const float* Mimg = nullptr);
+                        const float* Mimg = nullptr, const CdfEpilogue* cdf = nullptr);
 size_t trsm_image_bytes(int n, bool f32);
-
-// p = ell / sum(ell), cdf = inclusive prefix sum (fixed order), one CTA. All-zero ell ->
-// uniform p and the singular bit. Nothing is written when skip && *skip != 0.
-cudaError_t launch_cdf(const double* ell, int64_t I, double* p, double* cdf, unsigned* err,
-                       cudaStream_t st, const int* skip = nullptr);
 
 // Core initialisation N(0,1) by Philox + Box-Muller.
 cudaError_t launch_init_normal(double* out, int64_t count, uint64_t seed, uint32_t stream_id,

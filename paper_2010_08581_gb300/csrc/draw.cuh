@@ -1,0 +1,87 @@
+// Device helpers shared by the sampler kernels (row a2: Alg. 3 and Def. 3.4) and the
+// slice-chain kernels (row a3: Alg. 4), so that the per-stage entry points and the fused
+// driver kernel compute bit-identical results.
+#pragma once
+
+#include "common.cuh"
+
+namespace trk {
+
+// Uniform of sample j at ring position m: Philox4x32-10 block (j, m/2, update_id), words
+// (2(m%2), 2(m%2)+1) as (hi, lo), top 53 bits.
+__device__ __forceinline__ double draw_uniform(int64_t j, int m, uint32_t k0, uint32_t k1,
+                                               uint32_t uid_lo, uint32_t uid_hi) {
+  const u32x4 r = philox4x32_10(
+      u32x4{static_cast<uint32_t>(j), static_cast<uint32_t>(m >> 1), uid_lo, uid_hi}, k0, k1);
+  return (m & 1) ? u53(r.z, r.w) : u53(r.x, r.y);
+}
+
+// Smallest i with u < cdf[i]; if rounding leaves cdf[I-1] <= u, the largest i with p > 0.
+__device__ __forceinline__ int64_t inverse_cdf(const double* cdf, const double* p, int64_t I,
+                                               double u) {
+  int64_t lo = 0, hi = I;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (u < cdf[mid]) hi = mid; else lo = mid + 1;
+  }
+  if (lo >= I) {
+    lo = I - 1;
+    while (lo > 0 && !(p[lo] > 0.0)) --lo;
+  }
+  return lo;
+}
+
+// w = 1 / sqrt(J * prod_m p_m) with the product taken in ring order m = 0, 1, ...
+__device__ __forceinline__ double sample_weight(int64_t J, const double* pm, int npos) {
+  double q = 1.0;
+  for (int m = 0; m < npos; ++m) q = q * pm[m];
+  return 1.0 / sqrt(static_cast<double>(J) * q);
+}
+
+// One warp multiplies the sampled lateral slices in ring order into S (row-major,
+// R0 x cols, <= 256 entries) held in shared memory; G is a second 256-entry buffer.
+// index(m) returns the sampled index at ring position m. Returns the final column count.
+template <typename T, typename IndexFn>
+__device__ __forceinline__ int warp_slice_chain(const ChainArgs& a, IndexFn index, T* S, T* G,
+                                                int lane) {
+  {
+    const int64_t i = index(0);
+    const int ent = a.rl[0] * a.rr[0];
+    const double* src = a.core[0] + i * ent;
+    for (int e = lane; e < ent; e += 32) S[e] = static_cast<T>(src[e]);
+  }
+  const int R0 = a.rl[0];
+  int cols = a.rr[0];
+  for (int m = 1; m < a.npos; ++m) {
+    const int64_t i = index(m);
+    const int rr = a.rr[m];
+    const int ent = cols * rr;
+    const double* src = a.core[m] + i * ent;
+    for (int e = lane; e < ent; e += 32) G[e] = static_cast<T>(src[e]);
+    __syncwarp();
+    T acc[kMaxL / 32];
+    const int outs = R0 * rr;
+#pragma unroll
+    for (int q = 0; q < kMaxL / 32; ++q) {
+      const int e = lane + 32 * q;
+      T s = T(0);
+      if (e < outs) {
+        const int r = e / rr, c = e - r * rr;
+        for (int t = 0; t < cols; ++t) s += S[r * cols + t] * G[t * rr + c];
+      }
+      acc[q] = s;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < kMaxL / 32; ++q) {
+      const int e = lane + 32 * q;
+      if (e < outs) S[e] = acc[q];
+    }
+    __syncwarp();
+    cols = rr;
+  }
+  __syncwarp();
+  return cols;
+}
+
+}  // namespace trk

@@ -160,6 +160,7 @@ cudaError_t fit_attributes() {
 cudaError_t cholesky_attributes();
 cudaError_t trsm_attributes();
 cudaError_t normal_eq_tc_attributes();
+cudaError_t sample_chain_attributes();
 
 cudaError_t init_kernel_attributes(const char** which) {
   cudaError_t e = cholesky_attributes();
@@ -168,6 +169,8 @@ cudaError_t init_kernel_attributes(const char** which) {
   if (e != cudaSuccess) { *which = "trsm"; return e; }
   e = normal_eq_tc_attributes();
   if (e != cudaSuccess) { *which = "normal_eq_tc"; return e; }
+  e = sample_chain_attributes();
+  if (e != cudaSuccess) { *which = "sample_chain"; return e; }
   e = fit_attributes();
   if (e != cudaSuccess) *which = "fit";
   return e;

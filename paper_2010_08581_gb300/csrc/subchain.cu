@@ -5,7 +5,7 @@
 //
 // One warp per sample: the running product lives in shared memory (<= 16 x 16), each lane
 // owns up to 8 entries of the next product, and every slice is read once, contiguously.
-#include "common.cuh"
+#include "draw.cuh"
 
 namespace trk {
 namespace {
@@ -26,8 +26,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_subchain(ChainArgs a,
   if (j >= J) return;
   T* S = sS[warp];
   T* G = sG[warp];
-  const int R0 = a.rl[0];
-  const int Lout = R0 * a.rr[a.npos - 1];
+  const int Lout = a.rl[0] * a.rr[a.npos - 1];
 
   // Validate this sample's indices.
   bool bad = false;
@@ -41,41 +40,8 @@ __global__ void __launch_bounds__(kWarps * 32) k_subchain(ChainArgs a,
     return;
   }
 
-  {  // S = first slice
-    const int32_t i = idx[j * a.npos];
-    const int ent = a.rl[0] * a.rr[0];
-    const double* src = a.core[0] + static_cast<int64_t>(i) * ent;
-    for (int e = lane; e < ent; e += 32) S[e] = static_cast<T>(src[e]);
-  }
-  int cols = a.rr[0];
-  for (int m = 1; m < a.npos; ++m) {
-    const int32_t i = idx[j * a.npos + m];
-    const int rr = a.rr[m];
-    const int ent = cols * rr;  // a.rl[m] == cols
-    const double* src = a.core[m] + static_cast<int64_t>(i) * ent;
-    for (int e = lane; e < ent; e += 32) G[e] = static_cast<T>(src[e]);
-    __syncwarp();
-    T acc[kMaxEnt / 32];
-    const int outs = R0 * rr;
-#pragma unroll
-    for (int q = 0; q < kMaxEnt / 32; ++q) {
-      const int e = lane + 32 * q;
-      T s = T(0);
-      if (e < outs) {
-        const int r = e / rr, c = e - r * rr;
-        for (int t = 0; t < cols; ++t) s += S[r * cols + t] * G[t * rr + c];
-      }
-      acc[q] = s;
-    }
-    __syncwarp();
-#pragma unroll
-    for (int q = 0; q < kMaxEnt / 32; ++q) {
-      const int e = lane + 32 * q;
-      if (e < outs) S[e] = acc[q];
-    }
-    __syncwarp();
-    cols = rr;
-  }
+  auto index = [&](int m) -> int64_t { return idx[j * a.npos + m]; };
+  warp_slice_chain<T>(a, index, S, G, lane);
   __syncwarp();
   const T scale = w ? static_cast<T>(w[j]) : T(1);
   for (int e = lane; e < Lout; e += 32) A[j * Lout + e] = S[e] * scale;

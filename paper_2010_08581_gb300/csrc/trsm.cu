@@ -137,6 +137,59 @@ __device__ __forceinline__ void stage_async(void* dst, const void* src, int byte
   asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
 
+// Block-wide exclusive scan (fixed order) of one double per thread for TW warps.
+__device__ __forceinline__ double block_scan_tw(double v, double* wt, double* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) wt[warp] = inc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double run = 0.0;
+    for (int q = 0; q < TW; ++q) { const double t = wt[q]; wt[q] = run; run += t; }
+    *total = run;
+  }
+  __syncthreads();
+  const double r = wt[warp] + inc - v;
+  __syncthreads();
+  return r;
+}
+
+// p = ell / sum(ell) and its prefix sum, by the CTA that finishes last (mode 0 only).
+__device__ void cdf_epilogue(const CdfEpilogue& ep, const double* ell, int64_t I) {
+  __shared__ double wt[TW];
+  __shared__ double s_total;
+  if (ep.skip && *ep.skip) return;
+  const int t = threadIdx.x;
+  const int64_t chunk = (I + TW * 32 - 1) / (TW * 32);
+  const int64_t b = t * chunk, e = (b + chunk < I) ? b + chunk : I;
+  double s = 0.0;
+  for (int64_t i = b; i < e; ++i) s += __ldcg(ell + i);
+  block_scan_tw(s, wt, &s_total);
+  const double total = s_total;
+  if (!(total > 0.0) || !isfinite(total)) {
+    for (int64_t i = b; i < e; ++i) {
+      ep.p[i] = 1.0 / static_cast<double>(I);
+      ep.cdf[i] = static_cast<double>(i + 1) / static_cast<double>(I);
+    }
+    if (t == 0) atomicOr(ep.err, kErrSingular);
+    return;
+  }
+  double sp = 0.0;
+  for (int64_t i = b; i < e; ++i) sp += __ldcg(ell + i) / total;
+  double run = block_scan_tw(sp, wt, &s_total);
+  for (int64_t i = b; i < e; ++i) {
+    const double pi = __ldcg(ell + i) / total;
+    ep.p[i] = pi;
+    run += pi;
+    ep.cdf[i] = run;
+  }
+}
+
 template <typename T, int QN, int NB, bool SMEM>
 __global__ void __launch_bounds__(TW * 32) k_trsm(int n, const double* __restrict__ Lrow,
                                                   const double* __restrict__ Lcol,
@@ -147,7 +200,7 @@ __global__ void __launch_bounds__(TW * 32) k_trsm(int n, const double* __restric
                                                   const T* __restrict__ Limg,
                                                   const float* __restrict__ Mimg, int Rl, int Rr,
                                                   double* __restrict__ core_out,
-                                                  double* __restrict__ ell) {
+                                                  double* __restrict__ ell, CdfEpilogue ep) {
   extern __shared__ __align__(16) unsigned char trsm_smem[];
   if (info && *info) return;
   const int np = n + 1;
@@ -177,6 +230,42 @@ __global__ void __launch_bounds__(TW * 32) k_trsm(int n, const double* __restric
   Factor<T, SMEM> F{Ls, Lcol, Lrow, n};
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t v0 = (static_cast<int64_t>(blockIdx.x) * TW + warp) * NB;
+  if (mode == 0) {
+    if (v0 < nvec) {
+      T x[QN][NB];
+#pragma unroll
+      for (int q = 0; q < QN; ++q) {
+        const int r = lane + 32 * q;
+#pragma unroll
+        for (int v = 0; v < NB; ++v)
+          x[q][v] = (r < n && v0 + v < nvec) ? static_cast<T>(rhs[(v0 + v) * ld + r]) : T(0);
+      }
+      forward(x, F, inv, lane);
+#pragma unroll
+      for (int v = 0; v < NB; ++v) {
+        T s = T(0);
+#pragma unroll
+        for (int q = 0; q < QN; ++q)
+          if (lane + 32 * q < n) s += x[q][v] * x[q][v];   // rows >= n hold no data
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0 && v0 + v < nvec) ell[v0 + v] = static_cast<double>(s);
+      }
+    }
+    if (ep.counter) {      // the last CTA to finish forms p and the CDF
+      __shared__ int s_last;
+      __threadfence();
+      __syncthreads();
+      if (threadIdx.x == 0) s_last = (atomicAdd(ep.counter, 1u) == gridDim.x - 1) ? 1 : 0;
+      __syncthreads();
+      if (s_last) {
+        __threadfence();
+        cdf_epilogue(ep, ell, nvec);
+        if (threadIdx.x == 0) *ep.counter = 0u;
+      }
+    }
+    return;
+  }
   if (v0 >= nvec) return;
   T x[QN][NB];
 #pragma unroll
@@ -187,19 +276,6 @@ __global__ void __launch_bounds__(TW * 32) k_trsm(int n, const double* __restric
       x[q][v] = (r < n && v0 + v < nvec) ? static_cast<T>(rhs[(v0 + v) * ld + r]) : T(0);
   }
   forward(x, F, inv, lane);
-  if (mode == 0) {
-#pragma unroll
-    for (int v = 0; v < NB; ++v) {
-      T s = T(0);
-#pragma unroll
-      for (int q = 0; q < QN; ++q)
-        if (lane + 32 * q < n) s += x[q][v] * x[q][v];   // rows >= n hold no data
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0 && v0 + v < nvec) ell[v0 + v] = static_cast<double>(s);
-    }
-    return;
-  }
   backward(x, F, inv, lane);
   if (mode == 2) {
     // residual r = b - M z (M symmetric: column t of M = row t)
@@ -264,16 +340,18 @@ template <typename T, int QN, int NB>
 cudaError_t run_q(int n, const double* Lrow, const double* Lcol, const double* invdiag,
                   const int* info, int64_t nvec, const double* rhs, int64_t ld, int mode,
                   const double* M, const T* Limg, const float* Mimg, int Rl, int Rr,
-                  double* core_out, double* ell, cudaStream_t st) {
+                  double* core_out, double* ell, const CdfEpilogue& ep, cudaStream_t st) {
   const size_t staged = staged_bytes<T>(n, mode);
   const int64_t per_cta = static_cast<int64_t>(TW) * NB;
   const unsigned blocks = static_cast<unsigned>((nvec + per_cta - 1) / per_cta);
   if (staged <= 200 * 1024) {
     k_trsm<T, QN, NB, true><<<blocks, TW * 32, staged, st>>>(
-        n, Lrow, Lcol, invdiag, info, nvec, rhs, ld, mode, M, Limg, Mimg, Rl, Rr, core_out, ell);
+        n, Lrow, Lcol, invdiag, info, nvec, rhs, ld, mode, M, Limg, Mimg, Rl, Rr, core_out, ell,
+        ep);
   } else {
     k_trsm<T, QN, NB, false><<<blocks, TW * 32, kMaxL * sizeof(T), st>>>(
-        n, Lrow, Lcol, invdiag, info, nvec, rhs, ld, mode, M, Limg, Mimg, Rl, Rr, core_out, ell);
+        n, Lrow, Lcol, invdiag, info, nvec, rhs, ld, mode, M, Limg, Mimg, Rl, Rr, core_out, ell,
+        ep);
   }
   return cudaGetLastError();
 }
@@ -282,12 +360,12 @@ template <typename T, int NB>
 cudaError_t run(int n, const double* Lrow, const double* Lcol, const double* invdiag,
                 const int* info, int64_t nvec, const double* rhs, int64_t ld, int mode,
                 const double* M, const T* Limg, const float* Mimg, int Rl, int Rr,
-                double* core_out, double* ell, cudaStream_t st) {
+                double* core_out, double* ell, const CdfEpilogue& ep, cudaStream_t st) {
   switch ((n + 31) / 32) {
 #define TRSM_CASE(q)                                                                        \
   case q:                                                                                   \
     return run_q<T, q, NB>(n, Lrow, Lcol, invdiag, info, nvec, rhs, ld, mode, M, Limg, Mimg, \
-                           Rl, Rr, core_out, ell, st);
+                           Rl, Rr, core_out, ell, ep, st);
     TRSM_CASE(1) TRSM_CASE(2) TRSM_CASE(3) TRSM_CASE(4)
     TRSM_CASE(5) TRSM_CASE(6) TRSM_CASE(7) TRSM_CASE(8)
 #undef TRSM_CASE
@@ -322,13 +400,15 @@ cudaError_t attr() {
 cudaError_t launch_trsm(int mode, bool f32, int n, const double* Lrow, const double* Lcol,
                         const double* invdiag, const int* info, int64_t nvec, const double* rhs,
                         int64_t ld, const double* M, int Rl, int Rr, double* core_out,
-                        double* ell, cudaStream_t st, const void* Limg, const float* Mimg) {
+                        double* ell, cudaStream_t st, const void* Limg, const float* Mimg,
+                        const CdfEpilogue* cdf) {
   if (nvec <= 0) return cudaSuccess;
+  const CdfEpilogue ep = cdf ? *cdf : CdfEpilogue{};
   if (f32)
     return run<float, 2>(n, Lrow, Lcol, invdiag, info, nvec, rhs, ld, mode, M,
-                         static_cast<const float*>(Limg), Mimg, Rl, Rr, core_out, ell, st);
+                         static_cast<const float*>(Limg), Mimg, Rl, Rr, core_out, ell, ep, st);
   return run<double, 1>(n, Lrow, Lcol, invdiag, info, nvec, rhs, ld, mode, M,
-                        static_cast<const double*>(Limg), Mimg, Rl, Rr, core_out, ell, st);
+                        static_cast<const double*>(Limg), Mimg, Rl, Rr, core_out, ell, ep, st);
 }
 
 size_t trsm_image_bytes(int n, bool f32) {

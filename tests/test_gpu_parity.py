@@ -384,3 +384,19 @@ def test_als_sampled_is_deterministic_and_host_api_agrees(ctx):
     T.tr_als_sampled_host(ctx, X.pin_memory(), ranks, J, sweeps, 77, T.TR_PREC_MIXED, host)
     for x, y in zip(a, host):
         assert torch.equal(x.cpu(), y)
+
+
+@pytest.mark.parametrize("dims,ranks", [((30, 25, 20), (3, 4, 2)), ((12, 9, 10, 11), (2, 3, 2, 3))])
+def test_als_sampled_first_sweeps_match_oracle_fp64(ctx, dims, ranks):
+    """Two FP64 sweeps of the whole driver (fused sampler + subchain, leverage from B^T on
+    the concurrent branch) against the oracle's Alg. 2 with the normal-equation solve: the
+    same draws and the same arithmetic up to rounding."""
+    J, sweeps, seed = 300, 2, 21
+    X, _ = inputs.tr_plus_noise(dims, ranks, seed=6, rel_noise=1e-2, dtype=torch.float64)
+    init = np_cores(dims, ranks, 7)
+    ref = orc.tr_als_sampled(X.numpy(), init, J, sweeps, seed, solver="normal")
+    out = T.empty_cores(dims, ranks)
+    T.tr_als_sampled(ctx, X.to(DEV), ranks, J, sweeps, seed, T.TR_PREC_FP64, out,
+                     init_cores=[to_dev_core(c) for c in init])
+    for k in range(len(dims)):
+        assert rel(to_paper(out[k]), ref[k]) < 1e-8
