@@ -2,11 +2,13 @@
 // Used for the normal matrix of the sampled LS (row a6, Alg. 2 LS step) and for the R
 // factor of the Cholesky-based thin QR behind the leverage scores (row a1).
 //
-// Right-looking with one column of look-ahead. At step k column k is final; warp 0 applies
-// column k's update to column k+1 only, takes its pivot (FP64 rsqrt) and scales it, while
-// warps 1.. apply column k's rank-1 update to the trailing triangle of columns >= k+2
-// (its (m+1)m/2 entries spread evenly over the threads). One barrier per column. The
-// matrix lives in shared memory when n*n*8 <= 200 KB, otherwise in place in Lrow.
+// Right-looking, one column per step in two phases: all threads apply column k's rank-1
+// update to the trailing triangle (its (m+1)m/2 entries spread evenly over the threads),
+// then warp 0 alone takes the next pivot (FP64 rsqrt) and scales the next column. On
+// GB300 a dependent FP64 FMA takes about 68 cycles and the FP64 pipe issues about 2 FMAs
+// per clock per SM, so the pivot chain is kept off a busy pipe (overlapping it with the
+// trailing update measured 1.3x slower). The matrix lives in shared memory when
+// n*n*8 <= 200 KB, otherwise in place in Lrow.
 //
 // Besides L (row- and column-major) the kernel can write padded images that the
 // triangular-solve kernel copies straight into shared memory: img[c*(n+1) + r] = L[r][c]
@@ -66,50 +68,39 @@ __global__ void __launch_bounds__(CNT) k_cholesky(const double* __restrict__ G, 
     }
   }
   __syncthreads();
+  // Step k (column k final in colbuf[k&1]): all warps apply column k to the trailing
+  // triangle (columns >= k+1); then warp 0 alone finishes column k+1 (pivot, scale) with
+  // the FP64 pipe to itself, so the dependent pivot chain does not queue behind the
+  // trailing-update FMAs.
   for (int k = 0; k < n; ++k) {
     if (s_stop) break;
     const double* cur = colbuf[k & 1];
     double* nxt = colbuf[(k + 1) & 1];
-    const bool kp = keepv[k] != 0;
-    if (warp == 0) {
-      if (k + 1 < n) {
-        // column k+1: a_i = A[i][k+1] - L[i][k] L[k+1][k]; pivot; scale
-        const double lk1 = cur[k + 1];
-        double a[kMaxL / 32];
-#pragma unroll
-        for (int q = 0; q < kMaxL / 32; ++q) {
-          const int i = k + 1 + lane + 32 * q;
-          a[q] = 0.0;
-          if (i < n) a[q] = kp ? A[i * n + k + 1] - cur[i] * lk1 : A[i * n + k + 1];
-        }
-        const double d = __shfl_sync(0xffffffffu, a[0], 0);   // row k+1: lane 0, q = 0
-        const bool ok = d > s_tol;
-        const double inv = ok ? rsqrt(d) : 0.0;
-#pragma unroll
-        for (int q = 0; q < kMaxL / 32; ++q) {
-          const int i = k + 1 + lane + 32 * q;
-          if (i < n) {
-            const double v = ok ? ((i == k + 1) ? d * inv : a[q] * inv) : 0.0;
-            A[i * n + k + 1] = v;
-            nxt[i] = v;
-          }
-        }
-        if (lane == 0) {
-          keepv[k + 1] = ok ? 1 : 0;
-          if (!ok && mode == 0) s_stop = k + 2;
-        }
-      }
-    } else if (kp) {
-      // trailing triangle of columns >= k+2: rows i >= j >= k+2
-      const int m = n - k - 2;
-      const int P = m > 0 ? m * (m + 1) / 2 : 0;
-      for (int e = tid - 32; e < P; e += CNT - 32) {
+    if (keepv[k]) {
+      const int m = n - k - 1;
+      const int P = m * (m + 1) / 2;
+      for (int e = tid; e < P; e += CNT) {
         int ii = static_cast<int>((sqrtf(8.0f * static_cast<float>(e) + 1.0f) - 1.0f) * 0.5f);
         while (ii * (ii + 1) / 2 > e) --ii;
         while ((ii + 1) * (ii + 2) / 2 <= e) ++ii;
         const int jj = e - ii * (ii + 1) / 2;
-        const int i = k + 2 + ii, j = k + 2 + jj;
+        const int i = k + 1 + ii, j = k + 1 + jj;
         A[i * n + j] -= cur[i] * cur[j];
+      }
+    }
+    __syncthreads();
+    if (warp == 0 && k + 1 < n) {
+      const double d = A[(k + 1) * n + k + 1];
+      const bool ok = d > s_tol;
+      const double inv = ok ? rsqrt(d) : 0.0;
+      for (int i = k + 1 + lane; i < n; i += 32) {
+        const double v = ok ? ((i == k + 1) ? d * inv : A[i * n + k + 1] * inv) : 0.0;
+        A[i * n + k + 1] = v;
+        nxt[i] = v;
+      }
+      if (lane == 0) {
+        keepv[k + 1] = ok ? 1 : 0;
+        if (!ok && mode == 0) s_stop = k + 2;
       }
     }
     __syncthreads();
