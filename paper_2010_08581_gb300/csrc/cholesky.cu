@@ -13,14 +13,20 @@
 // Besides L (row- and column-major) the kernel can write padded images that the
 // triangular-solve kernel copies straight into shared memory: img[c*(n+1) + r] = L[r][c]
 // in FP64 and/or FP32, and the FP32 image of the symmetric input matrix.
+#include <cstdlib>
+
 #include "common.cuh"
 
 namespace trk {
 namespace {
 
 constexpr int CNT = 512;
+constexpr int CB = 32;   // diagonal block width (one warp)
+constexpr int BNT = 256; // threads of the blocked variant (registers for 32-wide rows)
 
-__global__ void __launch_bounds__(CNT) k_cholesky(const double* __restrict__ G, int n, int mode,
+// Look-ahead variant: warp 0 finishes column k+1 while the other warps update the
+// trailing triangle of columns >= k+2 (one barrier per column).
+__global__ void __launch_bounds__(CNT) k_cholesky_lookahead(const double* __restrict__ G, int n, int mode,
                                                   double tol_scale, double* Lrow, double* Lcol,
                                                   double* invdiag, int* keep_out, int* info,
                                                   unsigned* err, int use_smem,
@@ -68,39 +74,50 @@ __global__ void __launch_bounds__(CNT) k_cholesky(const double* __restrict__ G, 
     }
   }
   __syncthreads();
-  // Step k (column k final in colbuf[k&1]): all warps apply column k to the trailing
-  // triangle (columns >= k+1); then warp 0 alone finishes column k+1 (pivot, scale) with
-  // the FP64 pipe to itself, so the dependent pivot chain does not queue behind the
-  // trailing-update FMAs.
   for (int k = 0; k < n; ++k) {
     if (s_stop) break;
     const double* cur = colbuf[k & 1];
     double* nxt = colbuf[(k + 1) & 1];
-    if (keepv[k]) {
-      const int m = n - k - 1;
-      const int P = m * (m + 1) / 2;
-      for (int e = tid; e < P; e += CNT) {
+    const bool kp = keepv[k] != 0;
+    if (warp == 0) {
+      if (k + 1 < n) {
+        // column k+1: a_i = A[i][k+1] - L[i][k] L[k+1][k]; pivot; scale
+        const double lk1 = cur[k + 1];
+        double a[kMaxL / 32];
+#pragma unroll
+        for (int q = 0; q < kMaxL / 32; ++q) {
+          const int i = k + 1 + lane + 32 * q;
+          a[q] = 0.0;
+          if (i < n) a[q] = kp ? A[i * n + k + 1] - cur[i] * lk1 : A[i * n + k + 1];
+        }
+        const double d = __shfl_sync(0xffffffffu, a[0], 0);   // row k+1: lane 0, q = 0
+        const bool ok = d > s_tol;
+        const double inv = ok ? rsqrt(d) : 0.0;
+#pragma unroll
+        for (int q = 0; q < kMaxL / 32; ++q) {
+          const int i = k + 1 + lane + 32 * q;
+          if (i < n) {
+            const double v = ok ? ((i == k + 1) ? d * inv : a[q] * inv) : 0.0;
+            A[i * n + k + 1] = v;
+            nxt[i] = v;
+          }
+        }
+        if (lane == 0) {
+          keepv[k + 1] = ok ? 1 : 0;
+          if (!ok && mode == 0) s_stop = k + 2;
+        }
+      }
+    } else if (kp) {
+      // trailing triangle of columns >= k+2: rows i >= j >= k+2
+      const int m = n - k - 2;
+      const int P = m > 0 ? m * (m + 1) / 2 : 0;
+      for (int e = tid - 32; e < P; e += CNT - 32) {
         int ii = static_cast<int>((sqrtf(8.0f * static_cast<float>(e) + 1.0f) - 1.0f) * 0.5f);
         while (ii * (ii + 1) / 2 > e) --ii;
         while ((ii + 1) * (ii + 2) / 2 <= e) ++ii;
         const int jj = e - ii * (ii + 1) / 2;
-        const int i = k + 1 + ii, j = k + 1 + jj;
+        const int i = k + 2 + ii, j = k + 2 + jj;
         A[i * n + j] -= cur[i] * cur[j];
-      }
-    }
-    __syncthreads();
-    if (warp == 0 && k + 1 < n) {
-      const double d = A[(k + 1) * n + k + 1];
-      const bool ok = d > s_tol;
-      const double inv = ok ? rsqrt(d) : 0.0;
-      for (int i = k + 1 + lane; i < n; i += 32) {
-        const double v = ok ? ((i == k + 1) ? d * inv : A[i * n + k + 1] * inv) : 0.0;
-        A[i * n + k + 1] = v;
-        nxt[i] = v;
-      }
-      if (lane == 0) {
-        keepv[k + 1] = ok ? 1 : 0;
-        if (!ok && mode == 0) s_stop = k + 2;
       }
     }
     __syncthreads();
@@ -125,6 +142,155 @@ __global__ void __launch_bounds__(CNT) k_cholesky(const double* __restrict__ G, 
   }
 }
 
+
+// Blocked variant. For each 32-column block: (1) warp 0 factors the 32 x 32 diagonal
+// block in registers (lane r holds row r; the pivot chain needs no barrier and has the
+// FP64 pipe to itself); (2) every thread solves one row of the panel below against the
+// block (right-looking over the block's columns); (3) all threads apply the block's
+// rank-32 update to the trailing triangle, four independent partial sums per entry.
+__global__ void __launch_bounds__(BNT) k_cholesky_blocked(const double* __restrict__ G, int n,
+                                                          int mode, double tol_scale,
+                                                          double* Lrow, double* Lcol,
+                                                          double* invdiag, int* keep_out,
+                                                          int* info, unsigned* err,
+                                                          int use_smem, double* img64,
+                                                          float* img32, float* gimg32) {
+  extern __shared__ double smem[];
+  __shared__ double invv[kMaxL];
+  __shared__ int keepv[kMaxL];
+  __shared__ double s_tol;
+  __shared__ int s_stop;
+  double* A = use_smem ? smem : Lrow;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int np = n + 1;
+  for (int e = tid; e < n * n; e += BNT) {
+    const int i = e / n, j = e - (e / n) * n;
+    if (j <= i) {
+      const double g = G[static_cast<int64_t>(j) * n + i];
+      A[e] = g;
+      if (gimg32) {
+        gimg32[j * np + i] = static_cast<float>(g);
+        gimg32[i * np + j] = static_cast<float>(g);
+      }
+    } else {
+      A[e] = 0.0;
+    }
+  }
+  __syncthreads();
+  if (warp == 0) {
+    double md = 0.0;
+    for (int i = lane; i < n; i += 32) md = fmax(md, A[i * n + i]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) md = fmax(md, __shfl_xor_sync(0xffffffffu, md, o));
+    if (lane == 0) { s_tol = tol_scale * md; s_stop = 0; }
+  }
+  __syncthreads();
+  const double tol = s_tol;
+  for (int c0 = 0; c0 < n; c0 += CB) {
+    const int bw = (n - c0 < CB) ? n - c0 : CB;
+    // (1) diagonal block
+    if (warp == 0) {
+      double a[CB];
+      const int r = c0 + lane;
+#pragma unroll
+      for (int j = 0; j < CB; ++j) a[j] = (lane < bw && j <= lane) ? A[r * n + c0 + j] : 0.0;
+      int stop = 0;
+#pragma unroll
+      for (int j = 0; j < CB; ++j) {
+        if (j < bw) {
+          const double d = __shfl_sync(0xffffffffu, a[j], j);
+          const bool ok = d > tol;                // false for NaN and non-positive pivots
+          const double inv = ok ? rsqrt(d) : 0.0;
+          a[j] = ok ? ((lane == j) ? d * inv : a[j] * inv) : 0.0;   // lanes < j hold zero
+          if (lane == 0) {
+            keepv[c0 + j] = ok ? 1 : 0;
+            invv[c0 + j] = ok ? 1.0 / (d * inv) : 0.0;
+          }
+          if (!ok && mode == 0 && stop == 0) stop = c0 + j + 1;
+#pragma unroll
+          for (int t = j + 1; t < CB; ++t) {
+            const double ltj = __shfl_sync(0xffffffffu, a[j], t);
+            if (lane >= t) a[t] -= a[j] * ltj;
+          }
+        }
+      }
+      if (lane < bw) {
+#pragma unroll
+        for (int j = 0; j < CB; ++j)
+          if (j <= lane) A[r * n + c0 + j] = a[j];
+      }
+      if (lane == 0 && stop) s_stop = stop;
+    }
+    __syncthreads();
+    if (s_stop) break;
+    // (2) panel rows below the block: x <- x L_kk^-T, right-looking over the block columns
+    for (int r = c0 + bw + tid; r < n; r += BNT) {
+      double x[CB];
+#pragma unroll
+      for (int j = 0; j < CB; ++j) x[j] = (j < bw) ? A[r * n + c0 + j] : 0.0;
+#pragma unroll
+      for (int j = 0; j < CB; ++j) {
+        if (j < bw) {
+          x[j] *= invv[c0 + j];
+#pragma unroll
+          for (int t = j + 1; t < CB; ++t)
+            if (t < bw) x[t] -= x[j] * A[(c0 + t) * n + c0 + j];
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < CB; ++j)
+        if (j < bw) A[r * n + c0 + j] = x[j];
+    }
+    __syncthreads();
+    // (3) trailing update: A[i][j] -= sum_t A[i][c0+t] A[j][c0+t], i >= j >= c0 + bw
+    const int base = c0 + bw;
+    const int m = n - base;
+    const int P = m > 0 ? m * (m + 1) / 2 : 0;
+    for (int e = tid; e < P; e += BNT) {
+      int ii = static_cast<int>((sqrtf(8.0f * static_cast<float>(e) + 1.0f) - 1.0f) * 0.5f);
+      while (ii * (ii + 1) / 2 > e) --ii;
+      while ((ii + 1) * (ii + 2) / 2 <= e) ++ii;
+      const int jj = e - ii * (ii + 1) / 2;
+      const double* ri = A + (base + ii) * n + c0;
+      const double* rj = A + (base + jj) * n + c0;
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      int t = 0;
+      for (; t + 4 <= bw; t += 4) {
+        s0 = fma(ri[t], rj[t], s0);
+        s1 = fma(ri[t + 1], rj[t + 1], s1);
+        s2 = fma(ri[t + 2], rj[t + 2], s2);
+        s3 = fma(ri[t + 3], rj[t + 3], s3);
+      }
+      for (; t < bw; ++t) s0 = fma(ri[t], rj[t], s0);
+      A[(base + ii) * n + base + jj] -= (s0 + s1) + (s2 + s3);
+    }
+    __syncthreads();
+  }
+  const int stop = s_stop;
+  if (tid == 0) {
+    *info = stop;
+    if (stop) atomicOr(err, kErrSingular);
+  }
+  if (stop) return;
+  for (int e = tid; e < n * n; e += BNT) {
+    const int i = e / n, j = e - (e / n) * n;
+    const double v = (j <= i) ? A[e] : 0.0;
+    Lrow[e] = v;
+    Lcol[static_cast<int64_t>(j) * n + i] = v;
+    if (img64) img64[j * np + i] = v;
+    if (img32) img32[j * np + i] = static_cast<float>(v);
+  }
+  for (int k = tid; k < n; k += BNT) {
+    keep_out[k] = keepv[k];
+    invdiag[k] = invv[k];
+  }
+}
+
+bool use_blocked() {
+  const char* e = getenv("TRALS_CHOLESKY");
+  return !(e && e[0] == 'l');   // "lookahead" selects the look-ahead variant
+}
+
 }  // namespace
 
 cudaError_t launch_cholesky(const double* G, int n, int mode, double tol_scale, double* Lrow,
@@ -133,13 +299,21 @@ cudaError_t launch_cholesky(const double* G, int n, int mode, double tol_scale, 
   const size_t bytes = static_cast<size_t>(n) * n * sizeof(double);
   const int use_smem = bytes <= 200 * 1024 ? 1 : 0;
   const size_t dyn = use_smem ? bytes : 0;
-  k_cholesky<<<1, CNT, dyn, st>>>(G, n, mode, tol_scale, Lrow, Lcol, invdiag, keep, info, err,
-                                  use_smem, img64, img32, gimg32);
+  if (use_blocked())
+    k_cholesky_blocked<<<1, BNT, dyn, st>>>(G, n, mode, tol_scale, Lrow, Lcol, invdiag, keep,
+                                            info, err, use_smem, img64, img32, gimg32);
+  else
+    k_cholesky_lookahead<<<1, CNT, dyn, st>>>(G, n, mode, tol_scale, Lrow, Lcol, invdiag, keep,
+                                              info, err, use_smem, img64, img32, gimg32);
   return cudaGetLastError();
 }
 
 cudaError_t cholesky_attributes() {
-  return cudaFuncSetAttribute(k_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaError_t e = cudaFuncSetAttribute(k_cholesky_blocked,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_cholesky_lookahead, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              200 * 1024);
 }
 
 }  // namespace trk
