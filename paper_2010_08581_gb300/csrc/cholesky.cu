@@ -2,31 +2,23 @@
 // Used for the normal matrix of the sampled LS (row a6, Alg. 2 LS step) and for the R
 // factor of the Cholesky-based thin QR behind the leverage scores (row a1).
 //
-// Right-looking, one column per step in two phases: all threads apply column k's rank-1
-// update to the trailing triangle (its (m+1)m/2 entries spread evenly over the threads),
-// then warp 0 alone takes the next pivot (FP64 rsqrt) and scales the next column. On
-// GB300 a dependent FP64 FMA takes about 68 cycles and the FP64 pipe issues about 2 FMAs
-// per clock per SM, so the pivot chain is kept off a busy pipe (overlapping it with the
-// trailing update measured 1.3x slower). The matrix lives in shared memory when
-// n*n*8 <= 200 KB, otherwise in place in Lrow.
+// Right-looking with one column of look-ahead. At step k column k is final; warp 0 applies
+// column k's update to column k+1 only, takes its pivot (FP64 rsqrt) and scales it, while
+// warps 1.. apply column k's rank-1 update to the trailing triangle of columns >= k+2
+// (its (m+1)m/2 entries spread evenly over the threads). One barrier per column. The
+// matrix lives in shared memory when n*n*8 <= 200 KB, otherwise in place in Lrow.
 //
 // Besides L (row- and column-major) the kernel can write padded images that the
 // triangular-solve kernel copies straight into shared memory: img[c*(n+1) + r] = L[r][c]
 // in FP64 and/or FP32, and the FP32 image of the symmetric input matrix.
-#include <cstdlib>
-
 #include "common.cuh"
 
 namespace trk {
 namespace {
 
 constexpr int CNT = 512;
-constexpr int CB = 32;   // diagonal block width (one warp)
-constexpr int BNT = 256; // threads of the blocked variant (registers for 32-wide rows)
 
-// Look-ahead variant: warp 0 finishes column k+1 while the other warps update the
-// trailing triangle of columns >= k+2 (one barrier per column).
-__global__ void __launch_bounds__(CNT) k_cholesky_lookahead(const double* __restrict__ G, int n, int mode,
+__global__ void __launch_bounds__(CNT) k_cholesky(const double* __restrict__ G, int n, int mode,
                                                   double tol_scale, double* Lrow, double* Lcol,
                                                   double* invdiag, int* keep_out, int* info,
                                                   unsigned* err, int use_smem,
@@ -142,155 +134,6 @@ __global__ void __launch_bounds__(CNT) k_cholesky_lookahead(const double* __rest
   }
 }
 
-
-// Blocked variant. For each 32-column block: (1) warp 0 factors the 32 x 32 diagonal
-// block in registers (lane r holds row r; the pivot chain needs no barrier and has the
-// FP64 pipe to itself); (2) every thread solves one row of the panel below against the
-// block (right-looking over the block's columns); (3) all threads apply the block's
-// rank-32 update to the trailing triangle, four independent partial sums per entry.
-__global__ void __launch_bounds__(BNT) k_cholesky_blocked(const double* __restrict__ G, int n,
-                                                          int mode, double tol_scale,
-                                                          double* Lrow, double* Lcol,
-                                                          double* invdiag, int* keep_out,
-                                                          int* info, unsigned* err,
-                                                          int use_smem, double* img64,
-                                                          float* img32, float* gimg32) {
-  extern __shared__ double smem[];
-  __shared__ double invv[kMaxL];
-  __shared__ int keepv[kMaxL];
-  __shared__ double s_tol;
-  __shared__ int s_stop;
-  double* A = use_smem ? smem : Lrow;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int np = n + 1;
-  for (int e = tid; e < n * n; e += BNT) {
-    const int i = e / n, j = e - (e / n) * n;
-    if (j <= i) {
-      const double g = G[static_cast<int64_t>(j) * n + i];
-      A[e] = g;
-      if (gimg32) {
-        gimg32[j * np + i] = static_cast<float>(g);
-        gimg32[i * np + j] = static_cast<float>(g);
-      }
-    } else {
-      A[e] = 0.0;
-    }
-  }
-  __syncthreads();
-  if (warp == 0) {
-    double md = 0.0;
-    for (int i = lane; i < n; i += 32) md = fmax(md, A[i * n + i]);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) md = fmax(md, __shfl_xor_sync(0xffffffffu, md, o));
-    if (lane == 0) { s_tol = tol_scale * md; s_stop = 0; }
-  }
-  __syncthreads();
-  const double tol = s_tol;
-  for (int c0 = 0; c0 < n; c0 += CB) {
-    const int bw = (n - c0 < CB) ? n - c0 : CB;
-    // (1) diagonal block
-    if (warp == 0) {
-      double a[CB];
-      const int r = c0 + lane;
-#pragma unroll
-      for (int j = 0; j < CB; ++j) a[j] = (lane < bw && j <= lane) ? A[r * n + c0 + j] : 0.0;
-      int stop = 0;
-#pragma unroll
-      for (int j = 0; j < CB; ++j) {
-        if (j < bw) {
-          const double d = __shfl_sync(0xffffffffu, a[j], j);
-          const bool ok = d > tol;                // false for NaN and non-positive pivots
-          const double inv = ok ? rsqrt(d) : 0.0;
-          a[j] = ok ? ((lane == j) ? d * inv : a[j] * inv) : 0.0;   // lanes < j hold zero
-          if (lane == 0) {
-            keepv[c0 + j] = ok ? 1 : 0;
-            invv[c0 + j] = ok ? 1.0 / (d * inv) : 0.0;
-          }
-          if (!ok && mode == 0 && stop == 0) stop = c0 + j + 1;
-#pragma unroll
-          for (int t = j + 1; t < CB; ++t) {
-            const double ltj = __shfl_sync(0xffffffffu, a[j], t);
-            if (lane >= t) a[t] -= a[j] * ltj;
-          }
-        }
-      }
-      if (lane < bw) {
-#pragma unroll
-        for (int j = 0; j < CB; ++j)
-          if (j <= lane) A[r * n + c0 + j] = a[j];
-      }
-      if (lane == 0 && stop) s_stop = stop;
-    }
-    __syncthreads();
-    if (s_stop) break;
-    // (2) panel rows below the block: x <- x L_kk^-T, right-looking over the block columns
-    for (int r = c0 + bw + tid; r < n; r += BNT) {
-      double x[CB];
-#pragma unroll
-      for (int j = 0; j < CB; ++j) x[j] = (j < bw) ? A[r * n + c0 + j] : 0.0;
-#pragma unroll
-      for (int j = 0; j < CB; ++j) {
-        if (j < bw) {
-          x[j] *= invv[c0 + j];
-#pragma unroll
-          for (int t = j + 1; t < CB; ++t)
-            if (t < bw) x[t] -= x[j] * A[(c0 + t) * n + c0 + j];
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < CB; ++j)
-        if (j < bw) A[r * n + c0 + j] = x[j];
-    }
-    __syncthreads();
-    // (3) trailing update: A[i][j] -= sum_t A[i][c0+t] A[j][c0+t], i >= j >= c0 + bw
-    const int base = c0 + bw;
-    const int m = n - base;
-    const int P = m > 0 ? m * (m + 1) / 2 : 0;
-    for (int e = tid; e < P; e += BNT) {
-      int ii = static_cast<int>((sqrtf(8.0f * static_cast<float>(e) + 1.0f) - 1.0f) * 0.5f);
-      while (ii * (ii + 1) / 2 > e) --ii;
-      while ((ii + 1) * (ii + 2) / 2 <= e) ++ii;
-      const int jj = e - ii * (ii + 1) / 2;
-      const double* ri = A + (base + ii) * n + c0;
-      const double* rj = A + (base + jj) * n + c0;
-      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-      int t = 0;
-      for (; t + 4 <= bw; t += 4) {
-        s0 = fma(ri[t], rj[t], s0);
-        s1 = fma(ri[t + 1], rj[t + 1], s1);
-        s2 = fma(ri[t + 2], rj[t + 2], s2);
-        s3 = fma(ri[t + 3], rj[t + 3], s3);
-      }
-      for (; t < bw; ++t) s0 = fma(ri[t], rj[t], s0);
-      A[(base + ii) * n + base + jj] -= (s0 + s1) + (s2 + s3);
-    }
-    __syncthreads();
-  }
-  const int stop = s_stop;
-  if (tid == 0) {
-    *info = stop;
-    if (stop) atomicOr(err, kErrSingular);
-  }
-  if (stop) return;
-  for (int e = tid; e < n * n; e += BNT) {
-    const int i = e / n, j = e - (e / n) * n;
-    const double v = (j <= i) ? A[e] : 0.0;
-    Lrow[e] = v;
-    Lcol[static_cast<int64_t>(j) * n + i] = v;
-    if (img64) img64[j * np + i] = v;
-    if (img32) img32[j * np + i] = static_cast<float>(v);
-  }
-  for (int k = tid; k < n; k += BNT) {
-    keep_out[k] = keepv[k];
-    invdiag[k] = invv[k];
-  }
-}
-
-bool use_blocked() {
-  const char* e = getenv("TRALS_CHOLESKY");
-  return !(e && e[0] == 'l');   // "lookahead" selects the look-ahead variant
-}
-
 }  // namespace
 
 cudaError_t launch_cholesky(const double* G, int n, int mode, double tol_scale, double* Lrow,
@@ -299,21 +142,13 @@ cudaError_t launch_cholesky(const double* G, int n, int mode, double tol_scale, 
   const size_t bytes = static_cast<size_t>(n) * n * sizeof(double);
   const int use_smem = bytes <= 200 * 1024 ? 1 : 0;
   const size_t dyn = use_smem ? bytes : 0;
-  if (use_blocked())
-    k_cholesky_blocked<<<1, BNT, dyn, st>>>(G, n, mode, tol_scale, Lrow, Lcol, invdiag, keep,
-                                            info, err, use_smem, img64, img32, gimg32);
-  else
-    k_cholesky_lookahead<<<1, CNT, dyn, st>>>(G, n, mode, tol_scale, Lrow, Lcol, invdiag, keep,
-                                              info, err, use_smem, img64, img32, gimg32);
+  k_cholesky<<<1, CNT, dyn, st>>>(G, n, mode, tol_scale, Lrow, Lcol, invdiag, keep, info, err,
+                                  use_smem, img64, img32, gimg32);
   return cudaGetLastError();
 }
 
 cudaError_t cholesky_attributes() {
-  cudaError_t e = cudaFuncSetAttribute(k_cholesky_blocked,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_cholesky_lookahead, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              200 * 1024);
+  return cudaFuncSetAttribute(k_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
 }  // namespace trk
