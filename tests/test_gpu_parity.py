@@ -400,3 +400,20 @@ def test_als_sampled_first_sweeps_match_oracle_fp64(ctx, dims, ranks):
                      init_cores=[to_dev_core(c) for c in init])
     for k in range(len(dims)):
         assert rel(to_paper(out[k]), ref[k]) < 1e-8
+
+
+def test_als_sampled_end_to_end_4way_cosine_mixed(ctx):
+    """The 4-way smooth workload at reduced size: a sum of 20 separable low-frequency cosine
+    products plus 5 % uniform noise, a colour-like mode of size 3 (wide G_(2): I = 3 < L =
+    100), TR ranks 10, mixed precision, against the oracle's final fit."""
+    dims, ranks, J, sweeps = (48, 40, 3, 300), (10, 10, 10, 10), 3000, 4
+    X = inputs.cosine_sum(dims, seed=0)
+    init = np_cores(dims, ranks, 31)
+    ref = orc.tr_als_sampled(X.double().numpy(), init, J, sweeps, 9)
+    e_ref = orc.rel_error(ref, X.double().numpy())
+    Xd = X.to(DEV)
+    out = T.empty_cores(dims, ranks)
+    T.tr_als_sampled(ctx, Xd, ranks, J, sweeps, 9, T.TR_PREC_MIXED, out,
+                     init_cores=[to_dev_core(c) for c in init])
+    e_gpu = T.tr_rel_error(ctx, Xd, ranks, out)
+    assert abs(e_gpu - e_ref) < 0.01 * e_ref
