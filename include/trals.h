@@ -163,6 +163,32 @@ tr_status tr_rel_error(tr_ctx* ctx, const void* X, tr_dtype X_dtype, int N,
 tr_status tr_init_cores(tr_ctx* ctx, int N, const int64_t* dims, const int* ranks,
                         uint64_t seed, int k_begin, double* const* cores, tr_stream stream);
 
+/* One independent problem of a batch (see tr_als_sampled_batched). */
+typedef struct tr_instance {
+  const void* X;                   /* device, row-major [dims[0]]...[dims[N-1]]            */
+  int N;                           /* number of modes, 2..TR_MAX_MODES                      */
+  int64_t dims[TR_MAX_MODES];
+  int ranks[TR_MAX_MODES];         /* ranks[k] = paper's R_{k+1}, each in [1, 16]          */
+  int64_t J;                       /* samples per least-squares problem                     */
+  uint64_t seed;                   /* Philox key of this instance's draws (and its init)    */
+  double* cores[TR_MAX_MODES];     /* device FP64 slice-major [I_k][Rl_k][Rr_k], results   */
+  int init_given;                  /* nonzero: cores[1..N-1] already hold the initial cores */
+} tr_instance;
+
+/* Alg. 2 for `count` independent problems at once, synchronous. Every stage of every
+ * sweep is one launch for all instances (one CTA or a few per instance), so many small
+ * problems fill the GPU together. Each instance performs sweeps * N updates with the
+ * same draws, sizes and arithmetic as tr_als_sampled on that instance alone would with
+ * the same precision, except that the normal equations are summed in one fixed order per
+ * instance (no split over the samples); its results do not depend on the other instances
+ * of the batch. All instances share X_dtype and prec. The sequence of launches is
+ * captured once per batch geometry as a CUDA graph and replayed.
+ * Returns TR_ERR_SINGULAR if any update of any instance met a singular normal matrix
+ * (that core kept). */
+tr_status tr_als_sampled_batched(tr_ctx* ctx, const tr_instance* inst, int count,
+                                 tr_dtype X_dtype, int sweeps, tr_precision prec,
+                                 tr_stream stream);
+
 /* Least-squares step without any device allocation (the paper has no counterpart; this
  * is a deployment variant of tr_solve).
  *

@@ -10,6 +10,7 @@
 #include <string>
 #include <vector>
 
+#include "batched.cuh"
 #include "common.cuh"
 
 struct tr_ctx {
@@ -39,6 +40,10 @@ struct tr_ctx {
   cudaGraphExec_t gexec = nullptr;
   std::vector<uint64_t> gkey;
   bool gprof = false;
+  // CUDA graph of the last batched launch geometry
+  cudaGraphExec_t bexec = nullptr;
+  std::vector<uint64_t> bkey;
+  std::vector<trk::BInst> btab;     // host copy of the instance table
 };
 
 namespace {
@@ -619,6 +624,107 @@ tr_status fold_graph_marks(tr_ctx* ctx) {
   return TR_OK;
 }
 
+// ------------------------------------------------------------------------------------
+// Batched driver.
+// ------------------------------------------------------------------------------------
+size_t img_bytes(int n, bool f32) { return n > 0 ? trsm_image_bytes(n, f32) : 0; }
+
+struct BSizes {
+  int64_t Isum = 0, Imax = 0;
+  int Lmax = 0, n1 = 0, n2 = 0;
+};
+
+BSizes bsizes(const tr_instance& in) {
+  BSizes z;
+  for (int k = 0; k < in.N; ++k) {
+    const int64_t I = in.dims[k];
+    const int L = in.ranks[(k - 1 + in.N) % in.N] * in.ranks[k];
+    z.Isum += I;
+    z.Imax = I > z.Imax ? I : z.Imax;
+    z.Lmax = L > z.Lmax ? L : z.Lmax;
+    const int g1 = I >= L ? L : static_cast<int>(I);
+    z.n1 = g1 > z.n1 ? g1 : z.n1;
+    if (I < L) z.n2 = static_cast<int>(I) > z.n2 ? static_cast<int>(I) : z.n2;
+  }
+  return z;
+}
+
+// Carves one instance's buffers (base == nullptr: measure only).
+void carve_instance(Carver& c, const tr_instance& in, bool f64, BInst& d) {
+  const BSizes z = bsizes(in);
+  const size_t es = f64 ? 8 : 4;
+  int64_t off = 0;
+  double* pb = c.take<double>(z.Isum);
+  double* cb = c.take<double>(z.Isum);
+  for (int k = 0; k < in.N; ++k) {
+    d.p[k] = pb ? pb + off : nullptr;
+    d.cdf[k] = cb ? cb + off : nullptr;
+    off += in.dims[k];
+  }
+  d.A = c.take<char>(static_cast<size_t>(in.J) * z.Lmax * es);
+  d.Y = c.take<char>(static_cast<size_t>(in.J) * z.Imax * es);
+  const size_t L2 = static_cast<size_t>(z.Lmax) * z.Lmax;
+  d.M = c.take<double>(L2);
+  d.BT = c.take<double>(static_cast<size_t>(z.Imax) * z.Lmax);
+  d.Lrow = c.take<double>(L2);
+  d.Lcol = c.take<double>(L2);
+  d.invdiag = c.take<double>(z.Lmax);
+  d.keep = c.take<int>(z.Lmax);
+  d.info = c.take<int>(1);
+  d.limg = c.take<char>(img_bytes(z.Lmax, !f64));
+  d.mimg = f64 ? nullptr : reinterpret_cast<float*>(c.take<char>(img_bytes(z.Lmax, true)));
+  const size_t n12 = static_cast<size_t>(z.n1) * z.n1;
+  d.G1 = c.take<double>(n12);
+  d.L1row = c.take<double>(n12);
+  d.L1col = c.take<double>(n12);
+  d.inv1 = c.take<double>(z.n1);
+  d.keep1 = c.take<int>(z.n1);
+  d.info1 = c.take<int>(1);
+  d.img1 = reinterpret_cast<double*>(c.take<char>(img_bytes(z.n1, false)));
+  if (z.n2 > 0) {
+    const size_t n22 = static_cast<size_t>(z.n2) * z.n2;
+    d.G2 = c.take<double>(n22);
+    d.L2row = c.take<double>(n22);
+    d.L2col = c.take<double>(n22);
+    d.inv2 = c.take<double>(z.n2);
+    d.keep2 = c.take<int>(z.n2);
+    d.info2 = c.take<int>(1);
+    d.img2 = reinterpret_cast<double*>(c.take<char>(img_bytes(z.n2, false)));
+  } else {
+    d.G2 = d.L2row = d.L2col = d.inv2 = d.img2 = nullptr;
+    d.keep2 = d.info2 = nullptr;
+  }
+  d.ell = c.take<double>(z.Imax);
+}
+
+tr_status batched_issue(tr_ctx* ctx, const BLaunch& bl, int nmax_modes, int steps, bool draw,
+                        cudaStream_t st) {
+  if (draw) TR_LAUNCH("b_init_cores", bl_init_cores(bl, st));
+  for (int k = 1; k < nmax_modes; ++k) {
+    TR_LAUNCH("b_gram", bl_gram(bl, 0, k, 1, st));
+    TR_LAUNCH("b_cholesky_leverage", bl_cholesky(bl, 0, k, 1, ctx->d_err, st));
+    if (bl.n2max > 0) {
+      TR_LAUNCH("b_gram", bl_gram(bl, 0, k, 2, st));
+      TR_LAUNCH("b_cholesky_leverage", bl_cholesky(bl, 0, k, 2, ctx->d_err, st));
+    }
+    TR_LAUNCH("b_leverage_rows", bl_leverage_rows(bl, 0, k, ctx->d_err, st));
+  }
+  for (int step = 0; step < steps; ++step) {
+    TR_LAUNCH("b_sample_chain_gather", bl_sample_chain_gather(bl, step, st));
+    TR_LAUNCH("b_contract", bl_contract(bl, step, st));
+    TR_LAUNCH("b_cholesky_solve", bl_cholesky(bl, step, 0, 0, ctx->d_err, st));
+    TR_LAUNCH("b_solve", bl_solve(bl, step, st));
+    TR_LAUNCH("b_gram", bl_gram(bl, step, 0, 1, st));
+    TR_LAUNCH("b_cholesky_leverage", bl_cholesky(bl, step, 0, 1, ctx->d_err, st));
+    if (bl.n2max > 0) {
+      TR_LAUNCH("b_gram", bl_gram(bl, step, 0, 2, st));
+      TR_LAUNCH("b_cholesky_leverage", bl_cholesky(bl, step, 0, 2, ctx->d_err, st));
+    }
+    TR_LAUNCH("b_leverage_rows", bl_leverage_rows(bl, step, 0, ctx->d_err, st));
+  }
+  return TR_OK;
+}
+
 }  // namespace
 
 // ======================================================================================
@@ -684,6 +790,7 @@ void tr_destroy(tr_ctx* ctx) {
   if (ctx->arena) cudaFree(ctx->arena);
   if (ctx->host_stage) cudaFree(ctx->host_stage);
   drop_graph(ctx);
+  if (ctx->bexec) cudaGraphExecDestroy(ctx->bexec);
   if (ctx->cap) cudaStreamDestroy(ctx->cap);
   if (ctx->side) cudaStreamDestroy(ctx->side);
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
@@ -919,6 +1026,117 @@ tr_status tr_als_sampled_host(tr_ctx* ctx, const void* X_host, tr_dtype X_dtype,
   tr_status s = read_device_error(ctx, st);
   TR_TRY(fold_graph_marks(ctx));
   return s;
+}
+
+tr_status tr_als_sampled_batched(tr_ctx* ctx, const tr_instance* inst, int count,
+                                 tr_dtype X_dtype, int sweeps, tr_precision prec,
+                                 tr_stream stream) {
+  TR_TRY(check_ctx(ctx));
+  if (!inst || count < 1) return fail(ctx, TR_ERR_INVALID_ARG, "no instances");
+  if (sweeps < 0) return fail(ctx, TR_ERR_INVALID_ARG, "sweeps=%d", sweeps);
+  if (X_dtype != TR_F32 && X_dtype != TR_F64) return fail(ctx, TR_ERR_INVALID_ARG, "bad X dtype");
+  if (prec != TR_PREC_FP64 && prec != TR_PREC_MIXED)
+    return fail(ctx, TR_ERR_INVALID_ARG, "bad precision");
+  const bool f64 = prec == TR_PREC_FP64;
+  for (int i = 0; i < count; ++i) {
+    const tr_instance& in = inst[i];
+    TR_TRY(check_shape(ctx, in.N, in.dims, in.ranks));
+    if (!in.X) return fail(ctx, TR_ERR_INVALID_ARG, "instance %d: X is NULL", i);
+    if (in.J < 1 || in.J > INT32_MAX)
+      return fail(ctx, TR_ERR_INVALID_ARG, "instance %d: J=%lld", i, static_cast<long long>(in.J));
+    for (int k = 0; k < in.N; ++k)
+      if (!in.cores[k]) return fail(ctx, TR_ERR_INVALID_ARG, "instance %d: cores[%d] is NULL", i, k);
+  }
+  DeviceGuard g(ctx->device);
+  cudaStream_t st = S(stream);
+  // sizes
+  Carver dry(nullptr);
+  dry.take<BInst>(count);
+  dry.take<unsigned>(count);
+  std::vector<BInst> tab(count);
+  for (int i = 0; i < count; ++i) carve_instance(dry, inst[i], f64, tab[i]);
+  TR_TRY(ensure_ws(ctx, dry.off));
+  Carver c(ctx->arena);
+  BInst* dtab = c.take<BInst>(count);
+  unsigned* counters = c.take<unsigned>(count);
+  BLaunch bl{};
+  bl.tab = dtab;
+  bl.count = count;
+  bl.f64 = f64;
+  bl.xf64 = X_dtype == TR_F64;
+  int nmax_modes = 0, steps = 0;
+  bool draw = false;
+  for (int i = 0; i < count; ++i) {
+    const tr_instance& in = inst[i];
+    BInst& d = tab[i];
+    d = BInst{};
+    carve_instance(c, in, f64, d);
+    d.X = in.X;
+    d.N = in.N;
+    d.xf64 = X_dtype == TR_F64;
+    d.nupd = sweeps * in.N;
+    d.draw_init = in.init_given ? 0 : 1;
+    d.J = in.J;
+    d.seed = in.seed;
+    row_major_strides(in.N, in.dims, d.stride);
+    for (int k = 0; k < in.N; ++k) {
+      d.dims[k] = in.dims[k];
+      d.ranks[k] = in.ranks[k];
+      d.cores[k] = in.cores[k];
+    }
+    d.counter = counters + i;
+    const BSizes z = bsizes(in);
+    bl.Jmax = in.J > bl.Jmax ? in.J : bl.Jmax;
+    bl.Lmax = z.Lmax > bl.Lmax ? z.Lmax : bl.Lmax;
+    bl.Imax = z.Imax > bl.Imax ? z.Imax : bl.Imax;
+    bl.n1max = z.n1 > bl.n1max ? z.n1 : bl.n1max;
+    bl.n2max = z.n2 > bl.n2max ? z.n2 : bl.n2max;
+    nmax_modes = in.N > nmax_modes ? in.N : nmax_modes;
+    steps = d.nupd > steps ? d.nupd : steps;
+    draw = draw || d.draw_init;
+  }
+  ctx->btab = tab;
+  TR_CUDA(cudaMemcpyAsync(dtab, ctx->btab.data(), sizeof(BInst) * count, cudaMemcpyHostToDevice,
+                          st));
+  TR_CUDA(cudaMemsetAsync(counters, 0, sizeof(unsigned) * count, st));
+  if (!graphs_enabled()) {
+    TR_TRY(batched_issue(ctx, bl, nmax_modes, steps, draw, st));
+  } else {
+    std::vector<uint64_t> key = {static_cast<uint64_t>(count), static_cast<uint64_t>(bl.Jmax),
+                                 static_cast<uint64_t>(bl.Lmax), static_cast<uint64_t>(bl.Imax),
+                                 static_cast<uint64_t>(bl.n1max), static_cast<uint64_t>(bl.n2max),
+                                 static_cast<uint64_t>(f64), static_cast<uint64_t>(bl.xf64),
+                                 static_cast<uint64_t>(nmax_modes), static_cast<uint64_t>(steps),
+                                 static_cast<uint64_t>(draw), reinterpret_cast<uintptr_t>(dtab),
+                                 static_cast<uint64_t>(ctx->prof)};
+    if (!ctx->bexec || key != ctx->bkey) {
+      if (ctx->bexec) cudaGraphExecDestroy(ctx->bexec);
+      ctx->bexec = nullptr;
+      cudaGraph_t gr = nullptr;
+      const bool prof = ctx->prof;
+      ctx->prof = false;   // no profiler events inside the batched graph
+      TR_CUDA(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
+      tr_status s2 = batched_issue(ctx, bl, nmax_modes, steps, draw, ctx->cap);
+      cudaError_t e = cudaStreamEndCapture(ctx->cap, &gr);
+      ctx->prof = prof;
+      if (s2 != TR_OK) {
+        if (gr) cudaGraphDestroy(gr);
+        return s2;
+      }
+      if (e != cudaSuccess)
+        return fail(ctx, TR_ERR_CUDA, "batched graph capture failed: %s", cudaGetErrorString(e));
+      e = cudaGraphInstantiate(&ctx->bexec, gr, 0);
+      cudaGraphDestroy(gr);
+      if (e != cudaSuccess) {
+        ctx->bexec = nullptr;
+        return fail(ctx, TR_ERR_CUDA, "batched graph instantiation failed: %s",
+                    cudaGetErrorString(e));
+      }
+      ctx->bkey = key;
+    }
+    TR_CUDA(cudaGraphLaunch(ctx->bexec, st));
+  }
+  return read_device_error(ctx, st);
 }
 
 tr_status tr_rel_error(tr_ctx* ctx, const void* X, tr_dtype X_dtype, int N, const int64_t* dims,

@@ -1,0 +1,472 @@
+// Batched stages of TR-ALS-Sampled (Alg. 2 per instance, Alg. 3 + Alg. 4 for the sketch):
+// one launch per stage for every instance of the table; see batched.cuh.
+#include "batched.cuh"
+#include "cholesky_body.cuh"
+#include "draw.cuh"
+#include "trsm_body.cuh"
+
+namespace trk {
+namespace {
+
+// The core being updated (or, with init_k > 0, the core whose initial distribution is
+// formed) and its sizes.
+struct Cur {
+  bool active;
+  int n, Rl, Rr, L;
+  int64_t I;
+};
+
+__device__ __forceinline__ Cur current(const BInst& d, int step, int init_k) {
+  Cur c{};
+  if (init_k > 0) {
+    c.active = d.nupd > 0 && init_k < d.N;
+    c.n = init_k;
+  } else {
+    c.active = step < d.nupd;
+    c.n = c.active ? step % d.N : 0;
+  }
+  if (!c.active) return c;
+  c.Rl = d.ranks[(c.n - 1 + d.N) % d.N];
+  c.Rr = d.ranks[c.n];
+  c.L = c.Rl * c.Rr;
+  c.I = d.dims[c.n];
+  return c;
+}
+
+// ------------------------------------------------------------------------------------
+// Initial cores N(0,1) (same stream as launch_init_normal: stream id = core index).
+// ------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) kb_init_cores(const BInst* __restrict__ tab) {
+  const BInst& d = tab[blockIdx.x];
+  if (d.nupd <= 0 || !d.draw_init) return;
+  const uint32_t k0 = static_cast<uint32_t>(d.seed), k1 = static_cast<uint32_t>(d.seed >> 32);
+  for (int k = 1; k < d.N; ++k) {
+    const int64_t count = d.dims[k] * d.ranks[(k - 1 + d.N) % d.N] * d.ranks[k];
+    const int64_t pairs = (count + 1) / 2;
+    double* out = d.cores[k];
+    for (int64_t q = static_cast<int64_t>(blockIdx.y) * blockDim.x + threadIdx.x; q < pairs;
+         q += static_cast<int64_t>(gridDim.y) * blockDim.x) {
+      double z0, z1;
+      normal_pair(q, static_cast<uint32_t>(k), k0, k1, &z0, &z1);
+      out[2 * q] = z0;
+      if (2 * q + 1 < count) out[2 * q + 1] = z1;
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// Draws (Alg. 3), sampled subchain rows (Alg. 4) and sampled fibres (Alg. 2) for one chunk
+// of one instance's samples: one warp per sample.
+// ------------------------------------------------------------------------------------
+constexpr int SW = 8;     // warps per CTA
+constexpr int SPW = 4;    // samples per warp
+
+template <typename T, typename TX>
+__global__ void __launch_bounds__(SW * 32) kb_sample(const BInst* __restrict__ tab, int step) {
+  __shared__ T sS[SW][kMaxL];
+  __shared__ T sG[SW][kMaxL];
+  __shared__ ChainArgs ca;
+  const BInst& d = tab[blockIdx.x];
+  const Cur cu = current(d, step, 0);
+  if (!cu.active) return;
+  const int64_t j0 = static_cast<int64_t>(blockIdx.y) * SW * SPW;
+  if (j0 >= d.J) return;
+  const int N = d.N, npos = N - 1, n = cu.n;
+  if (threadIdx.x == 0) {
+    ca.npos = npos;
+    for (int m = 0; m < npos; ++m) {
+      const int mode = (n + 1 + m) % N;
+      ca.core[m] = d.cores[mode];
+      ca.I[m] = d.dims[mode];
+      ca.rl[m] = d.ranks[(mode - 1 + N) % N];
+      ca.rr[m] = d.ranks[mode];
+    }
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t k0 = static_cast<uint32_t>(d.seed), k1 = static_cast<uint32_t>(d.seed >> 32);
+  const uint32_t u0 = static_cast<uint32_t>(step), u1 = 0u;
+  const int mode_l = (lane < npos) ? (n + 1 + lane) % N : 0;
+  const TX* __restrict__ X = static_cast<const TX*>(d.X);
+  T* A = static_cast<T*>(d.A);
+  T* Y = static_cast<T*>(d.Y);
+  const int L = cu.L;
+  const int64_t I = cu.I, sn = d.stride[n];
+  for (int s = 0; s < SPW; ++s) {
+    const int64_t j = j0 + warp * SPW + s;
+    if (j >= d.J) break;
+    int64_t mine = 0;
+    double pmine = 1.0;
+    int64_t off = 0;
+    if (lane < npos) {
+      const double u = draw_uniform(j, lane, k0, k1, u0, u1);
+      mine = inverse_cdf(d.cdf[mode_l], d.p[mode_l], d.dims[mode_l], u);
+      pmine = d.p[mode_l][mine];
+      off = mine * d.stride[mode_l];
+    }
+    double pm[kMaxModes];
+    for (int m = 0; m < npos; ++m) pm[m] = __shfl_sync(0xffffffffu, pmine, m);
+    const double wj = sample_weight(d.J, pm, npos);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) off += __shfl_xor_sync(0xffffffffu, off, o);
+    auto index = [&](int m) -> int64_t {
+      return static_cast<int64_t>(__shfl_sync(0xffffffffu, static_cast<int>(mine), m));
+    };
+    warp_slice_chain<T>(ca, index, sS[warp], sG[warp], lane);
+    const T scale = static_cast<T>(wj);
+    for (int e = lane; e < L; e += 32) A[j * L + e] = sS[warp][e] * scale;
+    const TX* src = X + off;
+    for (int64_t e = lane; e < I; e += 32)
+      Y[j * I + e] = static_cast<T>(static_cast<T>(src[e * sn]) * scale);
+    __syncwarp();
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// Normal equations C = A^T [A | Y] per instance, 64 x 64 output tiles over all samples
+// (no split: one fixed summation order per entry); M = C[:, :L], B^T = C[:, L:]^T in FP64.
+// ------------------------------------------------------------------------------------
+constexpr int BM = 64, BN = 64, BK = 16, CT = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(CT) kb_contract(const BInst* __restrict__ tab, int step) {
+  __shared__ T As[BK][BM];
+  __shared__ T Bs[BK][BN];
+  const BInst& d = tab[blockIdx.x];
+  const Cur cu = current(d, step, 0);
+  if (!cu.active) return;
+  const int L = cu.L;
+  const int64_t I = cu.I, ldc = L + I;
+  const int ntr = (L + BM - 1) / BM;
+  const int ntc = static_cast<int>((ldc + BN - 1) / BN);
+  const int t = blockIdx.y;
+  if (t >= ntr * ntc) return;
+  const int r0 = (t / ntc) * BM;
+  const int64_t c0 = static_cast<int64_t>(t % ntc) * BN;
+  const T* __restrict__ A = static_cast<const T*>(d.A);
+  const T* __restrict__ Y = static_cast<const T*>(d.Y);
+  const int64_t J = d.J;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  T acc[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[u][v] = T(0);
+  for (int64_t jb = 0; jb < J; jb += BK) {
+#pragma unroll
+    for (int q = 0; q < (BK * BM) / CT; ++q) {
+      const int e = threadIdx.x + q * CT;
+      const int kk = e / BM, col = e % BM;
+      const int64_t j = jb + kk;
+      const int r = r0 + col;
+      As[kk][col] = (j < J && r < L) ? A[j * L + r] : T(0);
+      const int64_t c = c0 + col;
+      T b = T(0);
+      if (j < J) {
+        if (c < L) b = A[j * L + c];
+        else if (c < ldc) b = Y[j * I + (c - L)];
+      }
+      Bs[kk][col] = b;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      T a[4], b[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) a[u] = As[kk][ty + 16 * u];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) b[v] = Bs[kk][tx + 16 * v];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] += a[u] * b[v];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int r = r0 + ty + 16 * u;
+    if (r >= L) continue;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int64_t c = c0 + tx + 16 * v;
+      if (c < L) d.M[static_cast<int64_t>(r) * L + c] = static_cast<double>(acc[u][v]);
+      else if (c < ldc) d.BT[(c - L) * L + r] = static_cast<double>(acc[u][v]);
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// Gram matrices of the leverage passes (FP64, full square, 32 x 32 tiles over all rows).
+//   pass 1, tall (I >= L): G1 = S^T S (L x L); wide: G1 = S S^T (I x I), S = the I x L rows
+//           (the core at initialisation, B^T during the updates);
+//   pass 2 (wide modes only): G2 = C^T C (I x I), C = the pass-1 factor.
+// ------------------------------------------------------------------------------------
+constexpr int GT = 32, GK = 32, GNT = 256;
+
+__global__ void __launch_bounds__(GNT) kb_gram(const BInst* __restrict__ tab, int step, int init_k,
+                                               int pass) {
+  __shared__ double P[GK][GT + 1];
+  __shared__ double Q[GK][GT + 1];
+  const BInst& d = tab[blockIdx.x];
+  const Cur cu = current(d, step, init_k);
+  if (!cu.active) return;
+  const bool tall = cu.I >= cu.L;
+  if (pass == 2 && tall) return;
+  const double* S = init_k > 0 ? d.cores[cu.n] : d.BT;
+  const double* src;
+  int64_t K, lda;
+  int n;
+  bool trans;
+  double* G;
+  if (pass == 1) {
+    src = S; lda = cu.L; G = d.G1;
+    if (tall) { n = cu.L; K = cu.I; trans = false; }
+    else { n = static_cast<int>(cu.I); K = cu.L; trans = true; }
+  } else {
+    src = d.L1row; lda = cu.I; G = d.G2;
+    n = static_cast<int>(cu.I); K = cu.I; trans = false;
+  }
+  const int nt = (n + GT - 1) / GT;
+  const int t = blockIdx.y;
+  if (t >= nt * nt) return;
+  const int p0 = (t / nt) * GT, q0 = (t % nt) * GT;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  double acc[4] = {0, 0, 0, 0};
+  for (int64_t kb = 0; kb < K; kb += GK) {
+#pragma unroll
+    for (int r = 0; r < (GK * GT) / GNT; ++r) {
+      const int e = threadIdx.x + r * GNT;
+      int kk, col;
+      if (!trans) { kk = e / GT; col = e % GT; } else { col = e / GK; kk = e % GK; }
+      const int64_t k = kb + kk;
+      const int p = p0 + col, q = q0 + col;
+      double vp = 0.0, vq = 0.0;
+      if (k < K) {
+        if (p < n) vp = trans ? src[p * lda + k] : src[k * lda + p];
+        if (q < n) vq = trans ? src[q * lda + k] : src[k * lda + q];
+      }
+      P[kk][col] = vp;
+      Q[kk][col] = vq;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < GK; ++kk) {
+      const double b = Q[kk][tx];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc[u] += P[kk][ty + 8 * u] * b;
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int p = p0 + ty + 8 * u, q = q0 + tx;
+    if (p < n && q < n) G[static_cast<int64_t>(p) * n + q] = acc[u];
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// Cholesky factorisations, one CTA per instance.
+// ------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(CNT) kb_cholesky(const BInst* __restrict__ tab, int step,
+                                                   int init_k, int which, unsigned* err,
+                                                   int smem_bytes, int mixed) {
+  extern __shared__ double smem[];
+  const BInst& d = tab[blockIdx.x];
+  const Cur cu = current(d, step, init_k);
+  if (!cu.active) return;
+  const double eps = 2.220446049250313e-16;
+  const bool tall = cu.I >= cu.L;
+  if (which == 0) {
+    const int n = cu.L;
+    double* A = (static_cast<int64_t>(n) * n * 8 <= smem_bytes) ? smem : d.Lrow;
+    cholesky_cta(d.M, n, 0, static_cast<double>(n) * eps, A, d.Lrow, d.Lcol, d.invdiag, d.keep,
+                 d.info, err, mixed ? nullptr : static_cast<double*>(d.limg),
+                 mixed ? static_cast<float*>(d.limg) : nullptr, mixed ? d.mimg : nullptr);
+    return;
+  }
+  const double tol = static_cast<double>(cu.I > cu.L ? cu.I : cu.L) * eps;
+  if (which == 1) {
+    const int n = tall ? cu.L : static_cast<int>(cu.I);
+    double* A = (static_cast<int64_t>(n) * n * 8 <= smem_bytes) ? smem : d.L1row;
+    cholesky_cta(d.G1, n, 1, tol, A, d.L1row, d.L1col, d.inv1, d.keep1, d.info1, err, d.img1,
+                 nullptr, nullptr);
+    return;
+  }
+  if (tall) return;
+  const int n = static_cast<int>(cu.I);
+  double* A = (static_cast<int64_t>(n) * n * 8 <= smem_bytes) ? smem : d.L2row;
+  cholesky_cta(d.G2, n, 1, tol, A, d.L2row, d.L2col, d.inv2, d.keep2, d.info2, err, d.img2,
+               nullptr, nullptr);
+}
+
+// ------------------------------------------------------------------------------------
+// Triangular solves: the LS solve (mode 2 mixed / mode 1 FP64) writing the new core, and
+// the leverage rows with the fused p / CDF step.
+// ------------------------------------------------------------------------------------
+// Runtime choice of the register rows (QN = ceil(n/32)) and of shared-memory staging;
+// n <= 128 always fits in shared memory and n >= 161 never does.
+template <typename T, int NB>
+__device__ __forceinline__ void trsm_dispatch(bool smem, unsigned char* sm, int64_t cta, int n,
+                                              const double* Lrow, const double* Lcol,
+                                              const double* invdiag, const int* info,
+                                              int64_t nvec, const double* rhs, int64_t ld,
+                                              int mode, const double* M, const T* Limg,
+                                              const float* Mimg, int Rl, int Rr,
+                                              double* core_out, double* ell,
+                                              const CdfEpilogue& ep, int nctas) {
+#define TB_ARGS sm, cta, n, Lrow, Lcol, invdiag, info, nvec, rhs, ld, mode, M, Limg, Mimg, Rl, Rr, \
+                core_out, ell, ep, nctas
+  switch ((n + 31) / 32) {
+    case 1: trsm_cta<T, 1, NB, true>(TB_ARGS); break;
+    case 2: trsm_cta<T, 2, NB, true>(TB_ARGS); break;
+    case 3: trsm_cta<T, 3, NB, true>(TB_ARGS); break;
+    case 4: trsm_cta<T, 4, NB, true>(TB_ARGS); break;
+    case 5:
+      if (smem) trsm_cta<T, 5, NB, true>(TB_ARGS);
+      else trsm_cta<T, 5, NB, false>(TB_ARGS);
+      break;
+    case 6: trsm_cta<T, 6, NB, false>(TB_ARGS); break;
+    case 7: trsm_cta<T, 7, NB, false>(TB_ARGS); break;
+    case 8: trsm_cta<T, 8, NB, false>(TB_ARGS); break;
+    default: break;
+  }
+#undef TB_ARGS
+}
+
+template <typename T, int NB>
+__global__ void __launch_bounds__(TW * 32) kb_solve(const BInst* __restrict__ tab, int step,
+                                                    int smem_bytes) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const BInst& d = tab[blockIdx.x];
+  const Cur cu = current(d, step, 0);
+  if (!cu.active) return;
+  const int n = cu.L;
+  const int64_t per = static_cast<int64_t>(TW) * NB;
+  const int nctas = static_cast<int>((cu.I + per - 1) / per);
+  if (static_cast<int>(blockIdx.y) >= nctas) return;
+  const int mode = sizeof(T) == 4 ? 2 : 1;
+  const CdfEpilogue none{};
+  const bool smem = staged_bytes<T>(n, mode) <= static_cast<size_t>(smem_bytes);
+  trsm_dispatch<T, NB>(smem, sm, blockIdx.y, n, d.Lrow, d.Lcol, d.invdiag, d.info, cu.I, d.BT, n,
+                       mode, d.M, static_cast<const T*>(d.limg), d.mimg, cu.Rl, cu.Rr,
+                       d.cores[cu.n], nullptr, none, nctas);
+}
+
+__global__ void __launch_bounds__(TW * 32) kb_rows(const BInst* __restrict__ tab, int step,
+                                                   int init_k, unsigned* err, int smem_bytes) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const BInst& d = tab[blockIdx.x];
+  const Cur cu = current(d, step, init_k);
+  if (!cu.active) return;
+  const bool tall = cu.I >= cu.L;
+  const int n = tall ? cu.L : static_cast<int>(cu.I);
+  const double* rhs = tall ? (init_k > 0 ? d.cores[cu.n] : d.BT) : d.L1row;
+  const int64_t ld = tall ? cu.L : cu.I;
+  const double* Lr = tall ? d.L1row : d.L2row;
+  const double* Lc = tall ? d.L1col : d.L2col;
+  const double* iv = tall ? d.inv1 : d.inv2;
+  const double* im = tall ? d.img1 : d.img2;
+  const int nctas = static_cast<int>((cu.I + TW - 1) / TW);
+  if (static_cast<int>(blockIdx.y) >= nctas) return;
+  const CdfEpilogue ep{d.counter, d.p[cu.n], d.cdf[cu.n], init_k > 0 ? nullptr : d.info, err};
+  const bool smem = staged_bytes<double>(n, 0) <= static_cast<size_t>(smem_bytes);
+  trsm_dispatch<double, 1>(smem, sm, blockIdx.y, n, Lr, Lc, iv, nullptr, cu.I, rhs, ld, 0, nullptr,
+                           im, nullptr, 1, 1, nullptr, d.ell, ep, nctas);
+}
+
+constexpr int kDyn = 200 * 1024;
+
+int smem_for_cholesky(int nmax) {
+  const int64_t need = static_cast<int64_t>(nmax) * nmax * 8;
+  return need <= kDyn ? static_cast<int>(need) : 0;
+}
+
+}  // namespace
+
+cudaError_t bl_init_cores(const BLaunch& b, cudaStream_t st) {
+  dim3 grid(b.count, 16);
+  kb_init_cores<<<grid, 256, 0, st>>>(b.tab);
+  return cudaGetLastError();
+}
+
+cudaError_t bl_sample_chain_gather(const BLaunch& b, int step, cudaStream_t st) {
+  const int64_t per = SW * SPW;
+  dim3 grid(b.count, static_cast<unsigned>((b.Jmax + per - 1) / per));
+  if (b.f64 && b.xf64) kb_sample<double, double><<<grid, SW * 32, 0, st>>>(b.tab, step);
+  else if (b.f64) kb_sample<double, float><<<grid, SW * 32, 0, st>>>(b.tab, step);
+  else if (b.xf64) kb_sample<float, double><<<grid, SW * 32, 0, st>>>(b.tab, step);
+  else kb_sample<float, float><<<grid, SW * 32, 0, st>>>(b.tab, step);
+  return cudaGetLastError();
+}
+
+cudaError_t bl_contract(const BLaunch& b, int step, cudaStream_t st) {
+  const int ntr = (b.Lmax + BM - 1) / BM;
+  const int64_t ntc = (b.Lmax + b.Imax + BN - 1) / BN;
+  dim3 grid(b.count, static_cast<unsigned>(ntr * ntc));
+  if (b.f64) kb_contract<double><<<grid, CT, 0, st>>>(b.tab, step);
+  else kb_contract<float><<<grid, CT, 0, st>>>(b.tab, step);
+  return cudaGetLastError();
+}
+
+cudaError_t bl_cholesky(const BLaunch& b, int step, int init_k, int which, unsigned* err,
+                        cudaStream_t st) {
+  const int nmax = which == 0 ? b.Lmax : (which == 1 ? b.n1max : b.n2max);
+  if (nmax <= 0) return cudaSuccess;
+  const int dyn = smem_for_cholesky(nmax);
+  kb_cholesky<<<b.count, CNT, dyn, st>>>(b.tab, step, init_k, which, err, dyn, b.f64 ? 0 : 1);
+  return cudaGetLastError();
+}
+
+// Dynamic shared memory for the solve kernels: enough for every instance that takes the
+// shared-memory path (every n <= 128 does; n >= 161 never does).
+template <typename T>
+int solve_smem(int nmax, int mode) {
+  const int n = nmax < 160 ? nmax : 160;
+  const size_t need = staged_bytes<T>(n, mode);
+  return need <= static_cast<size_t>(kDyn) ? static_cast<int>(need) : kDyn;
+}
+
+cudaError_t bl_solve(const BLaunch& b, int step, cudaStream_t st) {
+  if (b.f64) {
+    const int dyn = solve_smem<double>(b.Lmax, 1);
+    dim3 grid(b.count, static_cast<unsigned>((b.Imax + TW - 1) / TW));
+    kb_solve<double, 1><<<grid, TW * 32, dyn, st>>>(b.tab, step, dyn);
+  } else {
+    const int dyn = solve_smem<float>(b.Lmax, 2);
+    dim3 grid(b.count, static_cast<unsigned>((b.Imax + 2 * TW - 1) / (2 * TW)));
+    kb_solve<float, 2><<<grid, TW * 32, dyn, st>>>(b.tab, step, dyn);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t bl_gram(const BLaunch& b, int step, int init_k, int pass, cudaStream_t st) {
+  const int nmax = pass == 1 ? b.n1max : b.n2max;
+  if (nmax <= 0) return cudaSuccess;
+  const int nt = (nmax + GT - 1) / GT;
+  dim3 grid(b.count, nt * nt);
+  kb_gram<<<grid, GNT, 0, st>>>(b.tab, step, init_k, pass);
+  return cudaGetLastError();
+}
+
+cudaError_t bl_leverage_rows(const BLaunch& b, int step, int init_k, unsigned* err,
+                             cudaStream_t st) {
+  const int nmax = b.n1max > b.n2max ? b.n1max : b.n2max;
+  const int dyn = solve_smem<double>(nmax, 0);
+  dim3 grid(b.count, static_cast<unsigned>((b.Imax + TW - 1) / TW));
+  kb_rows<<<grid, TW * 32, dyn, st>>>(b.tab, step, init_k, err, dyn);
+  return cudaGetLastError();
+}
+
+cudaError_t batched_attributes() {
+  cudaError_t e = cudaFuncSetAttribute(kb_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       kDyn);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(kb_solve<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kDyn);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(kb_solve<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kDyn);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(kb_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, kDyn);
+}
+
+}  // namespace trk

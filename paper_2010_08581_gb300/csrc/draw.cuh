@@ -16,6 +16,22 @@ __device__ __forceinline__ double draw_uniform(int64_t j, int m, uint32_t k0, ui
   return (m & 1) ? u53(r.z, r.w) : u53(r.x, r.y);
 }
 
+// N(0,1) pair q of the core initialiser: Philox4x32-10 counter (q lo, q hi, stream_id,
+// 0x4E4F524D), two 53-bit uniforms u1, u2; r = sqrt(-2 ln(1-u1)); (r cos 2 pi u2,
+// r sin 2 pi u2) (Box & Muller, 1958).
+__device__ __forceinline__ void normal_pair(int64_t q, uint32_t stream_id, uint32_t k0,
+                                            uint32_t k1, double* z0, double* z1) {
+  const u32x4 r = philox4x32_10(u32x4{static_cast<uint32_t>(q), static_cast<uint32_t>(q >> 32),
+                                      stream_id, 0x4E4F524Du},
+                                k0, k1);
+  const double u1 = u53(r.x, r.y), u2 = u53(r.z, r.w);
+  const double rad = sqrt(-2.0 * log1p(-u1));
+  double s, c;
+  sincospi(2.0 * u2, &s, &c);
+  *z0 = rad * c;
+  *z1 = rad * s;
+}
+
 // Smallest i with u < cdf[i]; if rounding leaves cdf[I-1] <= u, the largest i with p > 0.
 __device__ __forceinline__ int64_t inverse_cdf(const double* cdf, const double* p, int64_t I,
                                                double u) {

@@ -161,6 +161,7 @@ cudaError_t cholesky_attributes();
 cudaError_t trsm_attributes();
 cudaError_t normal_eq_tc_attributes();
 cudaError_t sample_chain_attributes();
+cudaError_t batched_attributes();
 
 cudaError_t init_kernel_attributes(const char** which) {
   cudaError_t e = cholesky_attributes();
@@ -171,6 +172,8 @@ cudaError_t init_kernel_attributes(const char** which) {
   if (e != cudaSuccess) { *which = "normal_eq_tc"; return e; }
   e = sample_chain_attributes();
   if (e != cudaSuccess) { *which = "sample_chain"; return e; }
+  e = batched_attributes();
+  if (e != cudaSuccess) { *which = "batched"; return e; }
   e = fit_attributes();
   if (e != cudaSuccess) *which = "fit";
   return e;

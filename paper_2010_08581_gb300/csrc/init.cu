@@ -1,14 +1,10 @@
 // The N(0,1) core initialiser (Sec. 3: cores drawn i.i.d. N(0,1)).
-#include "common.cuh"
+#include "draw.cuh"
 
 namespace trk {
 namespace {
 
-// ------------------------------------------------------------------------------------
-// N(0,1) by Philox4x32-10 + Box-Muller (Box & Muller, 1958): pair q uses counter
-// (q lo, q hi, stream_id, 0x4E4F524D), two 53-bit uniforms u1, u2; r = sqrt(-2 ln(1-u1)),
-// (r cos 2 pi u2, r sin 2 pi u2).
-// ------------------------------------------------------------------------------------
+// N(0,1) by Philox4x32-10 + Box-Muller, one pair per thread (normal_pair in draw.cuh).
 __global__ void k_init_normal(double* __restrict__ out, int64_t count, uint32_t k0, uint32_t k1,
                               uint32_t stream_id, const uint64_t* __restrict__ seed_dev) {
   const int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -18,15 +14,10 @@ __global__ void k_init_normal(double* __restrict__ out, int64_t count, uint32_t 
     k0 = static_cast<uint32_t>(s);
     k1 = static_cast<uint32_t>(s >> 32);
   }
-  const u32x4 r = philox4x32_10(u32x4{static_cast<uint32_t>(q), static_cast<uint32_t>(q >> 32),
-                                      stream_id, 0x4E4F524Du},
-                                k0, k1);
-  const double u1 = u53(r.x, r.y), u2 = u53(r.z, r.w);
-  const double rad = sqrt(-2.0 * log1p(-u1));
-  double s, c;
-  sincospi(2.0 * u2, &s, &c);
-  out[2 * q] = rad * c;
-  if (2 * q + 1 < count) out[2 * q + 1] = rad * s;
+  double z0, z1;
+  normal_pair(q, stream_id, k0, k1, &z0, &z1);
+  out[2 * q] = z0;
+  if (2 * q + 1 < count) out[2 * q + 1] = z1;
 }
 
 }  // namespace

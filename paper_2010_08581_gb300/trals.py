@@ -33,6 +33,16 @@ PP = ctypes.POINTER(c_vp)
 P64 = ctypes.POINTER(c_i64)
 PI = ctypes.POINTER(c_int)
 
+MAX_MODES = 16
+
+
+class TrInstance(ctypes.Structure):
+    """Mirror of ``tr_instance`` in include/trals.h."""
+    _fields_ = [("X", c_vp), ("N", c_int), ("dims", c_i64 * MAX_MODES),
+                ("ranks", c_int * MAX_MODES), ("J", c_i64), ("seed", c_u64),
+                ("cores", c_vp * MAX_MODES), ("init_given", c_int)]
+
+
 # name -> (restype, argtypes); mirrors include/trals.h
 SIGNATURES = {
     "tr_create": (c_int, [ctypes.POINTER(c_vp), c_int, c_sz]),
@@ -55,6 +65,8 @@ SIGNATURES = {
     "tr_rel_error": (c_int, [c_vp, c_vp, c_int, c_int, P64, PI, PP, ctypes.POINTER(c_dbl),
                              c_vp]),
     "tr_init_cores": (c_int, [c_vp, c_int, P64, PI, c_u64, c_int, PP, c_vp]),
+    "tr_als_sampled_batched": (c_int, [c_vp, ctypes.POINTER(TrInstance), c_int, c_int, c_int,
+                                       c_int, c_vp]),
     "tr_solve_noalloc": (c_int, [c_vp, c_vp, c_int, c_i64, c_int, c_int, c_i64, c_int, c_vp,
                                  c_vp, c_vp]),
     "tr_profile_begin": (c_int, [c_vp]),
@@ -252,6 +264,31 @@ def tr_als_sampled_host(ctx: Context, X_host: torch.Tensor, ranks, J: int, sweep
     ctx.check(load().tr_als_sampled_host(ctx.handle, c_vp(X_host.data_ptr()), _dt(X_host),
                                          len(dims), d, r, J, sweeps, seed, prec, ip, cp,
                                          _stream(stream)))
+
+
+def tr_als_sampled_batched(ctx: Context, problems, sweeps: int, prec: int, stream=None):
+    """problems: list of dicts with keys X (device tensor), ranks, J, seed, cores (list of
+    device FP64 (I, Rl, Rr) tensors receiving the result) and optional init (bool: the
+    cores already hold the initial cores). All X share one dtype."""
+    arr = (TrInstance * len(problems))()
+    dt = None
+    for i, pr in enumerate(problems):
+        X = pr["X"]
+        dt = _dt(X) if dt is None else dt
+        if _dt(X) != dt:
+            raise TypeError("all X of a batch must share one dtype")
+        inst = arr[i]
+        inst.X = X.data_ptr()
+        inst.N = X.ndim
+        for k, d in enumerate(X.shape):
+            inst.dims[k] = int(d)
+            inst.ranks[k] = int(pr["ranks"][k])
+            inst.cores[k] = pr["cores"][k].data_ptr()
+        inst.J = int(pr["J"])
+        inst.seed = int(pr["seed"])
+        inst.init_given = 1 if pr.get("init", False) else 0
+    ctx.check(load().tr_als_sampled_batched(ctx.handle, arr, len(problems), dt, sweeps, prec,
+                                            _stream(stream)))
 
 
 def tr_rel_error(ctx: Context, X: torch.Tensor, ranks, cores: List[torch.Tensor], stream=None):
