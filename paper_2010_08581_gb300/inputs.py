@@ -132,3 +132,20 @@ WORKLOADS = {
                             rel_noise=1e-2, dtype=torch.float32, seed=1, init_seed=1,
                             sample_seed=2),
 }
+
+
+def batched_workload(count: int, seed: int, device="cpu", imin=32, imax=200, rmin=3, rmax=8,
+                     rel_noise=1e-3, j_factor=10):
+    """Independent 3-way FP32 problems: each I_n ~ U{imin..imax}, each rank ~ U{rmin..rmax},
+    X = TR(N(0,1) cores) + noise of total norm rel_noise * ||TR||, J = j_factor * max_k L_k.
+    Returns a list of dicts (dims, ranks, J, X, seed)."""
+    g = _gen(seed)
+    out = []
+    for i in range(count):
+        dims = tuple(int(v) for v in torch.randint(imin, imax + 1, (3,), generator=g))
+        ranks = tuple(int(v) for v in torch.randint(rmin, rmax + 1, (3,), generator=g))
+        L = max(ranks[(k - 1) % 3] * ranks[k] for k in range(3))
+        X, _ = tr_plus_noise(dims, ranks, seed=seed * 100003 + i, rel_noise=rel_noise,
+                             device=device, dtype=torch.float32)
+        out.append(dict(dims=dims, ranks=ranks, J=j_factor * L, X=X, seed=seed * 7919 + i))
+    return out
