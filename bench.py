@@ -345,6 +345,86 @@ def run_batched(T, plain_fp64, dev, steps, warmup, stream):
             "speedup_vs_plain_fp64": round(rate / plain_rate, 1)}
 
 
+def run_serving(T, dev, seconds, rate=200.0, warmup_s=3.0, pool_size=128, seed=0):
+    """Continuous-batching server under a Poisson stream of decomposition requests: N in
+    {3, 4, 5}, entries log-uniform in [1e5, 1e8], ranks ~ U{4..16} per mode, J = 10 max L,
+    FP32 TR(N(0,1) cores) + 1e-2 noise, stop at fit change < 1e-4 (cap 30 sweeps), 150 GB
+    admission budget. X is materialised in HBM before the stream starts: a pool of
+    `pool_size` tensors with shapes from that distribution; request i uses pool entry
+    i mod pool_size with its own seed. Latency = scheduled arrival -> result ready."""
+    shapes = inputs.serving_requests(pool_size, seed)
+    pool = []
+    for i, sh in enumerate(shapes):
+        X, _ = inputs.tr_plus_noise(sh["dims"], sh["ranks"], seed=10_000 + i, rel_noise=1e-2,
+                                    device=dev)
+        pool.append((X, sh))
+    torch.cuda.synchronize()
+    pool_bytes = sum(X.numel() * 4 for X, _ in pool)
+    total_s = warmup_s + seconds
+    arrivals = [a for a in inputs.poisson_arrivals(int(rate * total_s * 1.5) + 16, rate, seed)
+                if a < total_s]
+    srv = T.Server(device=dev.index or 0, hbm_budget_bytes=150 << 30, arena_bytes=16 << 30,
+                   max_slots=1024, max_modes=5, max_dim=1024, max_rank=16, max_samples=2560,
+                   max_sweeps=30, fit_tol=1e-4, X_dtype=T.TR_F32, prec=T.TR_PREC_MIXED)
+    srv.start()
+    subs = []
+    t_start = time.monotonic_ns()
+    for i, at in enumerate(arrivals):
+        due = t_start + int(at * 1e9)
+        now = time.monotonic_ns()
+        if due > now:
+            time.sleep((due - now) / 1e9)
+        X, sh = pool[i % pool_size]
+        cores = T.empty_cores(sh["dims"], sh["ranks"], device=dev)
+        subs.append((srv.submit(X, sh["ranks"], sh["J"], 1 + i, cores), due, at, sh))
+    t_arrivals_end = time.monotonic_ns()
+    results = []
+    for t, due, at, sh in subs:
+        res = srv.wait(t, timeout_ms=300_000)
+        results.append((res, due, at, sh))
+        srv.release(t)
+    t_end = time.monotonic_ns()
+    st = srv.stats()
+    srv.stop()
+    srv.close()
+    meas = [(r, due, sh) for r, due, at, sh in results if at >= warmup_s and r["done"]]
+    lat = sorted((r["t_done_ns"] - due) / 1e6 for r, due, sh in meas)
+    queue = sorted((r["t_admit_ns"] - r["t_submit_ns"]) / 1e6 for r, due, sh in meas)
+    win_s = seconds
+    sweeps = [r["sweeps"] for r, _, _ in meas]
+    n_upd = sum(r["sweeps"] * len(sh["dims"]) for r, _, sh in meas)
+    conv = sum(1 for r, _, _ in meas if r["status"] == T.TR_OK)
+    late = max(0.0, (t_arrivals_end - t_start) / 1e9 - total_s)
+    return {
+        "workload": "Poisson stream, mean 200 req/s, N ~ U{3,4,5}, entries log-uniform in "
+                    "[1e5, 1e8], ranks ~ U{4..16}, J = 10 max_k L_k, FP32 TR + 1e-2 noise, "
+                    "stop at |fit change| < 1e-4 (cap 30 sweeps), 150 GB HBM budget, mixed "
+                    "precision, native worker thread",
+        "offered_req_per_s": rate, "seconds": seconds, "warmup_s": warmup_s,
+        "requests_measured": len(meas), "requests_total": len(results),
+        "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 2) if lat else None,
+                       "p99": round(float(np.percentile(lat, 99)), 2) if lat else None,
+                       "max": round(lat[-1], 2) if lat else None,
+                       "what": "scheduled arrival -> end of the tick that finished it"},
+        "admission_wait_ms": {"p50": round(float(np.percentile(queue, 50)), 3) if queue else None,
+                              "p99": round(float(np.percentile(queue, 99)), 3) if queue else None},
+        "throughput_req_per_s": round(len(meas) / win_s, 2),
+        "sweeps_per_s": round(sum(sweeps) / win_s, 1),
+        "updates_per_s": round(n_upd / win_s, 1),
+        "sweeps_per_request": {"mean": round(float(np.mean(sweeps)), 2) if sweeps else None,
+                               "p50": float(np.percentile(sweeps, 50)) if sweeps else None,
+                               "max": max(sweeps) if sweeps else None},
+        "converged_fraction": round(conv / max(1, len(meas)), 3),
+        "median_fit": round(float(np.median([r["fit"] for r, _, _ in meas])), 5) if meas else None,
+        "ticks": st["ticks"], "ms_per_tick": round(st["tick_ns"] / 1e6 / max(1, st["ticks"]), 3),
+        "peak_active": st["peak_active"],
+        "peak_charged_gb": round(st["peak_charged_bytes"] / 1e9, 3),
+        "x_pool": {"tensors": pool_size, "gb": round(pool_bytes / 1e9, 2)},
+        "drain_s": round((t_end - t_arrivals_end) / 1e9, 2),
+        "arrival_lateness_s": round(late, 3),
+    }
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -504,6 +584,10 @@ def run_ours(args):
     if not args.skip_batched and world == 1:
         batched = run_batched(T, plain_fp64, dev, max(1, min(args.steps, 5)), 1, stream)
 
+    serving = None
+    if not args.skip_serving and world == 1 and args.serve_seconds > 0:
+        serving = run_serving(T, dev, args.serve_seconds)
+
     peaks = measured_peaks()
     roof = roofline(prof, wl, peaks)
     tot_ms = sum(v[0] for v in prof.values())
@@ -536,6 +620,7 @@ def run_ours(args):
                            sorted(prof.items(), key=lambda kv: -kv[1][0])},
             "fp64_gpu_form": fp64,
             "batched_512": batched,
+            "serving": serving,
             "cpu_baseline": cpu,
             "clocks": clk,
         }
@@ -557,6 +642,8 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-batched", action="store_true")
+    ap.add_argument("--skip-serving", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=20.0)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

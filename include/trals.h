@@ -7,12 +7,12 @@
  * ---------------------------------------
  *  - Modes are 0-based: k = 0..N-1. ranks[k] is the paper's R_{k+1}; core k has left rank
  *    Rl_k = ranks[(k-1+N) % N] and right rank Rr_k = ranks[k] (the paper's
- *    G^(k+1) in R^{R_k x I_{k+1} x R_{k+1}}, Sec. 2.1, eq. 1).
+ *    G^(k+1) in R^{R_k x I_{k+1} x R_{k+1}}, Sec. 3.1, eq. 1).
  *  - Cores are FP64, slice-major: core_k[i][a][b] at offset (i*Rl_k + a)*Rr_k + b, so the
  *    lateral slice G(:, i, :) is one contiguous Rl_k x Rr_k row-major block.
  *  - X is dense, row-major (last mode fastest), FP32 or FP64.
  *  - Sampled multi-indices idx[J][N-1] (int32) are in ring order: position m holds the
- *    index of mode (k+1+m) % N (Def. 3.1 / Alg. 3).
+ *    index of mode (k+1+m) % N (Def. 2 / Alg. 3).
  *  - Design rows: row j, column c = a + Rl_k*b holds the (b, a) entry of the Rr_k x Rl_k
  *    slice product of Alg. 4 (the paper's column overline{r_{k-1} r_k}).
  *  - All tensor arguments are DEVICE pointers owned by the caller unless stated; arrays of
@@ -44,7 +44,7 @@ typedef enum tr_status {
   TR_ERR_SINGULAR = 4,     /* non-positive pivot in the normal equations, or zero core */
   TR_ERR_TIMEOUT = 5,      /* reserved for bounded device waits                         */
   TR_ERR_CUDA = 6,         /* a CUDA runtime call failed (see tr_last_error)            */
-  TR_ERR_NOT_CONVERGED = 7 /* reserved                                                  */
+  TR_ERR_NOT_CONVERGED = 7 /* a served request stopped at its sweep cap (result kept)    */
 } tr_status;
 
 typedef enum tr_dtype { TR_F32 = 0, TR_F64 = 1 } tr_dtype;
@@ -77,7 +77,7 @@ const char* tr_last_error(const tr_ctx* ctx);
  * (TR_ERR_SINGULAR, TR_ERR_INVALID_ARG for out-of-range sample indices, or TR_OK). */
 tr_status tr_status_sync(tr_ctx* ctx, tr_stream stream);
 
-/* Row a1 -- sampling distribution of one core (Def. 3.3; eq. for p^(n); Alg. 2, "compute
+/* Row a1 -- sampling distribution of one core (Def. 4; eq. for p^(n); Alg. 2, "compute
  * distributions" and "update n-th distribution").
  * core  : FP64 [I][Rl][Rr]; the matrix G_(2) is I x (Rl*Rr).
  * p     : FP64 [I] out, p[i] = ell_i(G_(2)) / sum_i ell_i(G_(2)).
@@ -88,7 +88,7 @@ tr_status tr_status_sync(tr_ctx* ctx, tr_stream stream);
 tr_status tr_leverage(tr_ctx* ctx, const double* core, int64_t I, int Rl, int Rr,
                       double* p, double* cdf, tr_stream stream);
 
-/* Row a2 -- J i.i.d. draws from q^{!=k} = prod_{j!=k} p^(j) (Alg. 3; Def. 3.4).
+/* Row a2 -- J i.i.d. draws from q^{!=k} = prod_{j!=k} p^(j) (Alg. 3; Def. 5).
  * p, cdf   : host arrays of N device pointers (entry k unused), FP64 [dims[j]].
  * seed, update_id : Philox4x32-10 key and counter words: the uniform for sample j at ring
  *            position m comes from counter (j, m/2, update_id lo, update_id hi), words
@@ -102,7 +102,7 @@ tr_status tr_sample(tr_ctx* ctx, int N, int k, const int64_t* dims,
                     uint64_t seed, uint64_t update_id, int32_t* idx, double* w,
                     tr_stream stream);
 
-/* Row a3 -- sampled subchain S G_[2]^{!=k} (Alg. 4; Def. 3.2).
+/* Row a3 -- sampled subchain S G_[2]^{!=k} (Alg. 4; Def. 3).
  * cores : host array of N device pointers (entry k unused), FP64 slice-major.
  * idx   : int32 [J][N-1] ring order; w: FP64 [J] row scales (NULL = 1).
  * A     : [J][Rl_k*Rr_k] out in A_dtype (TR_F32: products in FP32; TR_F64: in FP64).
@@ -111,7 +111,7 @@ tr_status tr_subchain(tr_ctx* ctx, int N, int k, const int64_t* dims, const int*
                       const double* const* cores, const int32_t* idx, const double* w,
                       int64_t J, void* A, tr_dtype A_dtype, tr_stream stream);
 
-/* Row a4 -- sampled fibres S X_[k]^T (Alg. 2, "compute X~"; Def. 3.1).
+/* Row a4 -- sampled fibres S X_[k]^T (Alg. 2, "compute X~"; Def. 2).
  * X : dense row-major [dims[0]]...[dims[N-1]] in X_dtype.
  * Y : [J][dims[k]] out in Y_dtype, Y[j][i] = w_j * X(.., i at mode k, ..).
  * w : FP64 [J] (NULL = 1). Out-of-range indices record TR_ERR_INVALID_ARG, zero rows. */
@@ -152,7 +152,7 @@ tr_status tr_als_sampled_host(tr_ctx* ctx, const void* X_host, tr_dtype X_dtype,
                               const double* const* init_cores_host,
                               double* const* cores_host, tr_stream stream);
 
-/* Relative error ||TR(cores) - X||_F / ||X||_F (Sec. 4.1), synchronous; *rel_err is a
+/* Relative error ||TR(cores) - X||_F / ||X||_F (Sec. 5.1), synchronous; *rel_err is a
  * host double. Reconstruction runs in X's precision with FP64 sums of squares. */
 tr_status tr_rel_error(tr_ctx* ctx, const void* X, tr_dtype X_dtype, int N,
                        const int64_t* dims, const int* ranks, const double* const* cores,
@@ -218,6 +218,116 @@ tr_status tr_als_sampled_batched(tr_ctx* ctx, const tr_instance* inst, int count
 tr_status tr_solve_noalloc(const void* A, const void* Y, tr_dtype dtype, int64_t J, int Rl,
                            int Rr, int64_t I, tr_precision prec, double* core_out,
                            int32_t* info, tr_stream stream);
+
+/* ------------------------------------------------------------------------------------
+ * Serving: continuous batching of independent decompositions (Alg. 2 per request, run
+ * until the relative fit 1 - ||TR - X||_F / ||X||_F changes by less than a tolerance from
+ * one sweep to the next, one of the stopping criteria of Sec. 4.1).
+ *
+ * A server owns a slot table, a device workspace arena and a set of CUDA graphs. Each
+ * "tick" replays one graph over all occupied slots: one core update per running request
+ * (or, for a newly admitted request, the initial distribution of one core), the exact fit of
+ * every request that completed a sweep, and the stop rule, all on the device. Requests that
+ * arrive while others run are admitted, in submission order, as soon as a slot, arena space
+ * and HBM budget are free, and join at the next tick; finished requests release theirs at
+ * the end of a tick. A request's result does not depend on which other requests share its
+ * ticks: every launch gives each slot its own CTAs and the launch geometry is fixed by the
+ * server configuration. With the same configuration, a request's cores after s sweeps equal
+ * those of tr_als_sampled_batched with `sweeps` = s on that request alone.
+ * ------------------------------------------------------------------------------------ */
+#define TR_MAX_SERVED_SWEEPS 64
+
+typedef struct tr_server tr_server;
+
+typedef struct tr_server_config {
+  int device;                 /* CUDA device ordinal                                        */
+  size_t hbm_budget_bytes;    /* admission limit on the sum, over admitted requests, of the
+                                 bytes of X, of the cores and of the slot workspace       */
+  size_t arena_bytes;         /* slot workspace allocated at creation (<= the budget)       */
+  int max_slots;              /* concurrent requests, 1..4096                               */
+  int max_modes;              /* limits every request must meet: N <= max_modes,           */
+  int64_t max_dim;            /*   every I_k <= max_dim,                                    */
+  int max_rank;               /*   every rank <= max_rank (<= 16),                          */
+  int64_t max_samples;        /*   J <= max_samples                                         */
+  int max_sweeps;             /* default sweep cap, 1..TR_MAX_SERVED_SWEEPS                */
+  double fit_tol;             /* default stop tolerance on |fit_s - fit_{s-1}|              */
+  tr_dtype X_dtype;           /* dtype of every request's X                                 */
+  tr_precision prec;          /* arithmetic of every request                                */
+} tr_server_config;
+
+/* One decomposition request. X and cores are DEVICE buffers owned by the caller; they must
+ * stay valid (X unchanged) until the request is reported done. */
+typedef struct tr_request {
+  const void* X;                   /* device, row-major [dims[0]]...[dims[N-1]], X_dtype   */
+  int N;
+  int64_t dims[TR_MAX_MODES];
+  int ranks[TR_MAX_MODES];
+  int64_t J;                       /* samples per least-squares problem                     */
+  uint64_t seed;                   /* Philox key of the request's draws (and its init)      */
+  double* cores[TR_MAX_MODES];     /* device FP64 slice-major, receive the result           */
+  int init_given;                  /* nonzero: cores[1..N-1] hold the initial cores         */
+  int max_sweeps;                  /* 0 = the server's default                               */
+  double fit_tol;                  /* < 0 = the server's default                             */
+} tr_request;
+
+typedef struct tr_result {
+  int done;                        /* 0 while queued or running                             */
+  tr_status status;                /* TR_OK (converged), TR_ERR_NOT_CONVERGED (sweep cap),
+                                      TR_ERR_SINGULAR (non-finite fit), TR_ERR_CUDA          */
+  int sweeps;                      /* completed sweeps                                       */
+  int singular_updates;            /* updates whose normal matrix was singular (core kept)  */
+  double fit;                      /* relative fit after the last sweep                      */
+  double fit_change;               /* |fit - previous sweep's fit|                           */
+  int64_t t_submit_ns;             /* CLOCK_MONOTONIC timestamps of submission, admission  */
+  int64_t t_admit_ns;              /*   and of the end of the tick that finished it         */
+  int64_t t_done_ns;
+  double fit_history[TR_MAX_SERVED_SWEEPS];  /* fit after each sweep                      */
+} tr_result;
+
+typedef struct tr_server_stats {
+  int64_t ticks;                   /* graph replays so far                                   */
+  int64_t tick_ns;                 /* host time spent in ticks (admission + replay + wait)   */
+  int64_t submitted, completed, rejected;
+  int64_t updates;                 /* core updates performed                                  */
+  int active;                      /* requests in slots                                      */
+  int queued;                      /* requests waiting for admission                         */
+  int peak_active;
+  size_t charged_bytes;            /* current sum of admitted requests' charges              */
+  size_t peak_charged_bytes;
+} tr_server_stats;
+
+/* Creates a server: checks the configuration, allocates the arena and the slot tables,
+ * and captures one CUDA graph per slot-count bucket (8, 16, ... up to max_slots). */
+tr_status tr_server_create(const tr_server_config* cfg, tr_server** out);
+/* Stops the worker (if started), waits for the device and frees everything; requests still
+ * queued or running are abandoned. */
+void tr_server_destroy(tr_server* srv);
+/* Message of the last failure of a call on this server (srv == NULL: of tr_server_create). */
+const char* tr_server_last_error(const tr_server* srv);
+
+/* Queues a request; thread-safe. Returns TR_ERR_INVALID_ARG for a request outside the
+ * server's limits and TR_ERR_BUDGET for one whose charge alone exceeds the budget or the
+ * arena; neither is queued. *ticket identifies the request in poll / wait. */
+tr_status tr_server_submit(tr_server* srv, const tr_request* req, int64_t* ticket);
+
+/* Runs one tick on the calling thread (not allowed while the worker runs): admits what
+ * fits, replays the graph of the occupied slots, waits for it and retires finished
+ * requests. *active (may be NULL) receives the number of occupied slots after the tick. */
+tr_status tr_server_tick(tr_server* srv, int* active);
+
+/* Starts / stops a native worker thread that ticks whenever requests are queued or running
+ * and sleeps otherwise. */
+tr_status tr_server_start(tr_server* srv);
+tr_status tr_server_stop(tr_server* srv);
+
+/* Result of a request, thread-safe. poll returns at once (out->done = 0 while the request
+ * is queued or running); wait blocks until it is done or timeout_ms passes
+ * (TR_ERR_TIMEOUT), ticking on the calling thread when no worker runs. A result can be read
+ * any number of times until tr_server_release(ticket). Unknown tickets: TR_ERR_INVALID_ARG. */
+tr_status tr_server_poll(tr_server* srv, int64_t ticket, tr_result* out);
+tr_status tr_server_wait(tr_server* srv, int64_t ticket, int64_t timeout_ms, tr_result* out);
+tr_status tr_server_release(tr_server* srv, int64_t ticket);
+tr_status tr_server_get_stats(tr_server* srv, tr_server_stats* out);
 
 /* Per-kernel timing. Between tr_profile_begin and tr_profile_end every kernel the context
  * launches is bracketed by a pair of CUDA events recorded on the launching stream.

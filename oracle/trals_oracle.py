@@ -6,12 +6,12 @@ CPU-baseline / reference legs of ``bench.py``; never by the CUDA library or its 
 
 Conventions (0-based; the paper is 1-based):
   * ``cores[k]`` has the paper's shape ``(R_{k-1}, I_k, R_k)`` = ``(Rl_k, I_k, Rr_k)``
-    (Sec. 2.1, eq. 1), with ``ranks[k]`` the paper's ``R_{k+1}`` and ``R_{-1} = R_{N-1}``.
+    (Sec. 3.1, eq. 1), with ``ranks[k]`` the paper's ``R_{k+1}`` and ``R_{-1} = R_{N-1}``.
   * ``X`` is a NumPy array of shape ``dims`` (C order). Where the paper's linear index
-    ``overline{i_1 ... i_N}`` appears (Sec. 2 notation, Def. 3.1, Def. 3.2) it is taken
+    ``overline{i_1 ... i_N}`` appears (Sec. 3 notation, Def. 2, Def. 3) it is taken
     with the FIRST listed index fastest, as the paper defines it.
   * Ring order of the other modes for core ``n``: ``n+1, ..., N-1, 0, ..., n-1``
-    (Def. 3.1, Def. 3.2, eq. for q).
+    (Def. 2, Def. 3, eq. for q).
 
 Every function names the passage it follows. Steps use only NumPy library primitives
 (matmul, einsum, cumsum, searchsorted, SVD, QR, Cholesky, triangular solve) in the order
@@ -33,7 +33,7 @@ __all__ = [
     "core_unfold2", "core_from_solution", "subchain_full", "subchain_unfold2",
     "leverage_scores", "core_distribution", "inverse_cdf", "draw_samples",
     "sampled_subchain", "sampled_fibres", "sampled_ls_normal", "sampled_ls_qr",
-    "sampled_core_update", "tr_als_sampled", "tr_als", "tr_als_update",
+    "sampled_core_update", "tr_als_sampled", "tr_als_sampled_until", "tr_als", "tr_als_update",
 ]
 
 # --------------------------------------------------------------------------------------
@@ -94,13 +94,13 @@ def philox_uniforms(J, m, seed, update_id):
 # Tensor ring format and unfoldings
 # --------------------------------------------------------------------------------------
 def ring_modes(N, n):
-    """Modes other than n in ring order n+1, ..., N-1, 0, ..., n-1 (Def. 3.1)."""
+    """Modes other than n in ring order n+1, ..., N-1, 0, ..., n-1 (Def. 2)."""
     return [(n + 1 + m) % N for m in range(N - 1)]
 
 
 def ring_linear_index(multi, dims, n):
     """overline{i_{n+1} ... i_N i_1 ... i_{n-1}} with the first listed index fastest
-    (Sec. 2 notation, used by Def. 3.1/3.2 and eq. for q). ``multi`` is (J, N-1) in ring
+    (Sec. 3 notation, used by Def. 2/3 and eq. for q). ``multi`` is (J, N-1) in ring
     order."""
     multi = np.asarray(multi, dtype=np.int64)
     lin = np.zeros(multi.shape[0], dtype=np.int64)
@@ -129,13 +129,13 @@ def tr_reconstruct(cores):
 
 
 def rel_error(cores, X):
-    """Relative error ||TR(cores) - X||_F / ||X||_F (Sec. 4.1)."""
+    """Relative error ||TR(cores) - X||_F / ||X||_F (Sec. 5.1)."""
     X = np.asarray(X, dtype=np.float64)
     return float(np.linalg.norm(tr_reconstruct(cores) - X) / np.linalg.norm(X))
 
 
 def unfold_classical(X, n):
-    """Classical mode-n unfolding X_(n), Def. 3.1: column index overline{i_1..i_{n-1}
+    """Classical mode-n unfolding X_(n), Def. 2: column index overline{i_1..i_{n-1}
     i_{n+1}..i_N}, first listed index fastest."""
     N = X.ndim
     order = [n] + [m for m in range(N) if m != n]
@@ -143,7 +143,7 @@ def unfold_classical(X, n):
 
 
 def unfold_ring(X, n):
-    """Mode-n unfolding X_[n], Def. 3.1: column index overline{i_{n+1}..i_N i_1..i_{n-1}},
+    """Mode-n unfolding X_[n], Def. 2: column index overline{i_{n+1}..i_N i_1..i_{n-1}},
     first listed index fastest."""
     order = [n] + ring_modes(X.ndim, n)
     return np.transpose(X, order).reshape(X.shape[n], -1, order="F")
@@ -151,7 +151,7 @@ def unfold_ring(X, n):
 
 def core_unfold2(core):
     """Classical mode-2 unfolding G_(2)^(n) of a core (R_{n-1}, I_n, R_n): row i_n, column
-    overline{r_{n-1} r_n} = r_{n-1} + R_{n-1} r_n (Def. 3.1)."""
+    overline{r_{n-1} r_n} = r_{n-1} + R_{n-1} r_n (Def. 2)."""
     Rl, I, Rr = core.shape
     return np.transpose(core, (1, 2, 0)).reshape(I, Rr * Rl)
 
@@ -164,7 +164,7 @@ def core_from_solution(Z, Rl, Rr):
 
 
 def subchain_full(cores, n):
-    """Subchain tensor G^{!=n}, Def. 3.2: shape (R_n, prod_{j!=n} I_j, R_{n-1}), middle index
+    """Subchain tensor G^{!=n}, Def. 3: shape (R_n, prod_{j!=n} I_j, R_{n-1}), middle index
     overline{i_{n+1}..i_{n-1}} with the first listed index fastest. Built by merging the
     other cores in ring order; each new mode becomes the slowest part of the index."""
     N = len(cores)
@@ -179,17 +179,17 @@ def subchain_full(cores, n):
 
 def subchain_unfold2(cores, n):
     """G_[2]^{!=n}: row = middle index of G^{!=n}, column overline{r_{n-1} r_n}
-    (Def. 3.1 applied to Def. 3.2)."""
+    (Def. 2 applied to Def. 3)."""
     T = subchain_full(cores, n)                        # (R_n, M, R_{n-1})
     Rn, M, Rm = T.shape
     return np.transpose(T, (1, 0, 2)).reshape(M, Rn * Rm)
 
 
 # --------------------------------------------------------------------------------------
-# Leverage scores and sampling distributions (Def. 3.3, eq. for p^(n), eq. for q^{!=n})
+# Leverage scores and sampling distributions (Def. 4, eq. for p^(n), eq. for q^{!=n})
 # --------------------------------------------------------------------------------------
 def leverage_scores(A):
-    """ell_i(A) = ||U(i, :)||_2^2, U = left singular vectors of A for its rank (Def. 3.3).
+    """ell_i(A) = ||U(i, :)||_2^2, U = left singular vectors of A for its rank (Def. 4).
 
     Numerical rank: singular values above max(K, L) * eps * s_max (the paper states no
     tolerance; this is the usual LAPACK-style choice)."""
@@ -204,7 +204,7 @@ def leverage_scores(A):
 
 def core_distribution(core):
     """p^(n)(i) = ell_i(G_(2)^(n)) / rank(G_(2)^(n)) (eq. for p^(n)); the divisor is taken
-    as sum_i ell_i, which equals the rank (Sec. 2.2). Returns (p, cdf) with cdf the
+    as sum_i ell_i, which equals the rank (Sec. 3.2). Returns (p, cdf) with cdf the
     sequential inclusive prefix sum in index order."""
     ell = leverage_scores(core_unfold2(core))
     p = ell / np.sum(ell)
@@ -226,7 +226,7 @@ def inverse_cdf(cdf, p, u):
 def draw_samples(ps, cdfs, n, J, seed, update_id):
     """Draw J i.i.d. multi-indices from q^{!=n} (Alg. 3): i_j ~ p^(j) independently for each
     j != n, in ring order. Returns idx (J, N-1) in ring order and the rescaling
-    w = 1 / sqrt(J q^{!=n}(i)) of Def. 3.4 (product taken in ring order)."""
+    w = 1 / sqrt(J q^{!=n}(i)) of Def. 5 (product taken in ring order)."""
     N = len(ps)
     modes = ring_modes(N, n)
     idx = np.empty((J, N - 1), dtype=np.int64)
@@ -294,23 +294,53 @@ def sampled_core_update(X, cores, ps, cdfs, n, J, seed, update_id, solver="qr"):
     return core_from_solution(Z, Rl, Rr), idx, w
 
 
+def _initial_distributions(cores):
+    """The distributions of cores 1..N-1 formed before the first sweep (Alg. 2)."""
+    N = len(cores)
+    ps, cdfs = [None] * N, [None] * N
+    for n in range(1, N):
+        ps[n], cdfs[n] = core_distribution(cores[n])
+    return ps, cdfs
+
+
+def _sweep(X, cores, ps, cdfs, J, seed, s, solver):
+    """One pass of the outer loop of Alg. 2: update every core in order n = 0..N-1, each
+    followed by its new distribution; sweep s, core n uses update_id = s * N + n."""
+    N = len(cores)
+    for n in range(N):
+        cores[n], _, _ = sampled_core_update(X, cores, ps, cdfs, n, J, seed, s * N + n, solver)
+        ps[n], cdfs[n] = core_distribution(cores[n])
+
+
 def tr_als_sampled(X, init_cores, J, sweeps, seed, solver="qr", callback=None):
     """TR-ALS-Sampled (Alg. 2) with a fixed number of sweeps. ``init_cores`` supplies
     G^(2..N) (paper numbering); core 0 is overwritten by its first update.
     The sample block of (sweep s, core n) uses update_id = s * N + n."""
     X = np.asarray(X, dtype=np.float64)
     cores = [np.array(G, dtype=np.float64, copy=True) for G in init_cores]
-    N = len(cores)
-    ps, cdfs = [None] * N, [None] * N
-    for n in range(1, N):
-        ps[n], cdfs[n] = core_distribution(cores[n])
+    ps, cdfs = _initial_distributions(cores)
     for s in range(sweeps):
-        for n in range(N):
-            cores[n], _, _ = sampled_core_update(X, cores, ps, cdfs, n, J, seed, s * N + n, solver)
-            ps[n], cdfs[n] = core_distribution(cores[n])
+        _sweep(X, cores, ps, cdfs, J, seed, s, solver)
         if callback is not None:
             callback(s, cores)
     return cores
+
+
+def tr_als_sampled_until(X, init_cores, J, seed, fit_tol, max_sweeps, solver="qr"):
+    """TR-ALS-Sampled (Alg. 2) terminated by the change of the relative error, the first
+    criterion of Sec. 4.1: after sweep s the fit f_s = 1 - ||TR - X||_F / ||X||_F is
+    computed exactly; the loop ends after a sweep s >= 2 with |f_s - f_{s-1}| < fit_tol,
+    or after ``max_sweeps`` sweeps. Returns (cores, fits, converged)."""
+    X = np.asarray(X, dtype=np.float64)
+    cores = [np.array(G, dtype=np.float64, copy=True) for G in init_cores]
+    ps, cdfs = _initial_distributions(cores)
+    fits = []
+    for s in range(max_sweeps):
+        _sweep(X, cores, ps, cdfs, J, seed, s, solver)
+        fits.append(1.0 - rel_error(cores, X))
+        if len(fits) >= 2 and abs(fits[-1] - fits[-2]) < fit_tol:
+            return cores, fits, True
+    return cores, fits, False
 
 
 def tr_als_update(X, cores, n):

@@ -12,6 +12,7 @@
 
 #include "batched.cuh"
 #include "common.cuh"
+#include "host_util.h"
 
 struct tr_ctx {
   int device = 0;
@@ -74,34 +75,6 @@ tr_status fail(tr_ctx* ctx, tr_status s, const char* fmt, ...) {
     tr_status s_ = (expr);                 \
     if (s_ != TR_OK) return s_;            \
   } while (0)
-
-// Makes ctx->device current for the duration of a call and restores the caller's device.
-struct DeviceGuard {
-  int prev = -1;
-  bool ok = true;
-  explicit DeviceGuard(int dev) {
-    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-    if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
-  }
-  ~DeviceGuard() {
-    int cur;
-    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-  }
-};
-
-// Bump allocator over the context arena. With base == nullptr it only measures.
-struct Carver {
-  char* base;
-  size_t off = 0;
-  explicit Carver(char* b, size_t start = 0) : base(b), off(start) {}
-  template <typename T>
-  T* take(size_t count) {
-    off = (off + 255) & ~size_t(255);
-    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
-    off += count * sizeof(T);
-    return p;
-  }
-};
 
 tr_status ensure_ws(tr_ctx* ctx, size_t bytes) {
   if (bytes <= ctx->arena_bytes) return TR_OK;
@@ -422,11 +395,6 @@ tr_status check_shape(tr_ctx* ctx, int N, const int64_t* dims, const int* ranks)
 
 int rl_of(const int* ranks, int N, int k) { return ranks[(k - 1 + N) % N]; }
 
-void row_major_strides(int N, const int64_t* dims, int64_t* stride) {
-  int64_t s = 1;
-  for (int k = N - 1; k >= 0; --k) { stride[k] = s; s *= dims[k]; }
-}
-
 tr_status read_device_error(tr_ctx* ctx, cudaStream_t st) {
   unsigned h = 0;
   TR_CUDA(cudaStreamSynchronize(st));
@@ -627,101 +595,13 @@ tr_status fold_graph_marks(tr_ctx* ctx) {
 // ------------------------------------------------------------------------------------
 // Batched driver.
 // ------------------------------------------------------------------------------------
-size_t img_bytes(int n, bool f32) { return n > 0 ? trsm_image_bytes(n, f32) : 0; }
-
-struct BSizes {
-  int64_t Isum = 0, Imax = 0;
-  int Lmax = 0, n1 = 0, n2 = 0;
-};
-
-BSizes bsizes(const tr_instance& in) {
-  BSizes z;
-  for (int k = 0; k < in.N; ++k) {
-    const int64_t I = in.dims[k];
-    const int L = in.ranks[(k - 1 + in.N) % in.N] * in.ranks[k];
-    z.Isum += I;
-    z.Imax = I > z.Imax ? I : z.Imax;
-    z.Lmax = L > z.Lmax ? L : z.Lmax;
-    const int g1 = I >= L ? L : static_cast<int>(I);
-    z.n1 = g1 > z.n1 ? g1 : z.n1;
-    if (I < L) z.n2 = static_cast<int>(I) > z.n2 ? static_cast<int>(I) : z.n2;
-  }
-  return z;
-}
-
-// Carves one instance's buffers (base == nullptr: measure only).
-void carve_instance(Carver& c, const tr_instance& in, bool f64, BInst& d) {
-  const BSizes z = bsizes(in);
-  const size_t es = f64 ? 8 : 4;
-  int64_t off = 0;
-  double* pb = c.take<double>(z.Isum);
-  double* cb = c.take<double>(z.Isum);
-  for (int k = 0; k < in.N; ++k) {
-    d.p[k] = pb ? pb + off : nullptr;
-    d.cdf[k] = cb ? cb + off : nullptr;
-    off += in.dims[k];
-  }
-  d.A = c.take<char>(static_cast<size_t>(in.J) * z.Lmax * es);
-  d.Y = c.take<char>(static_cast<size_t>(in.J) * z.Imax * es);
-  const size_t L2 = static_cast<size_t>(z.Lmax) * z.Lmax;
-  d.M = c.take<double>(L2);
-  d.BT = c.take<double>(static_cast<size_t>(z.Imax) * z.Lmax);
-  d.Lrow = c.take<double>(L2);
-  d.Lcol = c.take<double>(L2);
-  d.invdiag = c.take<double>(z.Lmax);
-  d.keep = c.take<int>(z.Lmax);
-  d.info = c.take<int>(1);
-  d.limg = c.take<char>(img_bytes(z.Lmax, !f64));
-  d.mimg = f64 ? nullptr : reinterpret_cast<float*>(c.take<char>(img_bytes(z.Lmax, true)));
-  const size_t n12 = static_cast<size_t>(z.n1) * z.n1;
-  d.G1 = c.take<double>(n12);
-  d.L1row = c.take<double>(n12);
-  d.L1col = c.take<double>(n12);
-  d.inv1 = c.take<double>(z.n1);
-  d.keep1 = c.take<int>(z.n1);
-  d.info1 = c.take<int>(1);
-  d.img1 = reinterpret_cast<double*>(c.take<char>(img_bytes(z.n1, false)));
-  if (z.n2 > 0) {
-    const size_t n22 = static_cast<size_t>(z.n2) * z.n2;
-    d.G2 = c.take<double>(n22);
-    d.L2row = c.take<double>(n22);
-    d.L2col = c.take<double>(n22);
-    d.inv2 = c.take<double>(z.n2);
-    d.keep2 = c.take<int>(z.n2);
-    d.info2 = c.take<int>(1);
-    d.img2 = reinterpret_cast<double*>(c.take<char>(img_bytes(z.n2, false)));
-  } else {
-    d.G2 = d.L2row = d.L2col = d.inv2 = d.img2 = nullptr;
-    d.keep2 = d.info2 = nullptr;
-  }
-  d.ell = c.take<double>(z.Imax);
-}
-
 tr_status batched_issue(tr_ctx* ctx, const BLaunch& bl, int nmax_modes, int steps, bool draw,
                         cudaStream_t st) {
-  if (draw) TR_LAUNCH("b_init_cores", bl_init_cores(bl, st));
-  for (int k = 1; k < nmax_modes; ++k) {
-    TR_LAUNCH("b_gram", bl_gram(bl, 0, k, 1, st));
-    TR_LAUNCH("b_cholesky_leverage", bl_cholesky(bl, 0, k, 1, ctx->d_err, st));
-    if (bl.n2max > 0) {
-      TR_LAUNCH("b_gram", bl_gram(bl, 0, k, 2, st));
-      TR_LAUNCH("b_cholesky_leverage", bl_cholesky(bl, 0, k, 2, ctx->d_err, st));
-    }
-    TR_LAUNCH("b_leverage_rows", bl_leverage_rows(bl, 0, k, ctx->d_err, st));
-  }
-  for (int step = 0; step < steps; ++step) {
-    TR_LAUNCH("b_sample_chain_gather", bl_sample_chain_gather(bl, step, st));
-    TR_LAUNCH("b_contract", bl_contract(bl, step, st));
-    TR_LAUNCH("b_cholesky_solve", bl_cholesky(bl, step, 0, 0, ctx->d_err, st));
-    TR_LAUNCH("b_solve", bl_solve(bl, step, st));
-    TR_LAUNCH("b_gram", bl_gram(bl, step, 0, 1, st));
-    TR_LAUNCH("b_cholesky_leverage", bl_cholesky(bl, step, 0, 1, ctx->d_err, st));
-    if (bl.n2max > 0) {
-      TR_LAUNCH("b_gram", bl_gram(bl, step, 0, 2, st));
-      TR_LAUNCH("b_cholesky_leverage", bl_cholesky(bl, step, 0, 2, ctx->d_err, st));
-    }
-    TR_LAUNCH("b_leverage_rows", bl_leverage_rows(bl, step, 0, ctx->d_err, st));
-  }
+  if (draw) TR_CUDA(bl_init_cores(bl, st));
+  for (int k = 1; k < nmax_modes; ++k)
+    TR_CUDA(issue_leverage(bl, 0, k, ctx->d_err, st, nullptr));
+  const StepStreams ss{st, ctx->side, ctx->ev_fork, ctx->ev_info, ctx->ev_join};
+  for (int step = 0; step < steps; ++step) TR_CUDA(issue_step(bl, step, ctx->d_err, ss));
   return TR_OK;
 }
 
@@ -1054,7 +934,8 @@ tr_status tr_als_sampled_batched(tr_ctx* ctx, const tr_instance* inst, int count
   dry.take<BInst>(count);
   dry.take<unsigned>(count);
   std::vector<BInst> tab(count);
-  for (int i = 0; i < count; ++i) carve_instance(dry, inst[i], f64, tab[i]);
+  for (int i = 0; i < count; ++i)
+    carve_instance(dry, inst[i].N, inst[i].dims, inst[i].ranks, inst[i].J, f64, tab[i]);
   TR_TRY(ensure_ws(ctx, dry.off));
   Carver c(ctx->arena);
   BInst* dtab = c.take<BInst>(count);
@@ -1070,7 +951,7 @@ tr_status tr_als_sampled_batched(tr_ctx* ctx, const tr_instance* inst, int count
     const tr_instance& in = inst[i];
     BInst& d = tab[i];
     d = BInst{};
-    carve_instance(c, in, f64, d);
+    carve_instance(c, in.N, in.dims, in.ranks, in.J, f64, d);
     d.X = in.X;
     d.N = in.N;
     d.xf64 = X_dtype == TR_F64;
@@ -1085,7 +966,7 @@ tr_status tr_als_sampled_batched(tr_ctx* ctx, const tr_instance* inst, int count
       d.cores[k] = in.cores[k];
     }
     d.counter = counters + i;
-    const BSizes z = bsizes(in);
+    const BSizes z = bsizes(in.N, in.dims, in.ranks);
     bl.Jmax = in.J > bl.Jmax ? in.J : bl.Jmax;
     bl.Lmax = z.Lmax > bl.Lmax ? z.Lmax : bl.Lmax;
     bl.Imax = z.Imax > bl.Imax ? z.Imax : bl.Imax;

@@ -3,29 +3,47 @@
 #include "batched.cuh"
 #include "cholesky_body.cuh"
 #include "draw.cuh"
+#include "fit_body.cuh"
 #include "trsm_body.cuh"
 
 namespace trk {
 namespace {
 
-// The core being updated (or, with init_k > 0, the core whose initial distribution is
-// formed) and its sizes.
+// The core being updated (or, in an initialisation step, the core whose initial distribution
+// is formed) and its sizes. Leverage stages (`lev`) run in both kinds of step; the sampling
+// and solve stages only in updates.
 struct Cur {
   bool active;
+  bool init;
   int n, Rl, Rr, L;
   int64_t I;
+  int t;             // update id (step) of an update
 };
 
-__device__ __forceinline__ Cur current(const BInst& d, int step, int init_k) {
+__device__ __forceinline__ Cur current(const BInst& d, int step, int init_k, bool lev) {
   Cur c{};
-  if (init_k > 0) {
-    c.active = d.nupd > 0 && init_k < d.N;
-    c.n = init_k;
-  } else {
-    c.active = step < d.nupd;
-    c.n = c.active ? step % d.N : 0;
+  int k = 0, t = step;
+  if (d.slot) {
+    const SlotState& s = *d.slot;
+    if (s.status != kSlotRunning) return c;
+    t = s.step;
+    if (t < 0) {
+      if (!lev) return c;
+      k = t + d.N;
+    }
+  } else if (init_k > 0) {
+    if (d.nupd <= 0 || init_k >= d.N) return c;
+    k = init_k;
   }
-  if (!c.active) return c;
+  if (k > 0) {
+    c.init = true;
+    c.n = k;
+  } else {
+    if (t >= d.nupd) return c;
+    c.n = t % d.N;
+    c.t = t;
+  }
+  c.active = true;
   c.Rl = d.ranks[(c.n - 1 + d.N) % d.N];
   c.Rr = d.ranks[c.n];
   c.L = c.Rl * c.Rr;
@@ -38,7 +56,12 @@ __device__ __forceinline__ Cur current(const BInst& d, int step, int init_k) {
 // ------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) kb_init_cores(const BInst* __restrict__ tab) {
   const BInst& d = tab[blockIdx.x];
-  if (d.nupd <= 0 || !d.draw_init) return;
+  if (!d.draw_init) return;
+  if (d.slot) {
+    if (d.slot->status != kSlotRunning || d.slot->step != 1 - d.N) return;
+  } else if (d.nupd <= 0) {
+    return;
+  }
   const uint32_t k0 = static_cast<uint32_t>(d.seed), k1 = static_cast<uint32_t>(d.seed >> 32);
   for (int k = 1; k < d.N; ++k) {
     const int64_t count = d.dims[k] * d.ranks[(k - 1 + d.N) % d.N] * d.ranks[k];
@@ -67,7 +90,7 @@ __global__ void __launch_bounds__(SW * 32) kb_sample(const BInst* __restrict__ t
   __shared__ T sG[SW][kMaxL];
   __shared__ ChainArgs ca;
   const BInst& d = tab[blockIdx.x];
-  const Cur cu = current(d, step, 0);
+  const Cur cu = current(d, step, 0, false);
   if (!cu.active) return;
   const int64_t j0 = static_cast<int64_t>(blockIdx.y) * SW * SPW;
   if (j0 >= d.J) return;
@@ -85,7 +108,7 @@ __global__ void __launch_bounds__(SW * 32) kb_sample(const BInst* __restrict__ t
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t k0 = static_cast<uint32_t>(d.seed), k1 = static_cast<uint32_t>(d.seed >> 32);
-  const uint32_t u0 = static_cast<uint32_t>(step), u1 = 0u;
+  const uint32_t u0 = static_cast<uint32_t>(cu.t), u1 = 0u;
   const int mode_l = (lane < npos) ? (n + 1 + lane) % N : 0;
   const TX* __restrict__ X = static_cast<const TX*>(d.X);
   T* A = static_cast<T*>(d.A);
@@ -133,7 +156,7 @@ __global__ void __launch_bounds__(CT) kb_contract(const BInst* __restrict__ tab,
   __shared__ T As[BK][BM];
   __shared__ T Bs[BK][BN];
   const BInst& d = tab[blockIdx.x];
-  const Cur cu = current(d, step, 0);
+  const Cur cu = current(d, step, 0, false);
   if (!cu.active) return;
   const int L = cu.L;
   const int64_t I = cu.I, ldc = L + I;
@@ -209,11 +232,11 @@ __global__ void __launch_bounds__(GNT) kb_gram(const BInst* __restrict__ tab, in
   __shared__ double P[GK][GT + 1];
   __shared__ double Q[GK][GT + 1];
   const BInst& d = tab[blockIdx.x];
-  const Cur cu = current(d, step, init_k);
+  const Cur cu = current(d, step, init_k, true);
   if (!cu.active) return;
   const bool tall = cu.I >= cu.L;
   if (pass == 2 && tall) return;
-  const double* S = init_k > 0 ? d.cores[cu.n] : d.BT;
+  const double* S = cu.init ? d.cores[cu.n] : d.BT;
   const double* src;
   int64_t K, lda;
   int n;
@@ -273,7 +296,7 @@ __global__ void __launch_bounds__(CNT) kb_cholesky(const BInst* __restrict__ tab
                                                    int smem_bytes, int mixed) {
   extern __shared__ double smem[];
   const BInst& d = tab[blockIdx.x];
-  const Cur cu = current(d, step, init_k);
+  const Cur cu = current(d, step, init_k, which != 0);
   if (!cu.active) return;
   const double eps = 2.220446049250313e-16;
   const bool tall = cu.I >= cu.L;
@@ -339,7 +362,7 @@ __global__ void __launch_bounds__(TW * 32) kb_solve(const BInst* __restrict__ ta
                                                     int smem_bytes) {
   extern __shared__ __align__(16) unsigned char sm[];
   const BInst& d = tab[blockIdx.x];
-  const Cur cu = current(d, step, 0);
+  const Cur cu = current(d, step, 0, false);
   if (!cu.active) return;
   const int n = cu.L;
   const int64_t per = static_cast<int64_t>(TW) * NB;
@@ -357,11 +380,11 @@ __global__ void __launch_bounds__(TW * 32) kb_rows(const BInst* __restrict__ tab
                                                    int init_k, unsigned* err, int smem_bytes) {
   extern __shared__ __align__(16) unsigned char sm[];
   const BInst& d = tab[blockIdx.x];
-  const Cur cu = current(d, step, init_k);
+  const Cur cu = current(d, step, init_k, true);
   if (!cu.active) return;
   const bool tall = cu.I >= cu.L;
   const int n = tall ? cu.L : static_cast<int>(cu.I);
-  const double* rhs = tall ? (init_k > 0 ? d.cores[cu.n] : d.BT) : d.L1row;
+  const double* rhs = tall ? (cu.init ? d.cores[cu.n] : d.BT) : d.L1row;
   const int64_t ld = tall ? cu.L : cu.I;
   const double* Lr = tall ? d.L1row : d.L2row;
   const double* Lc = tall ? d.L1col : d.L2col;
@@ -369,10 +392,96 @@ __global__ void __launch_bounds__(TW * 32) kb_rows(const BInst* __restrict__ tab
   const double* im = tall ? d.img1 : d.img2;
   const int nctas = static_cast<int>((cu.I + TW - 1) / TW);
   if (static_cast<int>(blockIdx.y) >= nctas) return;
-  const CdfEpilogue ep{d.counter, d.p[cu.n], d.cdf[cu.n], init_k > 0 ? nullptr : d.info, err};
+  const CdfEpilogue ep{d.counter, d.p[cu.n], d.cdf[cu.n], cu.init ? nullptr : d.info, err};
   const bool smem = staged_bytes<double>(n, 0) <= static_cast<size_t>(smem_bytes);
   trsm_dispatch<double, 1>(smem, sm, blockIdx.y, n, Lr, Lc, iv, nullptr, cu.I, rhs, ld, 0, nullptr,
                            im, nullptr, 1, 1, nullptr, d.ell, ep, nctas);
+}
+
+// ------------------------------------------------------------------------------------
+// Serving: relative fit 1 - ||TR - X|| / ||X|| (Sec. 5.1) of every slot that completed a
+// sweep in this tick, as kFitParts (or fewer) partial sums in a fixed order, then the stop
+// rule (|fit_s - fit_{s-1}| < tol after two or more sweeps, or the sweep cap) and the step
+// counters.
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ int64_t lead_count(const BInst& d) {
+  int64_t lead = 1;
+  for (int m = 0; m < d.N - 1; ++m) lead *= d.dims[m];
+  return lead;
+}
+
+// The slot's step is the last update of a sweep.
+__device__ __forceinline__ bool fit_due(const BInst& d) {
+  if (!d.slot) return false;
+  const SlotState& s = *d.slot;
+  return s.status == kSlotRunning && s.step >= 0 && s.step % d.N == d.N - 1;
+}
+
+template <typename T>
+__device__ __forceinline__ int fit_parts(const BInst& d) {
+  const int64_t nblk = (lead_count(d) + FitTile<T>::FL - 1) / FitTile<T>::FL;
+  return nblk < kFitParts ? static_cast<int>(nblk) : kFitParts;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(FNT) kb_fit(const BInst* __restrict__ tab) {
+  extern __shared__ __align__(16) unsigned char fit_dyn[];
+  __shared__ T chain[8][kMaxL];
+  __shared__ T slice[8][kMaxL];
+  __shared__ double red[2 * (FNT / 32)];
+  __shared__ FitArgs fa;
+  const BInst& d = tab[blockIdx.x];
+  if (!fit_due(d)) return;
+  const int parts = fit_parts<T>(d);
+  if (static_cast<int>(blockIdx.y) >= parts) return;
+  if (threadIdx.x == 0) {
+    fa.N = d.N;
+    for (int m = 0; m < d.N; ++m) {
+      fa.core[m] = d.cores[m];
+      fa.dims[m] = d.dims[m];
+      fa.ranks[m] = d.ranks[m];
+    }
+  }
+  __syncthreads();
+  double se = 0.0, sx = 0.0;
+  fit_blocks<T>(fa, static_cast<const T*>(d.X), lead_count(d), blockIdx.y, parts, fit_dyn, chain,
+                slice, se, sx);
+  fit_block_reduce(se, sx, red);
+  if (threadIdx.x == 0) {
+    d.fitp[blockIdx.y] = se;
+    d.fitp[kFitParts + blockIdx.y] = sx;
+  }
+}
+
+__global__ void __launch_bounds__(128) kb_advance(const BInst* __restrict__ tab, int count,
+                                                  int xf64) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const BInst& d = tab[i];
+  if (!d.slot) return;
+  SlotState& s = *d.slot;
+  if (s.status != kSlotRunning) return;
+  const int t = s.step;
+  if (t >= 0 && *d.info != 0) s.singular += 1;
+  if (fit_due(d)) {
+    const int parts = xf64 ? fit_parts<double>(d) : fit_parts<float>(d);
+    double se = 0.0, sx = 0.0;
+    for (int q = 0; q < parts; ++q) {
+      se += d.fitp[q];
+      sx += d.fitp[kFitParts + q];
+    }
+    const double rel = sx > 0.0 ? sqrt(se / sx) : (se > 0.0 ? INFINITY : 0.0);
+    const double fit = 1.0 - rel;
+    const int sw = s.sweeps + 1;
+    s.sweeps = sw;
+    s.fit_prev = s.fit;
+    s.fit = fit;
+    if (sw <= kMaxServedSweeps) d.hist[sw - 1] = fit;
+    if (!isfinite(fit)) s.status = kSlotFailed;
+    else if (sw >= 2 && fabs(fit - s.fit_prev) < s.tol) s.status = kSlotConverged;
+    else if (sw >= s.max_sweeps) s.status = kSlotCapped;
+  }
+  s.step = t + 1;
 }
 
 constexpr int kDyn = 200 * 1024;
@@ -458,6 +567,20 @@ cudaError_t bl_leverage_rows(const BLaunch& b, int step, int init_k, unsigned* e
   return cudaGetLastError();
 }
 
+cudaError_t bl_fit(const BLaunch& b, cudaStream_t st) {
+  dim3 grid(b.count, kFitParts);
+  if (b.xf64)
+    kb_fit<double><<<grid, FNT, fit_smem_bytes<double>(b.Lmax), st>>>(b.tab);
+  else
+    kb_fit<float><<<grid, FNT, fit_smem_bytes<float>(b.Lmax), st>>>(b.tab);
+  return cudaGetLastError();
+}
+
+cudaError_t bl_advance(const BLaunch& b, cudaStream_t st) {
+  kb_advance<<<(b.count + 127) / 128, 128, 0, st>>>(b.tab, b.count, b.xf64 ? 1 : 0);
+  return cudaGetLastError();
+}
+
 cudaError_t batched_attributes() {
   cudaError_t e = cudaFuncSetAttribute(kb_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        kDyn);
@@ -466,7 +589,13 @@ cudaError_t batched_attributes() {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(kb_solve<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kDyn);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(kb_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, kDyn);
+  e = cudaFuncSetAttribute(kb_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, kDyn);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(kb_fit<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(fit_smem_bytes<float>(kMaxL)));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(kb_fit<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              static_cast<int>(fit_smem_bytes<double>(kMaxL)));
 }
 
 }  // namespace trk

@@ -8,11 +8,41 @@
 // Instances advance in lockstep "steps": at step t an instance with N modes and
 // nupd = sweeps * N updates performs the update of core t % N in sweep t / N with
 // update_id t (the same counter the single-problem driver uses), or nothing if t >= nupd.
+//
+// A served instance (slot != nullptr) keeps its own step counter in device memory instead:
+// steps 1-N .. -1 form the initial distributions of cores 1 .. N-1 (Alg. 2 before the first
+// sweep), steps t >= 0 are updates as above, and after the last update of each sweep the
+// relative fit is evaluated and the stop rule applied on the device. Every launch of a
+// serving tick therefore serves slots at different points of their decompositions.
 #pragma once
 
 #include "common.cuh"
 
 namespace trk {
+
+constexpr int kMaxServedSweeps = 64;   // sweep cap and fit-history length of a served slot
+constexpr int kFitParts = 128;         // partial sums of one fit evaluation (fixed order)
+
+enum SlotStatus : int {
+  kSlotIdle = 0,
+  kSlotRunning = 1,
+  kSlotConverged = 2,   // |fit_s - fit_{s-1}| < tol
+  kSlotCapped = 3,      // max_sweeps reached without meeting tol
+  kSlotFailed = 4,      // non-finite fit
+};
+
+// Device-resident state of one served decomposition.
+struct SlotState {
+  int step;             // next step (negative: initial distribution of core step + N)
+  int status;           // SlotStatus
+  int sweeps;           // completed sweeps
+  int singular;         // updates whose normal equations were singular (core kept)
+  int max_sweeps;
+  int pad;
+  double tol;           // stop when |fit - fit_prev| < tol (after >= 2 sweeps)
+  double fit;           // 1 - ||TR - X||_F / ||X||_F after the last completed sweep
+  double fit_prev;
+};
 
 struct BInst {
   // problem
@@ -41,6 +71,10 @@ struct BInst {
   double* G2; double* L2row; double* L2col; double* inv2; int* keep2; int* info2; double* img2;
   double* ell;
   unsigned* counter;
+  // serving (nullptr for the batched driver)
+  SlotState* slot;
+  double* fitp;                  // 2 * kFitParts partial sums of the fit evaluation
+  double* hist;                  // kMaxServedSweeps fits, one per completed sweep
 };
 
 // Stage launchers (all instances of `tab[0..count)` in one launch each). `step` is the
@@ -69,6 +103,10 @@ cudaError_t bl_solve(const BLaunch& b, int step, cudaStream_t st);
 cudaError_t bl_gram(const BLaunch& b, int step, int init_k, int pass, cudaStream_t st);
 cudaError_t bl_leverage_rows(const BLaunch& b, int step, int init_k, unsigned* err,
                              cudaStream_t st);
+// Serving: relative fit of the slots that finished a sweep in this tick, then the stop rule
+// and the step counters of all running slots.
+cudaError_t bl_fit(const BLaunch& b, cudaStream_t st);
+cudaError_t bl_advance(const BLaunch& b, cudaStream_t st);
 cudaError_t batched_attributes();
 
 }  // namespace trk

@@ -1,4 +1,4 @@
-// Device helpers shared by the sampler kernels (row a2: Alg. 3 and Def. 3.4) and the
+// Device helpers shared by the sampler kernels (row a2: Alg. 3 and Def. 5) and the
 // slice-chain kernels (row a3: Alg. 4), so that the per-stage entry points and the fused
 // driver kernel compute bit-identical results.
 #pragma once

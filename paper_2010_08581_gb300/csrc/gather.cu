@@ -1,4 +1,4 @@
-// Row a4: sampled mode-n fibres of X (Alg. 2, "compute X~ = S X_[n]^T"; Def. 3.1).
+// Row a4: sampled mode-n fibres of X (Alg. 2, "compute X~ = S X_[n]^T"; Def. 2).
 // Y[j][i] = w_j * X(i_0, .., i at mode n, .., i_{N-1}) for the sampled multi-index j.
 //
 // One warp per sample row; lanes walk the fibre. When the gathered mode is the last

@@ -1,5 +1,5 @@
 // Gram matrices for the Cholesky-based thin QR behind the leverage scores (row a1:
-// Def. 3.3, eq. for p^(n)), and the fixed-order reduction of split partials used by the
+// Def. 4, eq. for p^(n)), and the fixed-order reduction of split partials used by the
 // Gram and by the normal-equation contraction (rows a1, a5).
 #include "common.cuh"
 

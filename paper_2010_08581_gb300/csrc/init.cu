@@ -1,4 +1,4 @@
-// The N(0,1) core initialiser (Sec. 3: cores drawn i.i.d. N(0,1)).
+// The N(0,1) core initialiser (Sec. 4: cores drawn i.i.d. N(0,1)).
 #include "draw.cuh"
 
 namespace trk {

@@ -1,5 +1,5 @@
 // Row a2: J i.i.d. draws from q^{!=n} = prod_{j != n} p^(j) (Alg. 3) by inverse CDF, and
-// the Def. 3.4 rescaling w_j = 1 / sqrt(J q(i_j)); and the fused draw + sampled-subchain
+// the Def. 5 rescaling w_j = 1 / sqrt(J q(i_j)); and the fused draw + sampled-subchain
 // kernel used by the driver (rows a2 + a3: Alg. 3 then Alg. 4 for the same samples).
 #include "draw.cuh"
 

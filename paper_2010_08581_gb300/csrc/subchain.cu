@@ -1,4 +1,4 @@
-// Row a3: sampled subchain rows (Alg. 4; Def. 3.2). For sample j the lateral slices
+// Row a3: sampled subchain rows (Alg. 4; Def. 3). For sample j the lateral slices
 // G^(n+1)(:, i_{n+1}, :) ... G^(n-1)(:, i_{n-1}, :) are multiplied in ring order into an
 // Rr_n x Rl_n matrix S_j (paper's R_n x R_{n-1}); row j of the sketch is w_j * S_j flattened
 // row-major, i.e. column a + Rl_n * b holds S_j[b][a] (the paper's overline{r_{n-1} r_n}).

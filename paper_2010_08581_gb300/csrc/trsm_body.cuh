@@ -1,7 +1,7 @@
 // Triangular solves with a Cholesky factor L (n <= 256) for many vectors, shared by the
 // single-problem kernel (trsm.cu) and the batched kernel (batched.cu):
 //   mode 0 (leverage rows, row a1): ell_v = || L^-1 a_v ||^2 -- row norms of Q = A R^-1 of
-//           the Cholesky-based thin QR (Def. 3.3), optionally followed by p and the CDF;
+//           the Cholesky-based thin QR (Def. 4), optionally followed by p and the CDF;
 //   mode 1 (LS solve, row a6):      z_v = L^-T L^-1 b_v, written into the new core;
 //   mode 2 (LS solve + one refinement step, row a6):
 //           z = L^-T L^-1 b;  r = b - M z;  z += L^-T L^-1 r.

@@ -3,10 +3,10 @@ the benchmark.
 
 This module only draws random numbers and lays them out; it holds no step of the sampled
 ALS method. Random cores are returned in the paper's shape ``(R_{k-1}, I_k, R_k)``
-(Sec. 2.1); ``slice_major`` converts them to the library's ``[I_k][Rl][Rr]`` layout.
+(Sec. 3.1); ``slice_major`` converts them to the library's ``[I_k][Rl][Rr]`` layout.
 
 Workload recipes (the paper's datasets are not available; these synthetic tensors stand
-in for its synthetic experiment of Sec. 4.1.1 and its image-stack workloads):
+in for its synthetic experiment of Sec. 5.1.1 and its image-stack workloads):
   * ``tr_plus_noise``: X = TR(cores) + Gaussian noise, cores i.i.d. N(0, 1), noise
     standard deviation ``rel * ||TR||_F / sqrt(prod I)`` so that the total noise norm is
     ``rel * ||TR||_F``.
@@ -149,3 +149,31 @@ def batched_workload(count: int, seed: int, device="cpu", imin=32, imax=200, rmi
                              device=device, dtype=torch.float32)
         out.append(dict(dims=dims, ranks=ranks, J=j_factor * L, X=X, seed=seed * 7919 + i))
     return out
+
+
+def serving_requests(count: int, seed: int, modes=(3, 4, 5), emin=1e5, emax=1e8, rmin=4,
+                     rmax=16, j_factor=10):
+    """Shapes of a stream of decomposition requests: N ~ U(modes); entry count E
+    log-uniform in [emin, emax]; I_k = max(2, round(E^(1/N) * exp(g_k - mean(g)))) with
+    g_k ~ U[-0.5, 0.5] (so prod I_k stays near E); each rank ~ U{rmin..rmax};
+    J = j_factor * max_k L_k. Returns a list of dicts (dims, ranks, J)."""
+    g = _gen(seed)
+    out = []
+    for _ in range(count):
+        N = int(modes[int(torch.randint(len(modes), (1,), generator=g))])
+        u = float(torch.rand(1, generator=g, dtype=torch.float64))
+        E = math.exp(math.log(emin) + u * (math.log(emax) - math.log(emin)))
+        gk = torch.rand(N, generator=g, dtype=torch.float64) - 0.5
+        gk = gk - gk.mean()
+        dims = tuple(max(2, int(round(E ** (1.0 / N) * math.exp(float(v))))) for v in gk)
+        ranks = tuple(int(v) for v in torch.randint(rmin, rmax + 1, (N,), generator=g))
+        L = max(ranks[(k - 1) % N] * ranks[k] for k in range(N))
+        out.append(dict(dims=dims, ranks=ranks, J=j_factor * L))
+    return out
+
+
+def poisson_arrivals(count: int, rate: float, seed: int) -> List[float]:
+    """Arrival times (seconds from 0) of a Poisson process of the given rate."""
+    g = _gen(seed)
+    gaps = -torch.log1p(-torch.rand(count, generator=g, dtype=torch.float64)) / rate
+    return torch.cumsum(gaps, 0).tolist()

@@ -43,6 +43,41 @@ class TrInstance(ctypes.Structure):
                 ("cores", c_vp * MAX_MODES), ("init_given", c_int)]
 
 
+MAX_SERVED_SWEEPS = 64
+
+
+class TrServerConfig(ctypes.Structure):
+    """Mirror of ``tr_server_config``."""
+    _fields_ = [("device", c_int), ("hbm_budget_bytes", c_sz), ("arena_bytes", c_sz),
+                ("max_slots", c_int), ("max_modes", c_int), ("max_dim", c_i64),
+                ("max_rank", c_int), ("max_samples", c_i64), ("max_sweeps", c_int),
+                ("fit_tol", c_dbl), ("X_dtype", c_int), ("prec", c_int)]
+
+
+class TrRequest(ctypes.Structure):
+    """Mirror of ``tr_request``."""
+    _fields_ = [("X", c_vp), ("N", c_int), ("dims", c_i64 * MAX_MODES),
+                ("ranks", c_int * MAX_MODES), ("J", c_i64), ("seed", c_u64),
+                ("cores", c_vp * MAX_MODES), ("init_given", c_int), ("max_sweeps", c_int),
+                ("fit_tol", c_dbl)]
+
+
+class TrResult(ctypes.Structure):
+    """Mirror of ``tr_result``."""
+    _fields_ = [("done", c_int), ("status", c_int), ("sweeps", c_int),
+                ("singular_updates", c_int), ("fit", c_dbl), ("fit_change", c_dbl),
+                ("t_submit_ns", c_i64), ("t_admit_ns", c_i64), ("t_done_ns", c_i64),
+                ("fit_history", c_dbl * MAX_SERVED_SWEEPS)]
+
+
+class TrServerStats(ctypes.Structure):
+    """Mirror of ``tr_server_stats``."""
+    _fields_ = [("ticks", c_i64), ("tick_ns", c_i64), ("submitted", c_i64),
+                ("completed", c_i64), ("rejected", c_i64), ("updates", c_i64),
+                ("active", c_int), ("queued", c_int), ("peak_active", c_int),
+                ("charged_bytes", c_sz), ("peak_charged_bytes", c_sz)]
+
+
 # name -> (restype, argtypes); mirrors include/trals.h
 SIGNATURES = {
     "tr_create": (c_int, [ctypes.POINTER(c_vp), c_int, c_sz]),
@@ -69,6 +104,17 @@ SIGNATURES = {
                                        c_int, c_vp]),
     "tr_solve_noalloc": (c_int, [c_vp, c_vp, c_int, c_i64, c_int, c_int, c_i64, c_int, c_vp,
                                  c_vp, c_vp]),
+    "tr_server_create": (c_int, [ctypes.POINTER(TrServerConfig), ctypes.POINTER(c_vp)]),
+    "tr_server_destroy": (None, [c_vp]),
+    "tr_server_last_error": (ctypes.c_char_p, [c_vp]),
+    "tr_server_submit": (c_int, [c_vp, ctypes.POINTER(TrRequest), ctypes.POINTER(c_i64)]),
+    "tr_server_tick": (c_int, [c_vp, PI]),
+    "tr_server_start": (c_int, [c_vp]),
+    "tr_server_stop": (c_int, [c_vp]),
+    "tr_server_poll": (c_int, [c_vp, c_i64, ctypes.POINTER(TrResult)]),
+    "tr_server_wait": (c_int, [c_vp, c_i64, c_i64, ctypes.POINTER(TrResult)]),
+    "tr_server_release": (c_int, [c_vp, c_i64]),
+    "tr_server_get_stats": (c_int, [c_vp, ctypes.POINTER(TrServerStats)]),
     "tr_profile_begin": (c_int, [c_vp]),
     "tr_profile_end": (c_int, [c_vp, c_vp]),
     "tr_profile_count": (c_int, [c_vp]),
@@ -324,3 +370,113 @@ def empty_cores(dims, ranks, device="cuda"):
     N = len(dims)
     return [torch.empty((dims[k], ranks[(k - 1) % N], ranks[k]), dtype=torch.float64,
                         device=device) for k in range(N)]
+
+
+def _result_dict(r: TrResult):
+    n = min(int(r.sweeps), MAX_SERVED_SWEEPS)
+    return dict(done=bool(r.done), status=int(r.status), sweeps=int(r.sweeps),
+                singular_updates=int(r.singular_updates), fit=float(r.fit),
+                fit_change=float(r.fit_change), t_submit_ns=int(r.t_submit_ns),
+                t_admit_ns=int(r.t_admit_ns), t_done_ns=int(r.t_done_ns),
+                fit_history=[float(r.fit_history[i]) for i in range(n)])
+
+
+class Server:
+    """Owns a ``tr_server``: continuous batching of decomposition requests on one device.
+
+    ``submit`` keeps references to the request's X and core tensors until ``release``."""
+
+    def __init__(self, *, device: int = 0, hbm_budget_bytes: int = 150 << 30,
+                 arena_bytes: Optional[int] = None, max_slots: int = 64, max_modes: int = 5,
+                 max_dim: int = 1024, max_rank: int = 16, max_samples: int = 2560,
+                 max_sweeps: int = 30, fit_tol: float = 1e-4, X_dtype: int = TR_F32,
+                 prec: int = TR_PREC_MIXED):
+        lib = load()
+        cfg = TrServerConfig()
+        cfg.device = int(device)
+        cfg.hbm_budget_bytes = int(hbm_budget_bytes)
+        cfg.arena_bytes = int(arena_bytes if arena_bytes is not None
+                              else min(hbm_budget_bytes, 8 << 30))
+        cfg.max_slots = int(max_slots)
+        cfg.max_modes = int(max_modes)
+        cfg.max_dim = int(max_dim)
+        cfg.max_rank = int(max_rank)
+        cfg.max_samples = int(max_samples)
+        cfg.max_sweeps = int(max_sweeps)
+        cfg.fit_tol = float(fit_tol)
+        cfg.X_dtype = int(X_dtype)
+        cfg.prec = int(prec)
+        h = c_vp()
+        st = lib.tr_server_create(ctypes.byref(cfg), ctypes.byref(h))
+        if st != TR_OK:
+            raise TrError(st, "tr_server_create failed: "
+                          + (lib.tr_server_last_error(None) or b"").decode())
+        self.handle = h
+        self.config = cfg
+        self._refs = {}
+
+    def _check(self, st: int):
+        if st != TR_OK:
+            raise TrError(st, (load().tr_server_last_error(self.handle) or b"").decode())
+
+    def submit(self, X: torch.Tensor, ranks, J: int, seed: int, cores: List[torch.Tensor],
+               init_given: bool = False, max_sweeps: int = 0, fit_tol: float = -1.0) -> int:
+        req = TrRequest()
+        req.X = X.data_ptr()
+        req.N = X.ndim
+        for k, d in enumerate(X.shape):
+            req.dims[k] = int(d)
+            req.ranks[k] = int(ranks[k])
+            req.cores[k] = cores[k].data_ptr()
+        req.J = int(J)
+        req.seed = int(seed)
+        req.init_given = 1 if init_given else 0
+        req.max_sweeps = int(max_sweeps)
+        req.fit_tol = float(fit_tol)
+        t = c_i64()
+        self._check(load().tr_server_submit(self.handle, ctypes.byref(req), ctypes.byref(t)))
+        self._refs[t.value] = (X, list(cores))
+        return t.value
+
+    def tick(self) -> int:
+        a = c_int()
+        self._check(load().tr_server_tick(self.handle, ctypes.byref(a)))
+        return a.value
+
+    def start(self):
+        self._check(load().tr_server_start(self.handle))
+
+    def stop(self):
+        self._check(load().tr_server_stop(self.handle))
+
+    def poll(self, ticket: int):
+        r = TrResult()
+        self._check(load().tr_server_poll(self.handle, int(ticket), ctypes.byref(r)))
+        return _result_dict(r)
+
+    def wait(self, ticket: int, timeout_ms: int = 600_000):
+        r = TrResult()
+        self._check(load().tr_server_wait(self.handle, int(ticket), int(timeout_ms),
+                                          ctypes.byref(r)))
+        return _result_dict(r)
+
+    def release(self, ticket: int):
+        self._check(load().tr_server_release(self.handle, int(ticket)))
+        self._refs.pop(int(ticket), None)
+
+    def stats(self):
+        s = TrServerStats()
+        self._check(load().tr_server_get_stats(self.handle, ctypes.byref(s)))
+        return {name: int(getattr(s, name)) for name, _ in TrServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().tr_server_destroy(self.handle)
+            self.handle = None
+            self._refs.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,4 +1,4 @@
-"""Pins for the oracle's least-squares steps and ALS drivers (Alg. 1, Alg. 2, Thm. 3.6).
+"""Pins for the oracle's least-squares steps and ALS drivers (Alg. 1, Alg. 2, Thm. 7).
 CPU only."""
 
 import numpy as np
@@ -8,7 +8,7 @@ import oracle as orc
 
 
 def test_sampled_ls_with_all_rows_is_exact_ls():
-    """With S = I (every row once, weight 1) the sampled LS is the exact LS (Def. 3.4)."""
+    """With S = I (every row once, weight 1) the sampled LS is the exact LS (Def. 5)."""
     rng = np.random.default_rng(0)
     A = rng.standard_normal((60, 9))
     Y = rng.standard_normal((60, 13))
@@ -63,7 +63,7 @@ def test_tr_als_sampled_recovers_exact_tr():
 
 
 def test_sampled_update_relative_error_guarantee():
-    """Thm. 3.6 at a size where its J bound is attainable: with J above the bound, the
+    """Thm. 7 at a size where its J bound is attainable: with J above the bound, the
     sampled solution is within (1 + eps) of the optimum in at least a (1 - delta) fraction
     of independent draws."""
     rng = np.random.default_rng(4)
@@ -91,7 +91,7 @@ def test_sampled_update_relative_error_guarantee():
 
 def test_tr_als_sampled_tracks_tr_als_on_noisy_data():
     """On a noisy low-rank tensor, Alg. 2 with a moderate J reaches an error close to Alg. 1
-    (the paper's experiments compare final errors this way, Sec. 4.1). Seed 2 is a start
+    (the paper's experiments compare final errors this way, Sec. 5.1). Seed 2 is a start
     from which both reach the noise floor; many random starts stall near 0.3 error."""
     rng = np.random.default_rng(2)
     dims, ranks = (12, 11, 10), (3, 3, 3)
@@ -104,3 +104,49 @@ def test_tr_als_sampled_tracks_tr_als_on_noisy_data():
     e_samp = orc.rel_error(orc.tr_als_sampled(X, init, J=400, sweeps=60, seed=1), X)
     assert e_full < 0.02
     assert e_samp < 1.5 * e_full
+
+
+def _noisy_problem(seed=2, dims=(12, 11, 10), ranks=(3, 3, 3)):
+    rng = np.random.default_rng(seed)
+    N = len(dims)
+    true = [rng.standard_normal((ranks[(k - 1) % N], dims[k], ranks[k])) for k in range(N)]
+    X = orc.tr_reconstruct(true)
+    X = X + 0.01 * np.linalg.norm(X) / np.sqrt(X.size) * rng.standard_normal(dims)
+    init = [rng.standard_normal(c.shape) for c in true]
+    return X, init
+
+
+def test_stop_rule_with_zero_tolerance_runs_the_cap():
+    """|f_s - f_{s-1}| < 0 never holds: the loop runs max_sweeps sweeps, its cores are those of
+    the fixed-sweep driver, and each recorded fit is 1 - rel_error of that sweep's cores."""
+    X, init = _noisy_problem()
+    cores, fits, conv = orc.tr_als_sampled_until(X, init, J=200, seed=1, fit_tol=0.0,
+                                                 max_sweeps=4)
+    assert not conv and len(fits) == 4
+    seen = []
+    ref = orc.tr_als_sampled(X, init, J=200, sweeps=4, seed=1,
+                             callback=lambda s, c: seen.append(1.0 - orc.rel_error(c, X)))
+    for a, b in zip(cores, ref):
+        np.testing.assert_array_equal(a, b)
+    np.testing.assert_array_equal(np.array(fits), np.array(seen))
+
+
+def test_stop_rule_with_infinite_tolerance_stops_after_two_sweeps():
+    """Any finite change is below an infinite tolerance, and the first comparison is
+    after sweep 2."""
+    X, init = _noisy_problem()
+    _, fits, conv = orc.tr_als_sampled_until(X, init, J=200, seed=1, fit_tol=np.inf,
+                                             max_sweeps=10)
+    assert conv and len(fits) == 2
+
+
+def test_stop_rule_on_exact_tr_stops_at_the_exact_fit():
+    """On a noise-free TR tensor the sampled updates converge to the exact cores (see the
+    recovery pin above), so the fit tends to 1 and its change vanishes: the loop stops
+    with |f_s - f_{s-1}| < tol and f_s within a few tol of 1."""
+    X, init = _exact_tr((6, 7, 8), (2, 2, 2), seed=0)
+    tol = 1e-9
+    _, fits, conv = orc.tr_als_sampled_until(X, init, J=40, seed=1, fit_tol=tol, max_sweeps=300)
+    assert conv
+    assert abs(fits[-1] - fits[-2]) < tol
+    assert fits[-1] > 1.0 - 1e-6

@@ -1,5 +1,5 @@
-"""Pins for the oracle's tensor-ring format, unfoldings and subchains (Sec. 2.1, eq. 1,
-Def. 3.1, Def. 3.2, the objective identity of Sec. 2.1 and Remark 2.1). CPU only."""
+"""Pins for the oracle's tensor-ring format, unfoldings and subchains (Sec. 3.1, eq. 1,
+Def. 2, Def. 3, the objective identity of Sec. 3.1 and Remark 1). CPU only."""
 
 import itertools
 import os
@@ -43,9 +43,9 @@ def test_reconstruct_matches_bruteforce(dims, ranks):
                                atol=1e-12)
 
 
-def test_remark21_tt_ranks():
+def test_remark1_tt_ranks():
     vals = {}
-    for line in open(os.path.join(GOLDEN, "remark21_tr_vs_tt.txt")):
+    for line in open(os.path.join(GOLDEN, "remark1_tr_vs_tt.txt")):
         if line.startswith("#") or not line.strip():
             continue
         k, *v = line.split()
@@ -97,7 +97,7 @@ def test_subchain_matches_definition():
             lin = int(orc.ring_linear_index(np.array([ii]), dims, n)[0])
             for rn in range(ranks[n]):
                 for rm in range(ranks[n - 1]):
-                    # Def. 3.2: sum over all r except r_{n-1}, r_n of prod_{j != n} G^(j)
+                    # Def. 3: sum over all r except r_{n-1}, r_n of prod_{j != n} G^(j)
                     tot = 0.0
                     free = [j for j in range(N) if j not in (n, (n - 1) % N)]
                     for rf in itertools.product(*[range(ranks[j]) for j in free]):
@@ -117,7 +117,7 @@ def test_subchain_matches_definition():
 
 @pytest.mark.parametrize("dims,ranks", [((4, 5, 3), (2, 3, 2)), ((3, 2, 4, 3), (2, 2, 3, 1))])
 def test_objective_identity(dims, ranks):
-    """||TR - X||_F = ||G_[2]^{!=n} G_(2)^(n)T - X_[n]^T||_F (Sec. 2.1), and more strongly the
+    """||TR - X||_F = ||G_[2]^{!=n} G_(2)^(n)T - X_[n]^T||_F (Sec. 3.1), and more strongly the
     unfolded reconstruction equals the product elementwise."""
     cores = _rand_cores(dims, ranks, 7)
     X = np.random.default_rng(8).standard_normal(dims)

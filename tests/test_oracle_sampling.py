@@ -1,5 +1,5 @@
-"""Pins for the oracle's random numbers, leverage scores and sampler (Def. 3.3, Def. 3.4,
-eq. for p^(n), eq. for q^{!=n}, Alg. 3, Lemma 3.5). CPU only."""
+"""Pins for the oracle's random numbers, leverage scores and sampler (Def. 4, Def. 5,
+eq. for p^(n), eq. for q^{!=n}, Alg. 3, Lemma 6). CPU only."""
 
 import itertools
 import os
@@ -126,11 +126,11 @@ def test_sampler_frequencies_and_weights():
     assert counts[q == 0].sum() == 0                       # zero-probability cells never drawn
     pos = q > 0
     assert stats.chisquare(counts[pos], J * q[pos]).pvalue > 1e-4
-    np.testing.assert_allclose(w ** 2 * J * q[lin], 1.0, rtol=1e-13)   # Def. 3.4 rescaling
+    np.testing.assert_allclose(w ** 2 * J * q[lin], 1.0, rtol=1e-13)   # Def. 5 rescaling
 
 
 def test_sketch_is_unbiased():
-    """E[S^T S] = I for S ~ D(J, q) (Def. 3.4): the mean of sum_j w_j^2 [v_j = i] is 1."""
+    """E[S^T S] = I for S ~ D(J, q) (Def. 5): the mean of sum_j w_j^2 [v_j = i] is 1."""
     dims = (2, 3, 4)
     rng = np.random.default_rng(6)
     ps = [rng.uniform(0.2, 1.0, d) for d in dims]
@@ -149,7 +149,7 @@ def test_sketch_is_unbiased():
 
 
 def test_lemma35_leverage_bound():
-    """Lemma 3.5 / its proof: ell_i(G_[2]^{!=n}) <= prod_{j!=n} ell_{i_j}(G_(2)^(j)), hence
+    """Lemma 6 / its proof: ell_i(G_[2]^{!=n}) <= prod_{j!=n} ell_{i_j}(G_(2)^(j)), hence
     q^{!=n} >= beta_n * p with p the exact leverage distribution of G_[2]^{!=n}."""
     dims, ranks = (5, 4, 6, 3), (2, 3, 2, 2)
     rng = np.random.default_rng(7)
