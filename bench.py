@@ -70,6 +70,12 @@ def allreduce_max(x: float, world: int) -> float:
     return float(t.item())
 
 
+def weak_scaling_value(units_per_rank: float, local_seconds: float, world: int) -> float:
+    """Whole-job throughput of `world` replicas: all ranks' units over the slowest rank's
+    time (max over ranks)."""
+    return world * units_per_rank / allreduce_max(local_seconds, world)
+
+
 def barrier(world: int):
     if world > 1:
         import torch.distributed as dist
@@ -519,8 +525,8 @@ def run_ours(args):
     barrier(world)
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    total_s = allreduce_max(sum(step_ms) / 1e3, world)
-    value = world * sweeps * args.steps / total_s
+    value = weak_scaling_value(sweeps * args.steps, sum(step_ms) / 1e3, world)
+    total_s = world * sweeps * args.steps / value
     fit = T.tr_rel_error(ctx, X, ranks, cores)
 
     # The same steps again with every kernel bracketed by CUDA events on its stream (the
