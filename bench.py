@@ -396,7 +396,12 @@ def run_serving(T, dev, seconds, rate=200.0, warmup_s=3.0, pool_size=128, seed=0
     meas = [(r, due, sh) for r, due, at, sh in results if at >= warmup_s and r["done"]]
     lat = sorted((r["t_done_ns"] - due) / 1e6 for r, due, sh in meas)
     queue = sorted((r["t_admit_ns"] - r["t_submit_ns"]) / 1e6 for r, due, sh in meas)
-    win_s = seconds
+    # sustained rate: measured requests over the time from the first measured arrival to
+    # the last measured completion (includes any backlog drained after the stream ends)
+    t0m = t_start + int(warmup_s * 1e9)
+    t1m = max((r["t_done_ns"] for r, _, _ in meas), default=t0m + 1)
+    win_s = max(seconds, (t1m - t0m) / 1e9)
+    in_window = sum(1 for r, _, _ in meas if r["t_done_ns"] <= t0m + int(seconds * 1e9))
     sweeps = [r["sweeps"] for r, _, _ in meas]
     n_upd = sum(r["sweeps"] * len(sh["dims"]) for r, _, sh in meas)
     conv = sum(1 for r, _, _ in meas if r["status"] == T.TR_OK)
@@ -415,6 +420,8 @@ def run_serving(T, dev, seconds, rate=200.0, warmup_s=3.0, pool_size=128, seed=0
         "admission_wait_ms": {"p50": round(float(np.percentile(queue, 50)), 3) if queue else None,
                               "p99": round(float(np.percentile(queue, 99)), 3) if queue else None},
         "throughput_req_per_s": round(len(meas) / win_s, 2),
+        "throughput_window_s": round(win_s, 2),
+        "completed_in_arrival_window": in_window,
         "sweeps_per_s": round(sum(sweeps) / win_s, 1),
         "updates_per_s": round(n_upd / win_s, 1),
         "sweeps_per_request": {"mean": round(float(np.mean(sweeps)), 2) if sweeps else None,

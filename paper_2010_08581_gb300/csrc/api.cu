@@ -1037,11 +1037,12 @@ tr_status tr_rel_error(tr_ctx* ctx, const void* X, tr_dtype X_dtype, int N, cons
   }
   DeviceGuard g(ctx->device);
   int blocks;
-  const size_t bytes = fit_workspace(fa, &blocks);
+  const bool xf64 = X_dtype == TR_F64;
+  const size_t bytes = fit_workspace(fa, xf64, &blocks);
   TR_TRY(ensure_ws(ctx, bytes));
   double* partial = reinterpret_cast<double*>(ctx->arena);
   cudaStream_t st = S(stream);
-  TR_LAUNCH("fit", launch_fit(fa, X, X_dtype == TR_F64, partial, blocks, st));
+  TR_LAUNCH("fit", launch_fit(fa, X, xf64, ctx->arena, blocks, st));
   std::vector<double> h(2 * static_cast<size_t>(blocks));
   TR_CUDA(cudaMemcpyAsync(h.data(), partial, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
   TR_CUDA(cudaStreamSynchronize(st));

@@ -404,12 +404,6 @@ __global__ void __launch_bounds__(TW * 32) kb_rows(const BInst* __restrict__ tab
 // rule (|fit_s - fit_{s-1}| < tol after two or more sweeps, or the sweep cap) and the step
 // counters.
 // ------------------------------------------------------------------------------------
-__device__ __forceinline__ int64_t lead_count(const BInst& d) {
-  int64_t lead = 1;
-  for (int m = 0; m < d.N - 1; ++m) lead *= d.dims[m];
-  return lead;
-}
-
 // The slot's step is the last update of a sweep.
 __device__ __forceinline__ bool fit_due(const BInst& d) {
   if (!d.slot) return false;
@@ -418,13 +412,43 @@ __device__ __forceinline__ bool fit_due(const BInst& d) {
 }
 
 template <typename T>
-__device__ __forceinline__ int fit_parts(const BInst& d) {
-  const int64_t nblk = (lead_count(d) + FitTile<T>::FL - 1) / FitTile<T>::FL;
+__device__ __forceinline__ int fit_parts(const FitSplit& f) {
+  const int64_t nblk = (f.rows + FitTile<T>::FL - 1) / FitTile<T>::FL;
   return nblk < kFitParts ? static_cast<int>(nblk) : kFitParts;
 }
 
+__device__ __forceinline__ void fit_args(const BInst& d, FitArgs& fa) {
+  fa.N = d.N;
+  for (int m = 0; m < d.N; ++m) {
+    fa.core[m] = d.cores[m];
+    fa.dims[m] = d.dims[m];
+    fa.ranks[m] = d.ranks[m];
+  }
+}
+
+constexpr int kFitRightCtas = 64;   // CTAs per slot forming the right factors
+
 template <typename T>
-__global__ void __launch_bounds__(FNT) kb_fit(const BInst* __restrict__ tab) {
+__global__ void __launch_bounds__(FNT) kb_fit_right(const BInst* __restrict__ tab) {
+  __shared__ T chain[8][kMaxL];
+  __shared__ T slice[8][kMaxL];
+  __shared__ FitArgs fa;
+  const BInst& d = tab[blockIdx.x];
+  if (!fit_due(d)) return;
+  if (threadIdx.x == 0) fit_args(d, fa);
+  __syncthreads();
+  const FitSplit f = fit_split(fa.N, fa.dims, fa.ranks);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  T* WT = static_cast<T*>(d.fitw);
+  for (int64_t q = static_cast<int64_t>(blockIdx.y) * (FNT / 32) + warp; q < f.cols;
+       q += static_cast<int64_t>(gridDim.y) * (FNT / 32))
+    fit_right_warp<T>(fa, f, q, WT, chain[warp], slice[warp], lane);
+}
+
+// Slots whose contraction length K lies in (k_lo, k_hi] (two launches with different
+// shared-memory sizes keep the common small-K case at several CTAs per SM).
+template <typename T>
+__global__ void __launch_bounds__(FNT) kb_fit(const BInst* __restrict__ tab, int k_lo, int k_hi) {
   extern __shared__ __align__(16) unsigned char fit_dyn[];
   __shared__ T chain[8][kMaxL];
   __shared__ T slice[8][kMaxL];
@@ -432,20 +456,15 @@ __global__ void __launch_bounds__(FNT) kb_fit(const BInst* __restrict__ tab) {
   __shared__ FitArgs fa;
   const BInst& d = tab[blockIdx.x];
   if (!fit_due(d)) return;
-  const int parts = fit_parts<T>(d);
-  if (static_cast<int>(blockIdx.y) >= parts) return;
-  if (threadIdx.x == 0) {
-    fa.N = d.N;
-    for (int m = 0; m < d.N; ++m) {
-      fa.core[m] = d.cores[m];
-      fa.dims[m] = d.dims[m];
-      fa.ranks[m] = d.ranks[m];
-    }
-  }
+  if (threadIdx.x == 0) fit_args(d, fa);
   __syncthreads();
+  const FitSplit f = fit_split(fa.N, fa.dims, fa.ranks);
+  if (f.K <= k_lo || f.K > k_hi) return;
+  const int parts = fit_parts<T>(f);
+  if (static_cast<int>(blockIdx.y) >= parts) return;
   double se = 0.0, sx = 0.0;
-  fit_blocks<T>(fa, static_cast<const T*>(d.X), lead_count(d), blockIdx.y, parts, fit_dyn, chain,
-                slice, se, sx);
+  fit_blocks<T>(fa, f, static_cast<const T*>(d.X), static_cast<const T*>(d.fitw), blockIdx.y,
+                parts, fit_dyn, chain, slice, se, sx);
   fit_block_reduce(se, sx, red);
   if (threadIdx.x == 0) {
     d.fitp[blockIdx.y] = se;
@@ -464,7 +483,8 @@ __global__ void __launch_bounds__(128) kb_advance(const BInst* __restrict__ tab,
   const int t = s.step;
   if (t >= 0 && *d.info != 0) s.singular += 1;
   if (fit_due(d)) {
-    const int parts = xf64 ? fit_parts<double>(d) : fit_parts<float>(d);
+    const FitSplit f = fit_split(d.N, d.dims, d.ranks);
+    const int parts = xf64 ? fit_parts<double>(f) : fit_parts<float>(f);
     double se = 0.0, sx = 0.0;
     for (int q = 0; q < parts; ++q) {
       se += d.fitp[q];
@@ -568,11 +588,21 @@ cudaError_t bl_leverage_rows(const BLaunch& b, int step, int init_k, unsigned* e
 }
 
 cudaError_t bl_fit(const BLaunch& b, cudaStream_t st) {
+  dim3 rgrid(b.count, kFitRightCtas);
   dim3 grid(b.count, kFitParts);
-  if (b.xf64)
-    kb_fit<double><<<grid, FNT, fit_smem_bytes<double>(b.Lmax), st>>>(b.tab);
-  else
-    kb_fit<float><<<grid, FNT, fit_smem_bytes<float>(b.Lmax), st>>>(b.tab);
+  constexpr int kSplitK = 128;
+  const int k_small = b.Lmax < kSplitK ? b.Lmax : kSplitK;
+  if (b.xf64) {
+    kb_fit_right<double><<<rgrid, FNT, 0, st>>>(b.tab);
+    kb_fit<double><<<grid, FNT, fit_smem_bytes<double>(k_small), st>>>(b.tab, 0, kSplitK);
+    if (b.Lmax > kSplitK)
+      kb_fit<double><<<grid, FNT, fit_smem_bytes<double>(b.Lmax), st>>>(b.tab, kSplitK, kMaxL);
+  } else {
+    kb_fit_right<float><<<rgrid, FNT, 0, st>>>(b.tab);
+    kb_fit<float><<<grid, FNT, fit_smem_bytes<float>(k_small), st>>>(b.tab, 0, kSplitK);
+    if (b.Lmax > kSplitK)
+      kb_fit<float><<<grid, FNT, fit_smem_bytes<float>(b.Lmax), st>>>(b.tab, kSplitK, kMaxL);
+  }
   return cudaGetLastError();
 }
 

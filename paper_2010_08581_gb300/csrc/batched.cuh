@@ -21,7 +21,7 @@
 namespace trk {
 
 constexpr int kMaxServedSweeps = 64;   // sweep cap and fit-history length of a served slot
-constexpr int kFitParts = 128;         // partial sums of one fit evaluation (fixed order)
+constexpr int kFitParts = 256;         // partial sums of one fit evaluation (fixed order)
 
 enum SlotStatus : int {
   kSlotIdle = 0,
@@ -74,6 +74,7 @@ struct BInst {
   // serving (nullptr for the batched driver)
   SlotState* slot;
   double* fitp;                  // 2 * kFitParts partial sums of the fit evaluation
+  void* fitw;                    // right factors of the fit's mode split (X's precision)
   double* hist;                  // kMaxServedSweeps fits, one per completed sweep
 };
 

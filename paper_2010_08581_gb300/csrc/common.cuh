@@ -164,8 +164,9 @@ struct FitArgs {
   int ranks[kMaxModes];
   int N;
 };
-size_t fit_workspace(const FitArgs& a, int* blocks);
-cudaError_t launch_fit(const FitArgs& a, const void* X, bool x_f64, double* partial,
-                       int blocks, cudaStream_t st);
+// Workspace: 2 * blocks partial sums, then the right factors of the mode split.
+size_t fit_workspace(const FitArgs& a, bool x_f64, int* blocks);
+cudaError_t launch_fit(const FitArgs& a, const void* X, bool x_f64, void* ws, int blocks,
+                       cudaStream_t st);
 
 }  // namespace trk

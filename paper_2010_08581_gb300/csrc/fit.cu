@@ -1,19 +1,31 @@
-// Relative error ||TR(cores) - X||_F / ||X||_F (Sec. 5.1) of one problem: partial sums of
-// the squared residual and of ||X||^2 per CTA (fit_body.cuh), reduced in a fixed order.
+// Relative error ||TR(cores) - X||_F / ||X||_F (Sec. 5.1) of one problem: the right factors
+// W^T of the mode split (fit_body.cuh), then partial sums of the squared residual and of
+// ||X||^2 per CTA, reduced on the host in a fixed order.
 #include "fit_body.cuh"
 
 namespace trk {
 namespace {
 
 template <typename T>
-__global__ void __launch_bounds__(FNT) k_fit(FitArgs a, const T* __restrict__ X, int64_t lead,
+__global__ void __launch_bounds__(FNT) k_fit_right(FitArgs a, FitSplit f, T* __restrict__ WT) {
+  __shared__ T chain[8][kMaxL];
+  __shared__ T slice[8][kMaxL];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t q = static_cast<int64_t>(blockIdx.x) * (FNT / 32) + warp;
+  if (q >= f.cols) return;
+  fit_right_warp<T>(a, f, q, WT, chain[warp], slice[warp], lane);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(FNT) k_fit(FitArgs a, FitSplit f, const T* __restrict__ X,
+                                             const T* __restrict__ WT,
                                              double* __restrict__ partial, int blocks) {
   extern __shared__ __align__(16) unsigned char fit_smem_raw[];
   __shared__ T chain[8][kMaxL];
   __shared__ T slice[8][kMaxL];
   __shared__ double red[2 * (FNT / 32)];
   double se = 0.0, sx = 0.0;
-  fit_blocks<T>(a, X, lead, blockIdx.x, gridDim.x, fit_smem_raw, chain, slice, se, sx);
+  fit_blocks<T>(a, f, X, WT, blockIdx.x, gridDim.x, fit_smem_raw, chain, slice, se, sx);
   fit_block_reduce(se, sx, red);
   if (threadIdx.x == 0) {
     partial[blockIdx.x] = se;
@@ -21,33 +33,41 @@ __global__ void __launch_bounds__(FNT) k_fit(FitArgs a, const T* __restrict__ X,
   }
 }
 
-int64_t lead_of(const FitArgs& a) {
-  int64_t lead = 1;
-  for (int m = 0; m < a.N - 1; ++m) lead *= a.dims[m];
-  return lead;
-}
+FitSplit split_of(const FitArgs& a) { return fit_split(a.N, a.dims, a.ranks); }
+
+size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
 
 }  // namespace
 
-size_t fit_workspace(const FitArgs& a, int* blocks) {
-  // FP32 tiles have 64 leading indices (FP64: 32); the grid is sized for the FP32 tiles.
-  int64_t b = (lead_of(a) + FitTile<float>::FL - 1) / FitTile<float>::FL;
+size_t fit_workspace(const FitArgs& a, bool x_f64, int* blocks) {
+  const FitSplit f = split_of(a);
+  const int FL = x_f64 ? FitTile<double>::FL : FitTile<float>::FL;
+  int64_t b = (f.rows + FL - 1) / FL;
   if (b > 152 * 4) b = 152 * 4;
   if (b < 1) b = 1;
   *blocks = static_cast<int>(b);
-  return static_cast<size_t>(2 * b) * sizeof(double);
+  const size_t es = x_f64 ? 8 : 4;
+  return round256(static_cast<size_t>(2 * b) * sizeof(double)) +
+         static_cast<size_t>(f.cols) * f.K * es;
 }
 
-cudaError_t launch_fit(const FitArgs& a, const void* X, bool x_f64, double* partial, int blocks,
+cudaError_t launch_fit(const FitArgs& a, const void* X, bool x_f64, void* ws, int blocks,
                        cudaStream_t st) {
-  const int64_t lead = lead_of(a);
-  const int Lq = a.ranks[a.N - 2] * a.ranks[a.N - 1];
-  if (x_f64)
-    k_fit<double><<<blocks, FNT, fit_smem_bytes<double>(Lq), st>>>(
-        a, static_cast<const double*>(X), lead, partial, blocks);
-  else
-    k_fit<float><<<blocks, FNT, fit_smem_bytes<float>(Lq), st>>>(
-        a, static_cast<const float*>(X), lead, partial, blocks);
+  const FitSplit f = split_of(a);
+  double* partial = static_cast<double*>(ws);
+  char* wt = static_cast<char*>(ws) + round256(static_cast<size_t>(2 * blocks) * sizeof(double));
+  const unsigned rb = static_cast<unsigned>((f.cols + FNT / 32 - 1) / (FNT / 32));
+  if (x_f64) {
+    double* WT = reinterpret_cast<double*>(wt);
+    k_fit_right<double><<<rb, FNT, 0, st>>>(a, f, WT);
+    k_fit<double><<<blocks, FNT, fit_smem_bytes<double>(f.K), st>>>(
+        a, f, static_cast<const double*>(X), WT, partial, blocks);
+  } else {
+    float* WT = reinterpret_cast<float*>(wt);
+    k_fit_right<float><<<rb, FNT, 0, st>>>(a, f, WT);
+    k_fit<float><<<blocks, FNT, fit_smem_bytes<float>(f.K), st>>>(
+        a, f, static_cast<const float*>(X), WT, partial, blocks);
+  }
   return cudaGetLastError();
 }
 

@@ -1,22 +1,29 @@
-// Relative-error partial sums ||TR(cores) - X||_F^2 and ||X||_F^2 (Sec. 5.1) without forming
-// TR(cores), shared by the single-problem kernel and the served fit evaluation.
+// Relative-error partial sums ||TR(cores) - X||_F^2 and ||X||_F^2 (Sec. 4.1, Sec. 5.1)
+// without forming TR(cores), shared by the single-problem kernels and the served fit.
 //
-// X is viewed as a (prod_{m<N-1} I_m) x I_{N-1} matrix. For a block of FL leading
-// multi-indices l the slice product P_l = G^(0)(:, i_0, :) ... G^(N-2)(:, i_{N-2}, :) is built
-// in shared memory (eq. 1 without the last core); then for every i of the last mode
-// TR(l, i) = trace(P_l G^(N-1)(:, i, :)) = sum_e V_l[e] Q_i[e], with Q_i the contiguous slice
-// i of the last core and V_l[c * Rr + a] = P_l[a][c]. Both operands are staged e-major
-// (V^T: Lq x FL, Q^T: Lq x FI) so that each thread computes an MI x MJ register tile of
-// TR(l, i) from two vector loads per e. Row e of V^T stores its 16 groups of MI entries in
-// the order g ^ (e & 15), which spreads the per-index column writes over the banks while
-// keeping each group contiguous. Squares are accumulated in FP64 per thread.
+// The modes are split at s (1 <= s <= N-1): X is viewed as a rows x cols matrix with
+// rows = prod_{m<s} I_m and cols = prod_{m>=s} I_m (row-major X). By eq. 1,
+//   TR(p, q) = trace(P_left(p) P_right(q)),
+//   P_left(p)  = G^(0)(:, i_0, :) ... G^(s-1)(:, i_{s-1}, :)    (R_{N-1} x R_{s-1}),
+//   P_right(q) = G^(s)(:, i_s, :) ... G^(N-1)(:, i_{N-1}, :)    (R_{s-1} x R_{N-1}),
+// so TR(p, q) = sum_e V_p[e] W_q[e] over e = b * R_{N-1} + a with V_p[e] = P_left[a][b] and
+// W_q[e] = P_right[b][a]: one dense contraction with K = R_{N-1} R_{s-1} <= 256.
+//
+// W is formed once per evaluation (fit_right_warp, e-major: W^T[e][q]) and V per block of FL
+// rows in shared memory. Each thread computes an MI x MJ register tile of TR from two
+// vector loads per e; squares of (X - TR) and of X are summed per tile in X's precision and
+// accumulated across tiles in FP64 per thread. The
+// split is chosen so that cols is large enough to amortise the row chains while W^T stays
+// small (fit_split).
 #pragma once
 
 #include "common.cuh"
 
 namespace trk {
 
-constexpr int FNT = 256;   // threads of a fit CTA
+constexpr int FNT = 256;                       // threads of a fit CTA
+constexpr int64_t kFitMinCols = 256;           // grow cols (move s left) up to this
+constexpr int64_t kFitMaxRight = 1ll << 22;    // max elements of W^T (cols * K)
 
 template <typename T>
 struct FitTile;
@@ -29,10 +36,33 @@ struct FitTile<double> {   // 32 x 32 outputs per tile, 2 x 2 per thread
   static constexpr int FL = 32, FI = 32, MI = 2, MJ = 2;
 };
 
-// Dynamic shared memory of a fit CTA for last-core slices of Lq = R_{N-2} R_{N-1} entries.
+struct FitSplit {
+  int s;          // first mode of the right group
+  int K;          // R_{N-1} * R_{s-1}
+  int64_t rows, cols;
+};
+
+__host__ __device__ inline FitSplit fit_split(int N, const int64_t* dims, const int* ranks) {
+  FitSplit f;
+  f.s = N - 1;
+  f.cols = dims[N - 1];
+  while (f.s > 1 && f.cols < kFitMinCols) {
+    const int64_t c2 = f.cols * dims[f.s - 1];
+    const int64_t k2 = static_cast<int64_t>(ranks[N - 1]) * ranks[f.s - 2];
+    if (c2 * k2 > kFitMaxRight) break;
+    f.s -= 1;
+    f.cols = c2;
+  }
+  f.rows = 1;
+  for (int m = 0; m < f.s; ++m) f.rows *= dims[m];
+  f.K = ranks[N - 1] * ranks[f.s - 1];
+  return f;
+}
+
+// Dynamic shared memory of a fit CTA for contraction length K.
 template <typename T>
-__host__ __device__ constexpr size_t fit_smem_bytes(int Lq) {
-  return static_cast<size_t>(Lq) * (FitTile<T>::FL + FitTile<T>::FI) * sizeof(T);
+__host__ __device__ constexpr size_t fit_smem_bytes(int K) {
+  return static_cast<size_t>(K) * (FitTile<T>::FL + FitTile<T>::FI) * sizeof(T);
 }
 
 // Loads `n` consecutive elements (n = 2 or 4, 16-byte aligned) from shared memory.
@@ -50,88 +80,124 @@ __device__ __forceinline__ void load_vec(const T* p, T* out) {
   }
 }
 
-// Accumulates the squared residual (se) and ||X||^2 (sx) over the leading blocks
-// first, first + stride, ... of X. All threads of the CTA must call it. `chain` and `slice`
-// are per-warp scratch of kMaxL elements (8 warps); `dyn` holds fit_smem_bytes<T>(Lq).
+// Product of the lateral slices of modes m0..m1-1 at indices ii[m] into S (row-major
+// R_{m0-1} x R_{m1-1}), one warp; G is per-warp scratch. Returns the column count.
 template <typename T>
-__device__ void fit_blocks(const FitArgs& a, const T* __restrict__ X, int64_t lead,
-                           int64_t first, int64_t stride, unsigned char* dyn,
-                           T (*chain)[kMaxL], T (*slice)[kMaxL], double& se, double& sx) {
+__device__ __forceinline__ int warp_slice_product(const FitArgs& a, int m0, int m1,
+                                                  const int64_t* ii, T* S, T* G, int lane) {
+  const int N = a.N;
+  int rows = a.ranks[(m0 - 1 + N) % N], cols = a.ranks[m0];
+  {
+    const double* src = a.core[m0] + ii[m0] * rows * cols;
+    for (int e = lane; e < rows * cols; e += 32) S[e] = static_cast<T>(src[e]);
+  }
+  for (int m = m0 + 1; m < m1; ++m) {
+    const int rr = a.ranks[m];
+    const double* src = a.core[m] + ii[m] * cols * rr;
+    for (int e = lane; e < cols * rr; e += 32) G[e] = static_cast<T>(src[e]);
+    __syncwarp();
+    T acc[kMaxL / 32];
+#pragma unroll
+    for (int q = 0; q < kMaxL / 32; ++q) {
+      const int e = lane + 32 * q;
+      T s = T(0);
+      if (e < rows * rr) {
+        const int r = e / rr, c = e - r * rr;
+        for (int t = 0; t < cols; ++t) s += S[r * cols + t] * G[t * rr + c];
+      }
+      acc[q] = s;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < kMaxL / 32; ++q) {
+      const int e = lane + 32 * q;
+      if (e < rows * rr) S[e] = acc[q];
+    }
+    __syncwarp();
+    cols = rr;
+  }
+  return cols;
+}
+
+// W^T[e][q] = P_right(q)[b][a] (e = b * R_{N-1} + a: the row-major index of P_right) for
+// column q, one warp; S and G are per-warp scratch of kMaxL elements.
+template <typename T>
+__device__ __forceinline__ void fit_right_warp(const FitArgs& a, const FitSplit& f, int64_t q,
+                                               T* __restrict__ WT, T* S, T* G, int lane) {
+  const int N = a.N;
+  int64_t ii[kMaxModes];
+  int64_t rem = q;
+  for (int m = N - 1; m >= f.s; --m) { ii[m] = rem % a.dims[m]; rem /= a.dims[m]; }
+  warp_slice_product<T>(a, f.s, N, ii, S, G, lane);
+  __syncwarp();
+  for (int e = lane; e < f.K; e += 32) WT[e * f.cols + q] = S[e];
+  __syncwarp();
+}
+
+// Accumulates the squared residual (se) and ||X||^2 (sx) over the row blocks
+// first, first + stride, ... All threads of the CTA must call it. `chain` and `slice` are
+// per-warp scratch of kMaxL elements (8 warps); `dyn` holds fit_smem_bytes<T>(f.K).
+template <typename T>
+__device__ void fit_blocks(const FitArgs& a, const FitSplit& f, const T* __restrict__ X,
+                           const T* __restrict__ WT, int64_t first, int64_t stride,
+                           unsigned char* dyn, T (*chain)[kMaxL], T (*slice)[kMaxL],
+                           double& se, double& sx) {
   constexpr int FL = FitTile<T>::FL, FI = FitTile<T>::FI;
   constexpr int MI = FitTile<T>::MI, MJ = FitTile<T>::MJ;
-  constexpr int TX = FI / MJ;   // threads along the last mode (16)
+  constexpr int TX = FI / MJ;   // threads along the columns (16)
   static_assert((FL / MI) * (FI / MJ) == FNT, "one register tile per thread");
   static_assert(FL / MI == 16, "16 swizzled groups per row of V^T");
+  // Row e of V^T stores its 16 groups of MI entries in the order g ^ (e & 15): the per-row
+  // column writes of the chain phase spread over the banks, each group stays contiguous.
   auto vpos = [](int e, int ll) { return e * FL + (((ll / MI) ^ (e & 15)) * MI) + ll % MI; };
   const int N = a.N;
-  const int Rl_last = a.ranks[N - 2], Rr_last = a.ranks[N - 1];
-  const int Lq = Rl_last * Rr_last;
-  T* Vt = reinterpret_cast<T*>(dyn);   // [Lq][FL]
-  T* Qt = Vt + Lq * FL;                // [Lq][FI]
-  const int64_t Ilast = a.dims[N - 1];
+  const int K = f.K;
+  const int Rlast = a.ranks[N - 1];
+  T* Vt = reinterpret_cast<T*>(dyn);   // [K][FL]
+  T* Qt = Vt + K * FL;                 // [K][FI]
+  const int64_t rows = f.rows, cols = f.cols;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ty = threadIdx.x / TX, tx = threadIdx.x % TX;
+  const bool vec_ok = sizeof(T) == 4 && (cols % 4) == 0 &&
+                      (reinterpret_cast<uintptr_t>(WT) % 16) == 0;
 
-  for (int64_t blk = first; blk * FL < lead; blk += stride) {
-    const int64_t l0 = blk * FL;
-    // 1. slice products of the FL leading indices, one warp per index.
+  for (int64_t blk = first; blk * FL < rows; blk += stride) {
+    const int64_t p0 = blk * FL;
+    // 1. V^T for the FL rows of the block, one warp per row.
     for (int ll = warp; ll < FL; ll += FNT / 32) {
-      const int64_t l = l0 + ll;
-      if (l >= lead) {
-        for (int e = lane; e < Lq; e += 32) Vt[vpos(e, ll)] = T(0);
+      const int64_t p = p0 + ll;
+      if (p >= rows) {
+        for (int e = lane; e < K; e += 32) Vt[vpos(e, ll)] = T(0);
         continue;
       }
-      int64_t rem = l;
       int64_t ii[kMaxModes];
-      for (int m = N - 2; m >= 0; --m) { ii[m] = rem % a.dims[m]; rem /= a.dims[m]; }
+      int64_t rem = p;
+      for (int m = f.s - 1; m >= 0; --m) { ii[m] = rem % a.dims[m]; rem /= a.dims[m]; }
       T* S = chain[warp];
-      T* G = slice[warp];
-      {
-        const int rl = a.ranks[N - 1], rr = a.ranks[0];
-        const double* src = a.core[0] + ii[0] * rl * rr;
-        for (int e = lane; e < rl * rr; e += 32) S[e] = static_cast<T>(src[e]);
-      }
-      int rows = a.ranks[N - 1], cols = a.ranks[0];
-      for (int m = 1; m <= N - 2; ++m) {
-        const int rr = a.ranks[m];
-        const double* src = a.core[m] + ii[m] * cols * rr;
-        for (int e = lane; e < cols * rr; e += 32) G[e] = static_cast<T>(src[e]);
-        __syncwarp();
-        T acc[kMaxL / 32];
-#pragma unroll
-        for (int q = 0; q < kMaxL / 32; ++q) {
-          const int e = lane + 32 * q;
-          T s = T(0);
-          if (e < rows * rr) {
-            const int r = e / rr, c = e - r * rr;
-            for (int t = 0; t < cols; ++t) s += S[r * cols + t] * G[t * rr + c];
-          }
-          acc[q] = s;
-        }
-        __syncwarp();
-#pragma unroll
-        for (int q = 0; q < kMaxL / 32; ++q) {
-          const int e = lane + 32 * q;
-          if (e < rows * rr) S[e] = acc[q];
-        }
-        __syncwarp();
-        cols = rr;
-      }
-      // S is Rr_last x Rl_last (P[a][c]); V[c * Rr_last + a] = P[a][c].
-      for (int e = lane; e < Lq; e += 32) {
-        const int c = e / Rr_last, aa = e - c * Rr_last;
-        Vt[vpos(e, ll)] = S[aa * cols + c];
+      const int Rs = warp_slice_product<T>(a, 0, f.s, ii, S, slice[warp], lane);
+      __syncwarp();
+      // S is R_{N-1} x R_{s-1} (P_left[a][b]); V[b * R_{N-1} + a] = P_left[a][b].
+      for (int e = lane; e < K; e += 32) {
+        const int b = e / Rlast, aa = e - b * Rlast;
+        Vt[vpos(e, ll)] = S[aa * Rs + b];
       }
       __syncwarp();
     }
     __syncthreads();
-    // 2. TR(l, i) for tiles of the last mode, MI x MJ per thread.
-    const double* Qg = a.core[N - 1];
-    for (int64_t i0 = 0; i0 < Ilast; i0 += FI) {
-      const int ni = static_cast<int>((Ilast - i0 < FI) ? Ilast - i0 : FI);
-      for (int o = threadIdx.x; o < FI * Lq; o += FNT) {
-        const int e = o / FI, iq = o - e * FI;
-        Qt[o] = iq < ni ? static_cast<T>(Qg[(i0 + iq) * Lq + e]) : T(0);
+    // 2. TR(p, q) for tiles of FI columns, MI x MJ per thread.
+    for (int64_t q0 = 0; q0 < cols; q0 += FI) {
+      const int nq = static_cast<int>((cols - q0 < FI) ? cols - q0 : FI);
+      if (vec_ok && nq == FI) {
+        for (int o = threadIdx.x; o < K * (FI / 4); o += FNT) {
+          const int e = o / (FI / 4), c4 = o - e * (FI / 4);
+          *reinterpret_cast<float4*>(Qt + e * FI + 4 * c4) =
+              *reinterpret_cast<const float4*>(WT + e * cols + q0 + 4 * c4);
+        }
+      } else {
+        for (int o = threadIdx.x; o < K * FI; o += FNT) {
+          const int e = o / FI, iq = o - e * FI;
+          Qt[o] = iq < nq ? WT[e * cols + q0 + iq] : T(0);
+        }
       }
       __syncthreads();
       T acc[MI][MJ];
@@ -141,7 +207,7 @@ __device__ void fit_blocks(const FitArgs& a, const T* __restrict__ X, int64_t le
         for (int v = 0; v < MJ; ++v) acc[u][v] = T(0);
       const T* qp = Qt + tx * MJ;
 #pragma unroll 4
-      for (int e = 0; e < Lq; ++e) {
+      for (int e = 0; e < K; ++e) {
         T vv[MI], qq[MJ];
         load_vec<T, MI>(Vt + e * FL + (ty ^ (e & 15)) * MI, vv);
         load_vec<T, MJ>(qp + e * FI, qq);
@@ -150,21 +216,26 @@ __device__ void fit_blocks(const FitArgs& a, const T* __restrict__ X, int64_t le
 #pragma unroll
           for (int v = 0; v < MJ; ++v) acc[u][v] += vv[u] * qq[v];
       }
+      // The tile's squares are summed in T and added to the FP64 totals once per tile
+      // (GB300's FP64 pipe is about 1/64 of its FP32 rate).
+      T se_t = T(0), sx_t = T(0);
 #pragma unroll
       for (int u = 0; u < MI; ++u) {
-        const int64_t l = l0 + ty * MI + u;
-        if (l >= lead) continue;
-        const T* xr = X + l * Ilast + i0;
+        const int64_t p = p0 + ty * MI + u;
+        if (p >= rows) continue;
+        const T* xr = X + p * cols + q0;
 #pragma unroll
         for (int v = 0; v < MJ; ++v) {
           const int iq = tx * MJ + v;
-          if (iq >= ni) continue;
-          const double x = static_cast<double>(xr[iq]);
-          const double d = x - static_cast<double>(acc[u][v]);
-          se += d * d;
-          sx += x * x;
+          if (iq >= nq) continue;
+          const T x = xr[iq];
+          const T d = x - acc[u][v];
+          se_t += d * d;
+          sx_t += x * x;
         }
       }
+      se += static_cast<double>(se_t);
+      sx += static_cast<double>(sx_t);
       __syncthreads();
     }
   }

@@ -23,6 +23,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "fit_body.cuh"
 #include "host_util.h"
 
 namespace trk {
@@ -175,11 +176,18 @@ void free_all(tr_server* s) {
   if (s->ev_join) cudaEventDestroy(s->ev_join);
 }
 
-// Workspace of one request (distributions and per-update scratch).
-size_t request_ws(const tr_request& r, bool f64) {
+// Workspace of one request: distributions, per-update scratch, and the right factors of
+// the fit's mode split (in X's precision).
+void carve_request(Carver& c, const tr_request& r, bool f64, bool xf64, BInst& d) {
+  carve_instance(c, r.N, r.dims, r.ranks, r.J, f64, d);
+  const FitSplit f = fit_split(r.N, r.dims, r.ranks);
+  d.fitw = c.take<char>(static_cast<size_t>(f.cols) * f.K * (xf64 ? 8 : 4));
+}
+
+size_t request_ws(const tr_request& r, bool f64, bool xf64) {
   Carver c(nullptr);
   BInst d{};
-  carve_instance(c, r.N, r.dims, r.ranks, r.J, f64, d);
+  carve_request(c, r, f64, xf64, d);
   return round256(c.off);
 }
 
@@ -216,7 +224,7 @@ void setup_slot(tr_server* s, int id, const tr_request& r) {
   BInst& d = s->htab[id];
   d = BInst{};
   Carver c(s->arena + s->slots[id].ws_off);
-  carve_instance(c, r.N, r.dims, r.ranks, r.J, s->f64, d);
+  carve_request(c, r, s->f64, s->xf64, d);
   d.X = r.X;
   d.N = r.N;
   d.xf64 = s->xf64 ? 1 : 0;
@@ -571,7 +579,7 @@ tr_status tr_server_submit(tr_server* s, const tr_request* req, int64_t* ticket)
     s->stats.rejected += 1;
     return chk;
   }
-  const size_t ws = request_ws(r, s->f64);
+  const size_t ws = request_ws(r, s->f64, s->xf64);
   const size_t charge = request_charge(r, s->xf64, ws);
   if (ws > s->cfg.arena_bytes || charge > s->cfg.hbm_budget_bytes) {
     {

@@ -329,7 +329,12 @@ def test_core_update_full_size_mixed(ctx):
 @pytest.mark.parametrize("dims,ranks,xdt", [((30, 20, 25), (3, 4, 5), torch.float64),
                                             ((30, 20, 25), (3, 4, 5), torch.float32),
                                             ((6, 5, 7, 4), (2, 3, 2, 4), torch.float64),
-                                            ((50, 40), (4, 6), torch.float64)])
+                                            ((50, 40), (4, 6), torch.float64),
+                                            # mode splits s = 2 (cols 300, 16-byte rows)
+                                            # and s = 2 of 5 modes, FP32
+                                            ((20, 30, 300), (4, 5, 3), torch.float32),
+                                            ((8, 6, 7, 5, 9), (3, 2, 4, 3, 2), torch.float32),
+                                            ((9, 70, 11, 13), (5, 4, 6, 3), torch.float32)])
 def test_rel_error_matches_oracle(ctx, dims, ranks, xdt):
     X, _ = inputs.tr_plus_noise(dims, ranks, seed=8, rel_noise=0.05, dtype=xdt)
     cores = np_cores(dims, ranks, 9)
