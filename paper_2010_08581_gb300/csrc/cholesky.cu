@@ -6,6 +6,8 @@
 namespace trk {
 namespace {
 
+constexpr int kCholDyn = 200 * 1024;   // the work matrix, when it fits
+
 __global__ void __launch_bounds__(CNT) k_cholesky(const double* __restrict__ G, int n, int mode,
                                                   double tol_scale, double* Lrow, double* Lcol,
                                                   double* invdiag, int* keep_out, int* info,
@@ -24,14 +26,15 @@ cudaError_t launch_cholesky_cluster(const double* G, int n, int mode, double tol
                                     int* info, unsigned* err, cudaStream_t st, double* img64,
                                     float* img32, float* gimg32);
 
-// The cluster form for n <= 144 unless TRALS_CHOL_ONE_CTA=1 selects the one-CTA kernel
-// (both give the same factors; the switch exists for comparisons).
+// The one-CTA kernel unless TRALS_CHOL_CLUSTER=1 selects the cluster form for n <= 144.
+// Both give the same factors; on GB300 the cluster form measured slower (each column's
+// hand-off between SMs costs more than the FP64 work it spreads), so it is opt-in.
 bool use_cluster_cholesky(int n) {
-  static const bool one_cta = [] {
-    const char* e = getenv("TRALS_CHOL_ONE_CTA");
+  static const bool cluster = [] {
+    const char* e = getenv("TRALS_CHOL_CLUSTER");
     return e && e[0] == '1';
   }();
-  return !one_cta && cholesky_cluster_fits(n);
+  return cluster && cholesky_cluster_fits(n);
 }
 
 cudaError_t launch_cholesky(const double* G, int n, int mode, double tol_scale, double* Lrow,
@@ -41,7 +44,7 @@ cudaError_t launch_cholesky(const double* G, int n, int mode, double tol_scale, 
     return launch_cholesky_cluster(G, n, mode, tol_scale, Lrow, Lcol, invdiag, keep, info, err,
                                    st, img64, img32, gimg32);
   const size_t bytes = static_cast<size_t>(n) * n * sizeof(double);
-  const int use_smem = bytes <= 200 * 1024 ? 1 : 0;
+  const int use_smem = bytes <= kCholDyn ? 1 : 0;
   const size_t dyn = use_smem ? bytes : 0;
   k_cholesky<<<1, CNT, dyn, st>>>(G, n, mode, tol_scale, Lrow, Lcol, invdiag, keep, info, err,
                                   use_smem, img64, img32, gimg32);
@@ -52,7 +55,7 @@ cudaError_t cholesky_cluster_attributes();
 
 cudaError_t cholesky_attributes() {
   const cudaError_t e =
-      cudaFuncSetAttribute(k_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      cudaFuncSetAttribute(k_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize, kCholDyn);
   if (e != cudaSuccess) return e;
   return cholesky_cluster_attributes();
 }

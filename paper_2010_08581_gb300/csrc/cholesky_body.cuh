@@ -9,6 +9,10 @@
 // (its (m+1)m/2 entries spread evenly over the threads). One barrier per column. A is the
 // n x n work array (shared memory, or the Lrow output itself).
 //
+// Every update is one fused multiply-add, a_ij = fma(-l_ik, l_jk, a_ij), so that the cluster
+// kernel (cholesky_cluster.cu), which applies the same updates in the same order, gives the
+// same factor.
+//
 // mode 0 (solve): a pivot <= tol_scale * max diag stops the factorisation (*info = column
 // + 1, singular bit). mode 1 (leverage): such a column is dropped (zero, keep = 0).
 // Besides L (row- and column-major) the kernel can write padded images that the
@@ -82,7 +86,7 @@ __device__ __forceinline__ void cholesky_cta(const double* __restrict__ G, int n
         for (int q = 0; q < kMaxL / 32; ++q) {
           const int i = k + 1 + lane + 32 * q;
           a[q] = 0.0;
-          if (i < n) a[q] = kp ? A[i * n + k + 1] - cur[i] * lk1 : A[i * n + k + 1];
+          if (i < n) a[q] = kp ? fma(-cur[i], lk1, A[i * n + k + 1]) : A[i * n + k + 1];
         }
         const double d = __shfl_sync(0xffffffffu, a[0], 0);   // row k+1: lane 0, q = 0
         const bool ok = d > s_tol;
@@ -111,7 +115,7 @@ __device__ __forceinline__ void cholesky_cta(const double* __restrict__ G, int n
         while ((ii + 1) * (ii + 2) / 2 <= e) ++ii;
         const int jj = e - ii * (ii + 1) / 2;
         const int i = k + 2 + ii, j = k + 2 + jj;
-        A[i * n + j] -= cur[i] * cur[j];
+        A[i * n + j] = fma(-cur[i], cur[j], A[i * n + j]);
       }
     }
     __syncthreads();

@@ -60,7 +60,8 @@ __global__ void __launch_bounds__(GNT) k_gram(const double* __restrict__ A, int6
 }
 
 // ------------------------------------------------------------------------------------
-// Fixed-order reduction of split partials (s = 0, 1, ..., splits-1) into FP64.
+// Fixed-order reduction of split partials (s = 0, 1, ..., splits-1) into FP64 (FP64
+// partials: FP64 sum; FP32 partials: compensated FP32 sum, then FP64).
 // Columns c < c_split go to out1[r*ld1 + c]; columns c >= c_split go transposed to
 // out2[(c - c_split)*ld2 + r]. One element per thread, loads coalesced along c.
 // ------------------------------------------------------------------------------------
@@ -75,16 +76,42 @@ __global__ void __launch_bounds__(256) k_reduce(const TP* __restrict__ partial, 
        e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const int64_t r = e / ncols, c = e - (e / ncols) * ncols;
     const TP* src = partial + r * pld + c;
-    double s = 0.0;
-    int q = 0;
-    for (; q + 8 <= splits; q += 8) {
-      double v[8];
+    double s;
+    if constexpr (sizeof(TP) == 4) {
+      // FP32 partials: Neumaier-compensated FP32 sum in the fixed order (the FP64 pipe is
+      // about 1/64 of the FP32 rate on this GPU), one conversion at the end.
+      float hi = 0.f, lo = 0.f;
+      int q = 0;
+      for (; q + 8 <= splits; q += 8) {
+        float v[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) v[u] = static_cast<double>(src[(q + u) * pstride]);
+        for (int u = 0; u < 8; ++u) v[u] = src[(q + u) * pstride];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) s += v[u];
+        for (int u = 0; u < 8; ++u) {
+          const float t = hi + v[u];
+          lo += (fabsf(hi) >= fabsf(v[u])) ? (hi - t) + v[u] : (v[u] - t) + hi;
+          hi = t;
+        }
+      }
+      for (; q < splits; ++q) {
+        const float v = src[q * pstride];
+        const float t = hi + v;
+        lo += (fabsf(hi) >= fabsf(v)) ? (hi - t) + v : (v - t) + hi;
+        hi = t;
+      }
+      s = static_cast<double>(hi) + static_cast<double>(lo);
+    } else {
+      s = 0.0;
+      int q = 0;
+      for (; q + 8 <= splits; q += 8) {
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = static_cast<double>(src[(q + u) * pstride]);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) s += v[u];
+      }
+      for (; q < splits; ++q) s += static_cast<double>(src[q * pstride]);
     }
-    for (; q < splits; ++q) s += static_cast<double>(src[q * pstride]);
     if (c < c_split) out1[r * ld1 + c] = s;
     else out2[(c - c_split) * ld2 + r] = s;
   }

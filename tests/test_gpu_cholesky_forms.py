@@ -1,7 +1,7 @@
 """The cluster FP64 Cholesky (n <= 144) and the one-CTA Cholesky give identical factors:
 the LS solve (mode 0, including a singular normal matrix) and the leverage distribution
-(mode 1, tall and wide cores) are bit-identical under both forms. The one-CTA form is
-selected with TRALS_CHOL_ONE_CTA=1 in a child process."""
+(mode 1, tall and wide cores) are bit-identical under both forms. The cluster form is
+selected with TRALS_CHOL_CLUSTER=1 in a child process."""
 
 import os
 import subprocess
@@ -54,11 +54,11 @@ torch.save(out, sys.argv[2])
 """
 
 
-def _run(tmp_path, name, one_cta):
+def _run(tmp_path, name, cluster):
     env = dict(os.environ)
-    env.pop("TRALS_CHOL_ONE_CTA", None)
-    if one_cta:
-        env["TRALS_CHOL_ONE_CTA"] = "1"
+    env.pop("TRALS_CHOL_CLUSTER", None)
+    if cluster:
+        env["TRALS_CHOL_CLUSTER"] = "1"
     path = str(tmp_path / name)
     r = subprocess.run([sys.executable, "-c", CHILD, ROOT, path], env=env, capture_output=True,
                        text=True, timeout=600)
@@ -67,8 +67,8 @@ def _run(tmp_path, name, one_cta):
 
 
 def test_cluster_and_one_cta_cholesky_agree_bitwise(tmp_path):
-    a = _run(tmp_path, "cluster.pt", False)
-    b = _run(tmp_path, "one_cta.pt", True)
+    a = _run(tmp_path, "one_cta.pt", False)
+    b = _run(tmp_path, "cluster.pt", True)
     assert a.keys() == b.keys()
     for k in a:
         assert torch.equal(a[k], b[k]), k
