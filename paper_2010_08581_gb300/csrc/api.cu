@@ -1042,10 +1042,10 @@ tr_status tr_rel_error(tr_ctx* ctx, const void* X, tr_dtype X_dtype, int N, cons
   TR_TRY(ensure_ws(ctx, bytes));
   double* partial = reinterpret_cast<double*>(ctx->arena);
   cudaStream_t st = S(stream);
-  TR_LAUNCH("fit", launch_fit(fa, X, xf64, ctx->arena, blocks, st));
+  TR_LAUNCH("fit", launch_fit(fa, X, xf64, ctx->arena, blocks, ctx->d_err, st));
   std::vector<double> h(2 * static_cast<size_t>(blocks));
   TR_CUDA(cudaMemcpyAsync(h.data(), partial, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
-  TR_CUDA(cudaStreamSynchronize(st));
+  TR_TRY(read_device_error(ctx, st));
   double se = 0.0, sx = 0.0;
   for (int b = 0; b < blocks; ++b) { se += h[b]; sx += h[blocks + b]; }
   *rel_err = sx > 0.0 ? std::sqrt(se / sx) : (se > 0.0 ? INFINITY : 0.0);

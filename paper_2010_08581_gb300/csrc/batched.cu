@@ -3,7 +3,7 @@
 #include "batched.cuh"
 #include "cholesky_body.cuh"
 #include "draw.cuh"
-#include "fit_body.cuh"
+#include "fit_tc.cuh"
 #include "trsm_body.cuh"
 
 namespace trk {
@@ -411,9 +411,9 @@ __device__ __forceinline__ bool fit_due(const BInst& d) {
   return s.status == kSlotRunning && s.step >= 0 && s.step % d.N == d.N - 1;
 }
 
-template <typename T>
-__device__ __forceinline__ int fit_parts(const FitSplit& f) {
-  const int64_t nblk = (f.rows + FitTile<T>::FL - 1) / FitTile<T>::FL;
+// Partial sums of one slot's fit: one per CTA, at most kFitParts.
+__device__ __forceinline__ int fit_parts(const FitSplit& f, bool xf64) {
+  const int64_t nblk = fit_row_blocks(f, xf64);
   return nblk < kFitParts ? static_cast<int>(nblk) : kFitParts;
 }
 
@@ -459,12 +459,39 @@ __global__ void __launch_bounds__(FNT) kb_fit(const BInst* __restrict__ tab, int
   if (threadIdx.x == 0) fit_args(d, fa);
   __syncthreads();
   const FitSplit f = fit_split(fa.N, fa.dims, fa.ranks);
-  if (f.K <= k_lo || f.K > k_hi) return;
-  const int parts = fit_parts<T>(f);
+  if (fit_use_tc(f, sizeof(T) == 8) || f.K <= k_lo || f.K > k_hi) return;
+  const int parts = fit_parts(f, sizeof(T) == 8);
   if (static_cast<int>(blockIdx.y) >= parts) return;
   double se = 0.0, sx = 0.0;
   fit_blocks<T>(fa, f, static_cast<const T*>(d.X), static_cast<const T*>(d.fitw), blockIdx.y,
                 parts, fit_dyn, chain, slice, se, sx);
+  fit_block_reduce(se, sx, red);
+  if (threadIdx.x == 0) {
+    d.fitp[blockIdx.y] = se;
+    d.fitp[kFitParts + blockIdx.y] = sx;
+  }
+}
+
+// Slots with FP32 X and K <= 128: the contraction on the tensor cores (fit_tc.cuh).
+__global__ void __launch_bounds__(FNT, 1) kb_fit_tc(const BInst* __restrict__ tab,
+                                                    unsigned* err) {
+  extern __shared__ __align__(1024) unsigned char fit_tc_dyn[];
+  __shared__ float chain[8][kMaxL];
+  __shared__ float slice[8][kMaxL];
+  __shared__ double red[2 * (FNT / 32)];
+  __shared__ FitArgs fa;
+  __shared__ FitTcShared sh;
+  const BInst& d = tab[blockIdx.x];
+  if (!fit_due(d) || d.xf64) return;
+  if (threadIdx.x == 0) fit_args(d, fa);
+  __syncthreads();
+  const FitSplit f = fit_split(fa.N, fa.dims, fa.ranks);
+  if (!fit_use_tc(f, false)) return;
+  const int parts = fit_parts(f, false);
+  if (static_cast<int>(blockIdx.y) >= parts) return;
+  double se = 0.0, sx = 0.0;
+  fit_tc_blocks(fa, f, static_cast<const float*>(d.X), static_cast<const float*>(d.fitw),
+                blockIdx.y, parts, fit_tc_dyn, chain, slice, sh, err, se, sx);
   fit_block_reduce(se, sx, red);
   if (threadIdx.x == 0) {
     d.fitp[blockIdx.y] = se;
@@ -484,7 +511,7 @@ __global__ void __launch_bounds__(128) kb_advance(const BInst* __restrict__ tab,
   if (t >= 0 && *d.info != 0) s.singular += 1;
   if (fit_due(d)) {
     const FitSplit f = fit_split(d.N, d.dims, d.ranks);
-    const int parts = xf64 ? fit_parts<double>(f) : fit_parts<float>(f);
+    const int parts = fit_parts(f, xf64 != 0);
     double se = 0.0, sx = 0.0;
     for (int q = 0; q < parts; ++q) {
       se += d.fitp[q];
@@ -587,7 +614,7 @@ cudaError_t bl_leverage_rows(const BLaunch& b, int step, int init_k, unsigned* e
   return cudaGetLastError();
 }
 
-cudaError_t bl_fit(const BLaunch& b, cudaStream_t st) {
+cudaError_t bl_fit(const BLaunch& b, unsigned* err, cudaStream_t st) {
   dim3 rgrid(b.count, kFitRightCtas);
   dim3 grid(b.count, kFitParts);
   constexpr int kSplitK = 128;
@@ -599,9 +626,9 @@ cudaError_t bl_fit(const BLaunch& b, cudaStream_t st) {
       kb_fit<double><<<grid, FNT, fit_smem_bytes<double>(b.Lmax), st>>>(b.tab, kSplitK, kMaxL);
   } else {
     kb_fit_right<float><<<rgrid, FNT, 0, st>>>(b.tab);
-    kb_fit<float><<<grid, FNT, fit_smem_bytes<float>(k_small), st>>>(b.tab, 0, kSplitK);
-    if (b.Lmax > kSplitK)
-      kb_fit<float><<<grid, FNT, fit_smem_bytes<float>(b.Lmax), st>>>(b.tab, kSplitK, kMaxL);
+    kb_fit_tc<<<grid, FNT, kFitTcSmem, st>>>(b.tab, err);
+    if (b.Lmax > kFitTcMaxK)
+      kb_fit<float><<<grid, FNT, fit_smem_bytes<float>(b.Lmax), st>>>(b.tab, kFitTcMaxK, kMaxL);
   }
   return cudaGetLastError();
 }
@@ -623,6 +650,9 @@ cudaError_t batched_attributes() {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(kb_fit<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(fit_smem_bytes<float>(kMaxL)));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(kb_fit_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(kFitTcSmem));
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(kb_fit<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               static_cast<int>(fit_smem_bytes<double>(kMaxL)));

@@ -106,7 +106,7 @@ cudaError_t bl_leverage_rows(const BLaunch& b, int step, int init_k, unsigned* e
                              cudaStream_t st);
 // Serving: relative fit of the slots that finished a sweep in this tick, then the stop rule
 // and the step counters of all running slots.
-cudaError_t bl_fit(const BLaunch& b, cudaStream_t st);
+cudaError_t bl_fit(const BLaunch& b, unsigned* err, cudaStream_t st);
 cudaError_t bl_advance(const BLaunch& b, cudaStream_t st);
 cudaError_t batched_attributes();
 

@@ -167,6 +167,6 @@ struct FitArgs {
 // Workspace: 2 * blocks partial sums, then the right factors of the mode split.
 size_t fit_workspace(const FitArgs& a, bool x_f64, int* blocks);
 cudaError_t launch_fit(const FitArgs& a, const void* X, bool x_f64, void* ws, int blocks,
-                       cudaStream_t st);
+                       unsigned* err, cudaStream_t st);
 
 }  // namespace trk

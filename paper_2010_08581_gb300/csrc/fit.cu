@@ -1,7 +1,7 @@
 // Relative error ||TR(cores) - X||_F / ||X||_F (Sec. 5.1) of one problem: the right factors
 // W^T of the mode split (fit_body.cuh), then partial sums of the squared residual and of
 // ||X||^2 per CTA, reduced on the host in a fixed order.
-#include "fit_body.cuh"
+#include "fit_tc.cuh"
 
 namespace trk {
 namespace {
@@ -33,6 +33,25 @@ __global__ void __launch_bounds__(FNT) k_fit(FitArgs a, FitSplit f, const T* __r
   }
 }
 
+__global__ void __launch_bounds__(FNT, 1) k_fit_tc(FitArgs a, FitSplit f,
+                                                   const float* __restrict__ X,
+                                                   const float* __restrict__ WT,
+                                                   double* __restrict__ partial, int blocks,
+                                                   unsigned* err) {
+  extern __shared__ __align__(1024) unsigned char fit_tc_raw[];
+  __shared__ float chain[8][kMaxL];
+  __shared__ float slice[8][kMaxL];
+  __shared__ double red[2 * (FNT / 32)];
+  __shared__ FitTcShared sh;
+  double se = 0.0, sx = 0.0;
+  fit_tc_blocks(a, f, X, WT, blockIdx.x, gridDim.x, fit_tc_raw, chain, slice, sh, err, se, sx);
+  fit_block_reduce(se, sx, red);
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x] = se;
+    partial[blocks + blockIdx.x] = sx;
+  }
+}
+
 FitSplit split_of(const FitArgs& a) { return fit_split(a.N, a.dims, a.ranks); }
 
 size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
@@ -41,9 +60,9 @@ size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
 
 size_t fit_workspace(const FitArgs& a, bool x_f64, int* blocks) {
   const FitSplit f = split_of(a);
-  const int FL = x_f64 ? FitTile<double>::FL : FitTile<float>::FL;
-  int64_t b = (f.rows + FL - 1) / FL;
-  if (b > 152 * 4) b = 152 * 4;
+  int64_t b = fit_row_blocks(f, x_f64);
+  const int64_t cap = fit_use_tc(f, x_f64) ? 152 : 152 * 4;   // the tensor-core form: 1 CTA/SM
+  if (b > cap) b = cap;
   if (b < 1) b = 1;
   *blocks = static_cast<int>(b);
   const size_t es = x_f64 ? 8 : 4;
@@ -52,7 +71,7 @@ size_t fit_workspace(const FitArgs& a, bool x_f64, int* blocks) {
 }
 
 cudaError_t launch_fit(const FitArgs& a, const void* X, bool x_f64, void* ws, int blocks,
-                       cudaStream_t st) {
+                       unsigned* err, cudaStream_t st) {
   const FitSplit f = split_of(a);
   double* partial = static_cast<double*>(ws);
   char* wt = static_cast<char*>(ws) + round256(static_cast<size_t>(2 * blocks) * sizeof(double));
@@ -65,8 +84,12 @@ cudaError_t launch_fit(const FitArgs& a, const void* X, bool x_f64, void* ws, in
   } else {
     float* WT = reinterpret_cast<float*>(wt);
     k_fit_right<float><<<rb, FNT, 0, st>>>(a, f, WT);
-    k_fit<float><<<blocks, FNT, fit_smem_bytes<float>(f.K), st>>>(
-        a, f, static_cast<const float*>(X), WT, partial, blocks);
+    if (fit_use_tc(f, false))
+      k_fit_tc<<<blocks, FNT, kFitTcSmem, st>>>(a, f, static_cast<const float*>(X), WT, partial,
+                                                 blocks, err);
+    else
+      k_fit<float><<<blocks, FNT, fit_smem_bytes<float>(f.K), st>>>(
+          a, f, static_cast<const float*>(X), WT, partial, blocks);
   }
   return cudaGetLastError();
 }
@@ -74,6 +97,9 @@ cudaError_t launch_fit(const FitArgs& a, const void* X, bool x_f64, void* ws, in
 cudaError_t fit_attributes() {
   cudaError_t e = cudaFuncSetAttribute(k_fit<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(fit_smem_bytes<double>(kMaxL)));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_fit_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(kFitTcSmem));
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_fit<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               static_cast<int>(fit_smem_bytes<float>(kMaxL)));

@@ -215,7 +215,7 @@ cudaError_t issue_tick(tr_server* s, int count, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   const StepStreams ss{st, s->side, s->ev_fork, s->ev_info, s->ev_join};
   if ((e = issue_step(bl, 0, s->derr, ss)) != cudaSuccess) return e;
-  if ((e = bl_fit(bl, st)) != cudaSuccess) return e;
+  if ((e = bl_fit(bl, s->derr, st)) != cudaSuccess) return e;
   return bl_advance(bl, st);
 }
 

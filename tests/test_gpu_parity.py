@@ -334,7 +334,10 @@ def test_core_update_full_size_mixed(ctx):
                                             # and s = 2 of 5 modes, FP32
                                             ((20, 30, 300), (4, 5, 3), torch.float32),
                                             ((8, 6, 7, 5, 9), (3, 2, 4, 3, 2), torch.float32),
-                                            ((9, 70, 11, 13), (5, 4, 6, 3), torch.float32)])
+                                            ((9, 70, 11, 13), (5, 4, 6, 3), torch.float32),
+                                            # K = 110 (tensor cores), K = 144 (SIMT)
+                                            ((60, 50, 140), (10, 11, 10), torch.float32),
+                                            ((40, 30, 20), (12, 12, 12), torch.float32)])
 def test_rel_error_matches_oracle(ctx, dims, ranks, xdt):
     X, _ = inputs.tr_plus_noise(dims, ranks, seed=8, rel_noise=0.05, dtype=xdt)
     cores = np_cores(dims, ranks, 9)
