@@ -4,10 +4,13 @@ One step = one whole decomposition through the C ABI (tr_als_sampled: initial le
 scores + 10 sweeps of Alg. 2, J = 4000, mixed precision) with X resident in HBM. The
 metric is sweeps/s = sweeps per step * steps / time. Besides it the JSON line carries the
 end-to-end number through the host-memory entry point, the roofline of the dominant
-kernel, the plain FP64 GPU form (the metric's comparator) and the FP64 CPU oracle on a
-bounded sample.
+kernel, the plain FP64 GPU form (the metric's comparator), the FP64 CPU oracle on a
+bounded sample, the 512-problem batched workload, and the serving leg: p50/p99
+decomposition latency of a Poisson stream of requests (200/s) through the native server.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--serve-seconds S] [--skip-cpu] [--skip-fp64] [--skip-batched]
+                  [--skip-serving]
 
 With N > 1 (torchrun), every rank decomposes its own tensor (replicas, weak scaling).
 """
@@ -351,7 +354,8 @@ def run_batched(T, plain_fp64, dev, steps, warmup, stream):
             "speedup_vs_plain_fp64": round(rate / plain_rate, 1)}
 
 
-def run_serving(T, dev, seconds, rate=200.0, warmup_s=3.0, pool_size=128, seed=0):
+def run_serving(T, dev, seconds, rate=200.0, warmup_s=3.0, pool_size=128, seed=0,
+                max_drain_s=60.0):
     """Continuous-batching server under a Poisson stream of decomposition requests: N in
     {3, 4, 5}, entries log-uniform in [1e5, 1e8], ranks ~ U{4..16} per mode, J = 10 max L,
     FP32 TR(N(0,1) cores) + 1e-2 noise, stop at fit change < 1e-4 (cap 30 sweeps), 150 GB
@@ -384,11 +388,24 @@ def run_serving(T, dev, seconds, rate=200.0, warmup_s=3.0, pool_size=128, seed=0
         cores = T.empty_cores(sh["dims"], sh["ranks"], device=dev)
         subs.append((srv.submit(X, sh["ranks"], sh["J"], 1 + i, cores), due, at, sh))
     t_arrivals_end = time.monotonic_ns()
+    # Drain for at most max_drain_s after the last arrival; requests still unfinished then
+    # are reported as such (an overloaded server would otherwise hold the bench for minutes).
+    deadline = t_arrivals_end + int(max_drain_s * 1e9)
     results = []
+    unfinished = 0
     for t, due, at, sh in subs:
-        res = srv.wait(t, timeout_ms=300_000)
+        left_ms = max(1, (deadline - time.monotonic_ns()) // 1_000_000)
+        try:
+            res = srv.wait(t, timeout_ms=int(left_ms))
+        except T.TrError as e:
+            if e.status != T.TR_ERR_TIMEOUT:
+                raise
+            res = srv.poll(t)
+        if res["done"]:
+            srv.release(t)
+        else:
+            unfinished += 1
         results.append((res, due, at, sh))
-        srv.release(t)
     t_end = time.monotonic_ns()
     st = srv.stats()
     srv.stop()
@@ -413,6 +430,7 @@ def run_serving(T, dev, seconds, rate=200.0, warmup_s=3.0, pool_size=128, seed=0
                     "precision, native worker thread",
         "offered_req_per_s": rate, "seconds": seconds, "warmup_s": warmup_s,
         "requests_measured": len(meas), "requests_total": len(results),
+        "unfinished_at_drain_deadline": unfinished, "max_drain_s": max_drain_s,
         "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 2) if lat else None,
                        "p99": round(float(np.percentile(lat, 99)), 2) if lat else None,
                        "max": round(lat[-1], 2) if lat else None,
