@@ -10,7 +10,7 @@ decomposition latency of a Poisson stream of requests (200/s) through the native
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--serve-seconds S] [--skip-cpu] [--skip-fp64] [--skip-batched]
-                  [--skip-serving]
+                  [--skip-configs] [--skip-serving]
 
 With N > 1 (torchrun), every rank decomposes its own tensor (replicas, weak scaling).
 """
@@ -354,6 +354,82 @@ def run_batched(T, plain_fp64, dev, steps, warmup, stream):
             "speedup_vs_plain_fp64": round(rate / plain_rate, 1)}
 
 
+def _time_calls(fn, reps, stream):
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fn()
+    torch.cuda.synchronize()
+    a.record(stream)
+    for i in range(reps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / 1e3 / reps
+
+
+def run_config1(T, plain_fp64, dev, stream, reps=5):
+    """100x100x100 FP64 TR of rank 5 + 1e-3 noise, J = 2000, 10 sweeps, FP64 path, against
+    the plain FP64 GPU form on the same problem and initial cores."""
+    wl = inputs.WORKLOADS["tr3_100_r5_fp64"]
+    X, _ = inputs.tr_plus_noise(wl["dims"], wl["ranks"], seed=wl["seed"],
+                                rel_noise=wl["rel_noise"], device=dev, dtype=torch.float64)
+    init = [c.to(dev) for c in inputs.random_cores(wl["dims"], wl["ranks"], wl["init_seed"])]
+    init_sm = [inputs.slice_major(c) for c in init]
+    ctx = T.Context(dev.index or 0)
+    out = T.empty_cores(wl["dims"], wl["ranks"], device=dev)
+    sec = _time_calls(lambda: T.tr_als_sampled(ctx, X, wl["ranks"], wl["J"], wl["sweeps"],
+                                               wl["sample_seed"], T.TR_PREC_FP64, out,
+                                               init_cores=init_sm), reps, stream)
+    err = T.tr_rel_error(ctx, X, wl["ranks"], out)
+    res = [None]
+
+    def plain():
+        res[0] = plain_fp64.als_sampled(X, init, wl["J"], wl["sweeps"], 1)
+    psec = _time_calls(plain, 2, stream)
+    perr = plain_fp64.rel_error(X, res[0])
+    ctx.close()
+    return {"workload": "100x100x100 FP64 TR(rank-5 N(0,1)) + 1e-3 noise, ranks 5, J = 2000, "
+                        "10 sweeps per decomposition, FP64 path",
+            "value": round(wl["sweeps"] / sec, 2), "unit": "sweeps/s",
+            "ms_per_decomposition": round(sec * 1e3, 3), "final_rel_err": err,
+            "plain_fp64_gpu_form": {"value": round(wl["sweeps"] / psec, 2), "unit": "sweeps/s",
+                                    "final_rel_err": perr},
+            "speedup_vs_plain_fp64": round(psec / sec, 2)}
+
+
+def run_config3(T, dev, stream, peaks, reps=3):
+    """4-way 256x256x3x2000 FP32 cosine workload, ranks 10, J = 8000, 20 sweeps, mixed; and
+    the fibre gather of its contiguous mode (I = 2000) timed per launch against HBM peak."""
+    dims, ranks, J, sweeps = (256, 256, 3, 2000), (10, 10, 10, 10), 8000, 20
+    X = inputs.cosine_sum(dims, seed=0, device=dev)
+    init = [inputs.slice_major(c).to(dev) for c in inputs.random_cores(dims, ranks, 1)]
+    ctx = T.Context(dev.index or 0)
+    out = T.empty_cores(dims, ranks, device=dev)
+    sec = _time_calls(lambda: T.tr_als_sampled(ctx, X, ranks, J, sweeps, 2, T.TR_PREC_MIXED,
+                                               out, init_cores=init), reps, stream)
+    err = T.tr_rel_error(ctx, X, ranks, out)
+    # gather of mode 3: J fibres of 2000 contiguous floats, read and written once
+    g = torch.Generator(device=dev)
+    g.manual_seed(5)
+    idx = torch.stack([torch.randint(0, d, (J,), generator=g, device=dev) for d in dims[:3]],
+                      1).to(torch.int32).contiguous()
+    w = torch.rand(J, generator=g, device=dev, dtype=torch.float64)
+    Y = torch.empty((J, dims[3]), device=dev)
+    gsec = _time_calls(lambda: T.tr_gather(ctx, X, 3, idx, w, Y), 50, stream)
+    gbytes = 2.0 * J * dims[3] * 4
+    peak, src = _peak_hbm(peaks)
+    ctx.close()
+    return {"workload": "256x256x3x2000 FP32 sum of 20 separable low-frequency cosine products "
+                        "+ 5% uniform noise, ranks 10, J = 8000, 20 sweeps, mixed precision",
+            "value": round(sweeps / sec, 2), "unit": "sweeps/s",
+            "ms_per_decomposition": round(sec * 1e3, 3), "final_rel_err": err,
+            "gather_mode3": {"bytes_per_launch": gbytes, "us_per_launch": round(gsec * 1e6, 2),
+                             "achieved_gbs": round(gbytes / gsec / 1e9, 1), "peak_gbs": peak,
+                             "frac": round(gbytes / gsec / 1e9 / peak, 4),
+                             "peak_source": f"{src} HBM copy",
+                             "what": "J = 8000 fibres of the contiguous mode (I = 2000, FP32), "
+                                     "read + weighted write, CUDA events over 50 launches"}}
+
+
 def run_serving(T, dev, seconds, rate=200.0, warmup_s=3.0, pool_size=128, seed=0,
                 max_drain_s=60.0):
     """Continuous-batching server under a Poisson stream of decomposition requests: N in
@@ -615,11 +691,16 @@ def run_ours(args):
     if not args.skip_batched and world == 1:
         batched = run_batched(T, plain_fp64, dev, max(1, min(args.steps, 5)), 1, stream)
 
+    peaks = measured_peaks()
+    config1 = config3 = None
+    if not args.skip_configs and world == 1:
+        config1 = run_config1(T, plain_fp64, dev, stream)
+        config3 = run_config3(T, dev, stream, peaks)
+
     serving = None
     if not args.skip_serving and world == 1 and args.serve_seconds > 0:
         serving = run_serving(T, dev, args.serve_seconds)
 
-    peaks = measured_peaks()
     roof = roofline(prof, wl, peaks)
     tot_ms = sum(v[0] for v in prof.values())
     if roof:
@@ -651,6 +732,8 @@ def run_ours(args):
                            sorted(prof.items(), key=lambda kv: -kv[1][0])},
             "fp64_gpu_form": fp64,
             "batched_512": batched,
+            "config1_fp64_100": config1,
+            "config3_cosine_4way": config3,
             "serving": serving,
             "cpu_baseline": cpu,
             "clocks": clk,
@@ -674,6 +757,7 @@ def main():
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-batched", action="store_true")
     ap.add_argument("--skip-serving", action="store_true")
+    ap.add_argument("--skip-configs", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=20.0)
     args = ap.parse_args()
     if args.impl == "reference":
