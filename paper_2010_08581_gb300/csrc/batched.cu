@@ -428,6 +428,8 @@ __device__ __forceinline__ void fit_args(const BInst& d, FitArgs& fa) {
 
 constexpr int kFitRightCtas = 64;   // CTAs per slot forming the right factors
 
+// Right factors of the fit: e-major W^T for the SIMT contraction, or the swizzled hi/lo
+// tiles of the tensor-core contraction.
 template <typename T>
 __global__ void __launch_bounds__(FNT) kb_fit_right(const BInst* __restrict__ tab) {
   __shared__ T chain[8][kMaxL];
@@ -439,9 +441,19 @@ __global__ void __launch_bounds__(FNT) kb_fit_right(const BInst* __restrict__ ta
   __syncthreads();
   const FitSplit f = fit_split(fa.N, fa.dims, fa.ranks);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t step = static_cast<int64_t>(gridDim.y) * (FNT / 32);
+  const int64_t q0 = static_cast<int64_t>(blockIdx.y) * (FNT / 32) + warp;
+  if constexpr (sizeof(T) == 4) {
+    if (fit_use_tc(f, false)) {
+      unsigned char* WS = static_cast<unsigned char*>(d.fitw);
+      const int64_t ncol = (f.cols + FTN - 1) / FTN * FTN;
+      for (int64_t q = q0; q < ncol; q += step)
+        fit_right_tc_warp(fa, f, q, WS, chain[warp], slice[warp], lane);
+      return;
+    }
+  }
   T* WT = static_cast<T*>(d.fitw);
-  for (int64_t q = static_cast<int64_t>(blockIdx.y) * (FNT / 32) + warp; q < f.cols;
-       q += static_cast<int64_t>(gridDim.y) * (FNT / 32))
+  for (int64_t q = q0; q < f.cols; q += step)
     fit_right_warp<T>(fa, f, q, WT, chain[warp], slice[warp], lane);
 }
 
@@ -490,7 +502,8 @@ __global__ void __launch_bounds__(FNT, 1) kb_fit_tc(const BInst* __restrict__ ta
   const int parts = fit_parts(f, false);
   if (static_cast<int>(blockIdx.y) >= parts) return;
   double se = 0.0, sx = 0.0;
-  fit_tc_blocks(fa, f, static_cast<const float*>(d.X), static_cast<const float*>(d.fitw),
+  fit_tc_blocks(fa, f, static_cast<const float*>(d.X),
+                static_cast<const unsigned char*>(d.fitw),
                 blockIdx.y, parts, fit_tc_dyn, chain, slice, sh, err, se, sx);
   fit_block_reduce(se, sx, red);
   if (threadIdx.x == 0) {

@@ -33,9 +33,20 @@ __global__ void __launch_bounds__(FNT) k_fit(FitArgs a, FitSplit f, const T* __r
   }
 }
 
+__global__ void __launch_bounds__(FNT) k_fit_right_tc(FitArgs a, FitSplit f,
+                                                     unsigned char* __restrict__ WS) {
+  __shared__ float chain[8][kMaxL];
+  __shared__ float slice[8][kMaxL];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t ncol = (f.cols + FTN - 1) / FTN * FTN;
+  const int64_t q = static_cast<int64_t>(blockIdx.x) * (FNT / 32) + warp;
+  if (q >= ncol) return;
+  fit_right_tc_warp(a, f, q, WS, chain[warp], slice[warp], lane);
+}
+
 __global__ void __launch_bounds__(FNT, 1) k_fit_tc(FitArgs a, FitSplit f,
                                                    const float* __restrict__ X,
-                                                   const float* __restrict__ WT,
+                                                   const unsigned char* __restrict__ WS,
                                                    double* __restrict__ partial, int blocks,
                                                    unsigned* err) {
   extern __shared__ __align__(1024) unsigned char fit_tc_raw[];
@@ -44,7 +55,7 @@ __global__ void __launch_bounds__(FNT, 1) k_fit_tc(FitArgs a, FitSplit f,
   __shared__ double red[2 * (FNT / 32)];
   __shared__ FitTcShared sh;
   double se = 0.0, sx = 0.0;
-  fit_tc_blocks(a, f, X, WT, blockIdx.x, gridDim.x, fit_tc_raw, chain, slice, sh, err, se, sx);
+  fit_tc_blocks(a, f, X, WS, blockIdx.x, gridDim.x, fit_tc_raw, chain, slice, sh, err, se, sx);
   fit_block_reduce(se, sx, red);
   if (threadIdx.x == 0) {
     partial[blockIdx.x] = se;
@@ -66,8 +77,9 @@ size_t fit_workspace(const FitArgs& a, bool x_f64, int* blocks) {
   if (b < 1) b = 1;
   *blocks = static_cast<int>(b);
   const size_t es = x_f64 ? 8 : 4;
-  return round256(static_cast<size_t>(2 * b) * sizeof(double)) +
-         static_cast<size_t>(f.cols) * f.K * es;
+  const size_t right = fit_use_tc(f, x_f64) ? fit_tc_right_bytes(f)
+                                            : static_cast<size_t>(f.cols) * f.K * es;
+  return round256(static_cast<size_t>(2 * b) * sizeof(double)) + right;
 }
 
 cudaError_t launch_fit(const FitArgs& a, const void* X, bool x_f64, void* ws, int blocks,
@@ -82,14 +94,19 @@ cudaError_t launch_fit(const FitArgs& a, const void* X, bool x_f64, void* ws, in
     k_fit<double><<<blocks, FNT, fit_smem_bytes<double>(f.K), st>>>(
         a, f, static_cast<const double*>(X), WT, partial, blocks);
   } else {
-    float* WT = reinterpret_cast<float*>(wt);
-    k_fit_right<float><<<rb, FNT, 0, st>>>(a, f, WT);
-    if (fit_use_tc(f, false))
-      k_fit_tc<<<blocks, FNT, kFitTcSmem, st>>>(a, f, static_cast<const float*>(X), WT, partial,
+    if (fit_use_tc(f, false)) {
+      unsigned char* WS = reinterpret_cast<unsigned char*>(wt);
+      const int64_t ncol = (f.cols + FTN - 1) / FTN * FTN;
+      k_fit_right_tc<<<static_cast<unsigned>((ncol + FNT / 32 - 1) / (FNT / 32)), FNT, 0, st>>>(
+          a, f, WS);
+      k_fit_tc<<<blocks, FNT, kFitTcSmem, st>>>(a, f, static_cast<const float*>(X), WS, partial,
                                                  blocks, err);
-    else
+    } else {
+      float* WT = reinterpret_cast<float*>(wt);
+      k_fit_right<float><<<rb, FNT, 0, st>>>(a, f, WT);
       k_fit<float><<<blocks, FNT, fit_smem_bytes<float>(f.K), st>>>(
           a, f, static_cast<const float*>(X), WT, partial, blocks);
+    }
   }
   return cudaGetLastError();
 }

@@ -134,6 +134,94 @@ __device__ __forceinline__ void fit_right_warp(const FitArgs& a, const FitSplit&
   __syncwarp();
 }
 
+// V_p[e] (e = b * R_{N-1} + a, V_p[e] = P_left(p)[a][b]) for the rows p0 .. p0 + nb - 1 of a
+// block, handed to put(ll, e, value) (rows past the end give zeros). All threads of the CTA
+// call it; it ends with a CTA barrier.
+//
+// Rows p = pre * J + last (J = I_{s-1}) share the prefix G^(0) .. G^(s-2) of their slice
+// chain, and consecutive rows mostly share it: each distinct prefix of the block is formed
+// once by one warp (into chain[w]), and every (row, b) item then finishes its column b of
+// P_left = prefix * G^(s-1)(:, last, :) in registers. The products and their summation order
+// are those of a per-row chain, so V is the same. Blocks with more than 8 prefixes (J < 16)
+// form every row's chain with one warp.
+template <typename T, typename Put>
+__device__ void build_left(const FitArgs& a, const FitSplit& f, int64_t p0, int nb,
+                           T (*chain)[kMaxL], T (*slice)[kMaxL], Put put) {
+  const int N = a.N, s = f.s, K = f.K;
+  const int Rlast = a.ranks[N - 1], Rs = a.ranks[s - 1];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t rows = f.rows;
+  const int64_t pend = (p0 + nb < rows) ? p0 + nb : rows;
+  if (s == 1) {   // P_left(p) is the slice G^(0)(:, p, :) itself
+    for (int it = tid; it < nb * K; it += FNT) {
+      const int ll = it / K, e = it - ll * K;
+      const int64_t p = p0 + ll;
+      const int b = e / Rlast, aa = e - b * Rlast;
+      put(ll, e, p < rows ? static_cast<T>(a.core[0][(p * Rlast + aa) * Rs + b]) : T(0));
+    }
+    __syncthreads();
+    return;
+  }
+  const int64_t J = a.dims[s - 1];
+  const int64_t pre_lo = p0 / J;
+  const int npre = pend > p0 ? static_cast<int>((pend - 1) / J - pre_lo + 1) : 0;
+  if (npre > FNT / 32) {
+    // many short prefixes: one warp per row forms the whole chain
+    for (int ll = warp; ll < nb; ll += FNT / 32) {
+      const int64_t p = p0 + ll;
+      if (p >= rows) {
+        for (int e = lane; e < K; e += 32) put(ll, e, T(0));
+        continue;
+      }
+      int64_t ii[kMaxModes];
+      int64_t rem = p;
+      for (int m = s - 1; m >= 0; --m) { ii[m] = rem % a.dims[m]; rem /= a.dims[m]; }
+      T* S = chain[warp];
+      const int rs = warp_slice_product<T>(a, 0, s, ii, S, slice[warp], lane);
+      __syncwarp();
+      for (int e = lane; e < K; e += 32) {
+        const int b = e / Rlast, aa = e - b * Rlast;
+        put(ll, e, S[aa * rs + b]);
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+    return;
+  }
+  const int Rm = a.ranks[s - 2];   // the rank between the prefix and G^(s-1)
+  if (warp < npre) {
+    int64_t ii[kMaxModes];
+    int64_t rem = pre_lo + warp;
+    for (int m = s - 2; m >= 0; --m) { ii[m] = rem % a.dims[m]; rem /= a.dims[m]; }
+    warp_slice_product<T>(a, 0, s - 1, ii, chain[warp], slice[warp], lane);   // Rlast x Rm
+  }
+  __syncthreads();
+  const double* Gs = a.core[s - 1];
+  for (int it = tid; it < nb * Rs; it += FNT) {
+    const int ll = it / Rs, b = it - ll * Rs;
+    const int64_t p = p0 + ll;
+    if (p >= rows) {
+      for (int aa = 0; aa < Rlast; ++aa) put(ll, b * Rlast + aa, T(0));
+      continue;
+    }
+    const int64_t pre = p / J, last = p - pre * J;
+    const T* P = chain[pre - pre_lo];
+    const double* g = Gs + last * Rm * Rs + b;   // column b of G^(s-1)(:, last, :)
+    T gc[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) gc[c] = c < Rm ? static_cast<T>(g[c * Rs]) : T(0);
+    for (int aa = 0; aa < Rlast; ++aa) {
+      const T* pr = P + aa * Rm;
+      T acc = T(0);
+#pragma unroll
+      for (int c = 0; c < 16; ++c)
+        if (c < Rm) acc += pr[c] * gc[c];
+      put(ll, b * Rlast + aa, acc);
+    }
+  }
+  __syncthreads();
+}
+
 // Accumulates the squared residual (se) and ||X||^2 (sx) over the row blocks
 // first, first + stride, ... All threads of the CTA must call it. `chain` and `slice` are
 // per-warp scratch of kMaxL elements (8 warps); `dyn` holds fit_smem_bytes<T>(f.K).
@@ -163,27 +251,9 @@ __device__ void fit_blocks(const FitArgs& a, const FitSplit& f, const T* __restr
 
   for (int64_t blk = first; blk * FL < rows; blk += stride) {
     const int64_t p0 = blk * FL;
-    // 1. V^T for the FL rows of the block, one warp per row.
-    for (int ll = warp; ll < FL; ll += FNT / 32) {
-      const int64_t p = p0 + ll;
-      if (p >= rows) {
-        for (int e = lane; e < K; e += 32) Vt[vpos(e, ll)] = T(0);
-        continue;
-      }
-      int64_t ii[kMaxModes];
-      int64_t rem = p;
-      for (int m = f.s - 1; m >= 0; --m) { ii[m] = rem % a.dims[m]; rem /= a.dims[m]; }
-      T* S = chain[warp];
-      const int Rs = warp_slice_product<T>(a, 0, f.s, ii, S, slice[warp], lane);
-      __syncwarp();
-      // S is R_{N-1} x R_{s-1} (P_left[a][b]); V[b * R_{N-1} + a] = P_left[a][b].
-      for (int e = lane; e < K; e += 32) {
-        const int b = e / Rlast, aa = e - b * Rlast;
-        Vt[vpos(e, ll)] = S[aa * Rs + b];
-      }
-      __syncwarp();
-    }
-    __syncthreads();
+    // 1. V^T for the FL rows of the block.
+    build_left<T>(a, f, p0, FL, chain, slice,
+                  [&](int ll, int e, T v) { Vt[vpos(e, ll)] = v; });
     // 2. TR(p, q) for tiles of FI columns, MI x MJ per thread.
     for (int64_t q0 = 0; q0 < cols; q0 += FI) {
       const int nq = static_cast<int>((cols - q0 < FI) ? cols - q0 : FI);

@@ -1,13 +1,15 @@
 // The relative-error contraction of fit_body.cuh on the 5th-generation tensor cores, for
 // X in FP32 and contraction length K <= 128.
 //
-// Per block of 128 rows the CTA forms V (the left slice products, one warp per row), splits
-// every entry into TF32 parts hi = rna(v), lo = rna(v - hi) and keeps both, K-major and
-// 128-byte swizzled, in shared memory for the whole block. For every tile of 128 columns
-// the K chunks (32 wide) of W^T stream through two shared-memory stages, split the same way;
-// one elected thread issues hi*hi + hi*lo + lo*hi per 8-wide k-step into one FP32
-// accumulator in tensor memory (about FP32 accuracy), committing each chunk to the stage's
-// mbarrier. The epilogue reads TR(p, q) back from tensor memory (warp w: rows 32 (w % 4)..,
+// The right factors W are formed once per evaluation (fit_right_tc_warp) already split
+// into TF32 parts hi = rna(w), lo = rna(w - hi) and laid out as the MMA's K-major,
+// 128-byte-swizzled operand tiles: [column tile][K chunk][hi 16 KB | lo 16 KB]. Per block of
+// 128 rows the CTA forms V (the left slice products, build_left), splits it the same way and
+// keeps it in shared memory for the whole block. For every tile of 128 columns one elected
+// thread streams the K chunks (32 wide) of W through two shared-memory stages with one bulk
+// copy each (transaction-byte mbarriers, one chunk ahead) and issues hi*hi + hi*lo + lo*hi
+// per 8-wide k-step into one FP32 accumulator in tensor memory (about FP32 accuracy),
+// committing each chunk to the stage's second mbarrier. The epilogue reads TR(p, q) back from tensor memory (warp w: rows 32 (w % 4)..,
 // columns 64 (w / 4)..), forms (X - TR)^2 and X^2 in FP32 per tile and adds them to FP64
 // per-thread totals. Every mbarrier wait is bounded: on expiry the CTA records the timeout
 // bit, waits (bounded) for its issued MMAs, frees its tensor memory and stops.
@@ -27,6 +29,13 @@ constexpr int FT_VBYTES = 2 * (kFitTcMaxK / FTK) * FT_TILE;   // V hi/lo, all ch
 constexpr int FT_STAGE = 2 * FT_TILE;             // W chunk hi + lo
 constexpr size_t kFitTcSmem = FT_VBYTES + 2 * FT_STAGE + 1024;
 
+// Bytes of the swizzled right factors for a split: column tiles x K chunks x (hi + lo).
+__host__ __device__ inline size_t fit_tc_right_bytes(const FitSplit& f) {
+  const int64_t tiles = (f.cols + FTN - 1) / FTN;
+  const int Kc = (f.K + FTK - 1) / FTK;
+  return static_cast<size_t>(tiles) * Kc * FT_STAGE;
+}
+
 // The tensor-core contraction serves FP32 X with K <= 128; the rest uses fit_blocks.
 __host__ __device__ inline bool fit_use_tc(const FitSplit& f, bool xf64) {
   return !xf64 && f.K <= kFitTcMaxK;
@@ -38,15 +47,47 @@ __host__ __device__ inline int64_t fit_row_blocks(const FitSplit& f, bool xf64) 
 }
 
 struct FitTcShared {
-  uint64_t mbar[2];
+  uint64_t full[2];     // a stage's bulk copy has landed (transaction bytes)
+  uint64_t empty[2];    // the MMAs that read a stage have finished (tcgen05.commit)
   uint32_t tmem_slot;
   int abort;
 };
 
+// Column q (< column tiles * 128) of the swizzled right factors, one warp; q >= cols and
+// entries e >= K are zero. S and G are per-warp scratch of kMaxL elements.
+__device__ inline void fit_right_tc_warp(const FitArgs& a, const FitSplit& f, int64_t q,
+                                         unsigned char* __restrict__ WS, float* S, float* G,
+                                         int lane) {
+  using namespace tc;
+  const int N = a.N;
+  const int Kc = (f.K + FTK - 1) / FTK;
+  const bool valid = q < f.cols;
+  if (valid) {
+    int64_t ii[kMaxModes];
+    int64_t rem = q;
+    for (int m = N - 1; m >= f.s; --m) { ii[m] = rem % a.dims[m]; rem /= a.dims[m]; }
+    warp_slice_product<float>(a, f.s, N, ii, S, G, lane);
+    __syncwarp();
+  }
+  const int64_t t = q / FTN;
+  const int col = static_cast<int>(q - t * FTN);
+  for (int e = lane; e < Kc * FTK; e += 32) {
+    const float w = (valid && e < f.K) ? S[e] : 0.f;
+    const float hi = tf32_rna(w), lo = tf32_rna(w - hi);
+    const int c = e / FTK, k = e - c * FTK;
+    unsigned char* tile = WS + (static_cast<size_t>(t) * Kc + c) * FT_STAGE;
+    const uint32_t off = sw128_offset(col, k);
+    *reinterpret_cast<float*>(tile + off) = hi;
+    *reinterpret_cast<float*>(tile + FT_TILE + off) = lo;
+  }
+  __syncwarp();
+}
+
 // Accumulates (se, sx) over the row blocks first, first + stride, ... All threads of the CTA
 // call it; `dyn` holds kFitTcSmem bytes of dynamic shared memory.
 __device__ inline void fit_tc_blocks(const FitArgs& a, const FitSplit& f,
-                                     const float* __restrict__ X, const float* __restrict__ WT,
+                                     const float* __restrict__ X,
+                                     const unsigned char* __restrict__ WS,
                                      int64_t first, int64_t stride, unsigned char* dyn,
                                      float (*chain)[kMaxL], float (*slice)[kMaxL],
                                      FitTcShared& sh, unsigned* err, double& se, double& sx) {
@@ -59,7 +100,6 @@ __device__ inline void fit_tc_blocks(const FitArgs& a, const FitSplit& f,
   unsigned char* stg = base + FT_VBYTES;    // stage s: hi at s * FT_STAGE, lo after it
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int K = f.K, Kc = (K + FTK - 1) / FTK;
-  const int Rlast = a.ranks[a.N - 1];
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
@@ -67,8 +107,10 @@ __device__ inline void fit_tc_blocks(const FitArgs& a, const FitSplit& f,
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    mbar_init(smem_u32(&sh.mbar[0]), 1);
-    mbar_init(smem_u32(&sh.mbar[1]), 1);
+    for (int q = 0; q < 2; ++q) {
+      mbar_init(smem_u32(&sh.full[q]), 1);
+      mbar_init(smem_u32(&sh.empty[q]), 1);
+    }
     sh.abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -76,68 +118,64 @@ __device__ inline void fit_tc_blocks(const FitArgs& a, const FitSplit& f,
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = sh.tmem_slot;
-  long long gc = 0;   // chunks issued so far: stage gc & 1, phase gc >> 1 of that stage
+  // Chunk g of this CTA: row block first + (g / per_block) * stride, column tile
+  // (g % per_block) / Kc, K chunk g % Kc; stage g & 1, phase g >> 1 of its barriers.
+  const int64_t tiles = (f.cols + FTN - 1) / FTN;
+  const long long per_block = tiles * Kc;
+  const int64_t my_blocks = (first * FTM < f.rows)
+                                ? ((f.rows + FTM - 1) / FTM - first + stride - 1) / stride : 0;
+  const long long total = my_blocks * per_block;
+  long long g = 0;          // next chunk to consume (thread 0)
+  long long issued = -1;    // last chunk whose copy was issued (thread 0)
+  auto issue = [&](long long h) {   // thread 0: copy chunk h into stage h & 1
+    const int s = static_cast<int>(h & 1);
+    if (h >= 2 && !mbar_wait(smem_u32(&sh.empty[s]), static_cast<uint32_t>(((h - 2) >> 1) & 1))) {
+      sh.abort = 1;
+      return;
+    }
+    const long long r = h % per_block;
+    const unsigned char* src = WS + static_cast<size_t>(r) * FT_STAGE;   // (tile * Kc + c)
+    const uint32_t full = smem_u32(&sh.full[s]);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 :: "r"(full), "r"(static_cast<uint32_t>(FT_STAGE)) : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        :: "r"(smem_u32(stg + s * FT_STAGE)), "l"(src), "r"(static_cast<uint32_t>(FT_STAGE)),
+           "r"(full) : "memory");
+    issued = h;
+  };
+  if (tid == 0 && total > 0) issue(0);
 
   for (int64_t blk = first; blk * FTM < f.rows; blk += stride) {
     const int64_t p0 = blk * FTM;
-    // 1. V for the block's rows, hi/lo TF32, into the resident K-major tiles.
-    for (int ll = warp; ll < FTM; ll += FNT / 32) {
-      const int64_t p = p0 + ll;
-      const bool valid = p < f.rows;
-      float* S = chain[warp];
-      int Rs = 1;
-      if (valid) {
-        int64_t ii[kMaxModes];
-        int64_t rem = p;
-        for (int m = f.s - 1; m >= 0; --m) { ii[m] = rem % a.dims[m]; rem /= a.dims[m]; }
-        Rs = warp_slice_product<float>(a, 0, f.s, ii, S, slice[warp], lane);
-        __syncwarp();
-      }
-      for (int e = lane; e < Kc * FTK; e += 32) {
-        float v = 0.f;
-        if (valid && e < K) {
-          const int b = e / Rlast, aa = e - b * Rlast;
-          v = S[aa * Rs + b];
-        }
-        const float hi = tf32_rna(v), lo = tf32_rna(v - hi);
-        const int c = e / FTK, k = e - c * FTK;
-        const uint32_t off = sw128_offset(ll, k);
-        *reinterpret_cast<float*>(vt + c * 2 * FT_TILE + off) = hi;
-        *reinterpret_cast<float*>(vt + c * 2 * FT_TILE + FT_TILE + off) = lo;
-      }
-      __syncwarp();
-    }
+    // 1. V for the block's rows, hi/lo TF32, into the resident K-major tiles (entries
+    // K .. Kc * FTK - 1 of every row are zero).
+    auto put = [&](int ll, int e, float v) {
+      const float hi = tf32_rna(v), lo = tf32_rna(v - hi);
+      const int c = e / FTK, k = e - c * FTK;
+      const uint32_t off = sw128_offset(ll, k);
+      *reinterpret_cast<float*>(vt + c * 2 * FT_TILE + off) = hi;
+      *reinterpret_cast<float*>(vt + c * 2 * FT_TILE + FT_TILE + off) = lo;
+    };
+    const int pad = Kc * FTK - K;
+    for (int it = tid; it < FTM * pad; it += FNT) put(it / pad, K + it % pad, 0.f);
+    build_left<float>(a, f, p0, FTM, chain, slice, put);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     // 2. Tiles of 128 columns.
     for (int64_t q0 = 0; q0 < f.cols; q0 += FTN) {
-      for (int c = 0; c < Kc; ++c, ++gc) {
-        const int s = static_cast<int>(gc & 1);
-        unsigned char* st = stg + s * FT_STAGE;
-        if (gc >= 2 && tid == 0) {   // the MMAs that last read this stage have finished
-          if (!mbar_wait(smem_u32(&sh.mbar[s]), static_cast<uint32_t>(((gc - 2) >> 1) & 1)))
+      if (tid == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        for (int c = 0; c < Kc && !sh.abort; ++c, ++g) {
+          if (g + 1 < total) issue(g + 1);   // one chunk ahead
+          if (sh.abort) break;
+          const int s = static_cast<int>(g & 1);
+          if (!mbar_wait(smem_u32(&sh.full[s]), static_cast<uint32_t>((g >> 1) & 1))) {
             sh.abort = 1;
-        }
-        __syncthreads();
-        if (sh.abort) break;
-        const int col = tid & (FTN - 1);
-        const int64_t q = q0 + col;
-#pragma unroll
-        for (int r = 0; r < FTK / 2; ++r) {
-          const int k = (tid >> 7) + 2 * r;
-          const int e = c * FTK + k;
-          const float w = (q < f.cols && e < K) ? WT[static_cast<int64_t>(e) * f.cols + q] : 0.f;
-          const float hi = tf32_rna(w), lo = tf32_rna(w - hi);
-          const uint32_t off = sw128_offset(col, k);
-          *reinterpret_cast<float*>(st + off) = hi;
-          *reinterpret_cast<float*>(st + FT_TILE + off) = lo;
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
-          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            break;
+          }
           const uint32_t a_hi = smem_u32(vt + c * 2 * FT_TILE), a_lo = a_hi + FT_TILE;
-          const uint32_t b_hi = smem_u32(st), b_lo = b_hi + FT_TILE;
+          const uint32_t b_hi = smem_u32(stg + s * FT_STAGE), b_lo = b_hi + FT_TILE;
 #pragma unroll
           for (int ks = 0; ks < FTK / 8; ++ks) {
             const uint32_t koff = ks * 32;
@@ -146,15 +184,14 @@ __device__ inline void fit_tc_blocks(const FitArgs& a, const FitSplit& f,
             mma_tf32(tmem, make_desc(a_hi + koff), make_desc(b_lo + koff), kIdesc, 1u);
             mma_tf32(tmem, make_desc(a_lo + koff), make_desc(b_hi + koff), kIdesc, 1u);
           }
-          mma_commit(smem_u32(&sh.mbar[s]));
+          mma_commit(smem_u32(&sh.empty[s]));
         }
-      }
-      if (sh.abort) break;
-      // The tile's last commit covers all of its MMAs.
-      if (tid == 0) {
-        const long long gl = gc - 1;
-        if (!mbar_wait(smem_u32(&sh.mbar[gl & 1]), static_cast<uint32_t>((gl >> 1) & 1)))
-          sh.abort = 1;
+        // The tile's last commit covers all of its MMAs.
+        if (!sh.abort) {
+          const long long gl = g - 1;
+          if (!mbar_wait(smem_u32(&sh.empty[gl & 1]), static_cast<uint32_t>((gl >> 1) & 1)))
+            sh.abort = 1;
+        }
       }
       __syncthreads();
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -170,13 +207,29 @@ __device__ inline void fit_tc_blocks(const FitArgs& a, const FitSplit& f,
         if (p < f.rows) {
           const float* xr = X + p * f.cols + q0 + col0;
           const int64_t left = f.cols - (q0 + col0);
+          if (left >= 32 && (reinterpret_cast<uintptr_t>(xr) & 15) == 0) {
+            float4 xv[8];
 #pragma unroll
-          for (int i = 0; i < 32; ++i) {
-            if (i < left) {
-              const float x = xr[i];
-              const float d = x - v[i];
-              se_t += d * d;
-              sx_t += x * x;
+            for (int u = 0; u < 8; ++u) xv[u] = __ldg(reinterpret_cast<const float4*>(xr) + u);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              const float xs[4] = {xv[u].x, xv[u].y, xv[u].z, xv[u].w};
+#pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                const float d = xs[j] - v[4 * u + j];
+                se_t += d * d;
+                sx_t += xs[j] * xs[j];
+              }
+            }
+          } else {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+              if (i < left) {
+                const float x = xr[i];
+                const float d = x - v[i];
+                se_t += d * d;
+                sx_t += x * x;
+              }
             }
           }
         }
@@ -188,13 +241,14 @@ __device__ inline void fit_tc_blocks(const FitArgs& a, const FitSplit& f,
     }
     if (sh.abort) break;
   }
-  // Wait (bounded) for every issued MMA before the tensor memory is freed.
-  if (tid == 0 && gc > 0) {
-    const long long gl = gc - 1;
-    if (!mbar_wait(smem_u32(&sh.mbar[gl & 1]), static_cast<uint32_t>((gl >> 1) & 1)))
+  // Wait (bounded) for every issued MMA and bulk copy before the tensor memory is freed
+  // and the CTA leaves.
+  if (tid == 0) {
+    if (g > 0 && !mbar_wait(smem_u32(&sh.empty[(g - 1) & 1]),
+                            static_cast<uint32_t>(((g - 1) >> 1) & 1)))
       sh.abort = 1;
-    if (gl >= 1 &&
-        !mbar_wait(smem_u32(&sh.mbar[(gl - 1) & 1]), static_cast<uint32_t>(((gl - 1) >> 1) & 1)))
+    if (issued >= g && !mbar_wait(smem_u32(&sh.full[issued & 1]),
+                                  static_cast<uint32_t>((issued >> 1) & 1)))
       sh.abort = 1;
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");

@@ -23,7 +23,7 @@
 #include <unordered_map>
 #include <vector>
 
-#include "fit_body.cuh"
+#include "fit_tc.cuh"
 #include "host_util.h"
 
 namespace trk {
@@ -181,7 +181,9 @@ void free_all(tr_server* s) {
 void carve_request(Carver& c, const tr_request& r, bool f64, bool xf64, BInst& d) {
   carve_instance(c, r.N, r.dims, r.ranks, r.J, f64, d);
   const FitSplit f = fit_split(r.N, r.dims, r.ranks);
-  d.fitw = c.take<char>(static_cast<size_t>(f.cols) * f.K * (xf64 ? 8 : 4));
+  const size_t simt = static_cast<size_t>(f.cols) * f.K * (xf64 ? 8 : 4);
+  const size_t tcb = fit_use_tc(f, xf64) ? fit_tc_right_bytes(f) : 0;
+  d.fitw = c.take<char>(simt > tcb ? simt : tcb);
 }
 
 size_t request_ws(const tr_request& r, bool f64, bool xf64) {
