@@ -135,8 +135,8 @@ __device__ __forceinline__ void fit_right_warp(const FitArgs& a, const FitSplit&
 }
 
 // V_p[e] (e = b * R_{N-1} + a, V_p[e] = P_left(p)[a][b]) for the rows p0 .. p0 + nb - 1 of a
-// block, handed to put(ll, e, value) (rows past the end give zeros). All threads of the CTA
-// call it; it ends with a CTA barrier.
+// block and the entries e0 <= e < e1, handed to put(ll, e, value) (rows past the end give
+// zeros). All threads of the CTA call it; it ends with a CTA barrier.
 //
 // Rows p = pre * J + last (J = I_{s-1}) share the prefix G^(0) .. G^(s-2) of their slice
 // chain, and consecutive rows mostly share it: each distinct prefix of the block is formed
@@ -145,16 +145,18 @@ __device__ __forceinline__ void fit_right_warp(const FitArgs& a, const FitSplit&
 // are those of a per-row chain, so V is the same. Blocks with more than 8 prefixes (J < 16)
 // form every row's chain with one warp.
 template <typename T, typename Put>
-__device__ void build_left(const FitArgs& a, const FitSplit& f, int64_t p0, int nb,
-                           T (*chain)[kMaxL], T (*slice)[kMaxL], Put put) {
-  const int N = a.N, s = f.s, K = f.K;
+__device__ void build_left(const FitArgs& a, const FitSplit& f, int64_t p0, int nb, int e0,
+                           int e1, T (*chain)[kMaxL], T (*slice)[kMaxL], Put put) {
+  const int N = a.N, s = f.s;
+  const int K = e1 < f.K ? e1 : f.K;   // entries K .. e1 - 1 are the caller's padding
   const int Rlast = a.ranks[N - 1], Rs = a.ranks[s - 1];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t rows = f.rows;
   const int64_t pend = (p0 + nb < rows) ? p0 + nb : rows;
   if (s == 1) {   // P_left(p) is the slice G^(0)(:, p, :) itself
-    for (int it = tid; it < nb * K; it += FNT) {
-      const int ll = it / K, e = it - ll * K;
+    const int w = K - e0;
+    for (int it = tid; it < nb * w; it += FNT) {
+      const int ll = it / w, e = e0 + (it - ll * w);
       const int64_t p = p0 + ll;
       const int b = e / Rlast, aa = e - b * Rlast;
       put(ll, e, p < rows ? static_cast<T>(a.core[0][(p * Rlast + aa) * Rs + b]) : T(0));
@@ -170,7 +172,7 @@ __device__ void build_left(const FitArgs& a, const FitSplit& f, int64_t p0, int 
     for (int ll = warp; ll < nb; ll += FNT / 32) {
       const int64_t p = p0 + ll;
       if (p >= rows) {
-        for (int e = lane; e < K; e += 32) put(ll, e, T(0));
+        for (int e = e0 + lane; e < K; e += 32) put(ll, e, T(0));
         continue;
       }
       int64_t ii[kMaxModes];
@@ -179,7 +181,7 @@ __device__ void build_left(const FitArgs& a, const FitSplit& f, int64_t p0, int 
       T* S = chain[warp];
       const int rs = warp_slice_product<T>(a, 0, s, ii, S, slice[warp], lane);
       __syncwarp();
-      for (int e = lane; e < K; e += 32) {
+      for (int e = e0 + lane; e < K; e += 32) {
         const int b = e / Rlast, aa = e - b * Rlast;
         put(ll, e, S[aa * rs + b]);
       }
@@ -197,11 +199,16 @@ __device__ void build_left(const FitArgs& a, const FitSplit& f, int64_t p0, int 
   }
   __syncthreads();
   const double* Gs = a.core[s - 1];
-  for (int it = tid; it < nb * Rs; it += FNT) {
-    const int ll = it / Rs, b = it - ll * Rs;
+  // columns b whose entries b * Rlast .. b * Rlast + Rlast - 1 meet [e0, K)
+  const int b0 = e0 / Rlast, b1 = (K + Rlast - 1) / Rlast;
+  const int nbc = b1 - b0;
+  for (int it = tid; it < nb * nbc; it += FNT) {
+    const int ll = it / nbc, b = b0 + (it - ll * nbc);
     const int64_t p = p0 + ll;
+    const int a0 = e0 > b * Rlast ? e0 - b * Rlast : 0;
+    const int a1 = K < (b + 1) * Rlast ? K - b * Rlast : Rlast;
     if (p >= rows) {
-      for (int aa = 0; aa < Rlast; ++aa) put(ll, b * Rlast + aa, T(0));
+      for (int aa = a0; aa < a1; ++aa) put(ll, b * Rlast + aa, T(0));
       continue;
     }
     const int64_t pre = p / J, last = p - pre * J;
@@ -210,7 +217,7 @@ __device__ void build_left(const FitArgs& a, const FitSplit& f, int64_t p0, int 
     T gc[16];
 #pragma unroll
     for (int c = 0; c < 16; ++c) gc[c] = c < Rm ? static_cast<T>(g[c * Rs]) : T(0);
-    for (int aa = 0; aa < Rlast; ++aa) {
+    for (int aa = a0; aa < a1; ++aa) {
       const T* pr = P + aa * Rm;
       T acc = T(0);
 #pragma unroll
@@ -252,7 +259,7 @@ __device__ void fit_blocks(const FitArgs& a, const FitSplit& f, const T* __restr
   for (int64_t blk = first; blk * FL < rows; blk += stride) {
     const int64_t p0 = blk * FL;
     // 1. V^T for the FL rows of the block.
-    build_left<T>(a, f, p0, FL, chain, slice,
+    build_left<T>(a, f, p0, FL, 0, K, chain, slice,
                   [&](int ll, int e, T v) { Vt[vpos(e, ll)] = v; });
     // 2. TR(p, q) for tiles of FI columns, MI x MJ per thread.
     for (int64_t q0 = 0; q0 < cols; q0 += FI) {
