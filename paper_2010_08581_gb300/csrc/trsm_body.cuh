@@ -18,19 +18,24 @@ namespace trk {
 
 constexpr int TW = 4;   // warps per CTA
 
+// The factor for the substitutions: the padded image s[c*(n+1) + r] = L[r][c] in shared
+// memory (SMEM), or in global memory when the Cholesky kernel wrote one (its FP32 or FP64
+// image in L2: no per-element conversion from FP64), else the FP64 column- and row-major
+// factor.
 template <typename T, bool SMEM>
 struct Factor {
-  const T* s;            // shared: s[c*(n+1) + r] = L[r][c]
+  const T* s;            // image, shared (SMEM) or global (gimg)
   const double* Lcol;    // global: Lcol[c*n + r] = L[r][c]
   const double* Lrow;    // global: Lrow[c*n + r] = L[c][r]
   int n;
+  bool gimg = false;     // !SMEM: s is a global image
   __device__ __forceinline__ T col(int c, int r) const {   // L[r][c]
     if constexpr (SMEM) return s[c * (n + 1) + r];
-    else return static_cast<T>(Lcol[c * n + r]);
+    else return gimg ? __ldg(s + c * (n + 1) + r) : static_cast<T>(Lcol[c * n + r]);
   }
   __device__ __forceinline__ T row(int c, int r) const {   // L[c][r]
     if constexpr (SMEM) return s[r * (n + 1) + c];
-    else return static_cast<T>(Lrow[c * n + r]);
+    else return gimg ? __ldg(s + r * (n + 1) + c) : static_cast<T>(Lrow[c * n + r]);
   }
 };
 
@@ -230,7 +235,7 @@ __device__ __forceinline__ void trsm_cta(unsigned char* trsm_smem, int64_t cta, 
     }
   }
   __syncthreads();
-  Factor<T, SMEM> F{Ls, Lcol, Lrow, n};
+  Factor<T, SMEM> F{SMEM ? Ls : Limg, Lcol, Lrow, n, !SMEM && Limg != nullptr};
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t v0 = (cta * TW + warp) * NB;
   if (mode == 0) {
@@ -307,6 +312,7 @@ __device__ __forceinline__ void trsm_cta(unsigned char* trsm_smem, int64_t cta, 
           if (r < n) {
             T m;
             if constexpr (SMEM) m = Ms[t * np + r];
+            else if (sizeof(T) == 4 && Mimg) m = static_cast<T>(__ldg(Mimg + t * np + r));
             else m = static_cast<T>(M[t * n + r]);
 #pragma unroll
             for (int v = 0; v < NB; ++v) res[q][v] -= m * zt[v];
