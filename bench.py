@@ -306,12 +306,16 @@ def oracle_sample(X_np, init_paper, wl, budget_s=15.0, max_sweeps=50):
 def run_batched(T, plain_fp64, dev, steps, warmup, stream):
     """512 independent 3-way FP32 problems (I_n ~ U{32..200}, ranks ~ U{3..8}, J = 10 max L,
     10 sweeps each) through tr_als_sampled_batched: one step = the whole batch."""
+    from paper_2010_08581_gb300 import autotune
     count, sweeps = 512, 10
     probs = inputs.batched_workload(count, seed=4, device=dev)
     ctxb = T.Context(dev.index if dev.index is not None else 0)
     for pr in probs:
         pr["cores"] = T.empty_cores(pr["dims"], pr["ranks"], device=dev)
         pr["init"] = False
+    t0 = time.perf_counter()
+    tuned = autotune.tune_batched(ctxb, probs, T.TR_PREC_MIXED)
+    tune_s = time.perf_counter() - t0
     for i in range(max(1, warmup)):
         T.tr_als_sampled_batched(ctxb, probs, sweeps, T.TR_PREC_MIXED)
     torch.cuda.synchronize()
@@ -351,7 +355,13 @@ def run_batched(T, plain_fp64, dev, steps, warmup, stream):
             "plain_fp64_gpu_form": {"value": round(plain_rate, 2), "unit": "instance-sweeps/s",
                                     "what": f"{nplain} of the problems decomposed one after "
                                             "another by the plain FP64 form"},
-            "speedup_vs_plain_fp64": round(rate / plain_rate, 1)}
+            "speedup_vs_plain_fp64": round(rate / plain_rate, 1),
+            "tiles": {"samples_per_warp": tuned["samples_per_warp"],
+                      "contract_tile": tuned["contract_tile"], "from_table": tuned["cached"],
+                      "tuning_s": round(tune_s, 3),
+                      "ms_per_one_sweep_call": tuned.get("ms"),
+                      "what": "launch shapes chosen by the project's autotuner on scratch "
+                              "copies of this batch (results do not depend on them)"}}
 
 
 def _time_calls(fn, reps, stream):

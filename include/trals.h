@@ -189,6 +189,23 @@ tr_status tr_als_sampled_batched(tr_ctx* ctx, const tr_instance* inst, int count
                                  tr_dtype X_dtype, int sweeps, tr_precision prec,
                                  tr_stream stream);
 
+/* Launch shapes of the batched driver's kernels, chosen per batch geometry by the
+ * project's autotuner (paper_2010_08581_gb300/autotune.py), which times the candidates on
+ * scratch copies of a batch. Neither field changes any result: samples are independent,
+ * and every entry of the normal equations is summed over the samples in the same order
+ * for either tile.
+ *   samples_per_warp : samples drawn and formed by one warp of the sampling kernel, 1..8
+ *   contract_tile    : output tile (64 or 32 square) of the normal-equation contraction
+ * A context starts with {4, 64}. tr_set_batched_tiles returns TR_ERR_INVALID_ARG for
+ * other values. */
+typedef struct tr_batched_tiles {
+  int samples_per_warp;
+  int contract_tile;
+} tr_batched_tiles;
+
+tr_status tr_set_batched_tiles(tr_ctx* ctx, const tr_batched_tiles* tiles);
+tr_status tr_get_batched_tiles(const tr_ctx* ctx, tr_batched_tiles* tiles);
+
 /* Least-squares step without any device allocation (the paper has no counterpart; this
  * is a deployment variant of tr_solve).
  *

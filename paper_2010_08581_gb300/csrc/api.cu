@@ -45,6 +45,7 @@ struct tr_ctx {
   cudaGraphExec_t bexec = nullptr;
   std::vector<uint64_t> bkey;
   std::vector<trk::BInst> btab;     // host copy of the instance table
+  tr_batched_tiles tiles{4, 64};    // launch shapes of the batched kernels
 };
 
 namespace {
@@ -945,6 +946,8 @@ tr_status tr_als_sampled_batched(tr_ctx* ctx, const tr_instance* inst, int count
   bl.count = count;
   bl.f64 = f64;
   bl.xf64 = X_dtype == TR_F64;
+  bl.spw = ctx->tiles.samples_per_warp;
+  bl.ctile = ctx->tiles.contract_tile;
   int nmax_modes = 0, steps = 0;
   bool draw = false;
   for (int i = 0; i < count; ++i) {
@@ -989,7 +992,8 @@ tr_status tr_als_sampled_batched(tr_ctx* ctx, const tr_instance* inst, int count
                                  static_cast<uint64_t>(f64), static_cast<uint64_t>(bl.xf64),
                                  static_cast<uint64_t>(nmax_modes), static_cast<uint64_t>(steps),
                                  static_cast<uint64_t>(draw), reinterpret_cast<uintptr_t>(dtab),
-                                 static_cast<uint64_t>(ctx->prof)};
+                                 static_cast<uint64_t>(ctx->prof),
+                                 static_cast<uint64_t>(bl.spw), static_cast<uint64_t>(bl.ctile)};
     if (!ctx->bexec || key != ctx->bkey) {
       if (ctx->bexec) cudaGraphExecDestroy(ctx->bexec);
       ctx->bexec = nullptr;
@@ -1018,6 +1022,25 @@ tr_status tr_als_sampled_batched(tr_ctx* ctx, const tr_instance* inst, int count
     TR_CUDA(cudaGraphLaunch(ctx->bexec, st));
   }
   return read_device_error(ctx, st);
+}
+
+tr_status tr_set_batched_tiles(tr_ctx* ctx, const tr_batched_tiles* tiles) {
+  TR_TRY(check_ctx(ctx));
+  if (!tiles) return fail(ctx, TR_ERR_INVALID_ARG, "tiles is NULL");
+  if (tiles->samples_per_warp < 1 || tiles->samples_per_warp > 8)
+    return fail(ctx, TR_ERR_INVALID_ARG, "samples_per_warp=%d outside [1, 8]",
+                tiles->samples_per_warp);
+  if (tiles->contract_tile != 64 && tiles->contract_tile != 32)
+    return fail(ctx, TR_ERR_INVALID_ARG, "contract_tile=%d is not 64 or 32",
+                tiles->contract_tile);
+  ctx->tiles = *tiles;
+  return TR_OK;
+}
+
+tr_status tr_get_batched_tiles(const tr_ctx* ctx, tr_batched_tiles* tiles) {
+  if (!ctx || !tiles) return TR_ERR_INVALID_ARG;
+  *tiles = ctx->tiles;
+  return TR_OK;
 }
 
 tr_status tr_rel_error(tr_ctx* ctx, const void* X, tr_dtype X_dtype, int N, const int64_t* dims,

@@ -82,17 +82,18 @@ __global__ void __launch_bounds__(256) kb_init_cores(const BInst* __restrict__ t
 // of one instance's samples: one warp per sample.
 // ------------------------------------------------------------------------------------
 constexpr int SW = 8;     // warps per CTA
-constexpr int SPW = 4;    // samples per warp
+constexpr int kSpwMax = 8;   // samples per warp: a launch parameter in [1, 8] (tiles)
 
 template <typename T, typename TX>
-__global__ void __launch_bounds__(SW * 32) kb_sample(const BInst* __restrict__ tab, int step) {
+__global__ void __launch_bounds__(SW * 32) kb_sample(const BInst* __restrict__ tab, int step,
+                                                     int spw) {
   __shared__ T sS[SW][kMaxL];
   __shared__ T sG[SW][kMaxL];
   __shared__ ChainArgs ca;
   const BInst& d = tab[blockIdx.x];
   const Cur cu = current(d, step, 0, false);
   if (!cu.active) return;
-  const int64_t j0 = static_cast<int64_t>(blockIdx.y) * SW * SPW;
+  const int64_t j0 = static_cast<int64_t>(blockIdx.y) * SW * spw;
   if (j0 >= d.J) return;
   const int N = d.N, npos = N - 1, n = cu.n;
   if (threadIdx.x == 0) {
@@ -115,8 +116,8 @@ __global__ void __launch_bounds__(SW * 32) kb_sample(const BInst* __restrict__ t
   T* Y = static_cast<T*>(d.Y);
   const int L = cu.L;
   const int64_t I = cu.I, sn = d.stride[n];
-  for (int s = 0; s < SPW; ++s) {
-    const int64_t j = j0 + warp * SPW + s;
+  for (int s = 0; s < spw; ++s) {
+    const int64_t j = j0 + warp * spw + s;
     if (j >= d.J) break;
     int64_t mine = 0;
     double pmine = 1.0;
@@ -146,13 +147,17 @@ __global__ void __launch_bounds__(SW * 32) kb_sample(const BInst* __restrict__ t
 }
 
 // ------------------------------------------------------------------------------------
-// Normal equations C = A^T [A | Y] per instance, 64 x 64 output tiles over all samples
+// Normal equations C = A^T [A | Y] per instance, square output tiles over all samples
 // (no split: one fixed summation order per entry); M = C[:, :L], B^T = C[:, L:]^T in FP64.
 // ------------------------------------------------------------------------------------
-constexpr int BM = 64, BN = 64, BK = 16, CT = 256;
+// TILE x TILE outputs per CTA, 4 x 4 per thread; every entry is summed over the samples in
+// the same order for either tile, so the tile (a launch parameter) never changes results.
+constexpr int BK = 16;
 
-template <typename T>
-__global__ void __launch_bounds__(CT) kb_contract(const BInst* __restrict__ tab, int step) {
+template <typename T, int TILE>
+__global__ void __launch_bounds__((TILE / 4) * (TILE / 4)) kb_contract(
+    const BInst* __restrict__ tab, int step) {
+  constexpr int BM = TILE, BN = TILE, TXN = TILE / 4, CT = TXN * TXN;
   __shared__ T As[BK][BM];
   __shared__ T Bs[BK][BN];
   const BInst& d = tab[blockIdx.x];
@@ -169,7 +174,7 @@ __global__ void __launch_bounds__(CT) kb_contract(const BInst* __restrict__ tab,
   const T* __restrict__ A = static_cast<const T*>(d.A);
   const T* __restrict__ Y = static_cast<const T*>(d.Y);
   const int64_t J = d.J;
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int tx = threadIdx.x % TXN, ty = threadIdx.x / TXN;
   T acc[4][4];
 #pragma unroll
   for (int u = 0; u < 4; ++u)
@@ -196,9 +201,9 @@ __global__ void __launch_bounds__(CT) kb_contract(const BInst* __restrict__ tab,
     for (int kk = 0; kk < BK; ++kk) {
       T a[4], b[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) a[u] = As[kk][ty + 16 * u];
+      for (int u = 0; u < 4; ++u) a[u] = As[kk][ty + TXN * u];
 #pragma unroll
-      for (int v = 0; v < 4; ++v) b[v] = Bs[kk][tx + 16 * v];
+      for (int v = 0; v < 4; ++v) b[v] = Bs[kk][tx + TXN * v];
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
@@ -208,11 +213,11 @@ __global__ void __launch_bounds__(CT) kb_contract(const BInst* __restrict__ tab,
   }
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
-    const int r = r0 + ty + 16 * u;
+    const int r = r0 + ty + TXN * u;
     if (r >= L) continue;
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
-      const int64_t c = c0 + tx + 16 * v;
+      const int64_t c = c0 + tx + TXN * v;
       if (c < L) d.M[static_cast<int64_t>(r) * L + c] = static_cast<double>(acc[u][v]);
       else if (c < ldc) d.BT[(c - L) * L + r] = static_cast<double>(acc[u][v]);
     }
@@ -560,22 +565,29 @@ cudaError_t bl_init_cores(const BLaunch& b, cudaStream_t st) {
 }
 
 cudaError_t bl_sample_chain_gather(const BLaunch& b, int step, cudaStream_t st) {
-  const int64_t per = SW * SPW;
+  const int spw = b.spw >= 1 && b.spw <= kSpwMax ? b.spw : 4;
+  const int64_t per = SW * spw;
   dim3 grid(b.count, static_cast<unsigned>((b.Jmax + per - 1) / per));
-  if (b.f64 && b.xf64) kb_sample<double, double><<<grid, SW * 32, 0, st>>>(b.tab, step);
-  else if (b.f64) kb_sample<double, float><<<grid, SW * 32, 0, st>>>(b.tab, step);
-  else if (b.xf64) kb_sample<float, double><<<grid, SW * 32, 0, st>>>(b.tab, step);
-  else kb_sample<float, float><<<grid, SW * 32, 0, st>>>(b.tab, step);
+  if (b.f64 && b.xf64) kb_sample<double, double><<<grid, SW * 32, 0, st>>>(b.tab, step, spw);
+  else if (b.f64) kb_sample<double, float><<<grid, SW * 32, 0, st>>>(b.tab, step, spw);
+  else if (b.xf64) kb_sample<float, double><<<grid, SW * 32, 0, st>>>(b.tab, step, spw);
+  else kb_sample<float, float><<<grid, SW * 32, 0, st>>>(b.tab, step, spw);
+  return cudaGetLastError();
+}
+
+template <int TILE>
+cudaError_t contract_tile(const BLaunch& b, int step, cudaStream_t st) {
+  const int ntr = (b.Lmax + TILE - 1) / TILE;
+  const int64_t ntc = (b.Lmax + b.Imax + TILE - 1) / TILE;
+  dim3 grid(b.count, static_cast<unsigned>(ntr * ntc));
+  constexpr int CT = (TILE / 4) * (TILE / 4);
+  if (b.f64) kb_contract<double, TILE><<<grid, CT, 0, st>>>(b.tab, step);
+  else kb_contract<float, TILE><<<grid, CT, 0, st>>>(b.tab, step);
   return cudaGetLastError();
 }
 
 cudaError_t bl_contract(const BLaunch& b, int step, cudaStream_t st) {
-  const int ntr = (b.Lmax + BM - 1) / BM;
-  const int64_t ntc = (b.Lmax + b.Imax + BN - 1) / BN;
-  dim3 grid(b.count, static_cast<unsigned>(ntr * ntc));
-  if (b.f64) kb_contract<double><<<grid, CT, 0, st>>>(b.tab, step);
-  else kb_contract<float><<<grid, CT, 0, st>>>(b.tab, step);
-  return cudaGetLastError();
+  return b.ctile == 32 ? contract_tile<32>(b, step, st) : contract_tile<64>(b, step, st);
 }
 
 cudaError_t bl_cholesky(const BLaunch& b, int step, int init_k, int which, unsigned* err,

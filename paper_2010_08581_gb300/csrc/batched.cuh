@@ -91,6 +91,9 @@ struct BLaunch {
   int64_t Imax;
   int n1max;                     // max leverage pass-1 Gram size
   int n2max;                     // max leverage pass-2 Gram size (0 if no wide mode)
+  // launch shapes (tr_batched_tiles): neither changes any result
+  int spw = 4;                   // samples per warp of the sampling kernel, 1..8
+  int ctile = 64;                // output tile of the normal-equation contraction, 64 or 32
 };
 
 cudaError_t bl_init_cores(const BLaunch& b, cudaStream_t st);

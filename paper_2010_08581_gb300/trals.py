@@ -46,6 +46,11 @@ class TrInstance(ctypes.Structure):
 MAX_SERVED_SWEEPS = 64
 
 
+class TrBatchedTiles(ctypes.Structure):
+    """Mirror of ``tr_batched_tiles``."""
+    _fields_ = [("samples_per_warp", c_int), ("contract_tile", c_int)]
+
+
 class TrServerConfig(ctypes.Structure):
     """Mirror of ``tr_server_config``."""
     _fields_ = [("device", c_int), ("hbm_budget_bytes", c_sz), ("arena_bytes", c_sz),
@@ -104,6 +109,8 @@ SIGNATURES = {
                                        c_int, c_vp]),
     "tr_solve_noalloc": (c_int, [c_vp, c_vp, c_int, c_i64, c_int, c_int, c_i64, c_int, c_vp,
                                  c_vp, c_vp]),
+    "tr_set_batched_tiles": (c_int, [c_vp, ctypes.POINTER(TrBatchedTiles)]),
+    "tr_get_batched_tiles": (c_int, [c_vp, ctypes.POINTER(TrBatchedTiles)]),
     "tr_server_create": (c_int, [ctypes.POINTER(TrServerConfig), ctypes.POINTER(c_vp)]),
     "tr_server_destroy": (None, [c_vp]),
     "tr_server_last_error": (ctypes.c_char_p, [c_vp]),
@@ -335,6 +342,17 @@ def tr_als_sampled_batched(ctx: Context, problems, sweeps: int, prec: int, strea
         inst.init_given = 1 if pr.get("init", False) else 0
     ctx.check(load().tr_als_sampled_batched(ctx.handle, arr, len(problems), dt, sweeps, prec,
                                             _stream(stream)))
+
+
+def tr_set_batched_tiles(ctx: Context, samples_per_warp: int, contract_tile: int):
+    t = TrBatchedTiles(int(samples_per_warp), int(contract_tile))
+    ctx.check(load().tr_set_batched_tiles(ctx.handle, ctypes.byref(t)))
+
+
+def tr_get_batched_tiles(ctx: Context):
+    t = TrBatchedTiles()
+    ctx.check(load().tr_get_batched_tiles(ctx.handle, ctypes.byref(t)))
+    return int(t.samples_per_warp), int(t.contract_tile)
 
 
 def tr_rel_error(ctx: Context, X: torch.Tensor, ranks, cores: List[torch.Tensor], stream=None):
