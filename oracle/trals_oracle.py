@@ -32,6 +32,7 @@ __all__ = [
     "tr_reconstruct", "rel_error", "unfold_classical", "unfold_ring",
     "core_unfold2", "core_from_solution", "subchain_full", "subchain_unfold2",
     "leverage_scores", "core_distribution", "inverse_cdf", "draw_samples",
+    "draw_samples_uniform",
     "sampled_subchain", "sampled_fibres", "sampled_ls_normal", "sampled_ls_qr",
     "sampled_core_update", "tr_als_sampled", "tr_als_sampled_until", "tr_als", "tr_als_update",
 ]
@@ -240,6 +241,27 @@ def draw_samples(ps, cdfs, n, J, seed, update_id):
     return idx, w
 
 
+def draw_samples_uniform(dims, n, J, seed, update_id):
+    """Draw J i.i.d. multi-indices from the uniform distribution q^{!=n} = 1 / prod_{j!=n} I_j,
+    the alternative to leverage-score sampling of Sec. 5 (uniform sampling experiment).
+    Each ring position m takes the same Philox uniform u as the leverage sampler and maps it
+    to the index floor(u * I) of a uniform draw on {0, ..., I-1} (clamped to I-1 should
+    rounding give I). The rescaling of Def. 5 is the same for every sample:
+    w = 1 / sqrt(J q) = sqrt(P / J) with P = prod_{j!=n} I_j, formed in ring order.
+    Returns idx (J, N-1) in ring order and w (J,)."""
+    N = len(dims)
+    modes = ring_modes(N, n)
+    idx = np.empty((J, N - 1), dtype=np.int64)
+    P = 1.0
+    for m, mode in enumerate(modes):
+        I = float(dims[mode])
+        u = philox_uniforms(J, m, seed, update_id)
+        idx[:, m] = np.minimum(np.floor(u * I), I - 1.0).astype(np.int64)
+        P = P * I
+    w = np.full(J, np.sqrt(P / float(J)), dtype=np.float64)
+    return idx, w
+
+
 def sampled_subchain(cores, n, idx, w):
     """Sketch S G_[2]^{!=n} (Alg. 4): row j is the vectorised product of the sampled lateral
     slices G^(n+1)(:, i_{n+1}, :) ... G^(n-1)(:, i_{n-1}, :) (an R_n x R_{n-1} matrix),
@@ -283,10 +305,15 @@ def sampled_ls_qr(A, Y):
     return solve_triangular(R, Q.T @ Y, lower=False)
 
 
-def sampled_core_update(X, cores, ps, cdfs, n, J, seed, update_id, solver="qr"):
+def sampled_core_update(X, cores, ps, cdfs, n, J, seed, update_id, solver="qr",
+                        sampling="leverage"):
     """One inner iteration of Alg. 2 for core n: draw S, sketch G and X, solve the sampled LS.
-    Returns (new core, idx, w)."""
-    idx, w = draw_samples(ps, cdfs, n, J, seed, update_id)
+    ``sampling="uniform"`` draws S from the uniform distribution instead (Sec. 5, uniform
+    sampling; ``ps``/``cdfs`` are then unused). Returns (new core, idx, w)."""
+    if sampling == "uniform":
+        idx, w = draw_samples_uniform(X.shape, n, J, seed, update_id)
+    else:
+        idx, w = draw_samples(ps, cdfs, n, J, seed, update_id)
     A = sampled_subchain(cores, n, idx, w)
     Y = sampled_fibres(X, n, idx, w)
     Z = (sampled_ls_qr if solver == "qr" else sampled_ls_normal)(A, Y)
@@ -294,49 +321,61 @@ def sampled_core_update(X, cores, ps, cdfs, n, J, seed, update_id, solver="qr"):
     return core_from_solution(Z, Rl, Rr), idx, w
 
 
-def _initial_distributions(cores):
-    """The distributions of cores 1..N-1 formed before the first sweep (Alg. 2)."""
+def _initial_distributions(cores, sampling="leverage"):
+    """The distributions of cores 1..N-1 formed before the first sweep (Alg. 2); none under
+    uniform sampling, which needs no distribution (Sec. 5)."""
     N = len(cores)
     ps, cdfs = [None] * N, [None] * N
+    if sampling == "uniform":
+        return ps, cdfs
     for n in range(1, N):
         ps[n], cdfs[n] = core_distribution(cores[n])
     return ps, cdfs
 
 
-def _sweep(X, cores, ps, cdfs, J, seed, s, solver):
+def _sweep(X, cores, ps, cdfs, J, seed, s, solver, sampling="leverage"):
     """One pass of the outer loop of Alg. 2: update every core in order n = 0..N-1, each
-    followed by its new distribution; sweep s, core n uses update_id = s * N + n."""
+    followed by its new distribution (leverage sampling only); sweep s, core n uses
+    update_id = s * N + n."""
     N = len(cores)
     for n in range(N):
-        cores[n], _, _ = sampled_core_update(X, cores, ps, cdfs, n, J, seed, s * N + n, solver)
-        ps[n], cdfs[n] = core_distribution(cores[n])
+        cores[n], _, _ = sampled_core_update(X, cores, ps, cdfs, n, J, seed, s * N + n, solver,
+                                             sampling)
+        if sampling != "uniform":
+            ps[n], cdfs[n] = core_distribution(cores[n])
 
 
-def tr_als_sampled(X, init_cores, J, sweeps, seed, solver="qr", callback=None):
+def tr_als_sampled(X, init_cores, J, sweeps, seed, solver="qr", callback=None,
+                   sampling="leverage"):
     """TR-ALS-Sampled (Alg. 2) with a fixed number of sweeps. ``init_cores`` supplies
     G^(2..N) (paper numbering); core 0 is overwritten by its first update.
-    The sample block of (sweep s, core n) uses update_id = s * N + n."""
+    The sample block of (sweep s, core n) uses update_id = s * N + n. ``sampling`` is
+    "leverage" (Alg. 2 as stated) or "uniform" (the Sec. 5 variant: uniform draws, no
+    distributions)."""
+    if sampling not in ("leverage", "uniform"):
+        raise ValueError(f"unknown sampling {sampling!r}")
     X = np.asarray(X, dtype=np.float64)
     cores = [np.array(G, dtype=np.float64, copy=True) for G in init_cores]
-    ps, cdfs = _initial_distributions(cores)
+    ps, cdfs = _initial_distributions(cores, sampling)
     for s in range(sweeps):
-        _sweep(X, cores, ps, cdfs, J, seed, s, solver)
+        _sweep(X, cores, ps, cdfs, J, seed, s, solver, sampling)
         if callback is not None:
             callback(s, cores)
     return cores
 
 
-def tr_als_sampled_until(X, init_cores, J, seed, fit_tol, max_sweeps, solver="qr"):
+def tr_als_sampled_until(X, init_cores, J, seed, fit_tol, max_sweeps, solver="qr",
+                         sampling="leverage"):
     """TR-ALS-Sampled (Alg. 2) terminated by the change of the relative error, the first
     criterion of Sec. 4.1: after sweep s the fit f_s = 1 - ||TR - X||_F / ||X||_F is
     computed exactly; the loop ends after a sweep s >= 2 with |f_s - f_{s-1}| < fit_tol,
     or after ``max_sweeps`` sweeps. Returns (cores, fits, converged)."""
     X = np.asarray(X, dtype=np.float64)
     cores = [np.array(G, dtype=np.float64, copy=True) for G in init_cores]
-    ps, cdfs = _initial_distributions(cores)
+    ps, cdfs = _initial_distributions(cores, sampling)
     fits = []
     for s in range(max_sweeps):
-        _sweep(X, cores, ps, cdfs, J, seed, s, solver)
+        _sweep(X, cores, ps, cdfs, J, seed, s, solver, sampling)
         fits.append(1.0 - rel_error(cores, X))
         if len(fits) >= 2 and abs(fits[-1] - fits[-2]) < fit_tol:
             return cores, fits, True

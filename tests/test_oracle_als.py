@@ -150,3 +150,33 @@ def test_stop_rule_on_exact_tr_stops_at_the_exact_fit():
     assert conv
     assert abs(fits[-1] - fits[-2]) < tol
     assert fits[-1] > 1.0 - 1e-6
+
+
+def test_uniform_sampled_update_is_exact_on_exact_tr():
+    """Noise-free TR, the other cores at their true values: each sampled LS under uniform
+    sampling (Sec. 5) is consistent and of full column rank, so the update returns the true
+    core whatever the row weights; a mismatch between sampled rows of G and of X fails."""
+    rng = np.random.default_rng(11)
+    dims, ranks = (9, 8, 7, 6), (2, 3, 2, 2)
+    N = len(dims)
+    true = [rng.standard_normal((ranks[(k - 1) % N], dims[k], ranks[k])) for k in range(N)]
+    X = orc.tr_reconstruct(true)
+    for n in range(N):
+        new, idx, w = orc.sampled_core_update(X, true, None, None, n, 60, seed=3, update_id=n,
+                                              sampling="uniform")
+        np.testing.assert_allclose(new, true[n], rtol=0, atol=1e-10 * np.abs(true[n]).max())
+        assert np.all(w == w[0])
+
+
+def test_uniform_tr_als_sampled_recovers_exact_tr():
+    """Alg. 2 with uniform sampling on a noise-free TR recovers the tensor like the leverage
+    version (same start as the leverage pin above)."""
+    X, init = _exact_tr((6, 7, 8), (2, 2, 2), seed=0)
+    cores = orc.tr_als_sampled(X, init, J=40, sweeps=300, seed=1, sampling="uniform")
+    assert orc.rel_error(cores, X) < 1e-9
+
+
+def test_uniform_sampling_rejects_unknown_names():
+    X, init = _exact_tr((4, 4, 4), (2, 2, 2), seed=0)
+    with pytest.raises(ValueError):
+        orc.tr_als_sampled(X, init, J=10, sweeps=1, seed=0, sampling="importance")

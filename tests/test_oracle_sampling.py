@@ -166,3 +166,59 @@ def test_lemma35_leverage_bound():
         beta = 1.0 / (ranks[n - 1] * ranks[n] *
                       np.prod([ranks[j] ** 2 for j in range(N) if j not in (n, (n - 1) % N)]))
         assert np.all(_product_q(ps, dims, n) >= beta * p_exact - 1e-15)
+
+
+# ----------------------------------------------------------------------------------------
+# Uniform sampling (the Sec. 5 alternative to leverage scores).
+# ----------------------------------------------------------------------------------------
+def _uniform_ps(dims):
+    return [np.full(d, 1.0 / d) for d in dims]
+
+
+def test_uniform_sampler_frequencies_and_weights():
+    """Every cell of prod_{j!=n} I_j is drawn with probability 1/prod I_j (chi-square), and
+    w^2 J q = 1 with q taken from the brute-force product of the uniform marginals."""
+    dims = (3, 4, 5)
+    n, J = 1, 200000
+    idx, w = orc.draw_samples_uniform(dims, n, J, seed=9, update_id=3)
+    for m, mode in enumerate(orc.ring_modes(3, n)):
+        assert idx[:, m].min() >= 0 and idx[:, m].max() < dims[mode]
+    q = _product_q(_uniform_ps(dims), dims, n)
+    lin = orc.ring_linear_index(idx, dims, n)
+    counts = np.bincount(lin, minlength=q.size)
+    assert stats.chisquare(counts, J * q).pvalue > 1e-4
+    np.testing.assert_allclose(w ** 2 * J * q[lin], 1.0, rtol=1e-13)
+
+
+def test_uniform_sketch_is_unbiased():
+    """E[S^T S] = I under uniform sampling (Def. 5 with q = 1 / prod I_j)."""
+    dims = (2, 3, 4)
+    n, J, T = 2, 30, 3000
+    K = dims[0] * dims[1]
+    acc = np.zeros(K)
+    for t in range(T):
+        idx, w = orc.draw_samples_uniform(dims, n, J, seed=23, update_id=t)
+        acc += np.bincount(orc.ring_linear_index(idx, dims, n), weights=w ** 2, minlength=K)
+    mean = acc / T
+    sd = np.sqrt((K - 1.0) / J / T)
+    assert np.all(np.abs(mean - 1.0) < 5 * sd)
+
+
+def test_uniform_draws_equal_inverse_cdf_of_uniform_distributions():
+    """With uniform marginals p = 1/I the leverage sampler (inverse CDF, pinned above) and
+    the uniform sampler take the same uniforms to the same indices and weights."""
+    dims = (7, 300, 5, 2)
+    n, J = 3, 50000
+    ps = _uniform_ps(dims)
+    cdfs = [np.arange(1, d + 1) / d for d in dims]
+    idx_l, w_l = orc.draw_samples(ps, cdfs, n, J, seed=77, update_id=2 ** 33 + 1)
+    idx_u, w_u = orc.draw_samples_uniform(dims, n, J, seed=77, update_id=2 ** 33 + 1)
+    np.testing.assert_array_equal(idx_u, idx_l)
+    np.testing.assert_allclose(w_u, w_l, rtol=1e-15)
+
+
+def test_uniform_index_clamps_at_the_top():
+    """floor(u * I) is I - 1 for the largest representable u < 1 (no index I)."""
+    u = np.array([1.0 - 2.0 ** -53])
+    for I in (1, 3, 2 ** 31 - 1):
+        assert int(np.minimum(np.floor(u * I), I - 1.0)[0]) == I - 1
