@@ -5,12 +5,13 @@ scores + 10 sweeps of Alg. 2, J = 4000, mixed precision) with X resident in HBM.
 metric is sweeps/s = sweeps per step * steps / time. Besides it the JSON line carries the
 end-to-end number through the host-memory entry point, the roofline of the dominant
 kernel, the plain FP64 GPU form (the metric's comparator), the FP64 CPU oracle on a
-bounded sample, the 512-problem batched workload, and the serving leg: p50/p99
-decomposition latency of a Poisson stream of requests (200/s) through the native server.
+bounded sample, the same decomposition with uniform sampling (Sec. 5 variant), the
+512-problem batched workload, and the serving leg: p50/p99 decomposition latency of a
+Poisson stream of requests (200/s) through the native server.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--serve-seconds S] [--skip-cpu] [--skip-fp64] [--skip-batched]
-                  [--skip-configs] [--skip-serving]
+                  [--serve-seconds S] [--skip-cpu] [--skip-fp64] [--skip-uniform]
+                  [--skip-batched] [--skip-configs] [--skip-serving]
 
 With N > 1 (torchrun), every rank decomposes its own tensor (replicas, weak scaling).
 """
@@ -364,6 +365,36 @@ def run_batched(T, plain_fp64, dev, steps, warmup, stream):
                               "copies of this batch (results do not depend on them)"}}
 
 
+def run_uniform(T, X, ranks, J, sweeps, init_dev, dims, stream, reps):
+    """The same decomposition with uniform draws (no distributions formed), at J and 5 J
+    samples per update: sweeps/s and the final relative error of each."""
+    ctx = T.Context(torch.cuda.current_device())
+    T.tr_set_sampling(ctx, T.TR_SAMPLING_UNIFORM)
+    out = {}
+    for mult in (1, 5):
+        Ju = J * mult
+        cores = T.empty_cores(dims, ranks, device=X.device)
+
+        def call(i):
+            T.tr_als_sampled(ctx, X, ranks, Ju, sweeps, 500 + i, T.TR_PREC_MIXED, cores,
+                             init_cores=init_dev)
+
+        for i in range(3):
+            call(i)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for i in range(reps):
+            call(3 + i)
+        b.record(stream)
+        torch.cuda.synchronize()
+        sec = a.elapsed_time(b) / 1e3
+        out[f"J={Ju}"] = {"value": round(sweeps * reps / sec, 3), "unit": "sweeps/s",
+                          "final_rel_err": T.tr_rel_error(ctx, X, ranks, cores)}
+    ctx.close()
+    return out
+
+
 def _time_calls(fn, reps, stream):
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     fn()
@@ -697,6 +728,13 @@ def run_ours(args):
                 "speedup": round(value / world / (sweeps * reps / sec), 2),
                 "equal_fit": abs(fit - fp64_fit) <= 0.01 * fp64_fit}
 
+    # uniform sampling (Sec. 5 variant) on the same workload: at the same J and at 5 J (the
+    # paper needs several times more uniform samples for the same error)
+    uniform = None
+    if not args.skip_uniform and world == 1:
+        uniform = run_uniform(T, X, ranks, J, sweeps, init_dev, dims, stream,
+                              max(1, min(args.steps, 5)))
+
     batched = None
     if not args.skip_batched and world == 1:
         batched = run_batched(T, plain_fp64, dev, max(1, min(args.steps, 5)), 1, stream)
@@ -741,6 +779,7 @@ def run_ours(args):
             "kernels_ms": {k: [round(v[0], 4), v[1]] for k, v in
                            sorted(prof.items(), key=lambda kv: -kv[1][0])},
             "fp64_gpu_form": fp64,
+            "uniform_sampling": uniform,
             "batched_512": batched,
             "config1_fp64_100": config1,
             "config3_cosine_4way": config3,
@@ -766,6 +805,7 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-batched", action="store_true")
+    ap.add_argument("--skip-uniform", action="store_true")
     ap.add_argument("--skip-serving", action="store_true")
     ap.add_argument("--skip-configs", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=20.0)

@@ -56,6 +56,13 @@ typedef enum tr_dtype { TR_F32 = 0, TR_F64 = 1 } tr_dtype;
  *                iterative refinement against the FP32-accurate normal-equation residual. */
 typedef enum tr_precision { TR_PREC_FP64 = 0, TR_PREC_MIXED = 1 } tr_precision;
 
+/* How tr_als_sampled, tr_als_sampled_host and tr_als_sampled_batched draw their samples.
+ * TR_SAMPLING_LEVERAGE: Alg. 2 as stated -- products of the cores' leverage-score
+ *                       distributions (Alg. 3), each refreshed after its core's update.
+ * TR_SAMPLING_UNIFORM : the uniform variant of Sec. 5 (draws as tr_sample_uniform); no
+ *                       distribution is ever formed, so the leverage stages are skipped. */
+typedef enum tr_sampling { TR_SAMPLING_LEVERAGE = 0, TR_SAMPLING_UNIFORM = 1 } tr_sampling;
+
 typedef struct tr_ctx tr_ctx;
 typedef void* tr_stream;
 
@@ -101,6 +108,17 @@ tr_status tr_sample(tr_ctx* ctx, int N, int k, const int64_t* dims,
                     const double* const* p, const double* const* cdf, int64_t J,
                     uint64_t seed, uint64_t update_id, int32_t* idx, double* w,
                     tr_stream stream);
+
+/* Row a2, uniform variant -- J i.i.d. draws from the uniform distribution
+ * q^{!=k} = 1 / prod_{j!=k} I_j, the alternative to leverage-score sampling that Sec. 5
+ * evaluates (uniform sampling experiment); no distribution is read.
+ * seed, update_id : as for tr_sample: the same Philox uniform u per (sample, position).
+ * idx      : int32 [J][N-1] out (ring order); index = floor(u * I) in FP64, clamped to I-1.
+ * w        : FP64 [J] out, every entry sqrt(P / J), P = prod of the sampled modes' sizes
+ *            formed in FP64 in ring order (= 1 / sqrt(J q) of Def. 5). */
+tr_status tr_sample_uniform(tr_ctx* ctx, int N, int k, const int64_t* dims, int64_t J,
+                            uint64_t seed, uint64_t update_id, int32_t* idx, double* w,
+                            tr_stream stream);
 
 /* Row a3 -- sampled subchain S G_[2]^{!=k} (Alg. 4; Def. 3).
  * cores : host array of N device pointers (entry k unused), FP64 slice-major.
@@ -188,6 +206,11 @@ typedef struct tr_instance {
 tr_status tr_als_sampled_batched(tr_ctx* ctx, const tr_instance* inst, int count,
                                  tr_dtype X_dtype, int sweeps, tr_precision prec,
                                  tr_stream stream);
+
+/* Sampling of the context's driver calls (a context starts with TR_SAMPLING_LEVERAGE).
+ * Other values return TR_ERR_INVALID_ARG. */
+tr_status tr_set_sampling(tr_ctx* ctx, tr_sampling sampling);
+tr_status tr_get_sampling(const tr_ctx* ctx, tr_sampling* sampling);
 
 /* Launch shapes of the batched driver's kernels, chosen per batch geometry by the
  * project's autotuner (paper_2010_08581_gb300/autotune.py), which times the candidates on

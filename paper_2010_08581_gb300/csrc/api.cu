@@ -46,6 +46,7 @@ struct tr_ctx {
   std::vector<uint64_t> bkey;
   std::vector<trk::BInst> btab;     // host copy of the instance table
   tr_batched_tiles tiles{4, 64};    // launch shapes of the batched kernels
+  tr_sampling sampling = TR_SAMPLING_LEVERAGE;   // draws of tr_als_sampled / batched
 };
 
 namespace {
@@ -359,6 +360,10 @@ tr_status update_run(tr_ctx* ctx, char* ws, size_t solve_ws, const void* A, cons
   SolvePlan s;
   solve_plan(c, J, L, I, f64, &s);
   TR_TRY(solve_contract(ctx, s, A, Y, f64, J, L, I, st));
+  if (!p) {   // uniform sampling: the new core needs no distribution
+    TR_TRY(solve_cholesky(ctx, s, f64, L, st));
+    return solve_rhs(ctx, s, Rl, Rr, I, !f64, core_out, st);
+  }
   TR_CUDA(cudaEventRecord(ctx->ev_fork, st));
   TR_CUDA(cudaStreamWaitEvent(side, ctx->ev_fork, 0));
   TR_TRY(solve_cholesky(ctx, s, f64, L, st));
@@ -481,9 +486,11 @@ tr_status als_issue(tr_ctx* ctx, const AlsPlan& P, uint64_t seed, const uint64_t
                                                   static_cast<uint32_t>(k), seed_dev, st));
     }
   }
-  for (int k = 1; k < N; ++k)
-    TR_TRY(leverage_run(ctx, P.ws, P.cores[k], dims[k], rl_of(ranks, N, k), ranks[k], P.p[k],
-                        P.cdf[k], st));
+  const bool uni = ctx->sampling == TR_SAMPLING_UNIFORM;
+  if (!uni)
+    for (int k = 1; k < N; ++k)
+      TR_TRY(leverage_run(ctx, P.ws, P.cores[k], dims[k], rl_of(ranks, N, k), ranks[k], P.p[k],
+                          P.cdf[k], st));
   int64_t stride[kMaxModes];
   row_major_strides(N, dims, stride);
   const bool x64 = P.xdt == TR_F64;
@@ -494,6 +501,7 @@ tr_status als_issue(tr_ctx* ctx, const AlsPlan& P, uint64_t seed, const uint64_t
       GatherArgs ga{};
       sa.npos = ca.npos = ga.npos = N - 1;
       sa.seed_dev = seed_dev;
+      sa.uniform = uni ? 1 : 0;
       for (int m = 0; m < N - 1; ++m) {
         const int mode = (n + 1 + m) % N;
         sa.p[m] = P.p[mode];
@@ -512,7 +520,7 @@ tr_status als_issue(tr_ctx* ctx, const AlsPlan& P, uint64_t seed, const uint64_t
       TR_LAUNCH("gather", launch_gather(ga, P.X, x64, P.idx, P.w, P.J, P.Y, f64, ctx->d_err, st));
       const int Rl = rl_of(ranks, N, n), Rr = ranks[n];
       TR_TRY(update_run(ctx, P.ws, P.solve_ws, P.A, P.Y, f64, P.J, Rl, Rr, dims[n], P.cores[n],
-                        P.p[n], P.cdf[n], st, side));
+                        uni ? nullptr : P.p[n], uni ? nullptr : P.cdf[n], st, side));
     }
   }
   return TR_OK;
@@ -536,6 +544,7 @@ std::vector<uint64_t> als_key(const tr_ctx* ctx, const AlsPlan& P) {
   u(P.init ? 1 : 0);
   u(reinterpret_cast<uintptr_t>(ctx->arena));
   u(ctx->arena_bytes);
+  u(static_cast<uint64_t>(ctx->sampling));
   return k;
 }
 
@@ -599,8 +608,9 @@ tr_status fold_graph_marks(tr_ctx* ctx) {
 tr_status batched_issue(tr_ctx* ctx, const BLaunch& bl, int nmax_modes, int steps, bool draw,
                         cudaStream_t st) {
   if (draw) TR_CUDA(bl_init_cores(bl, st));
-  for (int k = 1; k < nmax_modes; ++k)
-    TR_CUDA(issue_leverage(bl, 0, k, ctx->d_err, st, nullptr));
+  if (bl.leverage)
+    for (int k = 1; k < nmax_modes; ++k)
+      TR_CUDA(issue_leverage(bl, 0, k, ctx->d_err, st, nullptr));
   const StepStreams ss{st, ctx->side, ctx->ev_fork, ctx->ev_info, ctx->ev_join};
   for (int step = 0; step < steps; ++step) TR_CUDA(issue_step(bl, step, ctx->d_err, ss));
   return TR_OK;
@@ -724,6 +734,39 @@ tr_status tr_sample(tr_ctx* ctx, int N, int k, const int64_t* dims, const double
   DeviceGuard g(ctx->device);
   cudaStream_t st = S(stream);
   TR_LAUNCH("sample", launch_sample(sa, J, seed, update_id, idx, w, st));
+  return TR_OK;
+}
+
+tr_status tr_sample_uniform(tr_ctx* ctx, int N, int k, const int64_t* dims, int64_t J,
+                            uint64_t seed, uint64_t update_id, int32_t* idx, double* w,
+                            tr_stream stream) {
+  TR_TRY(check_ctx(ctx));
+  TR_TRY(check_shape(ctx, N, dims, nullptr));
+  if (k < 0 || k >= N) return fail(ctx, TR_ERR_INVALID_ARG, "k=%d outside [0, N)", k);
+  if (J < 1 || J > INT32_MAX) return fail(ctx, TR_ERR_INVALID_ARG, "J=%lld", static_cast<long long>(J));
+  if (!idx || !w) return fail(ctx, TR_ERR_INVALID_ARG, "null pointer");
+  SampleArgs sa{};
+  sa.npos = N - 1;
+  sa.uniform = 1;
+  for (int m = 0; m < N - 1; ++m) sa.I[m] = dims[(k + 1 + m) % N];
+  DeviceGuard g(ctx->device);
+  cudaStream_t st = S(stream);
+  TR_LAUNCH("sample", launch_sample(sa, J, seed, update_id, idx, w, st));
+  return TR_OK;
+}
+
+tr_status tr_set_sampling(tr_ctx* ctx, tr_sampling sampling) {
+  TR_TRY(check_ctx(ctx));
+  if (sampling != TR_SAMPLING_LEVERAGE && sampling != TR_SAMPLING_UNIFORM)
+    return fail(ctx, TR_ERR_INVALID_ARG, "sampling=%d is not a tr_sampling value",
+                static_cast<int>(sampling));
+  ctx->sampling = sampling;
+  return TR_OK;
+}
+
+tr_status tr_get_sampling(const tr_ctx* ctx, tr_sampling* sampling) {
+  if (!ctx || !sampling) return TR_ERR_INVALID_ARG;
+  *sampling = ctx->sampling;
   return TR_OK;
 }
 
@@ -948,6 +991,7 @@ tr_status tr_als_sampled_batched(tr_ctx* ctx, const tr_instance* inst, int count
   bl.xf64 = X_dtype == TR_F64;
   bl.spw = ctx->tiles.samples_per_warp;
   bl.ctile = ctx->tiles.contract_tile;
+  bl.leverage = ctx->sampling == TR_SAMPLING_LEVERAGE;
   int nmax_modes = 0, steps = 0;
   bool draw = false;
   for (int i = 0; i < count; ++i) {
@@ -960,6 +1004,7 @@ tr_status tr_als_sampled_batched(tr_ctx* ctx, const tr_instance* inst, int count
     d.xf64 = X_dtype == TR_F64;
     d.nupd = sweeps * in.N;
     d.draw_init = in.init_given ? 0 : 1;
+    d.uniform = bl.leverage ? 0 : 1;
     d.J = in.J;
     d.seed = in.seed;
     row_major_strides(in.N, in.dims, d.stride);
@@ -993,7 +1038,8 @@ tr_status tr_als_sampled_batched(tr_ctx* ctx, const tr_instance* inst, int count
                                  static_cast<uint64_t>(nmax_modes), static_cast<uint64_t>(steps),
                                  static_cast<uint64_t>(draw), reinterpret_cast<uintptr_t>(dtab),
                                  static_cast<uint64_t>(ctx->prof),
-                                 static_cast<uint64_t>(bl.spw), static_cast<uint64_t>(bl.ctile)};
+                                 static_cast<uint64_t>(bl.spw), static_cast<uint64_t>(bl.ctile),
+                                 static_cast<uint64_t>(bl.leverage)};
     if (!ctx->bexec || key != ctx->bkey) {
       if (ctx->bexec) cudaGraphExecDestroy(ctx->bexec);
       ctx->bexec = nullptr;

@@ -22,6 +22,7 @@ struct Cur {
 
 __device__ __forceinline__ Cur current(const BInst& d, int step, int init_k, bool lev) {
   Cur c{};
+  if (lev && d.uniform) return c;   // uniform sampling forms no distributions
   int k = 0, t = step;
   if (d.slot) {
     const SlotState& s = *d.slot;
@@ -116,6 +117,7 @@ __global__ void __launch_bounds__(SW * 32) kb_sample(const BInst* __restrict__ t
   T* Y = static_cast<T*>(d.Y);
   const int L = cu.L;
   const int64_t I = cu.I, sn = d.stride[n];
+  const double wuni = d.uniform ? uniform_weight(d.J, ca.I, npos) : 0.0;
   for (int s = 0; s < spw; ++s) {
     const int64_t j = j0 + warp * spw + s;
     if (j >= d.J) break;
@@ -124,13 +126,20 @@ __global__ void __launch_bounds__(SW * 32) kb_sample(const BInst* __restrict__ t
     int64_t off = 0;
     if (lane < npos) {
       const double u = draw_uniform(j, lane, k0, k1, u0, u1);
-      mine = inverse_cdf(d.cdf[mode_l], d.p[mode_l], d.dims[mode_l], u);
-      pmine = d.p[mode_l][mine];
+      if (d.uniform) {
+        mine = uniform_index(d.dims[mode_l], u);
+      } else {
+        mine = inverse_cdf(d.cdf[mode_l], d.p[mode_l], d.dims[mode_l], u);
+        pmine = d.p[mode_l][mine];
+      }
       off = mine * d.stride[mode_l];
     }
-    double pm[kMaxModes];
-    for (int m = 0; m < npos; ++m) pm[m] = __shfl_sync(0xffffffffu, pmine, m);
-    const double wj = sample_weight(d.J, pm, npos);
+    double wj = wuni;
+    if (!d.uniform) {
+      double pm[kMaxModes];
+      for (int m = 0; m < npos; ++m) pm[m] = __shfl_sync(0xffffffffu, pmine, m);
+      wj = sample_weight(d.J, pm, npos);
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) off += __shfl_xor_sync(0xffffffffu, off, o);
     auto index = [&](int m) -> int64_t {

@@ -51,6 +51,7 @@ struct BInst {
   int xf64;
   int nupd;                      // updates to perform (sweeps * N); 0 = inactive slot
   int draw_init;                 // draw cores 1..N-1 i.i.d. N(0,1) from seed before step 0
+  int uniform;                   // uniform sampling (Sec. 5): no distributions, p/cdf unused
   int64_t J;
   uint64_t seed;
   int64_t dims[kMaxModes];
@@ -94,6 +95,8 @@ struct BLaunch {
   // launch shapes (tr_batched_tiles): neither changes any result
   int spw = 4;                   // samples per warp of the sampling kernel, 1..8
   int ctile = 64;                // output tile of the normal-equation contraction, 64 or 32
+  bool leverage = true;          // some instance samples by leverage scores (else the
+                                 // distribution stages are not launched at all)
 };
 
 cudaError_t bl_init_cores(const BLaunch& b, cudaStream_t st);

@@ -53,6 +53,7 @@ struct SampleArgs {
   int64_t I[kMaxModes];
   int npos;                      // N - 1
   const uint64_t* seed_dev;      // if non-null, the Philox key is read from here
+  int uniform;                   // uniform sampling (Sec. 5): p and cdf unused
 };
 cudaError_t launch_sample(const SampleArgs& a, int64_t J, uint64_t seed, uint64_t update_id,
                           int32_t* idx, double* w, cudaStream_t st);

@@ -47,6 +47,22 @@ __device__ __forceinline__ int64_t inverse_cdf(const double* cdf, const double* 
   return lo;
 }
 
+// Uniform sampling (the Sec. 5 alternative to leverage scores): index floor(u * I) of a
+// uniform draw on {0, ..., I-1}, clamped to I-1 should the product round up to I.
+__device__ __forceinline__ int64_t uniform_index(int64_t I, double u) {
+  const double x = floor(__dmul_rn(u, static_cast<double>(I)));
+  const int64_t i = static_cast<int64_t>(x);
+  return i < I ? i : I - 1;
+}
+
+// Weight of every uniform sample, 1 / sqrt(J q) with q = 1 / P: sqrt(P / J), P the product
+// of the sampled modes' sizes taken in ring order.
+__device__ __forceinline__ double uniform_weight(int64_t J, const int64_t* I, int npos) {
+  double P = 1.0;
+  for (int m = 0; m < npos; ++m) P = __dmul_rn(P, static_cast<double>(I[m]));
+  return sqrt(P / static_cast<double>(J));
+}
+
 // w = 1 / sqrt(J * prod_m p_m) with the product taken in ring order m = 0, 1, ...
 __device__ __forceinline__ double sample_weight(int64_t J, const double* pm, int npos) {
   double q = 1.0;

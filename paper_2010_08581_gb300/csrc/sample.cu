@@ -1,6 +1,7 @@
 // Row a2: J i.i.d. draws from q^{!=n} = prod_{j != n} p^(j) (Alg. 3) by inverse CDF, and
-// the Def. 5 rescaling w_j = 1 / sqrt(J q(i_j)); and the fused draw + sampled-subchain
-// kernel used by the driver (rows a2 + a3: Alg. 3 then Alg. 4 for the same samples).
+// the Def. 5 rescaling w_j = 1 / sqrt(J q(i_j)), or from the uniform distribution (the
+// Sec. 5 variant, no distributions read); and the fused draw + sampled-subchain kernel used
+// by the driver (rows a2 + a3: Alg. 3 then Alg. 4 for the same samples).
 #include "draw.cuh"
 
 namespace trk {
@@ -17,6 +18,14 @@ __global__ void __launch_bounds__(256) k_sample(SampleArgs a, int64_t J, uint32_
     const uint64_t s = *a.seed_dev;
     key0 = static_cast<uint32_t>(s);
     key1 = static_cast<uint32_t>(s >> 32);
+  }
+  if (a.uniform) {
+    for (int m = 0; m < a.npos; ++m) {
+      const double u = draw_uniform(j, m, key0, key1, uid_lo, uid_hi);
+      idx[j * a.npos + m] = static_cast<int32_t>(uniform_index(a.I[m], u));
+    }
+    w[j] = uniform_weight(J, a.I, a.npos);
+    return;
   }
   double pm[kMaxModes];
   for (int m = 0; m < a.npos; ++m) {
@@ -52,7 +61,7 @@ __global__ void __launch_bounds__(FW * 32) k_sample_chain(SampleArgs sa, ChainAr
   }
   const double* pp[kMaxModes];
   const double* cp[kMaxModes];
-  {
+  if (!sa.uniform) {
     int64_t off = 0;
     for (int m = 0; m < sa.npos; ++m) {
       if (staged) {
@@ -75,6 +84,7 @@ __global__ void __launch_bounds__(FW * 32) k_sample_chain(SampleArgs sa, ChainAr
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int npos = sa.npos;
   const int Lout = ca.rl[0] * ca.rr[npos - 1];
+  const double wuni = sa.uniform ? uniform_weight(J, sa.I, npos) : 0.0;
   for (int s = 0; s < FSPW; ++s) {
     const int64_t j = (static_cast<int64_t>(blockIdx.x) * FW + warp) * FSPW + s;
     if (j >= J) break;
@@ -82,13 +92,20 @@ __global__ void __launch_bounds__(FW * 32) k_sample_chain(SampleArgs sa, ChainAr
     double pmine = 1.0;
     if (lane < npos) {
       const double u = draw_uniform(j, lane, key0, key1, uid_lo, uid_hi);
-      mine = inverse_cdf(cp[lane], pp[lane], sa.I[lane], u);
-      pmine = pp[lane][mine];
+      if (sa.uniform) {
+        mine = uniform_index(sa.I[lane], u);
+      } else {
+        mine = inverse_cdf(cp[lane], pp[lane], sa.I[lane], u);
+        pmine = pp[lane][mine];
+      }
       idx[j * npos + lane] = static_cast<int32_t>(mine);
     }
-    double pm[kMaxModes];
-    for (int m = 0; m < npos; ++m) pm[m] = __shfl_sync(0xffffffffu, pmine, m);
-    const double wj = sample_weight(J, pm, npos);
+    double wj = wuni;
+    if (!sa.uniform) {
+      double pm[kMaxModes];
+      for (int m = 0; m < npos; ++m) pm[m] = __shfl_sync(0xffffffffu, pmine, m);
+      wj = sample_weight(J, pm, npos);
+    }
     if (lane == 0) w[j] = wj;
     auto index = [&](int m) -> int64_t {
       return static_cast<int64_t>(__shfl_sync(0xffffffffu, static_cast<int>(mine), m));
@@ -118,7 +135,8 @@ cudaError_t launch_sample_chain(const SampleArgs& sa, const ChainArgs& ca, int64
                                 void* A, bool f64, cudaStream_t st) {
   if (J <= 0) return cudaSuccess;
   int64_t need = 0;
-  for (int m = 0; m < sa.npos; ++m) need += 2 * sa.I[m] * static_cast<int64_t>(sizeof(double));
+  if (!sa.uniform)
+    for (int m = 0; m < sa.npos; ++m) need += 2 * sa.I[m] * static_cast<int64_t>(sizeof(double));
   const int staged = need <= kStageBytes ? 1 : 0;
   const size_t dyn = staged ? static_cast<size_t>(need) : 0;
   const int64_t per = FW * FSPW;

@@ -21,6 +21,7 @@ TR_OK, TR_ERR_INVALID_ARG, TR_ERR_OOM, TR_ERR_BUDGET, TR_ERR_SINGULAR, TR_ERR_TI
     TR_ERR_CUDA, TR_ERR_NOT_CONVERGED = range(8)
 TR_F32, TR_F64 = 0, 1
 TR_PREC_FP64, TR_PREC_MIXED = 0, 1
+TR_SAMPLING_LEVERAGE, TR_SAMPLING_UNIFORM = 0, 1
 
 _STATUS_NAMES = ["TR_OK", "TR_ERR_INVALID_ARG", "TR_ERR_OOM", "TR_ERR_BUDGET",
                  "TR_ERR_SINGULAR", "TR_ERR_TIMEOUT", "TR_ERR_CUDA", "TR_ERR_NOT_CONVERGED"]
@@ -92,6 +93,8 @@ SIGNATURES = {
     "tr_leverage": (c_int, [c_vp, c_vp, c_i64, c_int, c_int, c_vp, c_vp, c_vp]),
     "tr_sample": (c_int, [c_vp, c_int, c_int, P64, PP, PP, c_i64, c_u64, c_u64, c_vp, c_vp,
                           c_vp]),
+    "tr_sample_uniform": (c_int, [c_vp, c_int, c_int, P64, c_i64, c_u64, c_u64, c_vp, c_vp,
+                                  c_vp]),
     "tr_subchain": (c_int, [c_vp, c_int, c_int, P64, PI, PP, c_vp, c_vp, c_i64, c_vp, c_int,
                             c_vp]),
     "tr_gather": (c_int, [c_vp, c_vp, c_int, c_int, P64, c_int, c_vp, c_vp, c_i64, c_vp, c_int,
@@ -109,6 +112,8 @@ SIGNATURES = {
                                        c_int, c_vp]),
     "tr_solve_noalloc": (c_int, [c_vp, c_vp, c_int, c_i64, c_int, c_int, c_i64, c_int, c_vp,
                                  c_vp, c_vp]),
+    "tr_set_sampling": (c_int, [c_vp, c_int]),
+    "tr_get_sampling": (c_int, [c_vp, PI]),
     "tr_set_batched_tiles": (c_int, [c_vp, ctypes.POINTER(TrBatchedTiles)]),
     "tr_get_batched_tiles": (c_int, [c_vp, ctypes.POINTER(TrBatchedTiles)]),
     "tr_server_create": (c_int, [ctypes.POINTER(TrServerConfig), ctypes.POINTER(c_vp)]),
@@ -238,6 +243,26 @@ def tr_sample(ctx: Context, k: int, dims, ps: List[torch.Tensor], cdfs: List[tor
     cp, _c = _ptrs(cdfs)
     ctx.check(load().tr_sample(ctx.handle, N, k, d, pp, cp, J, seed, update_id, _ptr(idx),
                                _ptr(w), _stream(stream)))
+
+
+def tr_sample_uniform(ctx: Context, k: int, dims, J: int, seed: int, update_id: int,
+                      idx: torch.Tensor, w: torch.Tensor, stream=None):
+    """Uniform draws (Sec. 5 variant): idx int32 (J, N-1) ring order, w float64 (J,)."""
+    N = len(dims)
+    d, _d = _i64s(dims)
+    ctx.check(load().tr_sample_uniform(ctx.handle, N, k, d, J, seed, update_id, _ptr(idx),
+                                       _ptr(w), _stream(stream)))
+
+
+def tr_set_sampling(ctx: Context, sampling: int):
+    """TR_SAMPLING_LEVERAGE or TR_SAMPLING_UNIFORM for the context's driver calls."""
+    ctx.check(load().tr_set_sampling(ctx.handle, int(sampling)))
+
+
+def tr_get_sampling(ctx: Context) -> int:
+    v = c_int()
+    ctx.check(load().tr_get_sampling(ctx.handle, ctypes.byref(v)))
+    return int(v.value)
 
 
 def tr_subchain(ctx: Context, k: int, dims, ranks, cores: List[torch.Tensor], idx: torch.Tensor,
