@@ -49,11 +49,14 @@ typedef enum tr_status {
 
 typedef enum tr_dtype { TR_F32 = 0, TR_F64 = 1 } tr_dtype;
 
-/* Arithmetic of the least-squares step (rows a3-a6).
+/* Arithmetic of the least-squares step (rows a3-a6); the sampling distributions (row a1)
+ * are FP64 under both.
  * TR_PREC_FP64 : design rows, fibres, contractions, Cholesky and solves in FP64.
- * TR_PREC_MIXED: design rows and fibres in FP32, contractions with FP32 accumulation,
- *                FP64 Cholesky of the normal matrix, FP64 solve and one step of
- *                iterative refinement against the FP32-accurate normal-equation residual. */
+ * TR_PREC_MIXED: design rows and fibres in FP32, contractions with FP32 accumulation.
+ *                The normal matrix is factored in FP32 when every pivot exceeds
+ *                L*eps32*max diag, else in FP64 (same singular rule as TR_PREC_FP64);
+ *                FP32 triangular solves and one step of iterative refinement against the
+ *                FP32-accurate normal-equation residual. */
 typedef enum tr_precision { TR_PREC_FP64 = 0, TR_PREC_MIXED = 1 } tr_precision;
 
 /* How tr_als_sampled, tr_als_sampled_host and tr_als_sampled_batched draw their samples.
@@ -138,8 +141,9 @@ tr_status tr_gather(tr_ctx* ctx, const void* X, tr_dtype X_dtype, int N,
                     int64_t J, void* Y, tr_dtype Y_dtype, tr_stream stream);
 
 /* Rows a5 + a6 -- solve the sampled LS argmin_Z || A Z - Y ||_F (Alg. 2, LS step) through
- * the normal equations M = A^T A, B = A^T Y, FP64 Cholesky M = L L^T, Z = M^-1 B (and, in
- * TR_PREC_MIXED, one refinement Z += M^-1 (B - M Z)), then write the new core
+ * the normal equations M = A^T A, B = A^T Y, Cholesky M = L L^T (FP64, or FP32 as
+ * tr_precision describes), Z = M^-1 B (and, in TR_PREC_MIXED, one refinement
+ * Z += M^-1 (B - M Z)), then write the new core
  * core_out[i][a][b] = Z[a + Rl*b][i].
  * A : [J][Rl*Rr], Y : [J][I], both in `dtype` (TR_F32 for TR_PREC_MIXED, TR_F64 for
  * TR_PREC_FP64). A pivot <= L*eps*max diag(M) records TR_ERR_SINGULAR and leaves

@@ -314,11 +314,19 @@ tr_status solve_contract(tr_ctx* ctx, const SolvePlan& s, const void* A, const v
 
 tr_status solve_cholesky(tr_ctx* ctx, const SolvePlan& s, bool f64, int L, cudaStream_t st) {
   const double eps = 2.220446049250313e-16;
+  if (!f64) {
+    const double eps32 = 1.1920928955078125e-07;
+    TR_LAUNCH("cholesky_solve",
+              launch_cholesky_mixed(s.M, L, static_cast<double>(L) * eps,
+                                    static_cast<double>(L) * eps32, s.Lrow, s.Lcol, s.invdiag,
+                                    s.keep, s.info, ctx->d_err, st, static_cast<float*>(s.limg),
+                                    s.mimg));
+    return TR_OK;
+  }
   TR_LAUNCH("cholesky_solve",
             launch_cholesky(s.M, L, 0, static_cast<double>(L) * eps, s.Lrow, s.Lcol, s.invdiag,
-                            s.keep, s.info, ctx->d_err, st,
-                            f64 ? static_cast<double*>(s.limg) : nullptr,
-                            f64 ? nullptr : static_cast<float*>(s.limg), s.mimg));
+                            s.keep, s.info, ctx->d_err, st, static_cast<double*>(s.limg),
+                            nullptr, nullptr));
   return TR_OK;
 }
 

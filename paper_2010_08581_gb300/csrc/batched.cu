@@ -312,20 +312,30 @@ __global__ void __launch_bounds__(CNT) kb_cholesky(const BInst* __restrict__ tab
   const BInst& d = tab[blockIdx.x];
   const Cur cu = current(d, step, init_k, which != 0);
   if (!cu.active) return;
-  const double eps = 2.220446049250313e-16;
+  const double eps = 2.220446049250313e-16, eps32 = 1.1920928955078125e-07;
   const bool tall = cu.I >= cu.L;
   if (which == 0) {
     const int n = cu.L;
-    double* A = (static_cast<int64_t>(n) * n * 8 <= smem_bytes) ? smem : d.Lrow;
+    const int64_t nn = static_cast<int64_t>(n) * n;
+    double* A = (nn * 8 <= smem_bytes) ? smem : d.Lrow;
+    if (mixed) {
+      float* A32 = (nn * 4 <= smem_bytes) ? reinterpret_cast<float*>(smem)
+                                          : reinterpret_cast<float*>(d.Lrow);
+      cholesky_cta_mixed<float>(d.M, n, 0, static_cast<double>(n) * eps,
+                                static_cast<double>(n) * eps32, A32, A, d.Lrow, d.Lcol,
+                                d.invdiag, d.keep, d.info, err, static_cast<float*>(d.limg),
+                                d.mimg);
+      return;
+    }
     cholesky_cta(d.M, n, 0, static_cast<double>(n) * eps, A, d.Lrow, d.Lcol, d.invdiag, d.keep,
-                 d.info, err, mixed ? nullptr : static_cast<double*>(d.limg),
-                 mixed ? static_cast<float*>(d.limg) : nullptr, mixed ? d.mimg : nullptr);
+                 d.info, err, static_cast<double*>(d.limg), nullptr, nullptr);
     return;
   }
   const double tol = static_cast<double>(cu.I > cu.L ? cu.I : cu.L) * eps;
   if (which == 1) {
     const int n = tall ? cu.L : static_cast<int>(cu.I);
-    double* A = (static_cast<int64_t>(n) * n * 8 <= smem_bytes) ? smem : d.L1row;
+    const int64_t nn = static_cast<int64_t>(n) * n;
+    double* A = (nn * 8 <= smem_bytes) ? smem : d.L1row;
     cholesky_cta(d.G1, n, 1, tol, A, d.L1row, d.L1col, d.inv1, d.keep1, d.info1, err, d.img1,
                  nullptr, nullptr);
     return;

@@ -1,4 +1,5 @@
-// Single-problem launch of the one-CTA FP64 Cholesky factorisation (cholesky_body.cuh).
+// Single-problem launches of the one-CTA Cholesky factorisation (cholesky_body.cuh): FP64,
+// and the mixed-precision LS step's FP32-then-FP64 form.
 #include <cstdlib>
 
 #include "cholesky_body.cuh"
@@ -18,7 +19,34 @@ __global__ void __launch_bounds__(CNT) k_cholesky(const double* __restrict__ G, 
                info, err, img64, img32, gimg32);
 }
 
+// The mixed-precision LS step: FP32 factorisation, FP64 when an FP32 pivot is too small.
+template <typename TI>
+__global__ void __launch_bounds__(CNT) k_cholesky_mixed(const double* __restrict__ G, int n,
+                                                        int mode, double tol64, double tol32,
+                                                        double* Lrow, double* Lcol,
+                                                        double* invdiag, int* keep_out,
+                                                        int* info, unsigned* err, int dyn_bytes,
+                                                        TI* img, float* gimg32) {
+  extern __shared__ double smem[];
+  const int64_t nn = static_cast<int64_t>(n) * n;
+  float* A32 = nn * 4 <= dyn_bytes ? reinterpret_cast<float*>(smem) : reinterpret_cast<float*>(Lrow);
+  double* A64 = nn * 8 <= dyn_bytes ? smem : Lrow;
+  cholesky_cta_mixed<TI>(G, n, mode, tol64, tol32, A32, A64, Lrow, Lcol, invdiag, keep_out, info,
+                         err, img, gimg32);
+}
+
 }  // namespace
+
+cudaError_t launch_cholesky_mixed(const double* G, int n, double tol64, double tol32,
+                                  double* Lrow, double* Lcol, double* invdiag, int* keep,
+                                  int* info, unsigned* err, cudaStream_t st, float* img32,
+                                  float* gimg32) {
+  const size_t nn = static_cast<size_t>(n) * n;
+  const size_t dyn = nn * 8 <= kCholDyn ? nn * 8 : (nn * 4 <= kCholDyn ? nn * 4 : 0);
+  k_cholesky_mixed<float><<<1, CNT, dyn, st>>>(G, n, 0, tol64, tol32, Lrow, Lcol, invdiag, keep,
+                                               info, err, static_cast<int>(dyn), img32, gimg32);
+  return cudaGetLastError();
+}
 
 bool cholesky_cluster_fits(int n);
 cudaError_t launch_cholesky_cluster(const double* G, int n, int mode, double tol_scale,
@@ -54,8 +82,11 @@ cudaError_t launch_cholesky(const double* G, int n, int mode, double tol_scale, 
 cudaError_t cholesky_cluster_attributes();
 
 cudaError_t cholesky_attributes() {
-  const cudaError_t e =
+  cudaError_t e =
       cudaFuncSetAttribute(k_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize, kCholDyn);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_cholesky_mixed<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           kCholDyn);
   if (e != cudaSuccess) return e;
   return cholesky_cluster_attributes();
 }

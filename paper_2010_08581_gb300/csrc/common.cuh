@@ -119,6 +119,13 @@ cudaError_t launch_reduce(const void* partial, bool partial_f32, int splits, int
 // 0 for dropped columns), keep[n], *info (0 = success); optionally the padded images read
 // by launch_trsm: img64/img32[c*(n+1) + r] = L[r][c] and gimg32[c*(n+1) + r] = G[r][c]
 // (buffers of trsm_image_bytes(n, ...) bytes).
+// Mixed-precision LS step: an FP32 factor when every pivot > tol32 * max diag, written as the
+// FP32 image img32 + invdiag + keep + info; otherwise the FP64 factorisation with tol64
+// (as launch_cholesky, mode 0).
+cudaError_t launch_cholesky_mixed(const double* G, int n, double tol64, double tol32,
+                                  double* Lrow, double* Lcol, double* invdiag, int* keep,
+                                  int* info, unsigned* err, cudaStream_t st, float* img32,
+                                  float* gimg32);
 cudaError_t launch_cholesky(const double* G, int n, int mode, double tol_scale, double* Lrow,
                             double* Lcol, double* invdiag, int* keep, int* info,
                             unsigned* err, cudaStream_t st, double* img64 = nullptr,

@@ -223,6 +223,42 @@ def test_solve_mixed(ctx, J, Rl, Rr, I):
     assert rel(to_paper(out), ref) < 1e-4
 
 
+def test_solve_mixed_column_scaled_takes_the_fp64_factor(ctx):
+    """Columns scaled down to 10^-3.5: the FP32 factorisation of the mixed LS step meets a
+    pivot below n*eps32*max diag, so the step factors in FP64 instead (an FP32-only step
+    would report the matrix singular). Cholesky's accuracy depends on the column-equilibrated
+    matrix, so the result still matches the oracle."""
+    J, Rl, Rr, I = 2000, 4, 4, 60
+    rng = np.random.default_rng(77)
+    L = Rl * Rr
+    scale = 10.0 ** (-3.5 * np.arange(L) / (L - 1))
+    A = (rng.standard_normal((J, L)) * scale).astype(np.float32)
+    Y = (A.astype(np.float64) @ rng.standard_normal((L, I)) +
+         0.05 * rng.standard_normal((J, I))).astype(np.float32)
+    Z = orc.sampled_ls_normal(A.astype(np.float64), Y.astype(np.float64))
+    M = A.astype(np.float64).T @ A.astype(np.float64)
+    piv = np.diag(np.linalg.cholesky(M)) ** 2
+    assert piv.min() < L * 2.0 ** -23 * np.diag(M).max()      # the FP32 branch must stop
+    ref = orc.core_from_solution(Z, Rl, Rr)
+    out = torch.empty((I, Rl, Rr), dtype=torch.float64, device=DEV)
+    T.tr_solve(ctx, torch.from_numpy(A).to(DEV), torch.from_numpy(Y).to(DEV), Rl, Rr,
+               T.TR_PREC_MIXED, out)
+    T.tr_status_sync(ctx)
+    assert rel(to_paper(out), ref) < 1e-4
+
+
+def test_solve_mixed_singular_leaves_core_unchanged(ctx):
+    J, Rl, Rr, I = 5, 4, 4, 9                 # J < L: the normal matrix is singular
+    A = torch.randn((J, Rl * Rr), dtype=torch.float32, device=DEV)
+    Y = torch.randn((J, I), dtype=torch.float32, device=DEV)
+    out = torch.full((I, Rl, Rr), 3.0, dtype=torch.float64, device=DEV)
+    T.tr_solve(ctx, A, Y, Rl, Rr, T.TR_PREC_MIXED, out)
+    with pytest.raises(T.TrError) as e:
+        T.tr_status_sync(ctx)
+    assert e.value.status == T.TR_ERR_SINGULAR
+    assert torch.all(out == 3.0)
+
+
 def test_solve_singular_leaves_core_unchanged(ctx):
     J, Rl, Rr, I = 5, 4, 4, 9                 # J < L: the normal matrix is singular
     A = torch.randn((J, Rl * Rr), dtype=torch.float64, device=DEV)
