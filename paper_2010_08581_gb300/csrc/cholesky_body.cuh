@@ -167,167 +167,143 @@ __device__ __forceinline__ bool cholesky_cta(const double* __restrict__ G, int n
   return true;
 }
 
-// FP32 factorisation of the mixed LS step for n <= kTileCholMax, with the trailing matrix
-// in registers. Warps 1.. own 4 x 4 tiles of the lower triangle (TPT tiles a thread, tile
-// rows and columns 4b..4b+3): at step k they load the 4 + 4 entries of column k they need and
-// apply 16 predicated FMAs; an entry of column k+2 is then final but for column k+1's update,
-// which warp 0 applies, so it is stored to the column-major buffer Acol. Warp 0 holds column
-// k in registers (lane l: rows l + 32q), forms column k+1 from Acol, takes its pivot and
-// publishes it to the double-buffered colbuf and to the image img (FP32 or FP64). One
-// barrier per column. Every entry receives the same fmaf updates in the same order as in
-// the generic FP32 form. Returns false (no factor written) when a pivot is <= tol_scale *
-// max diag.
-constexpr int kTileCholMax = 160;
+// FP32 factorisation of the mixed LS step for n <= kPanelCholMax: blocked right-looking with
+// panels of kPB columns. Warp 0 factors a panel in registers (lane l holds rows c0 + l + 32q
+// of the panel's columns): per column one shuffle for the pivot, one rsqrt, a scaling and
+// kPB-1 shuffles for the later panel columns, with no barrier. Then every thread applies the
+// panel's rank-kPB update to 4 x 4 tiles of the trailing lower triangle, reading the panel
+// columns as 16-byte vectors from the column-major work array A (leading dimension lda, a
+// multiple of 4; lda * n floats, which fit wherever n * n doubles do for n >= 4). Two barriers
+// per panel. Returns false (no factor written) when a pivot is <= tol_scale * max diag.
+constexpr int kPanelCholMax = 160;
+constexpr int kPB = 8;
 
-template <int TPT, typename TI>
-__device__ __forceinline__ bool cholesky_f32_tiles(const double* __restrict__ G, int n,
-                                                   double tol_scale, float* Acol,
-                                                   double* invdiag, int* keep_out, int* info,
-                                                   TI* img, float* gimg32) {
-  constexpr int QN = (kTileCholMax + 31) / 32;
-  __shared__ float colbuf[2][kTileCholMax];
-  __shared__ float s_ldiag[kTileCholMax];
+__host__ __device__ inline int panel_lda(int n) { return (n + 3) & ~3; }
+
+template <typename TI>
+__device__ __forceinline__ bool cholesky_f32_panel(const double* __restrict__ G, int n,
+                                                   double tol_scale, float* A, double* invdiag,
+                                                   int* keep_out, int* info, TI* img,
+                                                   float* gimg32) {
+  constexpr int QP = (kPanelCholMax + 31) / 32;
+  __shared__ float s_ldiag[kPanelCholMax];
   __shared__ float s_tol;
   __shared__ int s_stop;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int np = n + 1;
-  const int nb = (n + 3) >> 2;
-  const int ntiles = nb * (nb + 1) / 2;
-  // owner tiles and their entries
-  float a[TPT][4][4];
-  int ti[TPT], tj[TPT];
-  if (warp > 0) {
-#pragma unroll
-    for (int u = 0; u < TPT; ++u) {
-      const int t = (tid - 32) + (CNT - 32) * u;
-      int bi = -1, bj = 0;
-      if (t < ntiles) {
-        bi = static_cast<int>((sqrtf(8.0f * static_cast<float>(t) + 1.0f) - 1.0f) * 0.5f);
-        while (bi * (bi + 1) / 2 > t) --bi;
-        while ((bi + 1) * (bi + 2) / 2 <= t) ++bi;
-        bj = t - bi * (bi + 1) / 2;
-      }
-      ti[u] = bi * 4;
-      tj[u] = bj * 4;
-#pragma unroll
-      for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const int i = ti[u] + r, j = tj[u] + c;
-          a[u][r][c] = (bi >= 0 && i < n && j <= i)
-                           ? static_cast<float>(G[static_cast<int64_t>(j) * n + i]) : 0.0f;
-        }
-    }
-  }
-  if (gimg32)
-    for (int e = tid; e < n * n; e += CNT) {
-      const int i = e / n, j = e - (e / n) * n;
-      if (j <= i) {
-        const float g = static_cast<float>(G[static_cast<int64_t>(j) * n + i]);
+  const int np = n + 1, lda = panel_lda(n);
+  for (int e = tid; e < n * n; e += CNT) {
+    const int j = e / n, i = e - (e / n) * n;          // column-major walk of G
+    if (i >= j) {
+      const float g = static_cast<float>(G[e]);      // G symmetric: G[j*n + i] = (i, j)
+      A[j * lda + i] = g;
+      if (gimg32) {
         gimg32[j * np + i] = g;
         gimg32[i * np + j] = g;
       }
     }
-  // warp 0: column 0 (final after scaling) and column 1 (raw), max diagonal
-  float colv[QN];
+  }
   if (warp == 0) {
     float md = 0.0f;
-    for (int i = lane; i < n; i += 32)
-      md = fmaxf(md, static_cast<float>(G[static_cast<int64_t>(i) * n + i]));
+    for (int i = lane; i < n; i += 32) md = fmaxf(md, static_cast<float>(G[static_cast<int64_t>(i) * n + i]));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) md = fmaxf(md, __shfl_xor_sync(0xffffffffu, md, o));
-    const float tol = static_cast<float>(tol_scale) * md;
-    const float d = static_cast<float>(G[0]);
-    const bool ok = d > tol;
-    const float inv = ok ? rsqrtf(d) : 0.0f;
-#pragma unroll
-    for (int q = 0; q < QN; ++q) {
-      const int i = lane + 32 * q;
-      float v = 0.0f;
-      if (i < n) {
-        v = (i == 0) ? d * inv : static_cast<float>(G[i]) * inv;   // G[0][i] = G[i][0]
-        colbuf[0][i] = v;
-        if (n > 1) Acol[n + i] = (i >= 1) ? static_cast<float>(G[n + i]) : 0.0f;
-      }
-      colv[q] = v;
-    }
     if (lane == 0) {
-      s_tol = tol;
-      s_stop = ok ? 0 : 1;
-      s_ldiag[0] = colv[0];
-    }
-#pragma unroll
-    for (int q = 0; q < QN; ++q) {
-      const int i = lane + 32 * q;
-      if (i < n) img[i] = static_cast<TI>(colv[q]);              // column 0 of the image
+      s_tol = static_cast<float>(tol_scale) * md;
+      s_stop = 0;
     }
   }
   __syncthreads();
-  for (int k = 0; k < n; ++k) {
-    if (s_stop) break;
-    const float* cur = colbuf[k & 1];
+  for (int c0 = 0; c0 < n; c0 += kPB) {
+    const int w = (n - c0 < kPB) ? n - c0 : kPB;
     if (warp == 0) {
-      if (k + 1 < n) {
-        const float lk1 = cur[k + 1];
-        float av[QN];
+      float p[QP][kPB];
 #pragma unroll
-        for (int q = 0; q < QN; ++q) {
-          const int i = lane + 32 * q;
-          av[q] = (i >= k + 1 && i < n) ? fmaf(-colv[q], lk1, Acol[(k + 1) * n + i]) : 0.0f;
-        }
-        // the pivot row k+1 sits in lane (k+1)%32, slot (k+1)/32
-        const int pl = (k + 1) & 31, pq = (k + 1) >> 5;
-        float dsel = av[0];
+      for (int q = 0; q < QP; ++q) {
+        const int i = c0 + lane + 32 * q;
 #pragma unroll
-        for (int q = 1; q < QN; ++q) dsel = (q == pq) ? av[q] : dsel;
-        const float d = __shfl_sync(0xffffffffu, dsel, pl);
-        const bool ok = d > s_tol;
-        const float inv = ok ? rsqrtf(d) : 0.0f;
-        float* nxt = colbuf[(k + 1) & 1];
+        for (int jj = 0; jj < kPB; ++jj)
+          p[q][jj] = (i < n && jj < w && i >= c0 + jj) ? A[(c0 + jj) * lda + i] : 0.0f;
+      }
+      const float tol = s_tol;
+      bool ok = true;
 #pragma unroll
-        for (int q = 0; q < QN; ++q) {
-          const int i = lane + 32 * q;
-          float v = 0.0f;
-          if (i >= k + 1 && i < n) {
-            v = (i == k + 1) ? d * inv : av[q] * inv;
-            nxt[i] = v;
-            img[(k + 1) * np + i] = static_cast<TI>(v);
-          } else if (i < k + 1) {
-            img[(k + 1) * np + i] = TI(0);
+      for (int kk = 0; kk < kPB; ++kk) {
+        if (kk < w) {
+          const float d = __shfl_sync(0xffffffffu, p[0][kk], kk);    // row c0+kk: lane kk
+          ok = ok && (d > tol);
+          const float inv = ok ? rsqrtf(d) : 0.0f;
+#pragma unroll
+          for (int q = 0; q < QP; ++q) {
+            const int r = lane + 32 * q;                              // panel row
+            p[q][kk] = (r == kk) ? d * inv : (r > kk ? p[q][kk] * inv : 0.0f);
           }
-          colv[q] = v;
-        }
-        if (lane == 0) {
-          s_ldiag[k + 1] = d * inv;
-          if (!ok) s_stop = k + 2;
+#pragma unroll
+          for (int jj = kk + 1; jj < kPB; ++jj) {
+            const float ljk = __shfl_sync(0xffffffffu, p[0][kk], jj);  // row c0+jj: lane jj
+#pragma unroll
+            for (int q = 0; q < QP; ++q) p[q][jj] = fmaf(-p[q][kk], ljk, p[q][jj]);
+          }
         }
       }
-    } else {
-      const int j0 = k + 2;
 #pragma unroll
-      for (int u = 0; u < TPT; ++u) {
-        if (ti[u] + 3 < j0 || tj[u] + 3 < j0) continue;   // tile finished (or none)
-        float ci[4], cj[4];
+      for (int q = 0; q < QP; ++q) {
+        const int i = c0 + lane + 32 * q;
+        if (i < n) {
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          ci[r] = (ti[u] + r < n) ? cur[ti[u] + r] : 0.0f;
-          cj[r] = (tj[u] + r < n) ? cur[tj[u] + r] : 0.0f;
+          for (int jj = 0; jj < kPB; ++jj)
+            if (jj < w) {
+              const float v = (i >= c0 + jj) ? p[q][jj] : 0.0f;
+              A[(c0 + jj) * lda + i] = v;
+              img[(c0 + jj) * np + i] = static_cast<TI>(v);
+              if (i == c0 + jj) s_ldiag[i] = v;
+            }
+        }
+      }
+      if (lane == 0 && !ok) s_stop = 1;
+    }
+    __syncthreads();
+    if (s_stop) return false;
+    // trailing update of rows/columns [c0 + w, n): 4 x 4 tiles of the lower triangle
+    const int t0 = c0 + w;
+    const int m = n - t0;
+    if (m > 0) {
+      const int nb = (m + 3) >> 2;
+      const int ntiles = nb * (nb + 1) / 2;
+      for (int t = tid; t < ntiles; t += CNT) {
+        int bi = static_cast<int>((sqrtf(8.0f * static_cast<float>(t) + 1.0f) - 1.0f) * 0.5f);
+        while (bi * (bi + 1) / 2 > t) --bi;
+        while ((bi + 1) * (bi + 2) / 2 <= t) ++bi;
+        const int bj = t - bi * (bi + 1) / 2;
+        const int i0 = t0 + 4 * bi, j0 = t0 + 4 * bj;
+        float acc[4][4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {   // columns >= n do not exist (rows up to lda do)
+          const float4 v = (j0 + c < n) ? *reinterpret_cast<const float4*>(A + (j0 + c) * lda + i0)
+                                        : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+          acc[0][c] = v.x; acc[1][c] = v.y; acc[2][c] = v.z; acc[3][c] = v.w;
         }
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
+        for (int kk = 0; kk < kPB; ++kk) {
+          if (kk < w) {
+            const float4 li = *reinterpret_cast<const float4*>(A + (c0 + kk) * lda + i0);
+            const float4 lj = *reinterpret_cast<const float4*>(A + (c0 + kk) * lda + j0);
+            const float a4[4] = {li.x, li.y, li.z, li.w};
+            const float b4[4] = {lj.x, lj.y, lj.z, lj.w};
 #pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            const int i = ti[u] + r, j = tj[u] + c;
-            if (j >= j0 && j <= i && i < n) {
-              a[u][r][c] = fmaf(-ci[r], cj[c], a[u][r][c]);
-              if (j == j0) Acol[j * n + i] = a[u][r][c];
-            }
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+              for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(-a4[r], b4[c], acc[r][c]);
           }
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          if (j0 + c < n)
+            *reinterpret_cast<float4*>(A + (j0 + c) * lda + i0) =
+                make_float4(acc[0][c], acc[1][c], acc[2][c], acc[3][c]);
       }
     }
     __syncthreads();
   }
-  if (s_stop) return false;
   for (int k = tid; k < n; k += CNT) {
     keep_out[k] = 1;
     invdiag[k] = 1.0 / static_cast<double>(s_ldiag[k]);
@@ -352,12 +328,8 @@ __device__ __forceinline__ void cholesky_cta_mixed(const double* __restrict__ G,
   constexpr bool f32img = sizeof(TI) == 4;
   double* img64 = f32img ? nullptr : reinterpret_cast<double*>(img);
   float* img32 = f32img ? reinterpret_cast<float*>(img) : nullptr;
-  if (n <= kTileCholMax && img) {
-    const int nb = (n + 3) >> 2;
-    const bool done = nb * (nb + 1) / 2 <= CNT - 32
-        ? cholesky_f32_tiles<1, TI>(G, n, tol32, A32, invdiag, keep_out, info, img, gimg32)
-        : cholesky_f32_tiles<2, TI>(G, n, tol32, A32, invdiag, keep_out, info, img, gimg32);
-    if (done) return;
+  if (n >= 4 && n <= kPanelCholMax && img) {
+    if (cholesky_f32_panel<TI>(G, n, tol32, A32, invdiag, keep_out, info, img, gimg32)) return;
   } else if (cholesky_cta<float>(G, n, 0, tol32, A32, nullptr, nullptr, invdiag, keep_out,
                                  info, err, img64, img32, gimg32, false)) {
     return;
