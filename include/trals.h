@@ -49,14 +49,17 @@ typedef enum tr_status {
 
 typedef enum tr_dtype { TR_F32 = 0, TR_F64 = 1 } tr_dtype;
 
-/* Arithmetic of the least-squares step (rows a3-a6); the sampling distributions (row a1)
- * are FP64 under both.
+/* Arithmetic of the least-squares step (rows a3-a6) and of the drivers' distributions.
  * TR_PREC_FP64 : design rows, fibres, contractions, Cholesky and solves in FP64.
  * TR_PREC_MIXED: design rows and fibres in FP32, contractions with FP32 accumulation.
  *                The normal matrix is factored in FP32 when every pivot exceeds
  *                L*eps32*max diag, else in FP64 (same singular rule as TR_PREC_FP64);
  *                FP32 triangular solves and one step of iterative refinement against the
- *                FP32-accurate normal-equation residual. */
+ *                FP32-accurate normal-equation residual. In the drivers, the leverage Gram
+ *                of a tall matrix (I >= L) is factored in double-float (pairs of FP32,
+ *                about 46 significant bits) when every pivot exceeds
+ *                max(I,L)*2^-40*max diag, else in FP64 with column dropping; all other
+ *                leverage arithmetic, and tr_leverage, is FP64. */
 typedef enum tr_precision { TR_PREC_FP64 = 0, TR_PREC_MIXED = 1 } tr_precision;
 
 /* How tr_als_sampled, tr_als_sampled_host and tr_als_sampled_batched draw their samples.

@@ -190,12 +190,23 @@ LevPass carve_pass(Carver& c, int64_t rows, int cols, bool trans) {
   return p;
 }
 
+// `mixed` (a single tall pass of the mixed-precision drivers): the double-float factorisation
+// with FP64 fallback.
 tr_status run_pass(tr_ctx* ctx, const LevPass& p, const double* A, int64_t rows, int cols,
-                   int64_t lda, bool trans, double tol_scale, cudaStream_t st) {
+                   int64_t lda, bool trans, double tol_scale, cudaStream_t st,
+                   bool mixed = false) {
   const int n = trans ? static_cast<int>(rows) : cols;
   TR_LAUNCH("gram_f64", launch_gram(A, rows, cols, lda, trans, p.partial, p.splits, st));
   TR_LAUNCH("reduce_gram", launch_reduce(p.partial, false, p.splits, static_cast<int64_t>(n) * n,
                                          n, n, n, n, p.G, n, nullptr, 0, st));
+  if (mixed) {
+    const double eps = 2.220446049250313e-16, eps_ff = 9.094947017729282e-13;   // 2^-40
+    TR_LAUNCH("cholesky_leverage",
+              launch_cholesky_lev_mixed(p.G, n, tol_scale, tol_scale / eps * eps_ff, p.Lrow,
+                                        p.Lcol, p.invdiag, p.keep, p.info, ctx->d_err, st,
+                                        p.img));
+    return TR_OK;
+  }
   TR_LAUNCH("cholesky_leverage", launch_cholesky(p.G, n, 1, tol_scale, p.Lrow, p.Lcol,
                                                    p.invdiag, p.keep, p.info, ctx->d_err, st,
                                                    p.img));
@@ -223,9 +234,11 @@ size_t leverage_bytes(int64_t I, int L) {
 
 // Leverage scores of the rows of the I x L row-major matrix `mat` (a core's G_(2), or any
 // matrix with the same column space) and, from them, p and the CDF (unless *skip != 0).
+// `mixed` (the mixed-precision drivers): a tall matrix's Gram is factored in double-float
+// when no pivot is small (about 46 significant bits; rank decisions stay FP64).
 tr_status leverage_dist(tr_ctx* ctx, char* ws, const double* mat, int64_t I, int L, double* p,
                         double* cdf, const int* skip, cudaStream_t st,
-                        cudaEvent_t wait_before_rows = nullptr) {
+                        cudaEvent_t wait_before_rows = nullptr, bool mixed = false) {
   Carver c(ws);
   LevPass p1{}, p2{};
   double* ell;
@@ -237,7 +250,7 @@ tr_status leverage_dist(tr_ctx* ctx, char* ws, const double* mat, int64_t I, int
   TR_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned), st));
   const CdfEpilogue ep{counter, p, cdf, skip, ctx->d_err};
   if (I >= L) {
-    TR_TRY(run_pass(ctx, p1, mat, I, L, L, false, tol, st));
+    TR_TRY(run_pass(ctx, p1, mat, I, L, L, false, tol, st, mixed));
     if (wait_before_rows) TR_CUDA(cudaStreamWaitEvent(st, wait_before_rows, 0));
     TR_LAUNCH("leverage_rows", launch_trsm(0, false, L, p1.Lrow, p1.Lcol, p1.invdiag, nullptr, I,
                                            mat, L, nullptr, 1, 1, nullptr, ell, st, p1.img,
@@ -256,8 +269,8 @@ tr_status leverage_dist(tr_ctx* ctx, char* ws, const double* mat, int64_t I, int
 }
 
 tr_status leverage_run(tr_ctx* ctx, char* ws, const double* core, int64_t I, int Rl, int Rr,
-                       double* p, double* cdf, cudaStream_t st) {
-  return leverage_dist(ctx, ws, core, I, Rl * Rr, p, cdf, nullptr, st);
+                       double* p, double* cdf, cudaStream_t st, bool mixed = false) {
+  return leverage_dist(ctx, ws, core, I, Rl * Rr, p, cdf, nullptr, st, nullptr, mixed);
 }
 
 // ------------------------------------------------------------------------------------
@@ -379,7 +392,7 @@ tr_status update_run(tr_ctx* ctx, char* ws, size_t solve_ws, const void* A, cons
   // keep the old distribution when the core was not updated.
   TR_CUDA(cudaEventRecord(ctx->ev_info, st));
   TR_TRY(solve_rhs(ctx, s, Rl, Rr, I, !f64, core_out, st));
-  TR_TRY(leverage_dist(ctx, ws + solve_ws, s.BT, I, L, p, cdf, s.info, side, ctx->ev_info));
+  TR_TRY(leverage_dist(ctx, ws + solve_ws, s.BT, I, L, p, cdf, s.info, side, ctx->ev_info, !f64));
   TR_CUDA(cudaEventRecord(ctx->ev_join, side));
   TR_CUDA(cudaStreamWaitEvent(st, ctx->ev_join, 0));
   return TR_OK;
@@ -498,7 +511,7 @@ tr_status als_issue(tr_ctx* ctx, const AlsPlan& P, uint64_t seed, const uint64_t
   if (!uni)
     for (int k = 1; k < N; ++k)
       TR_TRY(leverage_run(ctx, P.ws, P.cores[k], dims[k], rl_of(ranks, N, k), ranks[k], P.p[k],
-                          P.cdf[k], st));
+                          P.cdf[k], st, !f64));
   int64_t stride[kMaxModes];
   row_major_strides(N, dims, stride);
   const bool x64 = P.xdt == TR_F64;

@@ -336,6 +336,14 @@ __global__ void __launch_bounds__(CNT) kb_cholesky(const BInst* __restrict__ tab
     const int n = tall ? cu.L : static_cast<int>(cu.I);
     const int64_t nn = static_cast<int64_t>(n) * n;
     double* A = (nn * 8 <= smem_bytes) ? smem : d.L1row;
+    if (mixed && tall) {   // double-float first; a wide pass-1 factor feeds pass 2 (FP64)
+      const double eps_ff = 9.094947017729282e-13;   // 2^-40
+      float* Aff = (panel_floats<FFOps>(n) * 4 <= smem_bytes) ? reinterpret_cast<float*>(smem)
+                                                               : nullptr;
+      cholesky_cta_lev_mixed(d.G1, n, tol, tol / eps * eps_ff, Aff, A, d.L1row, d.L1col, d.inv1,
+                             d.keep1, d.info1, err, d.img1);
+      return;
+    }
     cholesky_cta(d.G1, n, 1, tol, A, d.L1row, d.L1col, d.inv1, d.keep1, d.info1, err, d.img1,
                  nullptr, nullptr);
     return;
@@ -572,6 +580,8 @@ constexpr int kDyn = 200 * 1024;
 
 int smem_for_cholesky(int nmax) {
   const int64_t need = static_cast<int64_t>(nmax) * nmax * 8;
+  const int64_t ff = panel_floats<FFOps>(nmax) * 4;
+  if ((ff > need ? ff : need) <= kDyn) return static_cast<int>(ff > need ? ff : need);
   return need <= kDyn ? static_cast<int>(need) : 0;
 }
 

@@ -35,7 +35,34 @@ __global__ void __launch_bounds__(CNT) k_cholesky_mixed(const double* __restrict
                          err, img, gimg32);
 }
 
+// The mixed-precision drivers' leverage Gram (tall, mode 1): double-float, FP64 if needed.
+__global__ void __launch_bounds__(CNT) k_cholesky_lev_mixed(const double* __restrict__ G, int n,
+                                                            double tol64, double tolff,
+                                                            double* Lrow, double* Lcol,
+                                                            double* invdiag, int* keep_out,
+                                                            int* info, unsigned* err,
+                                                            int dyn_bytes, double* img64) {
+  extern __shared__ double smem[];
+  const int64_t nn = static_cast<int64_t>(n) * n;
+  float* Aff = panel_floats<FFOps>(n) * 4 <= dyn_bytes ? reinterpret_cast<float*>(smem) : nullptr;
+  double* A64 = nn * 8 <= dyn_bytes ? smem : Lrow;
+  cholesky_cta_lev_mixed(G, n, tol64, tolff, Aff, A64, Lrow, Lcol, invdiag, keep_out, info, err,
+                         img64);
+}
+
 }  // namespace
+
+cudaError_t launch_cholesky_lev_mixed(const double* G, int n, double tol64, double tolff,
+                                      double* Lrow, double* Lcol, double* invdiag, int* keep,
+                                      int* info, unsigned* err, cudaStream_t st, double* img64) {
+  const size_t nn = static_cast<size_t>(n) * n;
+  const size_t ff = static_cast<size_t>(panel_floats<FFOps>(n)) * 4;
+  const size_t want = nn * 8 > ff ? nn * 8 : ff;
+  const size_t dyn = want <= kCholDyn ? want : (nn * 8 <= kCholDyn ? nn * 8 : 0);
+  k_cholesky_lev_mixed<<<1, CNT, dyn, st>>>(G, n, tol64, tolff, Lrow, Lcol, invdiag, keep, info,
+                                            err, static_cast<int>(dyn), img64);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_cholesky_mixed(const double* G, int n, double tol64, double tol32,
                                   double* Lrow, double* Lcol, double* invdiag, int* keep,
@@ -86,6 +113,9 @@ cudaError_t cholesky_attributes() {
       cudaFuncSetAttribute(k_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize, kCholDyn);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_cholesky_mixed<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           kCholDyn);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_cholesky_lev_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            kCholDyn);
   if (e != cudaSuccess) return e;
   return cholesky_cluster_attributes();

@@ -167,44 +167,157 @@ __device__ __forceinline__ bool cholesky_cta(const double* __restrict__ G, int n
   return true;
 }
 
-// FP32 factorisation of the mixed LS step for n <= kPanelCholMax: blocked right-looking with
-// panels of kPB columns. Warp 0 factors a panel in registers (lane l holds rows c0 + l + 32q
-// of the panel's columns): per column one shuffle for the pivot, one rsqrt, a scaling and
-// kPB-1 shuffles for the later panel columns, with no barrier. Then every thread applies the
-// panel's rank-kPB update to 4 x 4 tiles of the trailing lower triangle, reading the panel
-// columns as 16-byte vectors from the column-major work array A (leading dimension lda, a
-// multiple of 4; lda * n floats, which fit wherever n * n doubles do for n >= 4). Two barriers
-// per panel. Returns false (no factor written) when a pivot is <= tol_scale * max diag.
+// Blocked right-looking Cholesky for n <= kPanelCholMax in a working arithmetic `Ops`:
+// FP32 (F32Ops, the mixed LS step) or double-float (FFOps, a value hi + lo of two FP32
+// numbers, about 46 significant bits: the mixed path's leverage Gram). Panels of Ops::kPB columns:
+// warp 0 factors a panel in registers (lane l holds rows c0 + l + 32q of the panel's
+// columns): per column one shuffle for the pivot, an rsqrt, a scaling and kPB-1 shuffles for
+// the later panel columns, with no barrier. Then every thread applies the panel's rank-kPB
+// update to 4 x 4 tiles of the trailing lower triangle, reading the panel columns as 16-byte
+// vectors from the column-major work array A (Ops::kPlanes planes of lda * n floats, lda a
+// multiple of 4). Two barriers per panel. Every entry receives its updates in column order.
+// The factor image img (FP32 or FP64, padded column-major) is written once at the end.
+// Returns false (no factor written) when a pivot is <= tol_scale * max diag.
 constexpr int kPanelCholMax = 160;
-constexpr int kPB = 8;
 
 __host__ __device__ inline int panel_lda(int n) { return (n + 3) & ~3; }
 
-template <typename TI>
-__device__ __forceinline__ bool cholesky_f32_panel(const double* __restrict__ G, int n,
-                                                   double tol_scale, float* A, double* invdiag,
-                                                   int* keep_out, int* info, TI* img,
-                                                   float* gimg32) {
+struct F32Ops {
+  using V = float;
+  static constexpr int kPlanes = 1;
+  static constexpr int kPB = 8;      // panel width
+  __device__ static V from(double g) { return static_cast<float>(g); }
+  __device__ static V zero() { return 0.0f; }
+  __device__ static float lead(V v) { return v; }
+  __device__ static double wide(V v) { return static_cast<double>(v); }
+  __device__ static V fnms(V x, V y, V a) { return fmaf(-x, y, a); }   // a - x*y
+  __device__ static V mul(V x, V y) { return x * y; }
+  __device__ static V rsqrt(V d) { return rsqrtf(d); }
+  __device__ static V shfl(V v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+  __device__ static V ld(const float* A, int o, int) { return A[o]; }
+  __device__ static void st(float* A, int o, int, V v) { A[o] = v; }
+  __device__ static void ld4(const float* A, int o, int, V (&v)[4]) {
+    const float4 t = *reinterpret_cast<const float4*>(A + o);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+  }
+  __device__ static void st4(float* A, int o, int, const V (&v)[4]) {
+    *reinterpret_cast<float4*>(A + o) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+};
+
+// Double-float values (Dekker 1971; products via fused multiply-add). fnms: the exact product
+// of the leading parts plus the cross terms, then a two-sum with the accumulator; rsqrt: the
+// FP32 estimate refined by one Newton step with the residual formed in double-float.
+struct ffv { float hi, lo; };
+struct FFOps {
+  using V = ffv;
+  static constexpr int kPlanes = 2;
+  static constexpr int kPB = 4;      // panel width (registers: a double-float is two floats)
+  __device__ static V from(double g) {
+    const float h = static_cast<float>(g);
+    return {h, static_cast<float>(g - static_cast<double>(h))};
+  }
+  __device__ static V zero() { return {0.0f, 0.0f}; }
+  __device__ static float lead(V v) { return v.hi; }
+  __device__ static double wide(V v) { return static_cast<double>(v.hi) + static_cast<double>(v.lo); }
+  __device__ static V fnms(V x, V y, V a) {
+    const float p = x.hi * y.hi;
+    float e = fmaf(x.hi, y.hi, -p);
+    e = fmaf(x.hi, y.lo, e);
+    e = fmaf(x.lo, y.hi, e);
+    const float s = a.hi - p;
+    const float b = s - a.hi;
+    float err = (a.hi - (s - b)) + (-p - b);
+    err += a.lo - e;
+    const float h = s + err;
+    return {h, err - (h - s)};
+  }
+  __device__ static V mul(V x, V y) {
+    const float p = x.hi * y.hi;
+    float e = fmaf(x.hi, y.hi, -p);
+    e = fmaf(x.hi, y.lo, e);
+    e = fmaf(x.lo, y.hi, e);
+    const float h = p + e;
+    return {h, e - (h - p)};
+  }
+  __device__ static V rsqrt(V d) {
+    const float y0 = rsqrtf(d.hi);
+    const float t = y0 * y0;
+    const V tt{t, fmaf(y0, y0, -t)};               // y0^2 exactly
+    const V dt = mul(d, tt);
+    const float r = (1.0f - dt.hi) - dt.lo;        // 1 - d y0^2 (small)
+    const float c = y0 * r * 0.5f;
+    const float h = y0 + c;
+    return {h, c - (h - y0)};
+  }
+  __device__ static V shfl(V v, int src) {
+    return {__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src)};
+  }
+  __device__ static V ld(const float* A, int o, int ps) { return {A[o], A[ps + o]}; }
+  __device__ static void st(float* A, int o, int ps, V v) { A[o] = v.hi; A[ps + o] = v.lo; }
+  __device__ static void ld4(const float* A, int o, int ps, V (&v)[4]) {
+    const float4 h = *reinterpret_cast<const float4*>(A + o);
+    const float4 l = *reinterpret_cast<const float4*>(A + ps + o);
+    v[0] = {h.x, l.x}; v[1] = {h.y, l.y}; v[2] = {h.z, l.z}; v[3] = {h.w, l.w};
+  }
+  __device__ static void st4(float* A, int o, int ps, const V (&v)[4]) {
+    *reinterpret_cast<float4*>(A + o) = make_float4(v[0].hi, v[1].hi, v[2].hi, v[3].hi);
+    *reinterpret_cast<float4*>(A + ps + o) = make_float4(v[0].lo, v[1].lo, v[2].lo, v[3].lo);
+  }
+};
+
+// Floats of the work array of cholesky_panel<Ops>.
+template <typename Ops>
+__host__ __device__ inline int64_t panel_floats(int n) {
+  return static_cast<int64_t>(Ops::kPlanes) * panel_lda(n) * n;
+}
+
+template <typename Ops, typename TI>
+__device__ __forceinline__ bool cholesky_panel(const double* __restrict__ G, int n,
+                                               double tol_scale, float* A, double* invdiag,
+                                               int* keep_out, int* info, TI* img,
+                                               float* gimg32) {
+  using V = typename Ops::V;
   constexpr int QP = (kPanelCholMax + 31) / 32;
-  __shared__ float s_ldiag[kPanelCholMax];
+  constexpr int kPB = Ops::kPB;
+  __shared__ double s_ldiag[kPanelCholMax];
   __shared__ float s_tol;
   __shared__ int s_stop;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int np = n + 1, lda = panel_lda(n);
-  for (int e = tid; e < n * n; e += CNT) {
-    const int j = e / n, i = e - (e / n) * n;          // column-major walk of G
-    if (i >= j) {
-      const float g = static_cast<float>(G[e]);      // G symmetric: G[j*n + i] = (i, j)
-      A[j * lda + i] = g;
-      if (gimg32) {
-        gimg32[j * np + i] = g;
-        gimg32[i * np + j] = g;
+  constexpr int NW = CNT / 32;
+  const int np = n + 1, lda = panel_lda(n), ps = lda * n;
+  // load: the lower triangle into A, the whole (symmetric) matrix into the FP32 image; each
+  // thread issues the loads of two columns before any store
+  for (int j0 = warp; j0 < n; j0 += 2 * NW) {
+    double g[2][QP];
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int q = 0; q < QP; ++q) {
+        const int j = j0 + h * NW, i = lane + 32 * q;
+        g[h][q] = (j < n && i < n) ? G[static_cast<int64_t>(j) * n + i] : 0.0;
       }
-    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int q = 0; q < QP; ++q) {
+        const int j = j0 + h * NW, i = lane + 32 * q;
+        if (j < n && i < n) {
+          if (gimg32) gimg32[j * np + i] = static_cast<float>(g[h][q]);
+          if (i >= j) Ops::st(A, j * lda + i, ps, Ops::from(g[h][q]));
+        }
+      }
   }
   if (warp == 0) {
+    float dg[QP];
+#pragma unroll
+    for (int q = 0; q < QP; ++q) {
+      const int i = lane + 32 * q;
+      dg[q] = (i < n) ? static_cast<float>(G[static_cast<int64_t>(i) * n + i]) : 0.0f;
+    }
     float md = 0.0f;
-    for (int i = lane; i < n; i += 32) md = fmaxf(md, static_cast<float>(G[static_cast<int64_t>(i) * n + i]));
+#pragma unroll
+    for (int q = 0; q < QP; ++q) md = fmaxf(md, dg[q]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) md = fmaxf(md, __shfl_xor_sync(0xffffffffu, md, o));
     if (lane == 0) {
@@ -216,32 +329,34 @@ __device__ __forceinline__ bool cholesky_f32_panel(const double* __restrict__ G,
   for (int c0 = 0; c0 < n; c0 += kPB) {
     const int w = (n - c0 < kPB) ? n - c0 : kPB;
     if (warp == 0) {
-      float p[QP][kPB];
+      V p[QP][kPB];
 #pragma unroll
       for (int q = 0; q < QP; ++q) {
         const int i = c0 + lane + 32 * q;
 #pragma unroll
         for (int jj = 0; jj < kPB; ++jj)
-          p[q][jj] = (i < n && jj < w && i >= c0 + jj) ? A[(c0 + jj) * lda + i] : 0.0f;
+          p[q][jj] = (i < n && jj < w && i >= c0 + jj) ? Ops::ld(A, (c0 + jj) * lda + i, ps)
+                                                       : Ops::zero();
       }
       const float tol = s_tol;
       bool ok = true;
 #pragma unroll
       for (int kk = 0; kk < kPB; ++kk) {
         if (kk < w) {
-          const float d = __shfl_sync(0xffffffffu, p[0][kk], kk);    // row c0+kk: lane kk
-          ok = ok && (d > tol);
-          const float inv = ok ? rsqrtf(d) : 0.0f;
+          const V d = Ops::shfl(p[0][kk], kk);                       // row c0+kk: lane kk
+          ok = ok && (Ops::lead(d) > tol);
+          const V inv = ok ? Ops::rsqrt(d) : Ops::zero();
 #pragma unroll
           for (int q = 0; q < QP; ++q) {
             const int r = lane + 32 * q;                              // panel row
-            p[q][kk] = (r == kk) ? d * inv : (r > kk ? p[q][kk] * inv : 0.0f);
+            p[q][kk] = (r == kk) ? Ops::mul(d, inv)
+                                 : (r > kk ? Ops::mul(p[q][kk], inv) : Ops::zero());
           }
 #pragma unroll
           for (int jj = kk + 1; jj < kPB; ++jj) {
-            const float ljk = __shfl_sync(0xffffffffu, p[0][kk], jj);  // row c0+jj: lane jj
+            const V ljk = Ops::shfl(p[0][kk], jj);                    // row c0+jj: lane jj
 #pragma unroll
-            for (int q = 0; q < QP; ++q) p[q][jj] = fmaf(-p[q][kk], ljk, p[q][jj]);
+            for (int q = 0; q < QP; ++q) p[q][jj] = Ops::fnms(p[q][kk], ljk, p[q][jj]);
           }
         }
       }
@@ -251,11 +366,9 @@ __device__ __forceinline__ bool cholesky_f32_panel(const double* __restrict__ G,
         if (i < n) {
 #pragma unroll
           for (int jj = 0; jj < kPB; ++jj)
-            if (jj < w) {
-              const float v = (i >= c0 + jj) ? p[q][jj] : 0.0f;
-              A[(c0 + jj) * lda + i] = v;
-              img[(c0 + jj) * np + i] = static_cast<TI>(v);
-              if (i == c0 + jj) s_ldiag[i] = v;
+            if (jj < w && i >= c0 + jj) {
+              Ops::st(A, (c0 + jj) * lda + i, ps, p[q][jj]);
+              if (i == c0 + jj) s_ldiag[i] = Ops::wide(p[q][jj]);
             }
         }
       }
@@ -275,38 +388,42 @@ __device__ __forceinline__ bool cholesky_f32_panel(const double* __restrict__ G,
         while ((bi + 1) * (bi + 2) / 2 <= t) ++bi;
         const int bj = t - bi * (bi + 1) / 2;
         const int i0 = t0 + 4 * bi, j0 = t0 + 4 * bj;
-        float acc[4][4];
+        V acc[4][4];   // acc[c][r]: column j0+c, row i0+r
 #pragma unroll
         for (int c = 0; c < 4; ++c) {   // columns >= n do not exist (rows up to lda do)
-          const float4 v = (j0 + c < n) ? *reinterpret_cast<const float4*>(A + (j0 + c) * lda + i0)
-                                        : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-          acc[0][c] = v.x; acc[1][c] = v.y; acc[2][c] = v.z; acc[3][c] = v.w;
+          if (j0 + c < n) {
+            Ops::ld4(A, (j0 + c) * lda + i0, ps, acc[c]);
+          } else {
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc[c][r] = Ops::zero();
+          }
         }
 #pragma unroll
         for (int kk = 0; kk < kPB; ++kk) {
           if (kk < w) {
-            const float4 li = *reinterpret_cast<const float4*>(A + (c0 + kk) * lda + i0);
-            const float4 lj = *reinterpret_cast<const float4*>(A + (c0 + kk) * lda + j0);
-            const float a4[4] = {li.x, li.y, li.z, li.w};
-            const float b4[4] = {lj.x, lj.y, lj.z, lj.w};
+            V li[4], lj[4];
+            Ops::ld4(A, (c0 + kk) * lda + i0, ps, li);
+            Ops::ld4(A, (c0 + kk) * lda + j0, ps, lj);
 #pragma unroll
-            for (int r = 0; r < 4; ++r)
+            for (int c = 0; c < 4; ++c)
 #pragma unroll
-              for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(-a4[r], b4[c], acc[r][c]);
+              for (int r = 0; r < 4; ++r) acc[c][r] = Ops::fnms(li[r], lj[c], acc[c][r]);
           }
         }
 #pragma unroll
         for (int c = 0; c < 4; ++c)
-          if (j0 + c < n)
-            *reinterpret_cast<float4*>(A + (j0 + c) * lda + i0) =
-                make_float4(acc[0][c], acc[1][c], acc[2][c], acc[3][c]);
+          if (j0 + c < n) Ops::st4(A, (j0 + c) * lda + i0, ps, acc[c]);
       }
     }
     __syncthreads();
   }
+  // the factor image, padded column-major: img[c*(n+1) + r] = L[r][c]
+  for (int j = warp; j < n; j += NW)
+    for (int i = lane; i < n; i += 32)
+      img[j * np + i] = (i >= j) ? static_cast<TI>(Ops::wide(Ops::ld(A, j * lda + i, ps))) : TI(0);
   for (int k = tid; k < n; k += CNT) {
     keep_out[k] = 1;
-    invdiag[k] = 1.0 / static_cast<double>(s_ldiag[k]);
+    invdiag[k] = 1.0 / s_ldiag[k];
   }
   if (tid == 0) *info = 0;
   return true;
@@ -329,7 +446,8 @@ __device__ __forceinline__ void cholesky_cta_mixed(const double* __restrict__ G,
   double* img64 = f32img ? nullptr : reinterpret_cast<double*>(img);
   float* img32 = f32img ? reinterpret_cast<float*>(img) : nullptr;
   if (n >= 4 && n <= kPanelCholMax && img) {
-    if (cholesky_f32_panel<TI>(G, n, tol32, A32, invdiag, keep_out, info, img, gimg32)) return;
+    if (cholesky_panel<F32Ops, TI>(G, n, tol32, A32, invdiag, keep_out, info, img, gimg32))
+      return;
   } else if (cholesky_cta<float>(G, n, 0, tol32, A32, nullptr, nullptr, invdiag, keep_out,
                                  info, err, img64, img32, gimg32, false)) {
     return;
@@ -337,6 +455,25 @@ __device__ __forceinline__ void cholesky_cta_mixed(const double* __restrict__ G,
   __syncthreads();
   cholesky_cta<double>(G, n, mode, tol64, A64, Lrow, Lcol, invdiag, keep_out, info, err, img64,
                        img32, gimg32, true);
+}
+
+// The mixed-precision drivers' leverage Gram of a tall matrix (mode 1): double-float first,
+// accepted only if every pivot exceeds tolff * max diag (no column is dropped); otherwise
+// the FP64 factorisation with tol64 and mode 1's column dropping. The image is FP64.
+// Aff is the double-float work array (panel_floats<FFOps>(n) floats), A64 the FP64 one (they
+// may alias). Lrow/Lcol receive the factor only on the FP64 branch.
+__device__ __forceinline__ void cholesky_cta_lev_mixed(const double* __restrict__ G, int n,
+                                                       double tol64, double tolff, float* Aff,
+                                                       double* A64, double* Lrow, double* Lcol,
+                                                       double* invdiag, int* keep_out,
+                                                       int* info, unsigned* err, double* img64) {
+  if (n >= 4 && n <= kPanelCholMax && img64 && Aff) {
+    if (cholesky_panel<FFOps, double>(G, n, tolff, Aff, invdiag, keep_out, info, img64, nullptr))
+      return;
+    __syncthreads();
+  }
+  cholesky_cta<double>(G, n, 1, tol64, A64, Lrow, Lcol, invdiag, keep_out, info, err, img64,
+                       nullptr, nullptr, true);
 }
 
 }  // namespace trk

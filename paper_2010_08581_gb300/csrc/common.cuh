@@ -126,6 +126,12 @@ cudaError_t launch_cholesky_mixed(const double* G, int n, double tol64, double t
                                   double* Lrow, double* Lcol, double* invdiag, int* keep,
                                   int* info, unsigned* err, cudaStream_t st, float* img32,
                                   float* gimg32);
+// Mixed-precision drivers' leverage Gram of a tall matrix (mode 1): double-float factor when
+// every pivot > tolff * max diag (FP64 image img64 + invdiag + keep + info), otherwise the FP64
+// factorisation with tol64 and column dropping (as launch_cholesky, mode 1).
+cudaError_t launch_cholesky_lev_mixed(const double* G, int n, double tol64, double tolff,
+                                      double* Lrow, double* Lcol, double* invdiag, int* keep,
+                                      int* info, unsigned* err, cudaStream_t st, double* img64);
 cudaError_t launch_cholesky(const double* G, int n, int mode, double tol_scale, double* Lrow,
                             double* Lcol, double* invdiag, int* keep, int* info,
                             unsigned* err, cudaStream_t st, double* img64 = nullptr,

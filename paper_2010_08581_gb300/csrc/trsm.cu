@@ -99,7 +99,7 @@ cudaError_t launch_trsm(int mode, bool f32, int n, const double* Lrow, const dou
   if (nvec <= 0) return cudaSuccess;
   const CdfEpilogue ep = cdf ? *cdf : CdfEpilogue{};
   if (f32)
-    return run<float, 2>(n, Lrow, Lcol, invdiag, info, nvec, rhs, ld, mode, M,
+    return run<float, 1>(n, Lrow, Lcol, invdiag, info, nvec, rhs, ld, mode, M,
                          static_cast<const float*>(Limg), Mimg, Rl, Rr, core_out, ell, ep, st);
   return run<double, 1>(n, Lrow, Lcol, invdiag, info, nvec, rhs, ld, mode, M,
                         static_cast<const double*>(Limg), Mimg, Rl, Rr, core_out, ell, ep, st);
@@ -110,7 +110,7 @@ size_t trsm_image_bytes(int n, bool f32) {
 }
 
 cudaError_t trsm_attributes() {
-  cudaError_t e = attr<float, 2>();
+  cudaError_t e = attr<float, 1>();
   if (e != cudaSuccess) return e;
   return attr<double, 1>();
 }
