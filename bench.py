@@ -5,12 +5,12 @@ scores + 10 sweeps of Alg. 2, J = 4000, mixed precision) with X resident in HBM.
 metric is sweeps/s = sweeps per step * steps / time. Besides it the JSON line carries the
 end-to-end number through the host-memory entry point, the roofline of the dominant
 kernel, the plain FP64 GPU form (the metric's comparator), the FP64 CPU oracle on a
-bounded sample, the same decomposition with uniform sampling (Sec. 5 variant), the
-512-problem batched workload, and the serving leg: p50/p99 decomposition latency of a
+bounded sample, the same decomposition with uniform sampling (Sec. 5 variant) and with
+dense TR-ALS (Alg. 1, the paper's comparison method), the 512-problem batched workload, and the serving leg: p50/p99 decomposition latency of a
 Poisson stream of requests (200/s) through the native server.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--serve-seconds S] [--skip-cpu] [--skip-fp64] [--skip-uniform]
+                  [--serve-seconds S] [--skip-cpu] [--skip-fp64] [--skip-uniform] [--skip-dense]
                   [--skip-batched] [--skip-configs] [--skip-serving]
 
 With N > 1 (torchrun), every rank decomposes its own tensor (replicas, weak scaling).
@@ -395,6 +395,39 @@ def run_uniform(T, X, ranks, J, sweeps, init_dev, dims, stream, reps):
     return out
 
 
+def run_dense(T, X, ranks, sweeps, init_dev, dims, stream, reps, sampled_value, sampled_err):
+    """Dense TR-ALS (Alg. 1, every row of each least-squares problem) on the same workload and
+    the same LS path: sweeps/s, final error, and the sampled method's speedup over it."""
+    ctx = T.Context(torch.cuda.current_device())
+    cores = T.empty_cores(dims, ranks, device=X.device)
+
+    def call():
+        T.tr_als(ctx, X, ranks, sweeps, 0, T.TR_PREC_MIXED, cores, init_cores=init_dev)
+
+    call()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        call()
+    b.record(stream)
+    torch.cuda.synchronize()
+    sec = a.elapsed_time(b) / 1e3
+    value = sweeps * reps / sec
+    err = T.tr_rel_error(ctx, X, ranks, cores)
+    T.tr_profile_begin(ctx)
+    call()
+    prof = T.tr_profile_end(ctx)
+    ctx.close()
+    return {"value": round(value, 3), "unit": "sweeps/s", "final_rel_err": err,
+            "sampled_speedup": round(sampled_value / value, 3),
+            "sampled_err_ratio": round(sampled_err / err, 4),
+            "kernels_ms_one_decomposition": {k: [round(v[0], 3), v[1]] for k, v in
+                                             sorted(prof.items(), key=lambda kv: -kv[1][0])},
+            "what": "TR-ALS (Alg. 1) through tr_als, mixed precision, same initial cores; "
+                    "sampled_speedup = the headline sweeps/s / this"}
+
+
 def _time_calls(fn, reps, stream):
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     fn()
@@ -735,6 +768,11 @@ def run_ours(args):
         uniform = run_uniform(T, X, ranks, J, sweeps, init_dev, dims, stream,
                               max(1, min(args.steps, 5)))
 
+    dense = None
+    if not args.skip_dense and world == 1:
+        dense = run_dense(T, X, ranks, sweeps, init_dev, dims, stream,
+                          max(1, min(args.steps, 3)), value / world, fit)
+
     batched = None
     if not args.skip_batched and world == 1:
         batched = run_batched(T, plain_fp64, dev, max(1, min(args.steps, 5)), 1, stream)
@@ -780,6 +818,7 @@ def run_ours(args):
                            sorted(prof.items(), key=lambda kv: -kv[1][0])},
             "fp64_gpu_form": fp64,
             "uniform_sampling": uniform,
+            "dense_tr_als": dense,
             "batched_512": batched,
             "config1_fp64_100": config1,
             "config3_cosine_4way": config3,
@@ -806,6 +845,7 @@ def main():
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-batched", action="store_true")
     ap.add_argument("--skip-uniform", action="store_true")
+    ap.add_argument("--skip-dense", action="store_true")
     ap.add_argument("--skip-serving", action="store_true")
     ap.add_argument("--skip-configs", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=20.0)

@@ -168,6 +168,18 @@ tr_status tr_als_sampled(tr_ctx* ctx, const void* X, tr_dtype X_dtype, int N,
                          uint64_t seed, tr_precision prec, const double* const* init_cores,
                          double* const* cores, tr_stream stream);
 
+/* Dense TR-ALS (Alg. 1), the comparison method of Sec. 5, with a fixed number of sweeps,
+ * synchronous. Core update n solves the full least-squares problem
+ * argmin_Z || G_[2]^{!=n} Z - X_[n]^T ||_F over all prod_{j!=n} I_j rows, each with weight 1
+ * (Def. 5 with S = I), through the same normal-equation path as tr_als_sampled (rows a3,
+ * a5, a6; same tr_precision arithmetic). No distribution is formed. Arguments as
+ * tr_als_sampled, without J (seed only draws the initial cores when init_cores is NULL).
+ * Workspace: about prod I * es + max_n prod_{j!=n} I_j * (L_max * es + 4 (N-1)) bytes plus
+ * the LS step's, es = 4 (TR_PREC_MIXED) or 8. Every dims[k] must be <= 2097120. */
+tr_status tr_als(tr_ctx* ctx, const void* X, tr_dtype X_dtype, int N, const int64_t* dims,
+                 const int* ranks, int sweeps, uint64_t seed, tr_precision prec,
+                 const double* const* init_cores, double* const* cores, tr_stream stream);
+
 /* Same as tr_als_sampled with X and the cores in HOST memory: X is copied to the device,
  * the method runs, and the cores are copied back into the host arrays cores_host[k]
  * (FP64 slice-major). init_cores_host may be NULL. Pinned host memory is fastest. */

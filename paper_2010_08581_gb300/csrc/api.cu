@@ -913,6 +913,80 @@ tr_status tr_als_sampled(tr_ctx* ctx, const void* X, tr_dtype X_dtype, int N, co
   return s;
 }
 
+tr_status tr_als(tr_ctx* ctx, const void* X, tr_dtype X_dtype, int N, const int64_t* dims,
+                 const int* ranks, int sweeps, uint64_t seed, tr_precision prec,
+                 const double* const* init_cores, double* const* cores, tr_stream stream) {
+  TR_TRY(check_ctx(ctx));
+  TR_TRY(check_als(ctx, X, X_dtype, N, dims, ranks, 1, sweeps, prec, cores, init_cores));
+  const bool f64 = prec == TR_PREC_FP64, x64 = X_dtype == TR_F64;
+  const size_t es = f64 ? 8 : 4;
+  // rows of each update: every multi-index of the other modes
+  std::vector<int64_t> P(N, 1);
+  int64_t numel = 1, Pmax = 0;
+  int Lmax = 0;
+  for (int k = 0; k < N; ++k) numel *= dims[k];
+  for (int n = 0; n < N; ++n) {
+    P[n] = numel / dims[n];
+    Pmax = P[n] > Pmax ? P[n] : Pmax;
+    const int L = rl_of(ranks, N, n) * ranks[n];
+    Lmax = L > Lmax ? L : Lmax;
+    if (dims[n] > 65535LL * 32)
+      return fail(ctx, TR_ERR_INVALID_ARG, "dims[%d]=%lld exceeds 2097120 (dense unfolding)", n,
+                  static_cast<long long>(dims[n]));
+  }
+  Carver dry(nullptr);
+  dry.take<int32_t>(static_cast<size_t>(Pmax) * (N - 1));
+  dry.take<char>(static_cast<size_t>(Pmax) * Lmax * es);
+  dry.take<char>(static_cast<size_t>(numel) * es);
+  const size_t persist = (dry.off + 255) & ~size_t(255);
+  size_t solve_max = 0;
+  for (int n = 0; n < N; ++n) {
+    const size_t b = solve_bytes(P[n], rl_of(ranks, N, n) * ranks[n], dims[n], f64);
+    solve_max = b > solve_max ? b : solve_max;
+  }
+  DeviceGuard g(ctx->device);
+  TR_TRY(ensure_ws(ctx, persist + solve_max + 256));
+  Carver c(ctx->arena);
+  int32_t* idx = c.take<int32_t>(static_cast<size_t>(Pmax) * (N - 1));
+  void* A = c.take<char>(static_cast<size_t>(Pmax) * Lmax * es);
+  void* Y = c.take<char>(static_cast<size_t>(numel) * es);
+  char* ws = ctx->arena + persist;
+  cudaStream_t st = S(stream);
+  for (int k = 1; k < N; ++k) {
+    const size_t count = static_cast<size_t>(dims[k]) * rl_of(ranks, N, k) * ranks[k];
+    if (init_cores) {
+      TR_CUDA(cudaMemcpyAsync(cores[k], init_cores[k], count * sizeof(double),
+                              cudaMemcpyDeviceToDevice, st));
+    } else {
+      TR_LAUNCH("init_normal", launch_init_normal(cores[k], static_cast<int64_t>(count), seed,
+                                                  static_cast<uint32_t>(k), nullptr, st));
+    }
+  }
+  DenseDims dd{};
+  for (int k = 0; k < N; ++k) dd.I[k] = dims[k];
+  for (int s = 0; s < sweeps; ++s) {
+    for (int n = 0; n < N; ++n) {
+      ChainArgs ca{};
+      ca.npos = N - 1;
+      for (int m = 0; m < N - 1; ++m) {
+        const int mode = (n + 1 + m) % N;
+        ca.core[m] = cores[mode];
+        ca.I[m] = dims[mode];
+        ca.rl[m] = rl_of(ranks, N, mode);
+        ca.rr[m] = ranks[mode];
+      }
+      TR_LAUNCH("enumerate", launch_enumerate(N, n, dd, idx, st));
+      TR_LAUNCH("subchain", launch_subchain(ca, idx, nullptr, P[n], A, f64, ctx->d_err, st));
+      // the last mode's rows are X itself when X already has the LS step's type
+      const void* Yn = (n == N - 1 && x64 == f64) ? X : Y;
+      if (Yn == Y) TR_LAUNCH("unfold", launch_unfold(X, x64, N, n, dd, Y, f64, st));
+      TR_TRY(update_run(ctx, ws, solve_max, A, Yn, f64, P[n], rl_of(ranks, N, n), ranks[n],
+                        dims[n], cores[n], nullptr, nullptr, st, ctx->side));
+    }
+  }
+  return read_device_error(ctx, st);
+}
+
 tr_status tr_als_sampled_host(tr_ctx* ctx, const void* X_host, tr_dtype X_dtype, int N,
                               const int64_t* dims, const int* ranks, int64_t J, int sweeps,
                               uint64_t seed, tr_precision prec,

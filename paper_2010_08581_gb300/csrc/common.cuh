@@ -84,6 +84,16 @@ cudaError_t launch_gather(const GatherArgs& a, const void* X, bool x_f64, const 
                           const double* w, int64_t J, void* Y, bool y_f64, unsigned* err,
                           cudaStream_t st);
 
+// Dense TR-ALS (Alg. 1) rows: every multi-index of the modes other than n in row-major order
+// (the last mode fastest), written in ring order as idx[P][N-1]; and Y = X_[n]^T with rows
+// in that order (Y[r][i], r = pre * P_post + post for X viewed as [P_pre][I_n][P_post]).
+struct DenseDims {
+  int64_t I[kMaxModes];
+};
+cudaError_t launch_enumerate(int N, int n, const DenseDims& d, int32_t* idx, cudaStream_t st);
+cudaError_t launch_unfold(const void* X, bool x_f64, int N, int n, const DenseDims& d, void* Y,
+                          bool y_f64, cudaStream_t st);
+
 // Normal-equation contraction: partial[s][r][c] = sum over the s-th chunk of rows j of
 // A[j][r] * [A | Y][j][c], r < L, c < L + I. Returns the number of chunks in *splits.
 size_t normal_eq_workspace(int64_t J, int L, int64_t I, bool f64, int* splits);

@@ -103,6 +103,7 @@ SIGNATURES = {
                          c_vp]),
     "tr_als_sampled": (c_int, [c_vp, c_vp, c_int, c_int, P64, PI, c_i64, c_int, c_u64, c_int,
                                PP, PP, c_vp]),
+    "tr_als": (c_int, [c_vp, c_vp, c_int, c_int, P64, PI, c_int, c_u64, c_int, PP, PP, c_vp]),
     "tr_als_sampled_host": (c_int, [c_vp, c_vp, c_int, c_int, P64, PI, c_i64, c_int, c_u64,
                                     c_int, PP, PP, c_vp]),
     "tr_rel_error": (c_int, [c_vp, c_vp, c_int, c_int, P64, PI, PP, ctypes.POINTER(c_dbl),
@@ -324,6 +325,22 @@ def tr_als_sampled(ctx: Context, X: torch.Tensor, ranks, J: int, sweeps: int, se
         ip = ctypes.cast(c_vp(None), PP)
     ctx.check(load().tr_als_sampled(ctx.handle, _ptr(X), _dt(X), len(dims), d, r, J, sweeps,
                                     seed, prec, ip, cp, _stream(stream)))
+
+
+def tr_als(ctx: Context, X: torch.Tensor, ranks, sweeps: int, seed: int, prec: int,
+           cores: List[torch.Tensor], init_cores: Optional[List[Optional[torch.Tensor]]] = None,
+           stream=None):
+    """Dense TR-ALS (Alg. 1): every row of each least-squares problem, weight 1."""
+    dims = list(X.shape)
+    d, _d = _i64s(dims)
+    r, _r = _ints(ranks)
+    cp, _c = _ptrs(cores)
+    if init_cores is not None:
+        ip, _i = _ptrs(init_cores)
+    else:
+        ip = ctypes.cast(c_vp(None), PP)
+    ctx.check(load().tr_als(ctx.handle, _ptr(X), _dt(X), len(dims), d, r, sweeps, seed, prec,
+                            ip, cp, _stream(stream)))
 
 
 def tr_als_sampled_host(ctx: Context, X_host: torch.Tensor, ranks, J: int, sweeps: int,
