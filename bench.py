@@ -11,6 +11,7 @@ Poisson stream of requests (200/s) through the native server.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--serve-seconds S] [--skip-cpu] [--skip-fp64] [--skip-uniform] [--skip-dense]
+                  [--paper-protocol]
                   [--skip-batched] [--skip-configs] [--skip-serving]
 
 With N > 1 (torchrun), every rank decomposes its own tensor (replicas, weak scaling).
@@ -428,6 +429,94 @@ def run_dense(T, X, ranks, sweeps, init_dev, dims, stream, reps, sampled_value, 
                     "sampled_speedup = the headline sweeps/s / this"}
 
 
+def _tolerate_singular(T, fn, flags):
+    """Run fn; a TR_ERR_SINGULAR status (that update kept its core) is recorded, not raised."""
+    try:
+        fn()
+    except T.TrError as e:
+        if e.status != T.TR_ERR_SINGULAR:
+            raise
+        flags["singular_updates"] = True
+
+
+def _converge_dense(T, ctx, X, ranks, cores, init, flags, tol=1e-6, cap=100):
+    """Alg. 1 one sweep per call until the relative error changes by less than tol (the
+    paper's TR-ALS criterion) or cap sweeps. Returns (sweeps, error, device ms of the sweeps)."""
+    ms, prev, it = 0.0, None, 0
+    cur_init = init
+    while it < cap:
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        _tolerate_singular(T, lambda: T.tr_als(ctx, X, ranks, 1, 0, T.TR_PREC_MIXED, cores,
+                                               init_cores=cur_init), flags)
+        b.record()
+        torch.cuda.synchronize()
+        ms += a.elapsed_time(b)
+        it += 1
+        err = T.tr_rel_error(ctx, X, ranks, cores)
+        cur_init = [c.clone() for c in cores]
+        if prev is not None and abs(prev - err) < tol:
+            break
+        prev = err
+    return it, err, ms
+
+
+def _grow_j(T, ctx, X, ranks, cores, init, sweeps, target, j0, dj, flags, jcap=40000):
+    """The smallest J (j0, j0 + dj, ...) whose sampled run of `sweeps` sweeps reaches an
+    error below target. Returns (J, error, device ms of that run) or the last try."""
+    J = j0
+
+    def run():
+        T.tr_als_sampled(ctx, X, ranks, J, sweeps, 11, T.TR_PREC_MIXED, cores, init_cores=init)
+
+    while True:
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        _tolerate_singular(T, run, flags)
+        torch.cuda.synchronize()
+        a.record()
+        _tolerate_singular(T, run, flags)
+        b.record()
+        torch.cuda.synchronize()
+        err = T.tr_rel_error(ctx, X, ranks, cores)
+        if err < target or J + dj > jcap:
+            return J, err, a.elapsed_time(b)
+        J += dj
+
+
+def run_paper_protocol(T, dev):
+    """The paper's decomposition protocol (Sec. 5 and its supplement) on GB300, one seeded
+    run per case: TR-ALS until the error changes by < 1e-6 (cap 100 sweeps), then the
+    sampled method with the same number of sweeps and J grown until its error is below
+    1.2x TR-ALS's. Cases: the coherent random tensors (R' = R = 10, I = 100..500) and the
+    three oscillatory functions on 4^10 points (R = 10)."""
+    ctx = T.Context(torch.cuda.current_device())
+    out = {"what": "TR-ALS to convergence, then the smallest J (paper's increments) with the "
+                   "sampled error < 1.2x; times are device ms of the whole decomposition; one "
+                   "seeded run per case (the paper reports medians of 10)"}
+    cases = [("coherent_I%d" % I, None, I) for I in (100, 200, 300, 400, 500)]
+    cases += [("oscillatory_" + nm, nm, None) for nm in inputs.OSCILLATORY]
+    for name, fn, I in cases:
+        if fn is None:
+            X, _ = inputs.coherent_tr(I, 10, seed=I, device=dev)
+            dims, ranks, j0, dj = (I, I, I), (10, 10, 10), 200, 100
+        else:
+            X = inputs.oscillatory(fn).to(dev)
+            dims, ranks, j0, dj = (4,) * 10, (10,) * 10, 1000, 1000
+        init = [inputs.slice_major(c).to(dev) for c in inputs.random_cores(dims, ranks, 77)]
+        cores = T.empty_cores(dims, ranks, device=dev)
+        fd, fs = {}, {}
+        it, e_als, ms_als = _converge_dense(T, ctx, X, ranks, cores, init, fd)
+        J, e_s, ms_s = _grow_j(T, ctx, X, ranks, cores, init, it, 1.2 * e_als, j0, dj, fs)
+        out[name] = {"sweeps": it, "tr_als_err": e_als, "tr_als_ms": round(ms_als, 3),
+                     "J": J, "sampled_err": e_s, "sampled_ms": round(ms_s, 3),
+                     "speedup": round(ms_als / ms_s, 2),
+                     "singular_updates": {"tr_als": bool(fd), "sampled": bool(fs)}}
+        del X
+        torch.cuda.empty_cache()
+    ctx.close()
+    return out
+
+
 def _time_calls(fn, reps, stream):
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     fn()
@@ -783,6 +872,10 @@ def run_ours(args):
         config1 = run_config1(T, plain_fp64, dev, stream)
         config3 = run_config3(T, dev, stream, peaks)
 
+    protocol = None
+    if args.paper_protocol and world == 1:
+        protocol = run_paper_protocol(T, dev)
+
     serving = None
     if not args.skip_serving and world == 1 and args.serve_seconds > 0:
         serving = run_serving(T, dev, args.serve_seconds)
@@ -823,6 +916,7 @@ def run_ours(args):
             "config1_fp64_100": config1,
             "config3_cosine_4way": config3,
             "serving": serving,
+            "paper_protocol": protocol,
             "cpu_baseline": cpu,
             "clocks": clk,
         }
@@ -846,6 +940,7 @@ def main():
     ap.add_argument("--skip-batched", action="store_true")
     ap.add_argument("--skip-uniform", action="store_true")
     ap.add_argument("--skip-dense", action="store_true")
+    ap.add_argument("--paper-protocol", action="store_true")
     ap.add_argument("--skip-serving", action="store_true")
     ap.add_argument("--skip-configs", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=20.0)

@@ -110,6 +110,44 @@ def cosine_sum(dims, seed: int, terms: int = 20, noise_amp: float = 0.05, device
     return X.to(dtype)
 
 
+def coherent_tr(I: int, true_rank: int, seed: int, N: int = 3, spike: float = 20.0,
+                noise_sd: float = 0.1, device="cpu", dtype=torch.float32):
+    """The randomly generated tensors of the paper's synthetic experiments (Sec. 5): N cores
+    of size R' x I x R' with i.i.d. N(0, 1) entries, one entry of each core (chosen uniformly
+    at random) set to ``spike`` to raise the coherence of the least-squares problems, combined
+    into the full tensor, plus i.i.d. N(0, noise_sd^2) noise. Returns (X, cores)."""
+    dims, ranks = [I] * N, [true_rank] * N
+    cores = random_cores(dims, ranks, seed)
+    g = _gen(seed + 104729)
+    for c in cores:
+        pos = int(torch.randint(c.numel(), (1,), generator=g))
+        c.view(-1)[pos] = spike
+    X = _ring_tensor(cores, device, torch.float64 if dtype == torch.float64 else torch.float32)
+    if noise_sd > 0:
+        gn = torch.Generator(device=X.device)
+        gn.manual_seed(int(seed) + 15485863)
+        X.add_(torch.randn(X.shape, generator=gn, device=X.device, dtype=X.dtype), alpha=noise_sd)
+    return X.to(dtype), cores
+
+
+# The paper's highly oscillatory functions (Sec. 5), sampled on a uniform grid of I^N points
+# of the interval given here (the paper does not state the intervals; see the readings).
+OSCILLATORY = {
+    "linear_growth": (lambda x: (x + 1.0) * torch.sin(100.0 * (x + 1.0) ** 2), 0.0, 1.0),
+    "airy": (lambda x: x ** -0.25 * torch.sin(2.0 * x ** 1.5 / 3.0), 1.0, 100.0),
+    "chirp": (lambda x: torch.sin(4.0 / x) * torch.cos(x ** 2), 0.0, 1.0),
+}
+
+
+def oscillatory(name: str, N: int = 10, I: int = 4, dtype=torch.float32) -> torch.Tensor:
+    """f(x_k), k = 0 .. I^N - 1, on the uniform grid x_k = a + (b - a)(k + 1) / I^N of
+    (a, b], reshaped to an N-way I x ... x I tensor (row-major: the last mode fastest)."""
+    f, a, b = OSCILLATORY[name]
+    K = I ** N
+    x = a + (b - a) * (torch.arange(K, dtype=torch.float64) + 1.0) / K
+    return f(x).reshape([I] * N).to(dtype).contiguous()
+
+
 def random_distribution(I: int, seed: int, zero_frac: float = 0.0) -> torch.Tensor:
     """A probability vector on [I] (FP64); a fraction of entries set exactly to zero."""
     g = _gen(seed)
