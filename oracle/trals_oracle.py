@@ -33,7 +33,8 @@ __all__ = [
     "core_unfold2", "core_from_solution", "subchain_full", "subchain_unfold2",
     "leverage_scores", "core_distribution", "inverse_cdf", "draw_samples",
     "draw_samples_uniform",
-    "sampled_subchain", "sampled_fibres", "sampled_ls_normal", "sampled_ls_qr",
+    "sampled_subchain", "sampled_fibres", "sampled_ls_normal", "sampled_ls_normal_drop",
+    "sampled_ls_qr",
     "sampled_core_update", "tr_als_sampled", "tr_als_sampled_until", "tr_als", "tr_als_update",
 ]
 
@@ -296,6 +297,33 @@ def sampled_ls_normal(A, Y):
     B = A.T @ Y
     Lf = np.linalg.cholesky(M)
     return solve_triangular(Lf.T, solve_triangular(Lf, B, lower=True), lower=False)
+
+
+def sampled_ls_normal_drop(A, Y, tol_scale):
+    """argmin_Z ||A Z - Y||_F for a possibly rank-deficient A: a basic least-squares
+    solution. The normal matrix M = A^T A is factored column by column (Cholesky); a column
+    whose pivot is <= tol_scale * max diag(M) is dropped (its unknowns are set to 0 and it
+    updates nothing), the others give L L^T = M restricted to the kept columns, and the
+    kept unknowns solve L L^T Z_k = (A^T Y)_k. With every column kept this is
+    sampled_ls_normal."""
+    M = A.T @ A
+    B = A.T @ Y
+    n = M.shape[0]
+    tol = tol_scale * np.max(np.diag(M))
+    Lf = np.zeros_like(M)
+    keep = np.zeros(n, dtype=bool)
+    for k in range(n):
+        d = M[k, k] - np.dot(Lf[k, :k], Lf[k, :k])
+        if not d > tol:
+            continue
+        keep[k] = True
+        Lf[k, k] = np.sqrt(d)
+        Lf[k + 1:, k] = (M[k + 1:, k] - Lf[k + 1:, :k] @ Lf[k, :k]) / Lf[k, k]
+    Z = np.zeros_like(B)
+    Lk = Lf[np.ix_(keep, keep)]
+    if keep.any():
+        Z[keep] = solve_triangular(Lk.T, solve_triangular(Lk, B[keep], lower=True), lower=False)
+    return Z, keep
 
 
 def sampled_ls_qr(A, Y):

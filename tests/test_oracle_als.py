@@ -180,3 +180,27 @@ def test_uniform_sampling_rejects_unknown_names():
     X, init = _exact_tr((4, 4, 4), (2, 2, 2), seed=0)
     with pytest.raises(ValueError):
         orc.tr_als_sampled(X, init, J=10, sweeps=1, seed=0, sampling="importance")
+
+
+def test_ls_drop_is_the_normal_solve_when_full_rank():
+    rng = np.random.default_rng(31)
+    A = rng.standard_normal((80, 12))
+    Y = rng.standard_normal((80, 5))
+    Z, keep = orc.sampled_ls_normal_drop(A, Y, 12 * 2.220446049250313e-16)
+    assert keep.all()
+    np.testing.assert_allclose(Z, np.linalg.lstsq(A, Y, rcond=None)[0], rtol=1e-10, atol=1e-12)
+
+
+def test_ls_drop_gives_a_basic_least_squares_solution():
+    """A with a repeated column and a zero column: the dropped unknowns are 0, the residual
+    is the least-squares minimum (numpy.linalg.lstsq), and A Z equals the projection of Y."""
+    rng = np.random.default_rng(32)
+    A = rng.standard_normal((60, 8))
+    A[:, 5] = A[:, 2]
+    A[:, 7] = 0.0
+    Y = rng.standard_normal((60, 4))
+    Z, keep = orc.sampled_ls_normal_drop(A, Y, 8 * 2.220446049250313e-16)
+    assert list(np.nonzero(~keep)[0]) == [5, 7]
+    assert np.all(Z[~keep] == 0.0)
+    Zl = np.linalg.lstsq(A, Y, rcond=None)[0]
+    np.testing.assert_allclose(A @ Z, A @ Zl, rtol=0, atol=1e-10)
