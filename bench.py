@@ -490,9 +490,11 @@ def run_paper_protocol(T, dev):
     1.2x TR-ALS's. Cases: the coherent random tensors (R' = R = 10, I = 100..500) and the
     three oscillatory functions on 4^10 points (R = 10)."""
     ctx = T.Context(torch.cuda.current_device())
+    T.tr_set_ls_rank(ctx, T.TR_LS_RANK_DROP)   # basic LS solutions, as a QR-based solve gives
     out = {"what": "TR-ALS to convergence, then the smallest J (paper's increments) with the "
                    "sampled error < 1.2x; times are device ms of the whole decomposition; one "
-                   "seeded run per case (the paper reports medians of 10)"}
+                   "seeded run per case (the paper reports medians of 10); LS steps drop "
+                   "columns with small pivots (basic solutions)"}
     cases = [("coherent_I%d" % I, None, I) for I in (100, 200, 300, 400, 500)]
     cases += [("oscillatory_" + nm, nm, None) for nm in inputs.OSCILLATORY]
     for name, fn, I in cases:

@@ -226,6 +226,18 @@ tr_status tr_als_sampled_batched(tr_ctx* ctx, const tr_instance* inst, int count
                                  tr_dtype X_dtype, int sweeps, tr_precision prec,
                                  tr_stream stream);
 
+/* What the LS step (tr_solve and every driver of the context) does with a pivot of the
+ * normal matrix <= L*eps*max diag (FP64 rule; the mixed path applies it on its FP64
+ * branch):
+ * TR_LS_RANK_STOP : record TR_ERR_SINGULAR and keep the core (the default);
+ * TR_LS_RANK_DROP : drop that column -- its unknowns are 0 and it updates nothing -- and
+ *                   solve for the rest: a basic least-squares solution of a rank-deficient
+ *                   design, as a QR-based solve returns (the paper's LS step is QR-based).
+ * Other values return TR_ERR_INVALID_ARG. */
+typedef enum tr_ls_rank { TR_LS_RANK_STOP = 0, TR_LS_RANK_DROP = 1 } tr_ls_rank;
+tr_status tr_set_ls_rank(tr_ctx* ctx, tr_ls_rank rule);
+tr_status tr_get_ls_rank(const tr_ctx* ctx, tr_ls_rank* rule);
+
 /* Sampling of the context's driver calls (a context starts with TR_SAMPLING_LEVERAGE).
  * Other values return TR_ERR_INVALID_ARG. */
 tr_status tr_set_sampling(tr_ctx* ctx, tr_sampling sampling);

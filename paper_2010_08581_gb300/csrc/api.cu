@@ -47,6 +47,7 @@ struct tr_ctx {
   std::vector<trk::BInst> btab;     // host copy of the instance table
   tr_batched_tiles tiles{4, 64};    // launch shapes of the batched kernels
   tr_sampling sampling = TR_SAMPLING_LEVERAGE;   // draws of tr_als_sampled / batched
+  tr_ls_rank ls_rank = TR_LS_RANK_STOP;          // rule for small pivots of the LS step
 };
 
 namespace {
@@ -327,17 +328,18 @@ tr_status solve_contract(tr_ctx* ctx, const SolvePlan& s, const void* A, const v
 
 tr_status solve_cholesky(tr_ctx* ctx, const SolvePlan& s, bool f64, int L, cudaStream_t st) {
   const double eps = 2.220446049250313e-16;
+  const int mode = ctx->ls_rank == TR_LS_RANK_DROP ? 1 : 0;
   if (!f64) {
     const double eps32 = 1.1920928955078125e-07;
     TR_LAUNCH("cholesky_solve",
-              launch_cholesky_mixed(s.M, L, static_cast<double>(L) * eps,
+              launch_cholesky_mixed(s.M, L, mode, static_cast<double>(L) * eps,
                                     static_cast<double>(L) * eps32, s.Lrow, s.Lcol, s.invdiag,
                                     s.keep, s.info, ctx->d_err, st, static_cast<float*>(s.limg),
                                     s.mimg));
     return TR_OK;
   }
   TR_LAUNCH("cholesky_solve",
-            launch_cholesky(s.M, L, 0, static_cast<double>(L) * eps, s.Lrow, s.Lcol, s.invdiag,
+            launch_cholesky(s.M, L, mode, static_cast<double>(L) * eps, s.Lrow, s.Lcol, s.invdiag,
                             s.keep, s.info, ctx->d_err, st, static_cast<double*>(s.limg),
                             nullptr, nullptr));
   return TR_OK;
@@ -566,6 +568,7 @@ std::vector<uint64_t> als_key(const tr_ctx* ctx, const AlsPlan& P) {
   u(reinterpret_cast<uintptr_t>(ctx->arena));
   u(ctx->arena_bytes);
   u(static_cast<uint64_t>(ctx->sampling));
+  u(static_cast<uint64_t>(ctx->ls_rank));
   return k;
 }
 
@@ -782,6 +785,21 @@ tr_status tr_set_sampling(tr_ctx* ctx, tr_sampling sampling) {
     return fail(ctx, TR_ERR_INVALID_ARG, "sampling=%d is not a tr_sampling value",
                 static_cast<int>(sampling));
   ctx->sampling = sampling;
+  return TR_OK;
+}
+
+tr_status tr_set_ls_rank(tr_ctx* ctx, tr_ls_rank rule) {
+  TR_TRY(check_ctx(ctx));
+  if (rule != TR_LS_RANK_STOP && rule != TR_LS_RANK_DROP)
+    return fail(ctx, TR_ERR_INVALID_ARG, "ls rank rule=%d is not a tr_ls_rank value",
+                static_cast<int>(rule));
+  ctx->ls_rank = rule;
+  return TR_OK;
+}
+
+tr_status tr_get_ls_rank(const tr_ctx* ctx, tr_ls_rank* rule) {
+  if (!ctx || !rule) return TR_ERR_INVALID_ARG;
+  *rule = ctx->ls_rank;
   return TR_OK;
 }
 
@@ -1087,6 +1105,7 @@ tr_status tr_als_sampled_batched(tr_ctx* ctx, const tr_instance* inst, int count
   bl.spw = ctx->tiles.samples_per_warp;
   bl.ctile = ctx->tiles.contract_tile;
   bl.leverage = ctx->sampling == TR_SAMPLING_LEVERAGE;
+  bl.ls_mode = ctx->ls_rank == TR_LS_RANK_DROP ? 1 : 0;
   int nmax_modes = 0, steps = 0;
   bool draw = false;
   for (int i = 0; i < count; ++i) {
@@ -1134,7 +1153,8 @@ tr_status tr_als_sampled_batched(tr_ctx* ctx, const tr_instance* inst, int count
                                  static_cast<uint64_t>(draw), reinterpret_cast<uintptr_t>(dtab),
                                  static_cast<uint64_t>(ctx->prof),
                                  static_cast<uint64_t>(bl.spw), static_cast<uint64_t>(bl.ctile),
-                                 static_cast<uint64_t>(bl.leverage)};
+                                 static_cast<uint64_t>(bl.leverage),
+                                 static_cast<uint64_t>(bl.ls_mode)};
     if (!ctx->bexec || key != ctx->bkey) {
       if (ctx->bexec) cudaGraphExecDestroy(ctx->bexec);
       ctx->bexec = nullptr;

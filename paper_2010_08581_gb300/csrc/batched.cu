@@ -307,7 +307,7 @@ __global__ void __launch_bounds__(GNT) kb_gram(const BInst* __restrict__ tab, in
 // ------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(CNT) kb_cholesky(const BInst* __restrict__ tab, int step,
                                                    int init_k, int which, unsigned* err,
-                                                   int smem_bytes, int mixed) {
+                                                   int smem_bytes, int mixed, int ls_mode) {
   extern __shared__ double smem[];
   const BInst& d = tab[blockIdx.x];
   const Cur cu = current(d, step, init_k, which != 0);
@@ -321,14 +321,14 @@ __global__ void __launch_bounds__(CNT) kb_cholesky(const BInst* __restrict__ tab
     if (mixed) {
       float* A32 = (nn * 4 <= smem_bytes) ? reinterpret_cast<float*>(smem)
                                           : reinterpret_cast<float*>(d.Lrow);
-      cholesky_cta_mixed<float>(d.M, n, 0, static_cast<double>(n) * eps,
+      cholesky_cta_mixed<float>(d.M, n, ls_mode, static_cast<double>(n) * eps,
                                 static_cast<double>(n) * eps32, A32, A, d.Lrow, d.Lcol,
                                 d.invdiag, d.keep, d.info, err, static_cast<float*>(d.limg),
                                 d.mimg);
       return;
     }
-    cholesky_cta(d.M, n, 0, static_cast<double>(n) * eps, A, d.Lrow, d.Lcol, d.invdiag, d.keep,
-                 d.info, err, static_cast<double*>(d.limg), nullptr, nullptr);
+    cholesky_cta(d.M, n, ls_mode, static_cast<double>(n) * eps, A, d.Lrow, d.Lcol, d.invdiag,
+                 d.keep, d.info, err, static_cast<double*>(d.limg), nullptr, nullptr);
     return;
   }
   const double tol = static_cast<double>(cu.I > cu.L ? cu.I : cu.L) * eps;
@@ -624,7 +624,8 @@ cudaError_t bl_cholesky(const BLaunch& b, int step, int init_k, int which, unsig
   const int nmax = which == 0 ? b.Lmax : (which == 1 ? b.n1max : b.n2max);
   if (nmax <= 0) return cudaSuccess;
   const int dyn = smem_for_cholesky(nmax);
-  kb_cholesky<<<b.count, CNT, dyn, st>>>(b.tab, step, init_k, which, err, dyn, b.f64 ? 0 : 1);
+  kb_cholesky<<<b.count, CNT, dyn, st>>>(b.tab, step, init_k, which, err, dyn, b.f64 ? 0 : 1,
+                                          b.ls_mode);
   return cudaGetLastError();
 }
 

@@ -97,6 +97,7 @@ struct BLaunch {
   int ctile = 64;                // output tile of the normal-equation contraction, 64 or 32
   bool leverage = true;          // some instance samples by leverage scores (else the
                                  // distribution stages are not launched at all)
+  int ls_mode = 0;               // small LS pivots: 0 stop (singular), 1 drop the column
 };
 
 cudaError_t bl_init_cores(const BLaunch& b, cudaStream_t st);

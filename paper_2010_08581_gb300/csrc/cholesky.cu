@@ -64,13 +64,13 @@ cudaError_t launch_cholesky_lev_mixed(const double* G, int n, double tol64, doub
   return cudaGetLastError();
 }
 
-cudaError_t launch_cholesky_mixed(const double* G, int n, double tol64, double tol32,
+cudaError_t launch_cholesky_mixed(const double* G, int n, int mode, double tol64, double tol32,
                                   double* Lrow, double* Lcol, double* invdiag, int* keep,
                                   int* info, unsigned* err, cudaStream_t st, float* img32,
                                   float* gimg32) {
   const size_t nn = static_cast<size_t>(n) * n;
   const size_t dyn = nn * 8 <= kCholDyn ? nn * 8 : (nn * 4 <= kCholDyn ? nn * 4 : 0);
-  k_cholesky_mixed<float><<<1, CNT, dyn, st>>>(G, n, 0, tol64, tol32, Lrow, Lcol, invdiag, keep,
+  k_cholesky_mixed<float><<<1, CNT, dyn, st>>>(G, n, mode, tol64, tol32, Lrow, Lcol, invdiag, keep,
                                                info, err, static_cast<int>(dyn), img32, gimg32);
   return cudaGetLastError();
 }

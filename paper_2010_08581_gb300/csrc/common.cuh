@@ -131,8 +131,8 @@ cudaError_t launch_reduce(const void* partial, bool partial_f32, int splits, int
 // (buffers of trsm_image_bytes(n, ...) bytes).
 // Mixed-precision LS step: an FP32 factor when every pivot > tol32 * max diag, written as the
 // FP32 image img32 + invdiag + keep + info; otherwise the FP64 factorisation with tol64
-// (as launch_cholesky, mode 0).
-cudaError_t launch_cholesky_mixed(const double* G, int n, double tol64, double tol32,
+// and the mode's rule (as launch_cholesky: 0 stops, 1 drops the column).
+cudaError_t launch_cholesky_mixed(const double* G, int n, int mode, double tol64, double tol32,
                                   double* Lrow, double* Lcol, double* invdiag, int* keep,
                                   int* info, unsigned* err, cudaStream_t st, float* img32,
                                   float* gimg32);

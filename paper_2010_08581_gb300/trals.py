@@ -22,6 +22,7 @@ TR_OK, TR_ERR_INVALID_ARG, TR_ERR_OOM, TR_ERR_BUDGET, TR_ERR_SINGULAR, TR_ERR_TI
 TR_F32, TR_F64 = 0, 1
 TR_PREC_FP64, TR_PREC_MIXED = 0, 1
 TR_SAMPLING_LEVERAGE, TR_SAMPLING_UNIFORM = 0, 1
+TR_LS_RANK_STOP, TR_LS_RANK_DROP = 0, 1
 
 _STATUS_NAMES = ["TR_OK", "TR_ERR_INVALID_ARG", "TR_ERR_OOM", "TR_ERR_BUDGET",
                  "TR_ERR_SINGULAR", "TR_ERR_TIMEOUT", "TR_ERR_CUDA", "TR_ERR_NOT_CONVERGED"]
@@ -113,6 +114,8 @@ SIGNATURES = {
                                        c_int, c_vp]),
     "tr_solve_noalloc": (c_int, [c_vp, c_vp, c_int, c_i64, c_int, c_int, c_i64, c_int, c_vp,
                                  c_vp, c_vp]),
+    "tr_set_ls_rank": (c_int, [c_vp, c_int]),
+    "tr_get_ls_rank": (c_int, [c_vp, PI]),
     "tr_set_sampling": (c_int, [c_vp, c_int]),
     "tr_get_sampling": (c_int, [c_vp, PI]),
     "tr_set_batched_tiles": (c_int, [c_vp, ctypes.POINTER(TrBatchedTiles)]),
@@ -258,6 +261,17 @@ def tr_sample_uniform(ctx: Context, k: int, dims, J: int, seed: int, update_id: 
 def tr_set_sampling(ctx: Context, sampling: int):
     """TR_SAMPLING_LEVERAGE or TR_SAMPLING_UNIFORM for the context's driver calls."""
     ctx.check(load().tr_set_sampling(ctx.handle, int(sampling)))
+
+
+def tr_set_ls_rank(ctx: Context, rule: int):
+    """TR_LS_RANK_STOP (default) or TR_LS_RANK_DROP for the context's LS steps."""
+    ctx.check(load().tr_set_ls_rank(ctx.handle, int(rule)))
+
+
+def tr_get_ls_rank(ctx: Context) -> int:
+    v = c_int()
+    ctx.check(load().tr_get_ls_rank(ctx.handle, ctypes.byref(v)))
+    return int(v.value)
 
 
 def tr_get_sampling(ctx: Context) -> int:
