@@ -168,6 +168,16 @@ tr_status tr_als_sampled(tr_ctx* ctx, const void* X, tr_dtype X_dtype, int N,
                          uint64_t seed, tr_precision prec, const double* const* init_cores,
                          double* const* cores, tr_stream stream);
 
+/* tr_als_sampled with one sample size per sweep (Sec. 4.2: J can be changed at any point
+ * at no cost): sweep s draws J_per_sweep[s] samples per update (host array of `sweeps`
+ * entries, each in [1, 2^31-1]); the workspace is sized for the largest. Everything else
+ * as tr_als_sampled. */
+tr_status tr_als_sampled_schedule(tr_ctx* ctx, const void* X, tr_dtype X_dtype, int N,
+                                  const int64_t* dims, const int* ranks,
+                                  const int64_t* J_per_sweep, int sweeps, uint64_t seed,
+                                  tr_precision prec, const double* const* init_cores,
+                                  double* const* cores, tr_stream stream);
+
 /* Dense TR-ALS (Alg. 1), the comparison method of Sec. 5, with a fixed number of sweeps,
  * synchronous. Core update n solves the full least-squares problem
  * argmin_Z || G_[2]^{!=n} Z - X_[n]^T ||_F over all prod_{j!=n} I_j rows, each with weight 1
@@ -233,6 +243,8 @@ tr_status tr_als_sampled_batched(tr_ctx* ctx, const tr_instance* inst, int count
  * TR_LS_RANK_DROP : drop that column -- its unknowns are 0 and it updates nothing -- and
  *                   solve for the rest: a basic least-squares solution of a rank-deficient
  *                   design, as a QR-based solve returns (the paper's LS step is QR-based).
+ *                   TR_PREC_MIXED drops at L*eps32*max diag, the resolution of its FP32
+ *                   triangular solves.
  * Other values return TR_ERR_INVALID_ARG. */
 typedef enum tr_ls_rank { TR_LS_RANK_STOP = 0, TR_LS_RANK_DROP = 1 } tr_ls_rank;
 tr_status tr_set_ls_rank(tr_ctx* ctx, tr_ls_rank rule);

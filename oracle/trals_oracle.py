@@ -373,20 +373,33 @@ def _sweep(X, cores, ps, cdfs, J, seed, s, solver, sampling="leverage"):
             ps[n], cdfs[n] = core_distribution(cores[n])
 
 
+def _sweep_sizes(J, sweeps):
+    """J as one sample size for every sweep, or a per-sweep schedule (Sec. 4.2: the sample
+    size can change between updates at no cost)."""
+    if np.ndim(J) == 0:
+        return [int(J)] * sweeps
+    Js = [int(j) for j in J]
+    if len(Js) != sweeps:
+        raise ValueError("a J schedule needs one entry per sweep")
+    return Js
+
+
 def tr_als_sampled(X, init_cores, J, sweeps, seed, solver="qr", callback=None,
                    sampling="leverage"):
     """TR-ALS-Sampled (Alg. 2) with a fixed number of sweeps. ``init_cores`` supplies
-    G^(2..N) (paper numbering); core 0 is overwritten by its first update.
+    G^(2..N) (paper numbering); core 0 is overwritten by its first update. ``J`` is the
+    sample size of every update, or a list with one sample size per sweep (Sec. 4.2).
     The sample block of (sweep s, core n) uses update_id = s * N + n. ``sampling`` is
     "leverage" (Alg. 2 as stated) or "uniform" (the Sec. 5 variant: uniform draws, no
     distributions)."""
     if sampling not in ("leverage", "uniform"):
         raise ValueError(f"unknown sampling {sampling!r}")
+    Js = _sweep_sizes(J, sweeps)
     X = np.asarray(X, dtype=np.float64)
     cores = [np.array(G, dtype=np.float64, copy=True) for G in init_cores]
     ps, cdfs = _initial_distributions(cores, sampling)
     for s in range(sweeps):
-        _sweep(X, cores, ps, cdfs, J, seed, s, solver, sampling)
+        _sweep(X, cores, ps, cdfs, Js[s], seed, s, solver, sampling)
         if callback is not None:
             callback(s, cores)
     return cores

@@ -441,6 +441,8 @@ tr_status read_device_error(tr_ctx* ctx, cudaStream_t st) {
 struct AlsPlan {
   const void* X; tr_dtype xdt; int N; const int64_t* dims; const int* ranks; int64_t J;
   int sweeps; tr_precision prec; const double* const* init; double* const* cores;
+  const int64_t* Js = nullptr;   // per-sweep sample sizes (Sec. 4.2), or null: J for all;
+                                 // J is then their maximum (workspace)
   std::vector<double*> p, cdf;
   int32_t* idx; double* w; void* A; void* Y; char* ws;
   size_t solve_ws;   // bytes of the stage region used by the LS step; leverage follows it
@@ -538,11 +540,12 @@ tr_status als_issue(tr_ctx* ctx, const AlsPlan& P, uint64_t seed, const uint64_t
       ga.In = dims[n];
       ga.stride_n = stride[n];
       const uint64_t uid = static_cast<uint64_t>(s) * N + n;
-      TR_LAUNCH("sample_chain", launch_sample_chain(sa, ca, P.J, seed, uid, P.idx, P.w, P.A, f64,
+      const int64_t Jn = P.Js ? P.Js[s] : P.J;
+      TR_LAUNCH("sample_chain", launch_sample_chain(sa, ca, Jn, seed, uid, P.idx, P.w, P.A, f64,
                                                     st));
-      TR_LAUNCH("gather", launch_gather(ga, P.X, x64, P.idx, P.w, P.J, P.Y, f64, ctx->d_err, st));
+      TR_LAUNCH("gather", launch_gather(ga, P.X, x64, P.idx, P.w, Jn, P.Y, f64, ctx->d_err, st));
       const int Rl = rl_of(ranks, N, n), Rr = ranks[n];
-      TR_TRY(update_run(ctx, P.ws, P.solve_ws, P.A, P.Y, f64, P.J, Rl, Rr, dims[n], P.cores[n],
+      TR_TRY(update_run(ctx, P.ws, P.solve_ws, P.A, P.Y, f64, Jn, Rl, Rr, dims[n], P.cores[n],
                         uni ? nullptr : P.p[n], uni ? nullptr : P.cdf[n], st, side));
     }
   }
@@ -562,6 +565,8 @@ std::vector<uint64_t> als_key(const tr_ctx* ctx, const AlsPlan& P) {
     u(P.init ? reinterpret_cast<uintptr_t>(P.init[i]) : 0);
   }
   u(static_cast<uint64_t>(P.J));
+  if (P.Js)
+    for (int s = 0; s < P.sweeps; ++s) u(static_cast<uint64_t>(P.Js[s]));
   u(static_cast<uint64_t>(P.sweeps));
   u(P.prec);
   u(P.init ? 1 : 0);
@@ -929,6 +934,30 @@ tr_status tr_als_sampled(tr_ctx* ctx, const void* X, tr_dtype X_dtype, int N, co
   tr_status s = read_device_error(ctx, S(stream));
   TR_TRY(fold_graph_marks(ctx));
   return s;
+}
+
+tr_status tr_als_sampled_schedule(tr_ctx* ctx, const void* X, tr_dtype X_dtype, int N,
+                                  const int64_t* dims, const int* ranks,
+                                  const int64_t* J_per_sweep, int sweeps, uint64_t seed,
+                                  tr_precision prec, const double* const* init_cores,
+                                  double* const* cores, tr_stream stream) {
+  TR_TRY(check_ctx(ctx));
+  if (!J_per_sweep && sweeps > 0) return fail(ctx, TR_ERR_INVALID_ARG, "J_per_sweep is NULL");
+  int64_t Jmax = 1;
+  for (int s = 0; s < sweeps; ++s) {
+    if (J_per_sweep[s] < 1 || J_per_sweep[s] > INT32_MAX)
+      return fail(ctx, TR_ERR_INVALID_ARG, "J_per_sweep[%d]=%lld", s,
+                  static_cast<long long>(J_per_sweep[s]));
+    Jmax = J_per_sweep[s] > Jmax ? J_per_sweep[s] : Jmax;
+  }
+  TR_TRY(check_als(ctx, X, X_dtype, N, dims, ranks, Jmax, sweeps, prec, cores, init_cores));
+  DeviceGuard g(ctx->device);
+  AlsPlan P{X, X_dtype, N, dims, ranks, Jmax, sweeps, prec, init_cores, cores};
+  P.Js = J_per_sweep;
+  TR_TRY(als_run(ctx, P, seed, S(stream)));
+  tr_status st = read_device_error(ctx, S(stream));
+  TR_TRY(fold_graph_marks(ctx));
+  return st;
 }
 
 tr_status tr_als(tr_ctx* ctx, const void* X, tr_dtype X_dtype, int N, const int64_t* dims,

@@ -432,7 +432,8 @@ __device__ __forceinline__ bool cholesky_panel(const double* __restrict__ G, int
 // FP32 first, FP64 if needed: the factorisation of the mixed-precision LS step's normal
 // matrix (mode 0, image TI = float). The FP32 attempt accepts the factor only if every pivot
 // exceeds tol32 * max diag (so it never drops a column); otherwise the same matrix is factored
-// in FP64 with tol64 and the mode's rule. A32 and A64 are the work arrays (they may alias).
+// in FP64 with the mode's rule: mode 0 stops at tol64, mode 1 drops columns at tol32 (the
+// resolution of the FP32 solves that follow). A32 and A64 are the work arrays (they may alias).
 // Lrow/Lcol receive the FP64 factor only on the FP64 branch. (The sampling distributions keep
 // their FP64 factorisation: FP32 rounding in p would change which indices the inverse CDF
 // draws.)
@@ -453,8 +454,10 @@ __device__ __forceinline__ void cholesky_cta_mixed(const double* __restrict__ G,
     return;
   }
   __syncthreads();
-  cholesky_cta<double>(G, n, mode, tol64, A64, Lrow, Lcol, invdiag, keep_out, info, err, img64,
-                       img32, gimg32, true);
+  // Dropping (mode 1) keeps only columns the FP32 triangular solves can resolve: the FP32
+  // tolerance. Stopping (mode 0) applies the FP64 rule.
+  cholesky_cta<double>(G, n, mode, mode == 1 ? tol32 : tol64, A64, Lrow, Lcol, invdiag,
+                       keep_out, info, err, img64, img32, gimg32, true);
 }
 
 // The mixed-precision drivers' leverage Gram of a tall matrix (mode 1): double-float first,

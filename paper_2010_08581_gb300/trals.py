@@ -105,6 +105,8 @@ SIGNATURES = {
     "tr_als_sampled": (c_int, [c_vp, c_vp, c_int, c_int, P64, PI, c_i64, c_int, c_u64, c_int,
                                PP, PP, c_vp]),
     "tr_als": (c_int, [c_vp, c_vp, c_int, c_int, P64, PI, c_int, c_u64, c_int, PP, PP, c_vp]),
+    "tr_als_sampled_schedule": (c_int, [c_vp, c_vp, c_int, c_int, P64, PI, P64, c_int, c_u64,
+                                        c_int, PP, PP, c_vp]),
     "tr_als_sampled_host": (c_int, [c_vp, c_vp, c_int, c_int, P64, PI, c_i64, c_int, c_u64,
                                     c_int, PP, PP, c_vp]),
     "tr_rel_error": (c_int, [c_vp, c_vp, c_int, c_int, P64, PI, PP, ctypes.POINTER(c_dbl),
@@ -326,9 +328,10 @@ def tr_init_cores(ctx: Context, dims, ranks, seed: int, k_begin: int, cores, str
                                    _stream(stream)))
 
 
-def tr_als_sampled(ctx: Context, X: torch.Tensor, ranks, J: int, sweeps: int, seed: int,
+def tr_als_sampled(ctx: Context, X: torch.Tensor, ranks, J, sweeps: int, seed: int,
                    prec: int, cores: List[torch.Tensor],
                    init_cores: Optional[List[Optional[torch.Tensor]]] = None, stream=None):
+    """J: one sample size, or a list with one per sweep (tr_als_sampled_schedule)."""
     dims = list(X.shape)
     d, _d = _i64s(dims)
     r, _r = _ints(ranks)
@@ -337,6 +340,12 @@ def tr_als_sampled(ctx: Context, X: torch.Tensor, ranks, J: int, sweeps: int, se
         ip, _i = _ptrs(init_cores)
     else:
         ip = ctypes.cast(c_vp(None), PP)
+    if isinstance(J, (list, tuple)):
+        js, _j = _i64s(J)
+        ctx.check(load().tr_als_sampled_schedule(ctx.handle, _ptr(X), _dt(X), len(dims), d, r,
+                                                 js, sweeps, seed, prec, ip, cp,
+                                                 _stream(stream)))
+        return
     ctx.check(load().tr_als_sampled(ctx.handle, _ptr(X), _dt(X), len(dims), d, r, J, sweeps,
                                     seed, prec, ip, cp, _stream(stream)))
 

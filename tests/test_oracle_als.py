@@ -204,3 +204,21 @@ def test_ls_drop_gives_a_basic_least_squares_solution():
     assert np.all(Z[~keep] == 0.0)
     Zl = np.linalg.lstsq(A, Y, rcond=None)[0]
     np.testing.assert_allclose(A @ Z, A @ Zl, rtol=0, atol=1e-10)
+
+
+def test_j_schedule():
+    """A constant schedule is the scalar J; sweep s of a schedule draws J_s samples per update
+    (the first sweep of a schedule equals a one-sweep run with J_0)."""
+    X, init = _exact_tr((6, 7, 8), (2, 2, 2), seed=0)
+    a = orc.tr_als_sampled(X, init, 40, 2, seed=3)
+    b = orc.tr_als_sampled(X, init, [40, 40], 2, seed=3)
+    for x, y in zip(a, b):
+        np.testing.assert_array_equal(x, y)
+    seen = []
+    orc.tr_als_sampled(X, init, [30, 50], 2, seed=3, callback=lambda s, c: seen.append(
+        [cc.copy() for cc in c]))
+    first = orc.tr_als_sampled(X, init, 30, 1, seed=3)
+    for x, y in zip(seen[0], first):
+        np.testing.assert_array_equal(x, y)
+    with pytest.raises(ValueError):
+        orc.tr_als_sampled(X, init, [30], 2, seed=3)
