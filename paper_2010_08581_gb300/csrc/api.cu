@@ -198,14 +198,25 @@ tr_status run_pass(tr_ctx* ctx, const LevPass& p, const double* A, int64_t rows,
                    bool mixed = false) {
   const int n = trans ? static_cast<int>(rows) : cols;
   TR_LAUNCH("gram_f64", launch_gram(A, rows, cols, lda, trans, p.partial, p.splits, st));
+  // the mixed tall pass: the reduction also writes the double-float planes of the Gram in
+  // the factorisation's work-array layout (into Lrow / Lcol, free until the factor's tail)
+  ReduceSplit sp;
+  const bool presplit = mixed && n >= 4 && n <= 160;
+  if (presplit) {
+    sp.hi = reinterpret_cast<float*>(p.Lrow);
+    sp.lo = reinterpret_cast<float*>(p.Lcol);
+    sp.lda = (n + 3) & ~3;
+  }
   TR_LAUNCH("reduce_gram", launch_reduce(p.partial, false, p.splits, static_cast<int64_t>(n) * n,
-                                         n, n, n, n, p.G, n, nullptr, 0, st));
+                                         n, n, n, n, p.G, n, nullptr, 0, st, sp));
   if (mixed) {
     const double eps = 2.220446049250313e-16, eps_ff = 9.094947017729282e-13;   // 2^-40
     TR_LAUNCH("cholesky_leverage",
               launch_cholesky_lev_mixed(p.G, n, tol_scale, tol_scale / eps * eps_ff, p.Lrow,
                                         p.Lcol, p.invdiag, p.keep, p.info, ctx->d_err, st,
-                                        p.img));
+                                        p.img, presplit ? sp.hi : nullptr,
+                                        presplit ? sp.lo : nullptr));
+    TR_LAUNCH("ff_image", launch_ff_image(p.Lrow, p.Lcol, n, p.info, p.img, st));
     return TR_OK;
   }
   TR_LAUNCH("cholesky_leverage", launch_cholesky(p.G, n, 1, tol_scale, p.Lrow, p.Lcol,
@@ -321,8 +332,17 @@ tr_status solve_contract(tr_ctx* ctx, const SolvePlan& s, const void* A, const v
   } else {
     TR_LAUNCH("normal_eq", launch_normal_eq(A, Y, f64, J, L, I, s.partial, s.splits, st));
   }
+  // mixed: the reduction also writes M's FP32 values in the factorisation's work-array
+  // layout (into Lrow, free until an FP64 fallback) and M's FP32 image
+  ReduceSplit sp;
+  if (!f64 && L >= 4 && L <= 160) {
+    sp.hi = reinterpret_cast<float*>(s.Lrow);
+    sp.lda = (L + 3) & ~3;
+    sp.img = s.mimg;
+    sp.np = L + 1;
+  }
   TR_LAUNCH("reduce_MB", launch_reduce(s.partial, !f64, s.splits, L * ld, ld, L, ld, L, s.M, L,
-                                       s.BT, L, st));
+                                       s.BT, L, st, sp));
   return TR_OK;
 }
 
@@ -335,7 +355,9 @@ tr_status solve_cholesky(tr_ctx* ctx, const SolvePlan& s, bool f64, int L, cudaS
               launch_cholesky_mixed(s.M, L, mode, static_cast<double>(L) * eps,
                                     static_cast<double>(L) * eps32, s.Lrow, s.Lcol, s.invdiag,
                                     s.keep, s.info, ctx->d_err, st, static_cast<float*>(s.limg),
-                                    s.mimg));
+                                    s.mimg,
+                                    L >= 4 && L <= 160 ? reinterpret_cast<float*>(s.Lrow)
+                                                       : nullptr));
     return TR_OK;
   }
   TR_LAUNCH("cholesky_solve",

@@ -355,6 +355,22 @@ __global__ void __launch_bounds__(CNT) kb_cholesky(const BInst* __restrict__ tab
                nullptr, nullptr);
 }
 
+// The FP64 image of a double-float leverage factor from the FP32 planes the factorisation
+// left in L1row / L1col (*info1 == 2; tall mixed instances only).
+__global__ void __launch_bounds__(256) kb_ff_image(const BInst* __restrict__ tab, int step,
+                                                   int init_k) {
+  const BInst& d = tab[blockIdx.x];
+  const Cur cu = current(d, step, init_k, true);
+  if (!cu.active || cu.I < cu.L || *d.info1 != 2) return;
+  const int n = cu.L;
+  const int64_t count = static_cast<int64_t>(n) * (n + 1);
+  const float* hi = reinterpret_cast<const float*>(d.L1row);
+  const float* lo = reinterpret_cast<const float*>(d.L1col);
+  for (int64_t e = static_cast<int64_t>(blockIdx.y) * blockDim.x + threadIdx.x; e < count;
+       e += static_cast<int64_t>(gridDim.y) * blockDim.x)
+    d.img1[e] = static_cast<double>(hi[e]) + static_cast<double>(lo[e]);
+}
+
 // ------------------------------------------------------------------------------------
 // Triangular solves: the LS solve (mode 2 mixed / mode 1 FP64) writing the new core, and
 // the leverage rows with the fused p / CDF step.
@@ -626,6 +642,12 @@ cudaError_t bl_cholesky(const BLaunch& b, int step, int init_k, int which, unsig
   const int dyn = smem_for_cholesky(nmax);
   kb_cholesky<<<b.count, CNT, dyn, st>>>(b.tab, step, init_k, which, err, dyn, b.f64 ? 0 : 1,
                                           b.ls_mode);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || which != 1 || b.f64) return e;
+  // double-float leverage factors leave FP32 planes: their FP64 image
+  const int64_t count = static_cast<int64_t>(nmax) * (nmax + 1);
+  dim3 grid(b.count, static_cast<unsigned>((count + 255) / 256 < 16 ? (count + 255) / 256 : 16));
+  kb_ff_image<<<grid, 256, 0, st>>>(b.tab, step, init_k);
   return cudaGetLastError();
 }
 

@@ -26,13 +26,14 @@ __global__ void __launch_bounds__(CNT) k_cholesky_mixed(const double* __restrict
                                                         double* Lrow, double* Lcol,
                                                         double* invdiag, int* keep_out,
                                                         int* info, unsigned* err, int dyn_bytes,
-                                                        TI* img, float* gimg32) {
+                                                        TI* img, float* gimg32,
+                                                        const float* pre) {
   extern __shared__ double smem[];
   const int64_t nn = static_cast<int64_t>(n) * n;
   float* A32 = nn * 4 <= dyn_bytes ? reinterpret_cast<float*>(smem) : reinterpret_cast<float*>(Lrow);
   double* A64 = nn * 8 <= dyn_bytes ? smem : Lrow;
   cholesky_cta_mixed<TI>(G, n, mode, tol64, tol32, A32, A64, Lrow, Lcol, invdiag, keep_out, info,
-                         err, img, gimg32);
+                         err, img, gimg32, A32 == reinterpret_cast<float*>(smem) ? pre : nullptr);
 }
 
 // The mixed-precision drivers' leverage Gram (tall, mode 1): double-float, FP64 if needed.
@@ -41,37 +42,61 @@ __global__ void __launch_bounds__(CNT) k_cholesky_lev_mixed(const double* __rest
                                                             double* Lrow, double* Lcol,
                                                             double* invdiag, int* keep_out,
                                                             int* info, unsigned* err,
-                                                            int dyn_bytes, double* img64) {
+                                                            int dyn_bytes, double* img64,
+                                                            const float* pre_hi,
+                                                            const float* pre_lo) {
   extern __shared__ double smem[];
   const int64_t nn = static_cast<int64_t>(n) * n;
   float* Aff = panel_floats<FFOps>(n) * 4 <= dyn_bytes ? reinterpret_cast<float*>(smem) : nullptr;
   double* A64 = nn * 8 <= dyn_bytes ? smem : Lrow;
   cholesky_cta_lev_mixed(G, n, tol64, tolff, Aff, A64, Lrow, Lcol, invdiag, keep_out, info, err,
-                         img64);
+                         img64, pre_hi, pre_lo);
+}
+
+// img64 = hi + lo from the two FP32 planes when the factorisation left them (*info == 2).
+__global__ void __launch_bounds__(256) k_ff_image(const float* __restrict__ hi,
+                                                  const float* __restrict__ lo, int64_t count,
+                                                  const int* __restrict__ info,
+                                                  double* __restrict__ img64) {
+  if (*info != 2) return;
+  for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < count;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    img64[e] = static_cast<double>(hi[e]) + static_cast<double>(lo[e]);
 }
 
 }  // namespace
 
+cudaError_t launch_ff_image(const double* Lrow, const double* Lcol, int n, const int* info,
+                            double* img64, cudaStream_t st) {
+  const int64_t count = static_cast<int64_t>(n) * (n + 1);
+  const unsigned blocks = static_cast<unsigned>((count + 255) / 256 < 152 ? (count + 255) / 256 : 152);
+  k_ff_image<<<blocks, 256, 0, st>>>(reinterpret_cast<const float*>(Lrow),
+                                     reinterpret_cast<const float*>(Lcol), count, info, img64);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_cholesky_lev_mixed(const double* G, int n, double tol64, double tolff,
                                       double* Lrow, double* Lcol, double* invdiag, int* keep,
-                                      int* info, unsigned* err, cudaStream_t st, double* img64) {
+                                      int* info, unsigned* err, cudaStream_t st, double* img64,
+                                      const float* pre_hi, const float* pre_lo) {
   const size_t nn = static_cast<size_t>(n) * n;
   const size_t ff = static_cast<size_t>(panel_floats<FFOps>(n)) * 4;
   const size_t want = nn * 8 > ff ? nn * 8 : ff;
   const size_t dyn = want <= kCholDyn ? want : (nn * 8 <= kCholDyn ? nn * 8 : 0);
   k_cholesky_lev_mixed<<<1, CNT, dyn, st>>>(G, n, tol64, tolff, Lrow, Lcol, invdiag, keep, info,
-                                            err, static_cast<int>(dyn), img64);
+                                            err, static_cast<int>(dyn), img64, pre_hi, pre_lo);
   return cudaGetLastError();
 }
 
 cudaError_t launch_cholesky_mixed(const double* G, int n, int mode, double tol64, double tol32,
                                   double* Lrow, double* Lcol, double* invdiag, int* keep,
                                   int* info, unsigned* err, cudaStream_t st, float* img32,
-                                  float* gimg32) {
+                                  float* gimg32, const float* pre) {
   const size_t nn = static_cast<size_t>(n) * n;
   const size_t dyn = nn * 8 <= kCholDyn ? nn * 8 : (nn * 4 <= kCholDyn ? nn * 4 : 0);
   k_cholesky_mixed<float><<<1, CNT, dyn, st>>>(G, n, mode, tol64, tol32, Lrow, Lcol, invdiag, keep,
-                                               info, err, static_cast<int>(dyn), img32, gimg32);
+                                               info, err, static_cast<int>(dyn), img32, gimg32,
+                                               pre);
   return cudaGetLastError();
 }
 

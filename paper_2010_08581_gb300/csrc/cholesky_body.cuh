@@ -276,19 +276,31 @@ template <typename Ops, typename TI>
 __device__ __forceinline__ bool cholesky_panel(const double* __restrict__ G, int n,
                                                double tol_scale, float* A, double* invdiag,
                                                int* keep_out, int* info, TI* img,
-                                               float* gimg32) {
+                                               float* gimg32, float* img_hi = nullptr,
+                                               float* img_lo = nullptr,
+                                               const float* pre_hi = nullptr,
+                                               const float* pre_lo = nullptr) {
   using V = typename Ops::V;
   constexpr int QP = (kPanelCholMax + 31) / 32;
   constexpr int kPB = Ops::kPB;
-  __shared__ double s_ldiag[kPanelCholMax];
+  __shared__ V s_ldiag[kPanelCholMax];   // in the working type: converted once, at the end
   __shared__ float s_tol;
   __shared__ int s_stop;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   constexpr int NW = CNT / 32;
   const int np = n + 1, lda = panel_lda(n), ps = lda * n;
   // load: the lower triangle into A, the whole (symmetric) matrix into the FP32 image; each
-  // thread issues the loads of two columns before any store
-  for (int j0 = warp; j0 < n; j0 += 2 * NW) {
+  // thread issues the loads of two columns before any store. With pre_hi (pre_lo) the
+  // reduction already wrote A's planes (and the FP32 image): a 16-byte copy.
+  if (pre_hi) {
+    const int tot = lda * n;                              // a multiple of 4
+    for (int e = tid * 4; e < tot; e += CNT * 4) {
+      *reinterpret_cast<float4*>(A + e) = *reinterpret_cast<const float4*>(pre_hi + e);
+      if constexpr (Ops::kPlanes == 2)
+        *reinterpret_cast<float4*>(A + ps + e) = *reinterpret_cast<const float4*>(pre_lo + e);
+    }
+  }
+  for (int j0 = pre_hi ? n : warp; j0 < n; j0 += 2 * NW) {
     double g[2][QP];
 #pragma unroll
     for (int h = 0; h < 2; ++h)
@@ -313,7 +325,9 @@ __device__ __forceinline__ bool cholesky_panel(const double* __restrict__ G, int
 #pragma unroll
     for (int q = 0; q < QP; ++q) {
       const int i = lane + 32 * q;
-      dg[q] = (i < n) ? static_cast<float>(G[static_cast<int64_t>(i) * n + i]) : 0.0f;
+      dg[q] = (i < n) ? (pre_hi ? pre_hi[i * lda + i]
+                                : static_cast<float>(G[static_cast<int64_t>(i) * n + i]))
+                      : 0.0f;
     }
     float md = 0.0f;
 #pragma unroll
@@ -368,7 +382,7 @@ __device__ __forceinline__ bool cholesky_panel(const double* __restrict__ G, int
           for (int jj = 0; jj < kPB; ++jj)
             if (jj < w && i >= c0 + jj) {
               Ops::st(A, (c0 + jj) * lda + i, ps, p[q][jj]);
-              if (i == c0 + jj) s_ldiag[i] = Ops::wide(p[q][jj]);
+              if (i == c0 + jj) s_ldiag[i] = p[q][jj];
             }
         }
       }
@@ -417,15 +431,29 @@ __device__ __forceinline__ bool cholesky_panel(const double* __restrict__ G, int
     }
     __syncthreads();
   }
-  // the factor image, padded column-major: img[c*(n+1) + r] = L[r][c]
-  for (int j = warp; j < n; j += NW)
-    for (int i = lane; i < n; i += 32)
-      img[j * np + i] = (i >= j) ? static_cast<TI>(Ops::wide(Ops::ld(A, j * lda + i, ps))) : TI(0);
+  // the factor image, padded column-major: img[c*(n+1) + r] = L[r][c]; or, for a
+  // double-float factor with img_hi/img_lo given, its two FP32 planes in that layout (the
+  // FP64 image is then formed by launch_ff_image, across many SMs: *info = 2 marks it)
+  if constexpr (Ops::kPlanes == 2) {
+    if (img_hi) {
+      for (int j = warp; j < n; j += NW)
+        for (int i = lane; i < n; i += 32) {
+          const V v = (i >= j) ? Ops::ld(A, j * lda + i, ps) : Ops::zero();
+          img_hi[j * np + i] = Ops::lead(v);
+          img_lo[j * np + i] = v.lo;
+        }
+    }
+  }
+  if (!img_hi)
+    for (int j = warp; j < n; j += NW)
+      for (int i = lane; i < n; i += 32)
+        img[j * np + i] =
+            (i >= j) ? static_cast<TI>(Ops::wide(Ops::ld(A, j * lda + i, ps))) : TI(0);
   for (int k = tid; k < n; k += CNT) {
     keep_out[k] = 1;
-    invdiag[k] = 1.0 / s_ldiag[k];
+    invdiag[k] = 1.0 / Ops::wide(s_ldiag[k]);
   }
-  if (tid == 0) *info = 0;
+  if (tid == 0) *info = img_hi ? 2 : 0;
   return true;
 }
 
@@ -442,12 +470,14 @@ __device__ __forceinline__ void cholesky_cta_mixed(const double* __restrict__ G,
                                                    double tol64, double tol32, float* A32,
                                                    double* A64, double* Lrow, double* Lcol,
                                                    double* invdiag, int* keep_out, int* info,
-                                                   unsigned* err, TI* img, float* gimg32) {
+                                                   unsigned* err, TI* img, float* gimg32,
+                                                   const float* pre = nullptr) {
   constexpr bool f32img = sizeof(TI) == 4;
   double* img64 = f32img ? nullptr : reinterpret_cast<double*>(img);
   float* img32 = f32img ? reinterpret_cast<float*>(img) : nullptr;
   if (n >= 4 && n <= kPanelCholMax && img) {
-    if (cholesky_panel<F32Ops, TI>(G, n, tol32, A32, invdiag, keep_out, info, img, gimg32))
+    if (cholesky_panel<F32Ops, TI>(G, n, tol32, A32, invdiag, keep_out, info, img, gimg32,
+                                   nullptr, nullptr, pre))
       return;
   } else if (cholesky_cta<float>(G, n, 0, tol32, A32, nullptr, nullptr, invdiag, keep_out,
                                  info, err, img64, img32, gimg32, false)) {
@@ -464,14 +494,20 @@ __device__ __forceinline__ void cholesky_cta_mixed(const double* __restrict__ G,
 // accepted only if every pivot exceeds tolff * max diag (no column is dropped); otherwise
 // the FP64 factorisation with tol64 and mode 1's column dropping. The image is FP64.
 // Aff is the double-float work array (panel_floats<FFOps>(n) floats), A64 the FP64 one (they
-// may alias). Lrow/Lcol receive the factor only on the FP64 branch.
+// may alias). Lrow/Lcol receive the factor only on the FP64 branch; on the double-float
+// branch they hold the image's hi / lo FP32 planes, *info = 2, and launch_ff_image (or the
+// batched kb_ff_image) forms img64 from them.
 __device__ __forceinline__ void cholesky_cta_lev_mixed(const double* __restrict__ G, int n,
                                                        double tol64, double tolff, float* Aff,
                                                        double* A64, double* Lrow, double* Lcol,
                                                        double* invdiag, int* keep_out,
-                                                       int* info, unsigned* err, double* img64) {
+                                                       int* info, unsigned* err, double* img64,
+                                                       const float* pre_hi = nullptr,
+                                                       const float* pre_lo = nullptr) {
   if (n >= 4 && n <= kPanelCholMax && img64 && Aff) {
-    if (cholesky_panel<FFOps, double>(G, n, tolff, Aff, invdiag, keep_out, info, img64, nullptr))
+    if (cholesky_panel<FFOps, double>(G, n, tolff, Aff, invdiag, keep_out, info, img64, nullptr,
+                                      reinterpret_cast<float*>(Lrow),
+                                      reinterpret_cast<float*>(Lcol), pre_hi, pre_lo))
       return;
     __syncthreads();
   }

@@ -116,10 +116,21 @@ cudaError_t launch_gram(const double* A, int64_t rows, int cols, int64_t lda, bo
 // Fixed-order reduction over splits s = 0..splits-1 of an nrows x ncols block of partials
 // (row stride pld, split stride pstride; FP32 or FP64) into FP64. Columns c < c_split go
 // to out1[r*ld1 + c]; columns c >= c_split go transposed to out2[(c - c_split)*ld2 + r].
+// Optional FP32 forms of out1 (an n x n symmetric matrix) for the one-CTA factorisations,
+// written by the same reduction: hi (and lo: the double-float split) at [r*lda + c] for
+// c >= r (the panel work-array layout), and img (the FP32 image of the whole matrix) at
+// [r*np + c]. Null pointers are skipped.
+struct ReduceSplit {
+  float* hi = nullptr;
+  float* lo = nullptr;
+  int lda = 0;
+  float* img = nullptr;
+  int np = 0;
+};
 cudaError_t launch_reduce(const void* partial, bool partial_f32, int splits, int64_t pstride,
                           int64_t pld, int64_t nrows, int64_t ncols, int64_t c_split,
                           double* out1, int64_t ld1, double* out2, int64_t ld2,
-                          cudaStream_t st);
+                          cudaStream_t st, const ReduceSplit& split = ReduceSplit{});
 
 // Cholesky G = L L^T of the n x n FP64 matrix G (row-major, ld n; only the upper triangle
 // G[j][i], j <= i, is read), one CTA. A pivot <= tol_scale * max diag is
@@ -135,13 +146,21 @@ cudaError_t launch_reduce(const void* partial, bool partial_f32, int splits, int
 cudaError_t launch_cholesky_mixed(const double* G, int n, int mode, double tol64, double tol32,
                                   double* Lrow, double* Lcol, double* invdiag, int* keep,
                                   int* info, unsigned* err, cudaStream_t st, float* img32,
-                                  float* gimg32);
+                                  float* gimg32, const float* pre = nullptr);
 // Mixed-precision drivers' leverage Gram of a tall matrix (mode 1): double-float factor when
 // every pivot > tolff * max diag (FP64 image img64 + invdiag + keep + info), otherwise the FP64
 // factorisation with tol64 and column dropping (as launch_cholesky, mode 1).
 cudaError_t launch_cholesky_lev_mixed(const double* G, int n, double tol64, double tolff,
                                       double* Lrow, double* Lcol, double* invdiag, int* keep,
-                                      int* info, unsigned* err, cudaStream_t st, double* img64);
+                                      int* info, unsigned* err, cudaStream_t st, double* img64,
+                                      const float* pre_hi = nullptr,
+                                      const float* pre_lo = nullptr);
+// pre / pre_hi, pre_lo: the work array's planes already written by launch_reduce (a
+// ReduceSplit with lda = (n + 3) & ~3), or null to convert from G.
+// After launch_cholesky_lev_mixed: img64 = hi + lo of the FP32 planes it left in Lrow / Lcol
+// when its double-float branch succeeded (*info == 2); otherwise nothing.
+cudaError_t launch_ff_image(const double* Lrow, const double* Lcol, int n, const int* info,
+                            double* img64, cudaStream_t st);
 cudaError_t launch_cholesky(const double* G, int n, int mode, double tol_scale, double* Lrow,
                             double* Lcol, double* invdiag, int* keep, int* info,
                             unsigned* err, cudaStream_t st, double* img64 = nullptr,

@@ -70,7 +70,8 @@ __global__ void __launch_bounds__(256) k_reduce(const TP* __restrict__ partial, 
                                                 int64_t pstride, int64_t pld, int64_t nrows,
                                                 int64_t ncols, int64_t c_split,
                                                 double* __restrict__ out1, int64_t ld1,
-                                                double* __restrict__ out2, int64_t ld2) {
+                                                double* __restrict__ out2, int64_t ld2,
+                                                ReduceSplit sp) {
   const int64_t total = nrows * ncols;
   for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
        e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
@@ -100,6 +101,11 @@ __global__ void __launch_bounds__(256) k_reduce(const TP* __restrict__ partial, 
         hi = t;
       }
       s = static_cast<double>(hi) + static_cast<double>(lo);
+      if (c < c_split) {   // the FP32 value of out1 is the rounded pair sum
+        const float f = hi + lo;
+        if (sp.hi && c >= r) sp.hi[r * sp.lda + c] = f;
+        if (sp.img) sp.img[r * sp.np + c] = f;
+      }
     } else {
       s = 0.0;
       int q = 0;
@@ -111,6 +117,11 @@ __global__ void __launch_bounds__(256) k_reduce(const TP* __restrict__ partial, 
         for (int u = 0; u < 8; ++u) s += v[u];
       }
       for (; q < splits; ++q) s += static_cast<double>(src[q * pstride]);
+      if (c < c_split && c >= r && sp.hi) {   // double-float split: hi + lo = s
+        const float h = static_cast<float>(s);
+        sp.hi[r * sp.lda + c] = h;
+        if (sp.lo) sp.lo[r * sp.lda + c] = static_cast<float>(s - static_cast<double>(h));
+      }
     }
     if (c < c_split) out1[r * ld1 + c] = s;
     else out2[(c - c_split) * ld2 + r] = s;
@@ -157,7 +168,7 @@ cudaError_t launch_gram(const double* A, int64_t rows, int cols, int64_t lda, bo
 cudaError_t launch_reduce(const void* partial, bool partial_f32, int splits, int64_t pstride,
                           int64_t pld, int64_t nrows, int64_t ncols, int64_t c_split,
                           double* out1, int64_t ld1, double* out2, int64_t ld2,
-                          cudaStream_t st) {
+                          cudaStream_t st, const ReduceSplit& split) {
   const int64_t total = nrows * ncols;
   if (total <= 0) return cudaSuccess;
   int64_t blocks = (total + 255) / 256;
@@ -165,11 +176,11 @@ cudaError_t launch_reduce(const void* partial, bool partial_f32, int splits, int
   if (partial_f32)
     k_reduce<float><<<static_cast<unsigned>(blocks), 256, 0, st>>>(
         static_cast<const float*>(partial), splits, pstride, pld, nrows, ncols, c_split, out1,
-        ld1, out2, ld2);
+        ld1, out2, ld2, split);
   else
     k_reduce<double><<<static_cast<unsigned>(blocks), 256, 0, st>>>(
         static_cast<const double*>(partial), splits, pstride, pld, nrows, ncols, c_split, out1,
-        ld1, out2, ld2);
+        ld1, out2, ld2, split);
   return cudaGetLastError();
 }
 
