@@ -49,8 +49,8 @@ __global__ void __launch_bounds__(CNT) k_cholesky_lev_mixed(const double* __rest
   const int64_t nn = static_cast<int64_t>(n) * n;
   float* Aff = panel_floats<FFOps>(n) * 4 <= dyn_bytes ? reinterpret_cast<float*>(smem) : nullptr;
   double* A64 = nn * 8 <= dyn_bytes ? smem : Lrow;
-  cholesky_cta_lev_mixed(G, n, tol64, tolff, Aff, A64, Lrow, Lcol, invdiag, keep_out, info, err,
-                         img64, pre_hi, pre_lo);
+  cholesky_cta_lev_mixed<4>(G, n, tol64, tolff, Aff, A64, Lrow, Lcol, invdiag, keep_out, info,
+                            err, img64, pre_hi, pre_lo);
 }
 
 // img64 = hi + lo from the two FP32 planes when the factorisation left them (*info == 2).
