@@ -375,10 +375,12 @@ __global__ void __launch_bounds__(256) kb_ff_image(const BInst* __restrict__ tab
 // Triangular solves: the LS solve (mode 2 mixed / mode 1 FP64) writing the new core, and
 // the leverage rows with the fused p / CDF step.
 // ------------------------------------------------------------------------------------
-// Runtime choice of the register rows (QN = ceil(n/32)) and of shared-memory staging;
-// n <= 128 always fits in shared memory and n >= 161 never does.
+// Runtime choice of the register rows (QN = ceil(n/32)) and of shared-memory staging:
+// n <= 128 always fits padded; beyond that the packed layout when it fits (`packed`), else
+// the image stays in global memory.
 template <typename T, int NB>
-__device__ __forceinline__ void trsm_dispatch(bool smem, unsigned char* sm, int64_t cta, int n,
+__device__ __forceinline__ void trsm_dispatch(bool smem, bool packed, unsigned char* sm,
+                                              int64_t cta, int n,
                                               const double* Lrow, const double* Lcol,
                                               const double* invdiag, const int* info,
                                               int64_t nvec, const double* rhs, int64_t ld,
@@ -395,11 +397,21 @@ __device__ __forceinline__ void trsm_dispatch(bool smem, unsigned char* sm, int6
     case 4: trsm_cta<T, 4, NB, true>(TB_ARGS); break;
     case 5:
       if (smem) trsm_cta<T, 5, NB, true>(TB_ARGS);
+      else if (packed) trsm_cta<T, 5, NB, true, true>(TB_ARGS);
       else trsm_cta<T, 5, NB, false>(TB_ARGS);
       break;
-    case 6: trsm_cta<T, 6, NB, false>(TB_ARGS); break;
-    case 7: trsm_cta<T, 7, NB, false>(TB_ARGS); break;
-    case 8: trsm_cta<T, 8, NB, false>(TB_ARGS); break;
+    case 6:
+      if (packed) trsm_cta<T, 6, NB, true, true>(TB_ARGS);
+      else trsm_cta<T, 6, NB, false>(TB_ARGS);
+      break;
+    case 7:
+      if (packed) trsm_cta<T, 7, NB, true, true>(TB_ARGS);
+      else trsm_cta<T, 7, NB, false>(TB_ARGS);
+      break;
+    case 8:
+      if (packed) trsm_cta<T, 8, NB, true, true>(TB_ARGS);
+      else trsm_cta<T, 8, NB, false>(TB_ARGS);
+      break;
     default: break;
   }
 #undef TB_ARGS
@@ -419,7 +431,9 @@ __global__ void __launch_bounds__(TW * 32) kb_solve(const BInst* __restrict__ ta
   const int mode = sizeof(T) == 4 ? 2 : 1;
   const CdfEpilogue none{};
   const bool smem = staged_bytes<T>(n, mode) <= static_cast<size_t>(smem_bytes);
-  trsm_dispatch<T, NB>(smem, sm, blockIdx.y, n, d.Lrow, d.Lcol, d.invdiag, d.info, cu.I, d.BT, n,
+  const bool packed = !smem && packed_bytes<T>(n) <= static_cast<size_t>(smem_bytes);
+  trsm_dispatch<T, NB>(smem, packed, sm, blockIdx.y, n, d.Lrow, d.Lcol, d.invdiag, d.info, cu.I,
+                       d.BT, n,
                        mode, d.M, static_cast<const T*>(d.limg), d.mimg, cu.Rl, cu.Rr,
                        d.cores[cu.n], nullptr, none, nctas);
 }
@@ -442,7 +456,9 @@ __global__ void __launch_bounds__(TW * 32) kb_rows(const BInst* __restrict__ tab
   if (static_cast<int>(blockIdx.y) >= nctas) return;
   const CdfEpilogue ep{d.counter, d.p[cu.n], d.cdf[cu.n], cu.init ? nullptr : d.info, err};
   const bool smem = staged_bytes<double>(n, 0) <= static_cast<size_t>(smem_bytes);
-  trsm_dispatch<double, 1>(smem, sm, blockIdx.y, n, Lr, Lc, iv, nullptr, cu.I, rhs, ld, 0, nullptr,
+  const bool packed = !smem && packed_bytes<double>(n) <= static_cast<size_t>(smem_bytes);
+  trsm_dispatch<double, 1>(smem, packed, sm, blockIdx.y, n, Lr, Lc, iv, nullptr, cu.I, rhs, ld, 0,
+                           nullptr,
                            im, nullptr, 1, 1, nullptr, d.ell, ep, nctas);
 }
 
@@ -656,7 +672,9 @@ cudaError_t bl_cholesky(const BLaunch& b, int step, int init_k, int which, unsig
 template <typename T>
 int solve_smem(int nmax, int mode) {
   const int n = nmax < 160 ? nmax : 160;
-  const size_t need = staged_bytes<T>(n, mode);
+  size_t need = staged_bytes<T>(n, mode);
+  const size_t pk = packed_bytes<T>(nmax);
+  if (nmax > 128 && pk <= static_cast<size_t>(kDyn) && pk > need) need = pk;
   return need <= static_cast<size_t>(kDyn) ? static_cast<int>(need) : kDyn;
 }
 

@@ -4,7 +4,7 @@
 namespace trk {
 namespace {
 
-template <typename T, int QN, int NB, bool SMEM>
+template <typename T, int QN, int NB, bool SMEM, bool PACK = false>
 __global__ void __launch_bounds__(TW * 32) k_trsm(int n, const double* __restrict__ Lrow,
                                                   const double* __restrict__ Lcol,
                                                   const double* __restrict__ invdiag,
@@ -16,7 +16,7 @@ __global__ void __launch_bounds__(TW * 32) k_trsm(int n, const double* __restric
                                                   double* __restrict__ core_out,
                                                   double* __restrict__ ell, CdfEpilogue ep) {
   extern __shared__ __align__(16) unsigned char trsm_smem[];
-  trsm_cta<T, QN, NB, SMEM>(trsm_smem, blockIdx.x, n, Lrow, Lcol, invdiag, info, nvec, rhs, ld,
+  trsm_cta<T, QN, NB, SMEM, PACK>(trsm_smem, blockIdx.x, n, Lrow, Lcol, invdiag, info, nvec, rhs, ld,
                             mode, M, Limg, Mimg, Rl, Rr, core_out, ell, ep, gridDim.x);
 }
 
@@ -28,8 +28,8 @@ cudaError_t run_q(int n, const double* Lrow, const double* Lcol, const double* i
   const size_t staged = staged_bytes<T>(n, mode);
   const int64_t per_cta = static_cast<int64_t>(TW) * NB;
   const unsigned blocks = static_cast<unsigned>((nvec + per_cta - 1) / per_cta);
-  // n <= 128 (QN <= 4) always fits in shared memory and n >= 161 (QN >= 6) never does, so
-  // only QN = 5 needs both variants.
+  // n <= 128 (QN <= 4) always fits in shared memory padded and n >= 161 (QN >= 6) never
+  // does; beyond the padded image the packed lower triangle when it fits.
   if constexpr (QN <= 5) {
     if (staged <= 200 * 1024) {
       k_trsm<T, QN, NB, true><<<blocks, TW * 32, staged, st>>>(
@@ -39,6 +39,13 @@ cudaError_t run_q(int n, const double* Lrow, const double* Lcol, const double* i
     }
   }
   if constexpr (QN >= 5) {
+    const size_t pb = packed_bytes<T>(n);
+    if (pb <= 200 * 1024) {
+      k_trsm<T, QN, NB, true, true><<<blocks, TW * 32, pb, st>>>(
+          n, Lrow, Lcol, invdiag, info, nvec, rhs, ld, mode, M, Limg, Mimg, Rl, Rr, core_out, ell,
+          ep);
+      return cudaGetLastError();
+    }
     k_trsm<T, QN, NB, false><<<blocks, TW * 32, kMaxL * sizeof(T), st>>>(
         n, Lrow, Lcol, invdiag, info, nvec, rhs, ld, mode, M, Limg, Mimg, Rl, Rr, core_out, ell,
         ep);
@@ -70,9 +77,13 @@ cudaError_t attr_q() {
     e = cudaFuncSetAttribute(k_trsm<T, QN, NB, true>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   if (e != cudaSuccess) return e;
-  if constexpr (QN >= 5)
+  if constexpr (QN >= 5) {
     e = cudaFuncSetAttribute(k_trsm<T, QN, NB, false>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_trsm<T, QN, NB, true, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  }
   return e;
 }
 

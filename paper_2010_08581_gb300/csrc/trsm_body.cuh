@@ -22,19 +22,25 @@ constexpr int TW = 4;   // warps per CTA
 // memory (SMEM), or in global memory when the Cholesky kernel wrote one (its FP32 or FP64
 // image in L2: no per-element conversion from FP64), else the FP64 column- and row-major
 // factor.
-template <typename T, bool SMEM>
+// PACK (with SMEM): the lower triangle packed column by column in shared memory, column c
+// starting at c*n - c(c-1)/2 -- for factors whose padded image does not fit (n > 160 in
+// FP32): n(n+1)/2 entries.
+template <typename T, bool SMEM, bool PACK = false>
 struct Factor {
   const T* s;            // image, shared (SMEM) or global (gimg)
   const double* Lcol;    // global: Lcol[c*n + r] = L[r][c]
   const double* Lrow;    // global: Lrow[c*n + r] = L[c][r]
   int n;
   bool gimg = false;     // !SMEM: s is a global image
-  __device__ __forceinline__ T col(int c, int r) const {   // L[r][c]
-    if constexpr (SMEM) return s[c * (n + 1) + r];
+  __device__ __forceinline__ int pk(int c) const { return c * n - (c * (c - 1)) / 2 - c; }
+  __device__ __forceinline__ T col(int c, int r) const {   // L[r][c], r >= c
+    if constexpr (PACK) return s[pk(c) + r];
+    else if constexpr (SMEM) return s[c * (n + 1) + r];
     else return gimg ? __ldg(s + c * (n + 1) + r) : static_cast<T>(Lcol[c * n + r]);
   }
-  __device__ __forceinline__ T row(int c, int r) const {   // L[c][r]
-    if constexpr (SMEM) return s[r * (n + 1) + c];
+  __device__ __forceinline__ T row(int c, int r) const {   // L[c][r], r < c
+    if constexpr (PACK) return s[pk(r) + c];
+    else if constexpr (SMEM) return s[r * (n + 1) + c];
     else return gimg ? __ldg(s + r * (n + 1) + c) : static_cast<T>(Lrow[c * n + r]);
   }
 };
@@ -57,9 +63,9 @@ __device__ __forceinline__ void put(T (&x)[QN][NB], int q, int v, T val) {
 // x <- L^-1 x. Rows are processed in blocks of 32 (register slot qb of every lane); inside a
 // block the pivot row's lane is a compile-time constant and the block's values live in one
 // register per vector, so one step is a shuffle, a multiply and independent FMAs.
-template <typename T, int QN, int NB, bool SMEM>
-__device__ __forceinline__ void forward(T (&x)[QN][NB], const Factor<T, SMEM>& F, const T* inv,
-                                        int lane) {
+template <typename T, int QN, int NB, bool SMEM, bool PACK>
+__device__ __forceinline__ void forward(T (&x)[QN][NB], const Factor<T, SMEM, PACK>& F,
+                                        const T* inv, int lane) {
   const int n = F.n;
   for (int qb = 0; qb < QN; ++qb) {
     T xb[NB];
@@ -97,9 +103,9 @@ __device__ __forceinline__ void forward(T (&x)[QN][NB], const Factor<T, SMEM>& F
 }
 
 // x <- L^-T x, blocks in reverse order.
-template <typename T, int QN, int NB, bool SMEM>
-__device__ __forceinline__ void backward(T (&x)[QN][NB], const Factor<T, SMEM>& F, const T* inv,
-                                         int lane) {
+template <typename T, int QN, int NB, bool SMEM, bool PACK>
+__device__ __forceinline__ void backward(T (&x)[QN][NB], const Factor<T, SMEM, PACK>& F,
+                                         const T* inv, int lane) {
   const int n = F.n;
   for (int qb = QN - 1; qb >= 0; --qb) {
     T xb[NB];
@@ -197,7 +203,7 @@ __device__ inline void cdf_epilogue(const CdfEpilogue& ep, const double* ell, in
   }
 }
 
-template <typename T, int QN, int NB, bool SMEM>
+template <typename T, int QN, int NB, bool SMEM, bool PACK = false>
 __device__ __forceinline__ void trsm_cta(unsigned char* trsm_smem, int64_t cta, int n,
                                          const double* __restrict__ Lrow,
                                                   const double* __restrict__ Lcol,
@@ -216,9 +222,16 @@ __device__ __forceinline__ void trsm_cta(unsigned char* trsm_smem, int64_t cta, 
                         static_cast<int>(sizeof(T));
   T* inv = reinterpret_cast<T*>(trsm_smem);                  // kMaxL entries
   T* Ls = inv + kMaxL;                                       // n*(n+1) (padded to 16 B)
-  T* Ms = Ls + (SMEM ? img_elems : 0);                       // mode 2
+  T* Ms = Ls + (SMEM && !PACK ? img_elems : 0);              // mode 2
   for (int c = threadIdx.x; c < n; c += blockDim.x) inv[c] = static_cast<T>(invdiag[c]);
-  if constexpr (SMEM) {
+  if constexpr (PACK) {
+    // the lower triangle, column by column, from the padded image (or the FP64 factor)
+    for (int c = threadIdx.x >> 5; c < n; c += TW) {
+      const int base = c * n - (c * (c - 1)) / 2 - c;
+      for (int r = c + (threadIdx.x & 31); r < n; r += 32)
+        Ls[base + r] = Limg ? Limg[c * np + r] : static_cast<T>(Lcol[c * n + r]);
+    }
+  } else if constexpr (SMEM) {
     if (Limg) {
       stage_async(Ls, Limg, img_elems * static_cast<int>(sizeof(T)));
     } else {
@@ -235,7 +248,7 @@ __device__ __forceinline__ void trsm_cta(unsigned char* trsm_smem, int64_t cta, 
     }
   }
   __syncthreads();
-  Factor<T, SMEM> F{SMEM ? Ls : Limg, Lcol, Lrow, n, !SMEM && Limg != nullptr};
+  Factor<T, SMEM, PACK> F{SMEM ? Ls : Limg, Lcol, Lrow, n, !SMEM && Limg != nullptr};
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t v0 = (cta * TW + warp) * NB;
   if (mode == 0) {
@@ -311,7 +324,7 @@ __device__ __forceinline__ void trsm_cta(unsigned char* trsm_smem, int64_t cta, 
           const int r = lane + 32 * q;
           if (r < n) {
             T m;
-            if constexpr (SMEM) m = Ms[t * np + r];
+            if constexpr (SMEM && !PACK) m = Ms[t * np + r];
             else if (sizeof(T) == 4 && Mimg) m = static_cast<T>(__ldg(Mimg + t * np + r));
             else m = static_cast<T>(M[t * n + r]);
 #pragma unroll
@@ -339,6 +352,13 @@ __device__ __forceinline__ void trsm_cta(unsigned char* trsm_smem, int64_t cta, 
   }
 }
 
+
+// Shared memory of the packed layout (the inverse diagonal and n(n+1)/2 factor entries).
+template <typename T>
+__host__ __device__ inline size_t packed_bytes(int n) {
+  return kMaxL * sizeof(T) +
+         ((static_cast<size_t>(n) * (n + 1) / 2 * sizeof(T) + 15) / 16) * 16;
+}
 
 template <typename T>
 __host__ __device__ inline size_t staged_bytes(int n, int mode) {
