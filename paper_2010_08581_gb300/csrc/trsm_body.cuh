@@ -225,12 +225,25 @@ __device__ __forceinline__ void trsm_cta(unsigned char* trsm_smem, int64_t cta, 
   T* Ms = Ls + (SMEM && !PACK ? img_elems : 0);              // mode 2
   for (int c = threadIdx.x; c < n; c += blockDim.x) inv[c] = static_cast<T>(invdiag[c]);
   if constexpr (PACK) {
-    // the lower triangle, column by column, from the padded image (or the FP64 factor)
+    // the lower triangle, column by column, from the padded image with element-sized
+    // asynchronous copies (all in flight at once), or converted from the FP64 factor
     for (int c = threadIdx.x >> 5; c < n; c += TW) {
       const int base = c * n - (c * (c - 1)) / 2 - c;
-      for (int r = c + (threadIdx.x & 31); r < n; r += 32)
-        Ls[base + r] = Limg ? Limg[c * np + r] : static_cast<T>(Lcol[c * n + r]);
+      for (int r = c + (threadIdx.x & 31); r < n; r += 32) {
+        if (Limg) {
+          const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(Ls + base + r));
+          if constexpr (sizeof(T) == 4)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d),
+                         "l"(Limg + c * np + r) : "memory");
+          else
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d),
+                         "l"(Limg + c * np + r) : "memory");
+        } else {
+          Ls[base + r] = static_cast<T>(Lcol[c * n + r]);
+        }
+      }
     }
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
   } else if constexpr (SMEM) {
     if (Limg) {
       stage_async(Ls, Limg, img_elems * static_cast<int>(sizeof(T)));
