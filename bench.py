@@ -173,7 +173,8 @@ def algorithmic_cost(kernel, wl):
       gather          : J*I*4 bytes read (fibres) + J*I*4 written
       subchain        : J*(N-1)*L*8 slice bytes read + J*L*4 written
       normal_eq_tc    : 2*J*L*(L + I) useful flops (TF32 tensor cores)
-      cholesky_*      : L^3/3 FP64 flops (one CTA)
+      cholesky_leverage: L^3/3 flops in double-float (FP32 pairs; one CTA, mixed path)
+      cholesky_solve  : L^3/3 flops in FP32 (one CTA, mixed path)
       solve_rhs       : 6*L^2*I FP32 flops (two triangular solve pairs + residual)
       gram_f64        : 2*I*L^2 FP64 flops
       leverage_rows   : I*L^2 FP64 flops
@@ -189,8 +190,8 @@ def algorithmic_cost(kernel, wl):
         "normal_eq": ("flops_f32", 2.0 * J * L * (L + I)),
         "normal_eq_tc": ("flops_tf32", 2.0 * J * L * (L + I)),
         "subchain": ("hbm", J * (N - 1) * L * 8.0 + J * L * s),
-        "cholesky_solve": ("flops_f64", L ** 3 / 3.0),
-        "cholesky_leverage": ("flops_f64", L ** 3 / 3.0),
+        "cholesky_solve": ("flops_f32", L ** 3 / 3.0),
+        "cholesky_leverage": ("flops_ff", L ** 3 / 3.0),
         "solve_rhs": ("flops_f32", 6.0 * L * L * I),
         "gram_f64": ("flops_f64", 2.0 * I * L * L),
         "leverage_rows": ("flops_f64", I * L * L),
@@ -256,8 +257,26 @@ def roofline(prof, wl, peaks):
             ach = amount / avg_s / 1e12
             return {"kernel": name, "bound": "alu", "achieved": round(ach, 4), "peak": round(peak, 2),
                     "unit": "TFLOP/s", "frac": round(ach / peak, 5),
+                    "frac_of_one_sm": round(ach / (peak / 152), 4),
                     "traffic": traffic_for(name),
                     "peak_source": "FP32 SIMT: 152 SMs x 128 FMA/clk x 2 x 2.07 GHz",
+                    "avg_launch_us": round(avg_s * 1e6, 3), "launches": n,
+                    "share_of_timed": None}
+        if kind == "flops_ff":
+            # double-float on the FP32 pipe: one multiply-add a - x*y is 15 FP32 instructions
+            # (Dekker's product via FMA, then a two-sum); 128 lanes/clk/SM at 2.07 GHz
+            per_sm = 128 * 2.07e9 * 2 / 15 / 1e12
+            peak = 152 * per_sm
+            ach = amount / avg_s / 1e12
+            return {"kernel": name, "bound": "alu", "achieved": round(ach, 6),
+                    "peak": round(peak, 3), "unit": "TFLOP/s", "frac": round(ach / peak, 5),
+                    "frac_of_one_sm": round(ach / per_sm, 4),
+                    "frac_of_one_sm_fp64": round(ach / (NOMINAL_FP64_TFLOPS / 152), 4),
+                    "traffic": traffic_for(name),
+                    "peak_source": "double-float on FP32 SIMT: 152 SMs x 128 lanes x 2.07 GHz x "
+                                   "2 flops / 15 instructions per multiply-add (one-CTA kernel: "
+                                   "see frac_of_one_sm; frac_of_one_sm_fp64 compares with one "
+                                   "SM's nominal FP64 rate)",
                     "avg_launch_us": round(avg_s * 1e6, 3), "launches": n,
                     "share_of_timed": None}
         if kind == "flops_tf32":
