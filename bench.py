@@ -850,6 +850,19 @@ def run_ours(args):
     e2e_value = world * sweeps * e2e_steps / e2e_s
     h2d = Xh.numel() * 4 + sum(c.numel() * 8 for c in init_h[1:])
     d2h = sum(c.numel() * 8 for c in out_h)
+    # the host link's rate for the same pinned buffer, one plain copy: the end-to-end rate
+    # differs from the device rate by about h2d / this per step
+    Xcopy = torch.empty_like(X)
+    h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        Xcopy.copy_(Xh, non_blocking=True)
+        h0.record(stream)
+        for _ in range(3):
+            Xcopy.copy_(Xh, non_blocking=True)
+        h1.record(stream)
+    torch.cuda.synchronize()
+    h2d_gbs = 3 * Xh.numel() * Xh.element_size() / (h0.elapsed_time(h1) / 1e3) / 1e9
+    del Xcopy
 
     # plain FP64 GPU form at the same workload (comparator of the metric)
     fp64 = None
@@ -920,7 +933,9 @@ def run_ours(args):
                            "p99": round(float(np.percentile(lat, 99)), 4),
                            "what": "one whole decomposition (10 sweeps) per step"},
             "e2e": {"value": round(e2e_value, 3), "unit": "sweeps/s", "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h, "steps": e2e_steps},
+                    "d2h_bytes_per_step": d2h, "steps": e2e_steps,
+                    "h2d_gbs": round(h2d_gbs, 1),
+                    "h2d_what": "pinned host -> device copy of X alone, CUDA events, 3 copies"},
             "gpu_launches": launches,
             "gpu_launches_note": "kernels of this library launched in the profiled repeat of "
                                  "the timed steps (same work as the timed region)",
