@@ -165,7 +165,8 @@ def test_subchain_rejects_out_of_range_index(ctx):
     assert torch.all(A[1] == 0)
 
 
-@pytest.mark.parametrize("dims", [(13, 17, 19), (5, 6, 7, 8), (40, 3), (2, 3, 4, 5, 6)])
+@pytest.mark.parametrize("dims", [(13, 17, 19), (5, 6, 7, 8), (40, 3), (2, 3, 4, 5, 6),
+                                  (300, 7, 5), (2, 600, 3)])
 @pytest.mark.parametrize("xdt,ydt", [(torch.float64, torch.float64), (torch.float32, torch.float32),
                                      (torch.float32, torch.float64)])
 def test_gather_matches_oracle(ctx, dims, xdt, ydt):
