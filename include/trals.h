@@ -42,7 +42,8 @@ typedef enum tr_status {
   TR_ERR_OOM = 2,          /* device allocation failed                                  */
   TR_ERR_BUDGET = 3,       /* workspace would exceed the context's HBM budget          */
   TR_ERR_SINGULAR = 4,     /* non-positive pivot in the normal equations, or zero core */
-  TR_ERR_TIMEOUT = 5,      /* reserved for bounded device waits                         */
+  TR_ERR_TIMEOUT = 5,      /* a bounded device wait expired (tensor-core pipeline,      */
+                           /* cluster factorisation), or tr_server_wait's time ran out */
   TR_ERR_CUDA = 6,         /* a CUDA runtime call failed (see tr_last_error)            */
   TR_ERR_NOT_CONVERGED = 7 /* a served request stopped at its sweep cap (result kept)    */
 } tr_status;
