@@ -52,7 +52,9 @@ _MASK32 = np.uint64(0xFFFFFFFF)
 
 
 def philox4x32_10(ctr, key):
-    """Philox4x32 with 10 rounds.
+    """Philox4x32 with 10 rounds (Salmon, Moraes, Dror & Shaw, "Parallel random numbers:
+    as easy as 1, 2, 3", SC 2011), the counter-based generator behind the draws of Alg. 3;
+    the paper leaves the generator open.
 
     ``ctr``: integer array of shape (..., 4) (32-bit words); ``key``: two 32-bit words.
     One round maps (c0, c1, c2, c3) to (hi(M1*c2) ^ c1 ^ k0, lo(M1*c2),
@@ -75,7 +77,8 @@ def philox4x32_10(ctr, key):
 
 
 def philox_uniforms(J, m, seed, update_id):
-    """Uniform variates u in [0, 1) for samples j = 0..J-1 at ring position m.
+    """Uniform variates u in [0, 1) for samples j = 0..J-1 at ring position m (the
+    independent draws of Alg. 3, one per sample and sampled mode).
 
     Counter = (j, m // 2, low32(update_id), high32(update_id)); key = (low32(seed),
     high32(seed)). Position m takes the word pair (2*(m % 2), 2*(m % 2) + 1) of the block
@@ -159,7 +162,8 @@ def core_unfold2(core):
 
 
 def core_from_solution(Z, Rl, Rr):
-    """Inverse of ``core_unfold2``: Z is G_(2)^(n)T of shape (R_{n-1} R_n, I_n)."""
+    """Inverse of ``core_unfold2``: Z is G_(2)^(n)T of shape (R_{n-1} R_n, I_n), the
+    solution of the LS step of Alg. 2 written back as core n (Def. 2)."""
     L, I = Z.shape
     assert L == Rl * Rr
     return np.ascontiguousarray(Z.reshape(Rr, Rl, I).transpose(1, 2, 0))
@@ -215,8 +219,8 @@ def core_distribution(core):
 
 
 def inverse_cdf(cdf, p, u):
-    """Index i ~ p for uniforms u: smallest i with u < cdf[i]; if rounding leaves
-    u >= cdf[-1], the largest i with p[i] > 0."""
+    """Index i ~ p for uniforms u (the per-mode draws of Alg. 3, Def. 5): smallest i
+    with u < cdf[i]; if rounding leaves u >= cdf[-1], the largest i with p[i] > 0."""
     i = np.searchsorted(cdf, u, side="right")
     over = i >= len(cdf)
     if np.any(over):
@@ -300,8 +304,8 @@ def sampled_ls_normal(A, Y):
 
 
 def sampled_ls_normal_drop(A, Y, tol_scale):
-    """argmin_Z ||A Z - Y||_F for a possibly rank-deficient A: a basic least-squares
-    solution. The normal matrix M = A^T A is factored column by column (Cholesky); a column
+    """argmin_Z ||A Z - Y||_F of the LS step of Alg. 2 for a possibly rank-deficient A:
+    a basic least-squares solution. The normal matrix M = A^T A is factored column by column (Cholesky); a column
     whose pivot is <= tol_scale * max diag(M) is dropped (its unknowns are set to 0 and it
     updates nothing), the others give L L^T = M restricted to the kept columns, and the
     kept unknowns solve L L^T Z_k = (A^T Y)_k. With every column kept this is
@@ -327,8 +331,8 @@ def sampled_ls_normal_drop(A, Y, tol_scale):
 
 
 def sampled_ls_qr(A, Y):
-    """argmin_Z ||A Z - Y||_F through a thin Householder QR of A (the QR-based solve the
-    paper costs in its complexity analysis)."""
+    """argmin_Z ||A Z - Y||_F of the LS step of Alg. 2 through a thin Householder QR of A
+    (the QR-based solve the paper costs in its complexity analysis, Sec. 4.3)."""
     Q, R = np.linalg.qr(A, mode="reduced")
     return solve_triangular(R, Q.T @ Y, lower=False)
 
