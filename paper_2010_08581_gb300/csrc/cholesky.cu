@@ -1,5 +1,6 @@
-// Single-problem launches of the one-CTA Cholesky factorisation (cholesky_body.cuh): FP64,
-// and the mixed-precision LS step's FP32-then-FP64 form.
+// Single-problem launches of the one-CTA Cholesky factorisation (cholesky_body.cuh) for
+// the leverage scores of Def. 4 (row a1) and the LS step of Alg. 2 (row a6): FP64, the
+// mixed LS step's FP32-then-FP64 form, and the double-float leverage form.
 #include <cstdlib>
 
 #include "cholesky_body.cuh"

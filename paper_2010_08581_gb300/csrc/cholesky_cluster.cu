@@ -1,18 +1,18 @@
-// FP64 Cholesky factorisation G = L L^T (rows a1 and a6) on a thread-block cluster of
-// CC CTAs, for n <= kClusterMaxN: the single-problem drivers' factorisations, whose
-// one-CTA form is bounded by one SM's FP64 pipe.
+// FP64 Cholesky factorisation G = L L^T (rows a1 and a6: the leverage scores of Def. 4 and
+// the LS step of Alg. 2) on a thread-block cluster of CC CTAs, for n <= kClusterMaxN: the
+// single-problem drivers' factorisations, whose one-CTA form is bounded by one SM's FP64
+// pipe.
 //
 // Column j is owned by CTA j % CC; CTA c keeps its columns in registers, thread i holding
 // row i. Right-looking with one column of look-ahead: when column k is final, its owner
 // writes it into its own column buffer k and sends the buffer to every other CTA that still
 // needs it with one bulk copy (distributed shared memory) that completes the transaction
-// bytes of that CTA's mbarrier k (armed once with the copy's size); every CTA waits for
-// column k, the
-// owner of column k+1 applies it to that column first, finalises and sends column k+1, and
-// then every CTA applies column k to the rest of its columns. Each buffer and mbarrier is
-// written once, so there is no reuse to order. Per element the updates, the pivot test and
-// the scaling are the same operations in the same order as the one-CTA kernel
-// (cholesky_body.cuh), so the factors are identical.
+// bytes of that CTA's mbarrier k (armed once with the copy's size). Every CTA waits for
+// column k; the owner of column k+1 applies it to that column first, finalises and sends
+// column k+1; then every CTA applies column k to the rest of its columns. Each buffer and
+// mbarrier is written once, so there is no reuse to order. Per element the updates, the
+// pivot test and the scaling are the same operations in the same order as the one-CTA
+// kernel (cholesky_body.cuh), so the factors are identical.
 //
 // mode 0 (solve): a pivot <= tol_scale * max diag stops the factorisation (*info = column
 // + 1, singular bit); the stop travels with the column to every CTA. mode 1 (leverage): such

@@ -1,5 +1,6 @@
-// The relative-error contraction of fit_body.cuh on the 5th-generation tensor cores, for
-// X in FP32 and contraction length K <= 128.
+// The relative-error contraction of fit_body.cuh (the error ||TR - X|| / ||X|| of Sec. 5
+// and the stop rule of Sec. 4.1) on the 5th-generation tensor cores, for X in FP32 and
+// contraction length K <= 128.
 //
 // The right factors W are formed once per evaluation (fit_right_tc_warp) already split
 // into TF32 parts hi = rna(w), lo = rna(w - hi) and laid out as the MMA's K-major,

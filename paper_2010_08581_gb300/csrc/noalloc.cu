@@ -1,6 +1,6 @@
-// tr_solve_noalloc: the least-squares step of tr_solve for callers that cannot allocate
-// device memory. Its scratch space is one file-scope device array of fixed size; the
-// function never calls cudaMalloc, cudaFree or any allocating library routine.
+// tr_solve_noalloc: the least-squares step of tr_solve (Alg. 2) for callers that cannot
+// allocate device memory. Its scratch space is one file-scope device array of fixed size;
+// the function never calls cudaMalloc, cudaFree or any allocating library routine.
 #include <mutex>
 #include <string>
 

@@ -1,4 +1,5 @@
-// Single-problem launch of the triangular solves (trsm_body.cuh).
+// Single-problem launch of the triangular solves (trsm_body.cuh): the LS step of Alg. 2
+// (row a6) and the leverage rows of Def. 4 (row a1).
 #include "trsm_body.cuh"
 
 namespace trk {
