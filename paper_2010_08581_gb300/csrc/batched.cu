@@ -1,56 +1,13 @@
 // Batched stages of TR-ALS-Sampled (Alg. 2 per instance, Alg. 3 + Alg. 4 for the sketch):
-// one launch per stage for every instance of the table; see batched.cuh.
-#include "batched.cuh"
-#include "cholesky_body.cuh"
+// one launch per stage for every instance of the table; see batched.cuh. This file holds
+// the initial cores, the draws with their rows and fibres, the normal-equation contraction
+// and the leverage Grams; the factorisations, solves and fit live in batched_chol.cu,
+// batched_solve32.cu, batched_solve64.cu and batched_fit.cu.
+#include "batched_kern.cuh"
 #include "draw.cuh"
-#include "fit_tc.cuh"
-#include "trsm_body.cuh"
 
 namespace trk {
 namespace {
-
-// The core being updated (or, in an initialisation step, the core whose initial distribution
-// is formed) and its sizes. Leverage stages (`lev`) run in both kinds of step; the sampling
-// and solve stages only in updates.
-struct Cur {
-  bool active;
-  bool init;
-  int n, Rl, Rr, L;
-  int64_t I;
-  int t;             // update id (step) of an update
-};
-
-__device__ __forceinline__ Cur current(const BInst& d, int step, int init_k, bool lev) {
-  Cur c{};
-  if (lev && d.uniform) return c;   // uniform sampling forms no distributions
-  int k = 0, t = step;
-  if (d.slot) {
-    const SlotState& s = *d.slot;
-    if (s.status != kSlotRunning) return c;
-    t = s.step;
-    if (t < 0) {
-      if (!lev) return c;
-      k = t + d.N;
-    }
-  } else if (init_k > 0) {
-    if (d.nupd <= 0 || init_k >= d.N) return c;
-    k = init_k;
-  }
-  if (k > 0) {
-    c.init = true;
-    c.n = k;
-  } else {
-    if (t >= d.nupd) return c;
-    c.n = t % d.N;
-    c.t = t;
-  }
-  c.active = true;
-  c.Rl = d.ranks[(c.n - 1 + d.N) % d.N];
-  c.Rr = d.ranks[c.n];
-  c.L = c.Rl * c.Rr;
-  c.I = d.dims[c.n];
-  return c;
-}
 
 // ------------------------------------------------------------------------------------
 // Initial cores N(0,1) (same stream as launch_init_normal: stream id = core index).
@@ -302,321 +259,6 @@ __global__ void __launch_bounds__(GNT) kb_gram(const BInst* __restrict__ tab, in
   }
 }
 
-// ------------------------------------------------------------------------------------
-// Cholesky factorisations, one CTA per instance.
-// ------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(CNT) kb_cholesky(const BInst* __restrict__ tab, int step,
-                                                   int init_k, int which, unsigned* err,
-                                                   int smem_bytes, int mixed, int ls_mode) {
-  extern __shared__ double smem[];
-  const BInst& d = tab[blockIdx.x];
-  const Cur cu = current(d, step, init_k, which != 0);
-  if (!cu.active) return;
-  const double eps = 2.220446049250313e-16, eps32 = 1.1920928955078125e-07;
-  const bool tall = cu.I >= cu.L;
-  if (which == 0) {
-    const int n = cu.L;
-    const int64_t nn = static_cast<int64_t>(n) * n;
-    double* A = (nn * 8 <= smem_bytes) ? smem : d.Lrow;
-    if (mixed) {
-      float* A32 = (nn * 4 <= smem_bytes) ? reinterpret_cast<float*>(smem)
-                                          : reinterpret_cast<float*>(d.Lrow);
-      cholesky_cta_mixed<float>(d.M, n, ls_mode, static_cast<double>(n) * eps,
-                                static_cast<double>(n) * eps32, A32, A, d.Lrow, d.Lcol,
-                                d.invdiag, d.keep, d.info, err, static_cast<float*>(d.limg),
-                                d.mimg);
-      return;
-    }
-    cholesky_cta(d.M, n, ls_mode, static_cast<double>(n) * eps, A, d.Lrow, d.Lcol, d.invdiag,
-                 d.keep, d.info, err, static_cast<double*>(d.limg), nullptr, nullptr);
-    return;
-  }
-  const double tol = static_cast<double>(cu.I > cu.L ? cu.I : cu.L) * eps;
-  if (which == 1) {
-    const int n = tall ? cu.L : static_cast<int>(cu.I);
-    const int64_t nn = static_cast<int64_t>(n) * n;
-    double* A = (nn * 8 <= smem_bytes) ? smem : d.L1row;
-    if (mixed && tall) {   // double-float first; a wide pass-1 factor feeds pass 2 (FP64)
-      const double eps_ff = 9.094947017729282e-13;   // 2^-40
-      float* Aff = (panel_floats<FFOps>(n) * 4 <= smem_bytes) ? reinterpret_cast<float*>(smem)
-                                                               : nullptr;
-      cholesky_cta_lev_mixed(d.G1, n, tol, tol / eps * eps_ff, Aff, A, d.L1row, d.L1col, d.inv1,
-                             d.keep1, d.info1, err, d.img1);
-      return;
-    }
-    cholesky_cta(d.G1, n, 1, tol, A, d.L1row, d.L1col, d.inv1, d.keep1, d.info1, err, d.img1,
-                 nullptr, nullptr);
-    return;
-  }
-  if (tall) return;
-  const int n = static_cast<int>(cu.I);
-  double* A = (static_cast<int64_t>(n) * n * 8 <= smem_bytes) ? smem : d.L2row;
-  cholesky_cta(d.G2, n, 1, tol, A, d.L2row, d.L2col, d.inv2, d.keep2, d.info2, err, d.img2,
-               nullptr, nullptr);
-}
-
-// The FP64 image of a double-float leverage factor from the FP32 planes the factorisation
-// left in L1row / L1col (*info1 == 2; tall mixed instances only).
-__global__ void __launch_bounds__(256) kb_ff_image(const BInst* __restrict__ tab, int step,
-                                                   int init_k) {
-  const BInst& d = tab[blockIdx.x];
-  const Cur cu = current(d, step, init_k, true);
-  if (!cu.active || cu.I < cu.L || *d.info1 != 2) return;
-  const int n = cu.L;
-  const int64_t count = static_cast<int64_t>(n) * (n + 1);
-  const float* hi = reinterpret_cast<const float*>(d.L1row);
-  const float* lo = reinterpret_cast<const float*>(d.L1col);
-  for (int64_t e = static_cast<int64_t>(blockIdx.y) * blockDim.x + threadIdx.x; e < count;
-       e += static_cast<int64_t>(gridDim.y) * blockDim.x)
-    d.img1[e] = static_cast<double>(hi[e]) + static_cast<double>(lo[e]);
-}
-
-// ------------------------------------------------------------------------------------
-// Triangular solves: the LS solve (mode 2 mixed / mode 1 FP64) writing the new core, and
-// the leverage rows with the fused p / CDF step.
-// ------------------------------------------------------------------------------------
-// Runtime choice of the register rows (QN = ceil(n/32)) and of shared-memory staging:
-// n <= 128 always fits padded; beyond that the packed layout when it fits (`packed`), else
-// the image stays in global memory.
-template <typename T, int NB>
-__device__ __forceinline__ void trsm_dispatch(bool smem, bool packed, unsigned char* sm,
-                                              int64_t cta, int n,
-                                              const double* Lrow, const double* Lcol,
-                                              const double* invdiag, const int* info,
-                                              int64_t nvec, const double* rhs, int64_t ld,
-                                              int mode, const double* M, const T* Limg,
-                                              const float* Mimg, int Rl, int Rr,
-                                              double* core_out, double* ell,
-                                              const CdfEpilogue& ep, int nctas) {
-#define TB_ARGS sm, cta, n, Lrow, Lcol, invdiag, info, nvec, rhs, ld, mode, M, Limg, Mimg, Rl, Rr, \
-                core_out, ell, ep, nctas
-  switch ((n + 31) / 32) {
-    case 1: trsm_cta<T, 1, NB, true>(TB_ARGS); break;
-    case 2: trsm_cta<T, 2, NB, true>(TB_ARGS); break;
-    case 3: trsm_cta<T, 3, NB, true>(TB_ARGS); break;
-    case 4: trsm_cta<T, 4, NB, true>(TB_ARGS); break;
-    case 5:
-      if (smem) trsm_cta<T, 5, NB, true>(TB_ARGS);
-      else if (packed) trsm_cta<T, 5, NB, true, true>(TB_ARGS);
-      else trsm_cta<T, 5, NB, false>(TB_ARGS);
-      break;
-    case 6:
-      if (packed) trsm_cta<T, 6, NB, true, true>(TB_ARGS);
-      else trsm_cta<T, 6, NB, false>(TB_ARGS);
-      break;
-    case 7:
-      if (packed) trsm_cta<T, 7, NB, true, true>(TB_ARGS);
-      else trsm_cta<T, 7, NB, false>(TB_ARGS);
-      break;
-    case 8:
-      if (packed) trsm_cta<T, 8, NB, true, true>(TB_ARGS);
-      else trsm_cta<T, 8, NB, false>(TB_ARGS);
-      break;
-    default: break;
-  }
-#undef TB_ARGS
-}
-
-template <typename T, int NB>
-__global__ void __launch_bounds__(TW * 32) kb_solve(const BInst* __restrict__ tab, int step,
-                                                    int smem_bytes) {
-  extern __shared__ __align__(16) unsigned char sm[];
-  const BInst& d = tab[blockIdx.x];
-  const Cur cu = current(d, step, 0, false);
-  if (!cu.active) return;
-  const int n = cu.L;
-  const int64_t per = static_cast<int64_t>(TW) * NB;
-  const int nctas = static_cast<int>((cu.I + per - 1) / per);
-  if (static_cast<int>(blockIdx.y) >= nctas) return;
-  const int mode = sizeof(T) == 4 ? 2 : 1;
-  const CdfEpilogue none{};
-  const bool smem = staged_bytes<T>(n, mode) <= static_cast<size_t>(smem_bytes);
-  const bool packed = !smem && packed_bytes<T>(n) <= static_cast<size_t>(smem_bytes);
-  trsm_dispatch<T, NB>(smem, packed, sm, blockIdx.y, n, d.Lrow, d.Lcol, d.invdiag, d.info, cu.I,
-                       d.BT, n,
-                       mode, d.M, static_cast<const T*>(d.limg), d.mimg, cu.Rl, cu.Rr,
-                       d.cores[cu.n], nullptr, none, nctas);
-}
-
-__global__ void __launch_bounds__(TW * 32) kb_rows(const BInst* __restrict__ tab, int step,
-                                                   int init_k, unsigned* err, int smem_bytes) {
-  extern __shared__ __align__(16) unsigned char sm[];
-  const BInst& d = tab[blockIdx.x];
-  const Cur cu = current(d, step, init_k, true);
-  if (!cu.active) return;
-  const bool tall = cu.I >= cu.L;
-  const int n = tall ? cu.L : static_cast<int>(cu.I);
-  const double* rhs = tall ? (cu.init ? d.cores[cu.n] : d.BT) : d.L1row;
-  const int64_t ld = tall ? cu.L : cu.I;
-  const double* Lr = tall ? d.L1row : d.L2row;
-  const double* Lc = tall ? d.L1col : d.L2col;
-  const double* iv = tall ? d.inv1 : d.inv2;
-  const double* im = tall ? d.img1 : d.img2;
-  const int nctas = static_cast<int>((cu.I + TW - 1) / TW);
-  if (static_cast<int>(blockIdx.y) >= nctas) return;
-  const CdfEpilogue ep{d.counter, d.p[cu.n], d.cdf[cu.n], cu.init ? nullptr : d.info, err};
-  const bool smem = staged_bytes<double>(n, 0) <= static_cast<size_t>(smem_bytes);
-  const bool packed = !smem && packed_bytes<double>(n) <= static_cast<size_t>(smem_bytes);
-  trsm_dispatch<double, 1>(smem, packed, sm, blockIdx.y, n, Lr, Lc, iv, nullptr, cu.I, rhs, ld, 0,
-                           nullptr,
-                           im, nullptr, 1, 1, nullptr, d.ell, ep, nctas);
-}
-
-// ------------------------------------------------------------------------------------
-// Serving: relative fit 1 - ||TR - X|| / ||X|| (Sec. 5.1) of every slot that completed a
-// sweep in this tick, as kFitParts (or fewer) partial sums in a fixed order, then the stop
-// rule (|fit_s - fit_{s-1}| < tol after two or more sweeps, or the sweep cap) and the step
-// counters.
-// ------------------------------------------------------------------------------------
-// The slot's step is the last update of a sweep.
-__device__ __forceinline__ bool fit_due(const BInst& d) {
-  if (!d.slot) return false;
-  const SlotState& s = *d.slot;
-  return s.status == kSlotRunning && s.step >= 0 && s.step % d.N == d.N - 1;
-}
-
-// Partial sums of one slot's fit: one per CTA, at most kFitParts.
-__device__ __forceinline__ int fit_parts(const FitSplit& f, bool xf64) {
-  const int64_t nblk = fit_row_blocks(f, xf64);
-  return nblk < kFitParts ? static_cast<int>(nblk) : kFitParts;
-}
-
-__device__ __forceinline__ void fit_args(const BInst& d, FitArgs& fa) {
-  fa.N = d.N;
-  for (int m = 0; m < d.N; ++m) {
-    fa.core[m] = d.cores[m];
-    fa.dims[m] = d.dims[m];
-    fa.ranks[m] = d.ranks[m];
-  }
-}
-
-constexpr int kFitRightCtas = 64;   // CTAs per slot forming the right factors
-
-// Right factors of the fit: e-major W^T for the SIMT contraction, or the swizzled hi/lo
-// tiles of the tensor-core contraction.
-template <typename T>
-__global__ void __launch_bounds__(FNT) kb_fit_right(const BInst* __restrict__ tab) {
-  __shared__ T chain[8][kMaxL];
-  __shared__ T slice[8][kMaxL];
-  __shared__ FitArgs fa;
-  const BInst& d = tab[blockIdx.x];
-  if (!fit_due(d)) return;
-  if (threadIdx.x == 0) fit_args(d, fa);
-  __syncthreads();
-  const FitSplit f = fit_split(fa.N, fa.dims, fa.ranks);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t step = static_cast<int64_t>(gridDim.y) * (FNT / 32);
-  const int64_t q0 = static_cast<int64_t>(blockIdx.y) * (FNT / 32) + warp;
-  if constexpr (sizeof(T) == 4) {
-    if (fit_use_tc(f, false)) {
-      unsigned char* WS = static_cast<unsigned char*>(d.fitw);
-      const int64_t ncol = (f.cols + FTN - 1) / FTN * FTN;
-      for (int64_t q = q0; q < ncol; q += step)
-        fit_right_tc_warp(fa, f, q, WS, chain[warp], slice[warp], lane);
-      return;
-    }
-  }
-  T* WT = static_cast<T*>(d.fitw);
-  for (int64_t q = q0; q < f.cols; q += step)
-    fit_right_warp<T>(fa, f, q, WT, chain[warp], slice[warp], lane);
-}
-
-// Slots whose contraction length K lies in (k_lo, k_hi] (two launches with different
-// shared-memory sizes keep the common small-K case at several CTAs per SM).
-template <typename T>
-__global__ void __launch_bounds__(FNT) kb_fit(const BInst* __restrict__ tab, int k_lo, int k_hi) {
-  extern __shared__ __align__(16) unsigned char fit_dyn[];
-  __shared__ T chain[8][kMaxL];
-  __shared__ T slice[8][kMaxL];
-  __shared__ double red[2 * (FNT / 32)];
-  __shared__ FitArgs fa;
-  const BInst& d = tab[blockIdx.x];
-  if (!fit_due(d)) return;
-  if (threadIdx.x == 0) fit_args(d, fa);
-  __syncthreads();
-  const FitSplit f = fit_split(fa.N, fa.dims, fa.ranks);
-  if (fit_use_tc(f, sizeof(T) == 8) || f.K <= k_lo || f.K > k_hi) return;
-  const int parts = fit_parts(f, sizeof(T) == 8);
-  if (static_cast<int>(blockIdx.y) >= parts) return;
-  double se = 0.0, sx = 0.0;
-  fit_blocks<T>(fa, f, static_cast<const T*>(d.X), static_cast<const T*>(d.fitw), blockIdx.y,
-                parts, fit_dyn, chain, slice, se, sx);
-  fit_block_reduce(se, sx, red);
-  if (threadIdx.x == 0) {
-    d.fitp[blockIdx.y] = se;
-    d.fitp[kFitParts + blockIdx.y] = sx;
-  }
-}
-
-// Slots with FP32 X and K <= 128: the contraction on the tensor cores (fit_tc.cuh).
-__global__ void __launch_bounds__(FNT, 1) kb_fit_tc(const BInst* __restrict__ tab,
-                                                    unsigned* err) {
-  extern __shared__ __align__(1024) unsigned char fit_tc_dyn[];
-  __shared__ float chain[8][kMaxL];
-  __shared__ float slice[8][kMaxL];
-  __shared__ double red[2 * (FNT / 32)];
-  __shared__ FitArgs fa;
-  __shared__ FitTcShared sh;
-  const BInst& d = tab[blockIdx.x];
-  if (!fit_due(d) || d.xf64) return;
-  if (threadIdx.x == 0) fit_args(d, fa);
-  __syncthreads();
-  const FitSplit f = fit_split(fa.N, fa.dims, fa.ranks);
-  if (!fit_use_tc(f, false)) return;
-  const int parts = fit_parts(f, false);
-  if (static_cast<int>(blockIdx.y) >= parts) return;
-  double se = 0.0, sx = 0.0;
-  fit_tc_blocks(fa, f, static_cast<const float*>(d.X),
-                static_cast<const unsigned char*>(d.fitw),
-                blockIdx.y, parts, fit_tc_dyn, chain, slice, sh, err, se, sx);
-  fit_block_reduce(se, sx, red);
-  if (threadIdx.x == 0) {
-    d.fitp[blockIdx.y] = se;
-    d.fitp[kFitParts + blockIdx.y] = sx;
-  }
-}
-
-__global__ void __launch_bounds__(128) kb_advance(const BInst* __restrict__ tab, int count,
-                                                  int xf64) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= count) return;
-  const BInst& d = tab[i];
-  if (!d.slot) return;
-  SlotState& s = *d.slot;
-  if (s.status != kSlotRunning) return;
-  const int t = s.step;
-  if (t >= 0 && *d.info != 0) s.singular += 1;
-  if (fit_due(d)) {
-    const FitSplit f = fit_split(d.N, d.dims, d.ranks);
-    const int parts = fit_parts(f, xf64 != 0);
-    double se = 0.0, sx = 0.0;
-    for (int q = 0; q < parts; ++q) {
-      se += d.fitp[q];
-      sx += d.fitp[kFitParts + q];
-    }
-    const double rel = sx > 0.0 ? sqrt(se / sx) : (se > 0.0 ? INFINITY : 0.0);
-    const double fit = 1.0 - rel;
-    const int sw = s.sweeps + 1;
-    s.sweeps = sw;
-    s.fit_prev = s.fit;
-    s.fit = fit;
-    if (sw <= kMaxServedSweeps) d.hist[sw - 1] = fit;
-    if (!isfinite(fit)) s.status = kSlotFailed;
-    else if (sw >= 2 && fabs(fit - s.fit_prev) < s.tol) s.status = kSlotConverged;
-    else if (sw >= s.max_sweeps) s.status = kSlotCapped;
-  }
-  s.step = t + 1;
-}
-
-constexpr int kDyn = 200 * 1024;
-
-int smem_for_cholesky(int nmax) {
-  const int64_t need = static_cast<int64_t>(nmax) * nmax * 8;
-  const int64_t ff = panel_floats<FFOps>(nmax) * 4;
-  if ((ff > need ? ff : need) <= kDyn) return static_cast<int>(ff > need ? ff : need);
-  return need <= kDyn ? static_cast<int>(need) : 0;
-}
-
 }  // namespace
 
 cudaError_t bl_init_cores(const BLaunch& b, cudaStream_t st) {
@@ -651,46 +293,6 @@ cudaError_t bl_contract(const BLaunch& b, int step, cudaStream_t st) {
   return b.ctile == 32 ? contract_tile<32>(b, step, st) : contract_tile<64>(b, step, st);
 }
 
-cudaError_t bl_cholesky(const BLaunch& b, int step, int init_k, int which, unsigned* err,
-                        cudaStream_t st) {
-  const int nmax = which == 0 ? b.Lmax : (which == 1 ? b.n1max : b.n2max);
-  if (nmax <= 0) return cudaSuccess;
-  const int dyn = smem_for_cholesky(nmax);
-  kb_cholesky<<<b.count, CNT, dyn, st>>>(b.tab, step, init_k, which, err, dyn, b.f64 ? 0 : 1,
-                                          b.ls_mode);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess || which != 1 || b.f64) return e;
-  // double-float leverage factors leave FP32 planes: their FP64 image
-  const int64_t count = static_cast<int64_t>(nmax) * (nmax + 1);
-  dim3 grid(b.count, static_cast<unsigned>((count + 255) / 256 < 16 ? (count + 255) / 256 : 16));
-  kb_ff_image<<<grid, 256, 0, st>>>(b.tab, step, init_k);
-  return cudaGetLastError();
-}
-
-// Dynamic shared memory for the solve kernels: enough for every instance that takes the
-// shared-memory path (every n <= 128 does; n >= 161 never does).
-template <typename T>
-int solve_smem(int nmax, int mode) {
-  const int n = nmax < 160 ? nmax : 160;
-  size_t need = staged_bytes<T>(n, mode);
-  const size_t pk = packed_bytes<T>(nmax);
-  if (nmax > 128 && pk <= static_cast<size_t>(kDyn) && pk > need) need = pk;
-  return need <= static_cast<size_t>(kDyn) ? static_cast<int>(need) : kDyn;
-}
-
-cudaError_t bl_solve(const BLaunch& b, int step, cudaStream_t st) {
-  if (b.f64) {
-    const int dyn = solve_smem<double>(b.Lmax, 1);
-    dim3 grid(b.count, static_cast<unsigned>((b.Imax + TW - 1) / TW));
-    kb_solve<double, 1><<<grid, TW * 32, dyn, st>>>(b.tab, step, dyn);
-  } else {
-    const int dyn = solve_smem<float>(b.Lmax, 2);
-    dim3 grid(b.count, static_cast<unsigned>((b.Imax + 2 * TW - 1) / (2 * TW)));
-    kb_solve<float, 2><<<grid, TW * 32, dyn, st>>>(b.tab, step, dyn);
-  }
-  return cudaGetLastError();
-}
-
 cudaError_t bl_gram(const BLaunch& b, int step, int init_k, int pass, cudaStream_t st) {
   const int nmax = pass == 1 ? b.n1max : b.n2max;
   if (nmax <= 0) return cudaSuccess;
@@ -700,57 +302,18 @@ cudaError_t bl_gram(const BLaunch& b, int step, int init_k, int pass, cudaStream
   return cudaGetLastError();
 }
 
-cudaError_t bl_leverage_rows(const BLaunch& b, int step, int init_k, unsigned* err,
-                             cudaStream_t st) {
-  const int nmax = b.n1max > b.n2max ? b.n1max : b.n2max;
-  const int dyn = solve_smem<double>(nmax, 0);
-  dim3 grid(b.count, static_cast<unsigned>((b.Imax + TW - 1) / TW));
-  kb_rows<<<grid, TW * 32, dyn, st>>>(b.tab, step, init_k, err, dyn);
-  return cudaGetLastError();
-}
-
-cudaError_t bl_fit(const BLaunch& b, unsigned* err, cudaStream_t st) {
-  dim3 rgrid(b.count, kFitRightCtas);
-  dim3 grid(b.count, kFitParts);
-  constexpr int kSplitK = 128;
-  const int k_small = b.Lmax < kSplitK ? b.Lmax : kSplitK;
-  if (b.xf64) {
-    kb_fit_right<double><<<rgrid, FNT, 0, st>>>(b.tab);
-    kb_fit<double><<<grid, FNT, fit_smem_bytes<double>(k_small), st>>>(b.tab, 0, kSplitK);
-    if (b.Lmax > kSplitK)
-      kb_fit<double><<<grid, FNT, fit_smem_bytes<double>(b.Lmax), st>>>(b.tab, kSplitK, kMaxL);
-  } else {
-    kb_fit_right<float><<<rgrid, FNT, 0, st>>>(b.tab);
-    kb_fit_tc<<<grid, FNT, kFitTcSmem, st>>>(b.tab, err);
-    if (b.Lmax > kFitTcMaxK)
-      kb_fit<float><<<grid, FNT, fit_smem_bytes<float>(b.Lmax), st>>>(b.tab, kFitTcMaxK, kMaxL);
-  }
-  return cudaGetLastError();
-}
-
-cudaError_t bl_advance(const BLaunch& b, cudaStream_t st) {
-  kb_advance<<<(b.count + 127) / 128, 128, 0, st>>>(b.tab, b.count, b.xf64 ? 1 : 0);
-  return cudaGetLastError();
+cudaError_t bl_solve(const BLaunch& b, int step, cudaStream_t st) {
+  return b.f64 ? bl_solve_f64(b, step, st) : bl_solve_f32(b, step, st);
 }
 
 cudaError_t batched_attributes() {
-  cudaError_t e = cudaFuncSetAttribute(kb_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       kDyn);
+  cudaError_t e = batched_chol_attributes();
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(kb_solve<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kDyn);
+  e = batched_solve32_attributes();
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(kb_solve<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kDyn);
+  e = batched_solve64_attributes();
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(kb_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, kDyn);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(kb_fit<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           static_cast<int>(fit_smem_bytes<float>(kMaxL)));
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(kb_fit_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           static_cast<int>(kFitTcSmem));
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(kb_fit<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              static_cast<int>(fit_smem_bytes<double>(kMaxL)));
+  return batched_fit_attributes();
 }
 
 }  // namespace trk

@@ -1,8 +1,6 @@
 // Single-problem launches of the one-CTA Cholesky factorisation (cholesky_body.cuh) for
 // the leverage scores of Def. 4 (row a1) and the LS step of Alg. 2 (row a6): FP64, the
 // mixed LS step's FP32-then-FP64 form, and the double-float leverage form.
-#include <cstdlib>
-
 #include "cholesky_body.cuh"
 
 namespace trk {
@@ -70,7 +68,7 @@ __global__ void __launch_bounds__(256) k_ff_image(const float* __restrict__ hi,
 cudaError_t launch_ff_image(const double* Lrow, const double* Lcol, int n, const int* info,
                             double* img64, cudaStream_t st) {
   const int64_t count = static_cast<int64_t>(n) * (n + 1);
-  const unsigned blocks = static_cast<unsigned>((count + 255) / 256 < 152 ? (count + 255) / 256 : 152);
+  const unsigned blocks = static_cast<unsigned>((count + 255) / 256 < sm_count() ? (count + 255) / 256 : sm_count());
   k_ff_image<<<blocks, 256, 0, st>>>(reinterpret_cast<const float*>(Lrow),
                                      reinterpret_cast<const float*>(Lcol), count, info, img64);
   return cudaGetLastError();
@@ -101,29 +99,9 @@ cudaError_t launch_cholesky_mixed(const double* G, int n, int mode, double tol64
   return cudaGetLastError();
 }
 
-bool cholesky_cluster_fits(int n);
-cudaError_t launch_cholesky_cluster(const double* G, int n, int mode, double tol_scale,
-                                    double* Lrow, double* Lcol, double* invdiag, int* keep,
-                                    int* info, unsigned* err, cudaStream_t st, double* img64,
-                                    float* img32, float* gimg32);
-
-// The one-CTA kernel unless TRALS_CHOL_CLUSTER=1 selects the cluster form for n <= 144.
-// Both give the same factors; on GB300 the cluster form measured slower (each column's
-// hand-off between SMs costs more than the FP64 work it spreads), so it is opt-in.
-bool use_cluster_cholesky(int n) {
-  static const bool cluster = [] {
-    const char* e = getenv("TRALS_CHOL_CLUSTER");
-    return e && e[0] == '1';
-  }();
-  return cluster && cholesky_cluster_fits(n);
-}
-
 cudaError_t launch_cholesky(const double* G, int n, int mode, double tol_scale, double* Lrow,
                             double* Lcol, double* invdiag, int* keep, int* info, unsigned* err,
                             cudaStream_t st, double* img64, float* img32, float* gimg32) {
-  if (use_cluster_cholesky(n))
-    return launch_cholesky_cluster(G, n, mode, tol_scale, Lrow, Lcol, invdiag, keep, info, err,
-                                   st, img64, img32, gimg32);
   const size_t bytes = static_cast<size_t>(n) * n * sizeof(double);
   const int use_smem = bytes <= kCholDyn ? 1 : 0;
   const size_t dyn = use_smem ? bytes : 0;
@@ -132,8 +110,6 @@ cudaError_t launch_cholesky(const double* G, int n, int mode, double tol_scale, 
   return cudaGetLastError();
 }
 
-cudaError_t cholesky_cluster_attributes();
-
 cudaError_t cholesky_attributes() {
   cudaError_t e =
       cudaFuncSetAttribute(k_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize, kCholDyn);
@@ -141,10 +117,8 @@ cudaError_t cholesky_attributes() {
   e = cudaFuncSetAttribute(k_cholesky_mixed<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            kCholDyn);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_cholesky_lev_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           kCholDyn);
-  if (e != cudaSuccess) return e;
-  return cholesky_cluster_attributes();
+  return cudaFuncSetAttribute(k_cholesky_lev_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              kCholDyn);
 }
 
 }  // namespace trk

@@ -10,9 +10,7 @@
 //
 // The working type T is double or float. In FP64 the trailing triangle's (m+1)m/2 entries
 // are spread evenly over the threads (every lane busy: the FP64 pipe is the bound); every
-// update is one fused multiply-add, a_ij = fma(-l_ik, l_jk, a_ij), so that the cluster
-// kernel (cholesky_cluster.cu), which applies the same updates in the same order, gives
-// the same factor. In FP32 (the mixed-precision LS step, whose triangular solves already
+// update is one fused multiply-add, a_ij = fma(-l_ik, l_jk, a_ij). In FP32 (the mixed-precision LS step, whose triangular solves already
 // run in FP32) a warp takes whole rows and its lanes the columns, with no index arithmetic
 // per entry.
 //

@@ -196,6 +196,10 @@ size_t trsm_image_bytes(int n, bool f32);
 cudaError_t launch_init_normal(double* out, int64_t count, uint64_t seed, uint32_t stream_id,
                                const uint64_t* seed_dev, cudaStream_t st);
 
+// Number of SMs of the current device (queried once per device and cached); grids of the
+// streaming kernels and the split counts of the contractions are sized from it.
+int sm_count();
+
 // Raise the dynamic shared-memory limit of the kernels that need it (once per device);
 // on failure *which names the kernel.
 cudaError_t init_kernel_attributes(const char** which);

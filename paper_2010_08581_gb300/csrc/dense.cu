@@ -61,7 +61,7 @@ cudaError_t unfold_t(const TX* X, int64_t Ppre, int64_t In, int64_t Ppost, TY* Y
                      cudaStream_t st) {
   if (Ppost == 1) {
     const int64_t count = Ppre * In;
-    const unsigned blocks = static_cast<unsigned>(count / 256 + 1 < 152 * 16 ? count / 256 + 1 : 152 * 16);
+    const unsigned blocks = static_cast<unsigned>(count / 256 + 1 < sm_count() * 16 ? count / 256 + 1 : sm_count() * 16);
     k_convert<TX, TY><<<blocks, 256, 0, st>>>(X, count, Y);
     return cudaGetLastError();
   }

@@ -72,7 +72,7 @@ size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
 size_t fit_workspace(const FitArgs& a, bool x_f64, int* blocks) {
   const FitSplit f = split_of(a);
   int64_t b = fit_row_blocks(f, x_f64);
-  const int64_t cap = fit_use_tc(f, x_f64) ? 152 : 152 * 4;   // the tensor-core form: 1 CTA/SM
+  const int64_t cap = fit_use_tc(f, x_f64) ? sm_count() : sm_count() * 4;   // the tensor-core form: 1 CTA/SM
   if (b > cap) b = cap;
   if (b < 1) b = 1;
   *blocks = static_cast<int>(b);

@@ -247,11 +247,9 @@ __device__ void fit_blocks(const FitArgs& a, const FitSplit& f, const T* __restr
   auto vpos = [](int e, int ll) { return e * FL + (((ll / MI) ^ (e & 15)) * MI) + ll % MI; };
   const int N = a.N;
   const int K = f.K;
-  const int Rlast = a.ranks[N - 1];
   T* Vt = reinterpret_cast<T*>(dyn);   // [K][FL]
   T* Qt = Vt + K * FL;                 // [K][FI]
   const int64_t rows = f.rows, cols = f.cols;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ty = threadIdx.x / TX, tx = threadIdx.x % TX;
   const bool vec_ok = sizeof(T) == 4 && (cols % 4) == 0 &&
                       (reinterpret_cast<uintptr_t>(WT) % 16) == 0;

@@ -68,7 +68,7 @@ template <typename TX, typename TY>
 cudaError_t run(const GatherArgs& a, const void* X, const int32_t* idx, const double* w,
                 int64_t J, void* Y, unsigned* err, cudaStream_t st) {
   int64_t blocks = (J + kWarps - 1) / kWarps;
-  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks > sm_count() * 16) blocks = sm_count() * 16;
   k_gather<TX, TY><<<static_cast<unsigned>(blocks), kWarps * 32, 0, st>>>(
       a, static_cast<const TX*>(X), idx, w, J, static_cast<TY*>(Y), err);
   return cudaGetLastError();

@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(256) k_reduce(const TP* __restrict__ partial, 
 }
 
 int plan_splits(int64_t K, int tiles, int min_chunk, int64_t* chunk) {
-  int64_t s = (2 * 152 + tiles - 1) / tiles;
+  int64_t s = (2 * sm_count() + tiles - 1) / tiles;
   const int64_t maxs = (K + min_chunk - 1) / min_chunk;
   if (s > maxs) s = maxs;
   if (s < 1) s = 1;
@@ -172,7 +172,7 @@ cudaError_t launch_reduce(const void* partial, bool partial_f32, int splits, int
   const int64_t total = nrows * ncols;
   if (total <= 0) return cudaSuccess;
   int64_t blocks = (total + 255) / 256;
-  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks > sm_count() * 16) blocks = sm_count() * 16;
   if (partial_f32)
     k_reduce<float><<<static_cast<unsigned>(blocks), 256, 0, st>>>(
         static_cast<const float*>(partial), splits, pstride, pld, nrows, ncols, c_split, out1,

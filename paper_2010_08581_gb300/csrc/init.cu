@@ -1,4 +1,6 @@
 // The N(0,1) core initialiser (Sec. 4: cores drawn i.i.d. N(0,1)).
+#include <atomic>
+
 #include "draw.cuh"
 
 namespace trk {
@@ -21,6 +23,26 @@ __global__ void k_init_normal(double* __restrict__ out, int64_t count, uint32_t 
 }
 
 }  // namespace
+
+int sm_count() {
+  constexpr int kMaxDev = 64;
+  static std::atomic<int> cache[kMaxDev];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
+    cudaGetLastError();
+    dev = -1;
+  } else if (const int v = cache[dev].load(std::memory_order_relaxed); v > 0) {
+    return v;
+  }
+  int n = 0;
+  if (dev < 0 || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      n <= 0) {
+    cudaGetLastError();
+    return 148;   // a conservative count when no device can be queried
+  }
+  cache[dev].store(n, std::memory_order_relaxed);
+  return n;
+}
 
 cudaError_t launch_init_normal(double* out, int64_t count, uint64_t seed, uint32_t stream_id,
                                const uint64_t* seed_dev, cudaStream_t st) {

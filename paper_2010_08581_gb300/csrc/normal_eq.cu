@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(NT) k_normal_eq(const T* __restrict__ A,
 
 void plan(int64_t J, int L, int64_t I, int* splits, int64_t* chunk) {
   const int64_t tiles = ((L + BM - 1) / BM) * ((L + I + BN - 1) / BN);
-  int64_t s = (4 * 152 + tiles - 1) / tiles;
+  int64_t s = (4 * sm_count() + tiles - 1) / tiles;
   const int64_t maxs = (J + 63) / 64;  // at least 64 rows per chunk
   if (s > maxs) s = maxs;
   if (s < 1) s = 1;

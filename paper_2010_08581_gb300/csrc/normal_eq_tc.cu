@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(NT, 1) k_normal_eq_tc(const float* __restrict_
 
 void plan_tc(int64_t J, int L, int64_t I, int* splits, int64_t* chunk) {
   const int64_t tiles = ((L + TM - 1) / TM) * ((L + I + TN - 1) / TN);
-  int64_t s = (148 + tiles - 1) / tiles;
+  int64_t s = (sm_count() + tiles - 1) / tiles;
   const int64_t maxs = (J + 4 * TK - 1) / (4 * TK);   // at least 4 stages per CTA
   if (s > maxs) s = maxs;
   if (s < 1) s = 1;

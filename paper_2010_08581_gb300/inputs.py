@@ -1,8 +1,10 @@
 """Seeded synthetic inputs for TR-ALS-Sampled, shared by the tests, the oracle checks and
 the benchmark.
 
-This module only draws random numbers and lays them out; it holds no step of the sampled
-ALS method. Random cores are returned in the paper's shape ``(R_{k-1}, I_k, R_k)``
+This module draws random numbers and lays them out. To build a tensor from random cores it
+contracts the ring once (eq. 1, in ``_ring_tensor``); neither the oracle nor the CUDA path
+computes a tested result with that contraction, and it holds no other step of the method
+(no leverage scores, draws, design rows, fibres or least-squares solves). Random cores are returned in the paper's shape ``(R_{k-1}, I_k, R_k)``
 (Sec. 3.1); ``slice_major`` converts them to the library's ``[I_k][Rl][Rr]`` layout.
 
 Workload recipes (the paper's datasets are not available; these synthetic tensors stand
