@@ -32,7 +32,7 @@ __all__ = [
     "tr_reconstruct", "rel_error", "unfold_classical", "unfold_ring",
     "core_unfold2", "core_from_solution", "subchain_full", "subchain_unfold2",
     "leverage_scores", "core_distribution", "inverse_cdf", "draw_samples",
-    "draw_samples_uniform",
+    "draw_samples_uniform", "merge_duplicates",
     "sampled_subchain", "sampled_fibres", "sampled_ls_normal", "sampled_ls_normal_drop",
     "sampled_ls_qr",
     "sampled_core_update", "tr_als_sampled", "tr_als_sampled_until", "tr_als", "tr_als_update",
@@ -267,6 +267,21 @@ def draw_samples_uniform(dims, n, J, seed, update_id):
     return idx, w
 
 
+def merge_duplicates(idx, w):
+    """Merge repeated draws (Sec. 4.2): rows of the sketch that come from the same
+    multi-index are identical and carry the same rescaling w (Def. 5 depends only on the
+    multi-index), so the c copies of a row contribute c * w^2 a a^T to the normal equations,
+    which one row with weight sqrt(c) * w contributes as well. Returns (idx, w, counts) with
+    one row per distinct multi-index, in the order of first occurrence."""
+    idx = np.asarray(idx, dtype=np.int64)
+    w = np.asarray(w, dtype=np.float64)
+    _, first, inverse, counts = np.unique(idx, axis=0, return_index=True, return_inverse=True,
+                                          return_counts=True)
+    order = np.argsort(first, kind="stable")
+    return idx[first[order]], w[first[order]] * np.sqrt(counts[order].astype(np.float64)), \
+        counts[order]
+
+
 def sampled_subchain(cores, n, idx, w):
     """Sketch S G_[2]^{!=n} (Alg. 4): row j is the vectorised product of the sampled lateral
     slices G^(n+1)(:, i_{n+1}, :) ... G^(n-1)(:, i_{n-1}, :) (an R_n x R_{n-1} matrix),
@@ -337,18 +352,35 @@ def sampled_ls_qr(A, Y):
     return solve_triangular(R, Q.T @ Y, lower=False)
 
 
+def _solve(A, Y, solver):
+    """The LS step of Alg. 2 by the named solver: "qr" (the paper's QR-based solve),
+    "normal" (normal equations, Cholesky; stops on a singular design) or "normal_drop"
+    (normal equations with dependent columns dropped at pivot <= L * eps * max diag(A^T A),
+    the basic solution a rank-revealing QR-based solve gives)."""
+    if solver == "qr":
+        return sampled_ls_qr(A, Y)
+    if solver == "normal":
+        return sampled_ls_normal(A, Y)
+    if solver == "normal_drop":
+        return sampled_ls_normal_drop(A, Y, A.shape[1] * np.finfo(np.float64).eps)[0]
+    raise ValueError(f"unknown solver {solver!r}")
+
+
 def sampled_core_update(X, cores, ps, cdfs, n, J, seed, update_id, solver="qr",
-                        sampling="leverage"):
+                        sampling="leverage", merge=False):
     """One inner iteration of Alg. 2 for core n: draw S, sketch G and X, solve the sampled LS.
     ``sampling="uniform"`` draws S from the uniform distribution instead (Sec. 5, uniform
-    sampling; ``ps``/``cdfs`` are then unused). Returns (new core, idx, w)."""
+    sampling; ``ps``/``cdfs`` are then unused). ``merge`` merges repeated draws into one
+    weighted row (``merge_duplicates``, Sec. 4.2). Returns (new core, idx, w)."""
     if sampling == "uniform":
         idx, w = draw_samples_uniform(X.shape, n, J, seed, update_id)
     else:
         idx, w = draw_samples(ps, cdfs, n, J, seed, update_id)
+    if merge:
+        idx, w, _ = merge_duplicates(idx, w)
     A = sampled_subchain(cores, n, idx, w)
     Y = sampled_fibres(X, n, idx, w)
-    Z = (sampled_ls_qr if solver == "qr" else sampled_ls_normal)(A, Y)
+    Z = _solve(A, Y, solver)
     Rl, _, Rr = cores[n].shape
     return core_from_solution(Z, Rl, Rr), idx, w
 
@@ -365,45 +397,58 @@ def _initial_distributions(cores, sampling="leverage"):
     return ps, cdfs
 
 
-def _sweep(X, cores, ps, cdfs, J, seed, s, solver, sampling="leverage"):
-    """One pass of the outer loop of Alg. 2: update every core in order n = 0..N-1, each
-    followed by its new distribution (leverage sampling only); sweep s, core n uses
-    update_id = s * N + n."""
+def _sweep(X, cores, ps, cdfs, Js, seed, s, solver, sampling="leverage", merge=False):
+    """One pass of the outer loop of Alg. 2: update every core in order n = 0..N-1 with
+    Js[n] samples, each followed by its new distribution (leverage sampling only); sweep s,
+    core n uses update_id = s * N + n."""
     N = len(cores)
     for n in range(N):
-        cores[n], _, _ = sampled_core_update(X, cores, ps, cdfs, n, J, seed, s * N + n, solver,
-                                             sampling)
+        cores[n], _, _ = sampled_core_update(X, cores, ps, cdfs, n, Js[n], seed, s * N + n,
+                                             solver, sampling, merge)
         if sampling != "uniform":
             ps[n], cdfs[n] = core_distribution(cores[n])
 
 
-def _sweep_sizes(J, sweeps):
-    """J as one sample size for every sweep, or a per-sweep schedule (Sec. 4.2: the sample
-    size can change between updates at no cost)."""
+def _sweep_sizes(J, sweeps, N):
+    """The sample size of every update, Js[s][n] (Sec. 4.2: the sample size can change at any
+    point at no cost): J is one size for all updates, a list with one size per sweep, or a
+    list of sweeps lists with one size per core update."""
     if np.ndim(J) == 0:
-        return [int(J)] * sweeps
-    Js = [int(j) for j in J]
-    if len(Js) != sweeps:
+        return [[int(J)] * N for _ in range(sweeps)]
+    rows = list(J)
+    if len(rows) != sweeps:
         raise ValueError("a J schedule needs one entry per sweep")
-    return Js
+    out = []
+    for r in rows:
+        if np.ndim(r) == 0:
+            out.append([int(r)] * N)
+        else:
+            if len(r) != N:
+                raise ValueError("a per-update J schedule needs one entry per core")
+            out.append([int(v) for v in r])
+    return out
 
 
 def tr_als_sampled(X, init_cores, J, sweeps, seed, solver="qr", callback=None,
-                   sampling="leverage"):
+                   sampling="leverage", merge=False):
     """TR-ALS-Sampled (Alg. 2) with a fixed number of sweeps. ``init_cores`` supplies
     G^(2..N) (paper numbering); core 0 is overwritten by its first update. ``J`` is the
     sample size of every update, or a list with one sample size per sweep (Sec. 4.2).
+    A list of per-sweep lists gives one sample size per core update. ``merge`` merges
+    repeated draws into one weighted row (Sec. 4.2; the normal equations are unchanged).
     The sample block of (sweep s, core n) uses update_id = s * N + n. ``sampling`` is
     "leverage" (Alg. 2 as stated) or "uniform" (the Sec. 5 variant: uniform draws, no
-    distributions)."""
+    distributions). ``solver`` names the LS step (see ``_solve``); with "normal_drop" a
+    rank-deficient design gets a basic solution, and the next distribution is, as always,
+    the leverage of the new core (Alg. 2, "update n-th distribution")."""
     if sampling not in ("leverage", "uniform"):
         raise ValueError(f"unknown sampling {sampling!r}")
-    Js = _sweep_sizes(J, sweeps)
+    Js = _sweep_sizes(J, sweeps, len(init_cores))
     X = np.asarray(X, dtype=np.float64)
     cores = [np.array(G, dtype=np.float64, copy=True) for G in init_cores]
     ps, cdfs = _initial_distributions(cores, sampling)
     for s in range(sweeps):
-        _sweep(X, cores, ps, cdfs, Js[s], seed, s, solver, sampling)
+        _sweep(X, cores, ps, cdfs, Js[s], seed, s, solver, sampling, merge)
         if callback is not None:
             callback(s, cores)
     return cores
@@ -420,7 +465,7 @@ def tr_als_sampled_until(X, init_cores, J, seed, fit_tol, max_sweeps, solver="qr
     ps, cdfs = _initial_distributions(cores, sampling)
     fits = []
     for s in range(max_sweeps):
-        _sweep(X, cores, ps, cdfs, J, seed, s, solver, sampling)
+        _sweep(X, cores, ps, cdfs, [int(J)] * len(cores), seed, s, solver, sampling)
         fits.append(1.0 - rel_error(cores, X))
         if len(fits) >= 2 and abs(fits[-1] - fits[-2]) < fit_tol:
             return cores, fits, True

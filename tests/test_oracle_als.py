@@ -3,8 +3,10 @@ CPU only."""
 
 import numpy as np
 import pytest
+import torch
 
 import oracle as orc
+from paper_2010_08581_gb300 import inputs
 
 
 def test_sampled_ls_with_all_rows_is_exact_ls():
@@ -222,3 +224,41 @@ def test_j_schedule():
         np.testing.assert_array_equal(x, y)
     with pytest.raises(ValueError):
         orc.tr_als_sampled(X, init, [30], 2, seed=3)
+
+
+def _zero_slice_ring():
+    """A noise-free ring (9 x 8 x 7, ranks 3) whose rank index 2 between cores 0 and 1 is
+    unused: core 1's slices have a zero first row and core 0's a zero last column. Every
+    update of core 0 and core 1 then has a design with exactly zero columns."""
+    dims, ranks = (9, 8, 7), (3, 3, 3)
+    true = [c.numpy() for c in inputs.random_cores(dims, ranks, 21)]
+    true[1][2, :, :] = 0.0
+    true[0][:, :, 2] = 0.0
+    X = orc.tr_reconstruct(true)
+    pert = [c.numpy() for c in inputs.random_cores(dims, ranks, 22)]
+    init = [t + 0.05 * p for t, p in zip(true, pert)]
+    init[1][2, :, :] = 0.0
+    init[0][:, :, 2] = 0.0
+    return X, init
+
+
+def test_drop_driver_recovers_an_exact_ring_with_dependent_columns():
+    """Alg. 2 with the column-dropping LS step (basic solutions): the plain normal-equation
+    driver meets a singular normal matrix, the dropping driver recovers the exact tensor
+    ring to 1e-10, and the unused rank slices stay exactly zero."""
+    X, init = _zero_slice_ring()
+    with pytest.raises(np.linalg.LinAlgError):
+        orc.tr_als_sampled(X, init, 300, 1, 4, solver="normal")
+    out = orc.tr_als_sampled(X, init, 300, 60, 4, solver="normal_drop")
+    assert orc.rel_error(out, X) < 1e-10
+    assert np.all(out[1][2] == 0.0) and np.all(out[0][:, :, 2] == 0.0)
+
+
+def test_drop_driver_equals_normal_driver_for_full_rank_designs():
+    X, _ = inputs.tr_plus_noise((12, 10, 9), (2, 3, 2), seed=5, rel_noise=1e-2,
+                                dtype=torch.float64)
+    init = [c.numpy() for c in inputs.random_cores((12, 10, 9), (2, 3, 2), 6)]
+    a = orc.tr_als_sampled(X.numpy(), init, 200, 3, 7, solver="normal")
+    b = orc.tr_als_sampled(X.numpy(), init, 200, 3, 7, solver="normal_drop")
+    for x, y in zip(a, b):
+        np.testing.assert_allclose(y, x, rtol=1e-9, atol=1e-12)
