@@ -50,8 +50,12 @@ def workload_config(wl):
     return {
         "workload": f"{WORKLOAD}: 500x500x500 FP32 X = TR(rank-10 N(0,1) cores) + 1e-2 rel. "
                     f"Gaussian noise; target ranks 10, J={wl['J']}, {wl['sweeps']} sweeps per "
-                    "step (one whole decomposition), mixed precision (FP32 rows/fibres/"
-                    "contractions, FP64 Cholesky + refinement + leverage)",
+                    "step (one whole decomposition), mixed precision: FP32 design rows and "
+                    "fibres; TF32x3 tensor-core normal equations with FP32 accumulation; "
+                    "normal matrix factored in FP32 (FP64 if a pivot is small) with FP32 "
+                    "triangular solves and one refinement step; leverage Gram formed in FP64 "
+                    "and factored in double-float (FP64 if a pivot is small), FP64 leverage "
+                    "rows",
         "dims": list(wl["dims"]), "ranks": list(wl["ranks"]), "J": wl["J"],
         "sweeps_per_step": wl["sweeps"],
         "l2": "inputs larger than L2: X is 500 MB (> 129 MB L2); samples are redrawn every "
@@ -324,6 +328,35 @@ def oracle_sample(X_np, init_paper, wl, budget_s=15.0, max_sweeps=50):
     return sweeps, dt, ncores
 
 
+def oracle_sample_single_thread(budget_s=10.0):
+    """The same bounded oracle sample in a child process whose BLAS and OpenMP pools are held
+    to one thread (the thread counts are fixed when NumPy loads, hence the child). Returns
+    (sweeps, seconds) or None if the child fails."""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS",
+              "BLIS_NUM_THREADS", "VECLIB_MAXIMUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[k] = "1"
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    code = (
+        "import json, sys, torch\n"
+        f"sys.path.insert(0, {ROOT!r})\n"
+        "import bench\n"
+        "from paper_2010_08581_gb300 import inputs\n"
+        "torch.set_num_threads(1)\n"
+        "wl = inputs.WORKLOADS[bench.WORKLOAD]\n"
+        "X, _ = inputs.tr_plus_noise(wl['dims'], wl['ranks'], seed=wl['seed'], "
+        "rel_noise=wl['rel_noise'], dtype=torch.float32)\n"
+        "init = [c.numpy() for c in inputs.random_cores(wl['dims'], wl['ranks'], wl['init_seed'])]\n"
+        f"sw, dt, _ = bench.oracle_sample(X.numpy(), init, wl, budget_s={budget_s!r}, max_sweeps=50)\n"
+        "print(json.dumps({'sweeps': sw, 'seconds': dt}))\n")
+    try:
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                           timeout=budget_s * 20 + 120)
+        return json.loads(r.stdout.strip().splitlines()[-1])
+    except Exception:
+        return None
+
+
 def run_batched(T, plain_fp64, dev, steps, warmup, stream):
     """512 independent 3-way FP32 problems (I_n ~ U{32..200}, ranks ~ U{3..8}, J = 10 max L,
     10 sweeps each) through tr_als_sampled_batched: one step = the whole batch."""
@@ -383,6 +416,38 @@ def run_batched(T, plain_fp64, dev, steps, warmup, stream):
                       "ms_per_one_sweep_call": tuned.get("ms"),
                       "what": "launch shapes chosen by the project's autotuner on scratch "
                               "copies of this batch (results do not depend on them)"}}
+
+
+def run_fp64_factorisations(T, X, ranks, J, sweeps, init_dev, wl, stream, reps, value, fit):
+    """The headline decomposition with TR_FACTOR_FP64: the normal matrix and the leverage
+    Gram factored in FP64 (the rest of the mixed path unchanged), same inputs and seeds."""
+    ctx = T.Context(torch.cuda.current_device())
+    T.tr_set_factorization(ctx, T.TR_FACTOR_FP64)
+    cores = T.empty_cores(wl["dims"], ranks, device=X.device)
+
+    def call(i):
+        T.tr_als_sampled(ctx, X, ranks, J, sweeps, wl["sample_seed"] + i, T.TR_PREC_MIXED, cores,
+                         init_cores=init_dev)
+
+    for i in range(2):
+        call(i)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for i in range(reps):
+        call(i)
+    b.record(stream)
+    torch.cuda.synchronize()
+    sec = a.elapsed_time(b) / 1e3
+    err = T.tr_rel_error(ctx, X, ranks, cores)
+    ctx.close()
+    v = sweeps * reps / sec
+    return {"value": round(v, 3), "unit": "sweeps/s", "final_rel_err": err,
+            "default_over_this": round(value / v, 3),
+            "equal_fit": abs(err - fit) <= 0.01 * err,
+            "what": "normal matrix and leverage Gram factored in FP64 (TR_FACTOR_FP64); "
+                    "rows, fibres, contraction, FP32 solves with one refinement step as in "
+                    "the headline"}
 
 
 def run_uniform(T, X, ranks, J, sweeps, init_dev, dims, stream, reps):
@@ -779,6 +844,12 @@ def run_ours(args):
                "sample": f"{sw} whole sweeps of the same workload by the NumPy FP64 oracle "
                          f"(paper's QR solve), {dt:.1f} s on the host; cores = visible CPUs "
                          "(NumPy's BLAS default thread count)"}
+        st = oracle_sample_single_thread(min(10.0, args.cpu_seconds))
+        if st:
+            cpu["single_thread"] = {
+                "value": round(st["sweeps"] / st["seconds"], 4), "unit": "sweeps/s", "cores": 1,
+                "sample": f"{st['sweeps']} whole sweeps by the same oracle in a child process "
+                          f"with BLAS/OpenMP held to one thread, {st['seconds']:.1f} s"}
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -884,6 +955,13 @@ def run_ours(args):
                 "speedup": round(value / world / (sweeps * reps / sec), 2),
                 "equal_fit": abs(fit - fp64_fit) <= 0.01 * fp64_fit}
 
+    # the same decomposition with both factorisations in FP64 (configuration 2 as stated:
+    # "FP64 Cholesky plus one refinement step"), same inputs and seeds
+    fp64fact = None
+    if not args.skip_fp64 and world == 1:
+        fp64fact = run_fp64_factorisations(T, X, ranks, J, sweeps, init_dev, wl, stream,
+                                           max(1, min(args.steps, 5)), value, fit)
+
     # uniform sampling (Sec. 5 variant) on the same workload: at the same J and at 5 J (the
     # paper needs several times more uniform samples for the same error)
     uniform = None
@@ -946,6 +1024,7 @@ def run_ours(args):
             "kernels_ms": {k: [round(v[0], 4), v[1]] for k, v in
                            sorted(prof.items(), key=lambda kv: -kv[1][0])},
             "fp64_gpu_form": fp64,
+            "fp64_factorisations": fp64fact,
             "uniform_sampling": uniform,
             "dense_tr_als": dense,
             "batched_512": batched,

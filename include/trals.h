@@ -42,8 +42,8 @@ typedef enum tr_status {
   TR_ERR_OOM = 2,          /* device allocation failed                                  */
   TR_ERR_BUDGET = 3,       /* workspace would exceed the context's HBM budget          */
   TR_ERR_SINGULAR = 4,     /* non-positive pivot in the normal equations, or zero core */
-  TR_ERR_TIMEOUT = 5,      /* a bounded device wait expired (tensor-core pipeline,      */
-                           /* cluster factorisation), or tr_server_wait's time ran out */
+  TR_ERR_TIMEOUT = 5,      /* a bounded device wait expired (tensor-core pipeline; see  */
+                           /* tr_set_wait_limit), or tr_server_wait's time ran out     */
   TR_ERR_CUDA = 6,         /* a CUDA runtime call failed (see tr_last_error)            */
   TR_ERR_NOT_CONVERGED = 7 /* a served request stopped at its sweep cap (result kept)    */
 } tr_status;
@@ -88,7 +88,8 @@ void tr_destroy(tr_ctx* ctx);
 const char* tr_last_error(const tr_ctx* ctx);
 
 /* Wait for `stream`, then return and clear the device-side error record of the context
- * (TR_ERR_SINGULAR, TR_ERR_INVALID_ARG for out-of-range sample indices, or TR_OK). */
+ * (TR_ERR_TIMEOUT for an expired bounded wait, TR_ERR_INVALID_ARG for out-of-range sample
+ * indices, TR_ERR_SINGULAR, or TR_OK; the first that applies in this order). */
 tr_status tr_status_sync(tr_ctx* ctx, tr_stream stream);
 
 /* Row a1 -- sampling distribution of one core (Def. 4; eq. for p^(n); Alg. 2, "compute
@@ -96,8 +97,12 @@ tr_status tr_status_sync(tr_ctx* ctx, tr_stream stream);
  * core  : FP64 [I][Rl][Rr]; the matrix G_(2) is I x (Rl*Rr).
  * p     : FP64 [I] out, p[i] = ell_i(G_(2)) / sum_i ell_i(G_(2)).
  * cdf   : FP64 [I] out, inclusive prefix sum of p in index order.
- * Leverage scores come from a Cholesky-based thin QR of G_(2) (or of G_(2)^T when
- * I < Rl*Rr) in FP64, with dependent columns dropped at pivot <= max(I,L)*eps*max diag.
+ * Leverage scores, in FP64: for a wide G_(2) with few rows (I < L = Rl*Rr, I <= 48) by
+ * one-sided Jacobi rotations of its rows, keeping the directions whose singular value is
+ * above max(I,L)*eps*sigma_max (the rule of a singular value decomposition); otherwise from
+ * a Cholesky-based thin QR of G_(2) (or of G_(2)^T when I < L), with dependent columns
+ * dropped at pivot <= max(I,L)*eps*max diag, which resolves singular values down to about
+ * sqrt(max(I,L)*eps)*sigma_max. The drivers form every distribution the same way.
  * A zero core records TR_ERR_SINGULAR and yields the uniform distribution. */
 tr_status tr_leverage(tr_ctx* ctx, const double* core, int64_t I, int Rl, int Rr,
                       double* p, double* cdf, tr_stream stream);
@@ -179,6 +184,35 @@ tr_status tr_als_sampled_schedule(tr_ctx* ctx, const void* X, tr_dtype X_dtype, 
                                   tr_precision prec, const double* const* init_cores,
                                   double* const* cores, tr_stream stream);
 
+/* tr_als_sampled with one sample size per core update (Sec. 4.2: J can be changed at any
+ * point at no cost): the update of core n in sweep s draws J_per_update[s*N + n] samples
+ * (host array of sweeps*N entries, each in [1, 2^31-1]); the workspace is sized for the
+ * largest. Everything else as tr_als_sampled. */
+tr_status tr_als_sampled_adaptive(tr_ctx* ctx, const void* X, tr_dtype X_dtype, int N,
+                                  const int64_t* dims, const int* ranks,
+                                  const int64_t* J_per_update, int sweeps, uint64_t seed,
+                                  tr_precision prec, const double* const* init_cores,
+                                  double* const* cores, tr_stream stream);
+
+/* Merging repeated draws (Sec. 4.2). Draws are made with replacement, so a multi-index can
+ * be drawn several times; its rows of the sketch are then identical and carry the same
+ * weight w (Def. 5), and c copies of a row contribute to the normal equations what one row
+ * with weight sqrt(c) * w contributes.
+ * tr_merge_samples: idx [J][N-1], w [J] (device, as tr_sample writes them) -> idx_out, w_out
+ *   (device, capacity J) with one row per distinct multi-index, in the order of first
+ *   occurrence, weight w * sqrt(count); *J_out (device int64) receives their number. Rows
+ *   of idx_out / w_out beyond *J_out are not written. J must be in [1, 8192] and the product
+ *   of the sampled modes' sizes below 2^63, else TR_ERR_INVALID_ARG before any launch.
+ * tr_set_merge_duplicates(ctx, 1): the single-problem drivers of this context merge every
+ *   update's draws before forming rows and fibres (updates with J above 8192 or an index
+ *   space of 2^63 or more are not merged); the rows, fibres and contraction then run over the
+ *   merged count only. Results equal the unmerged ones up to rounding. Off by default. */
+tr_status tr_merge_samples(tr_ctx* ctx, int N, int k, const int64_t* dims, const int32_t* idx,
+                           const double* w, int64_t J, int32_t* idx_out, double* w_out,
+                           int64_t* J_out, tr_stream stream);
+tr_status tr_set_merge_duplicates(tr_ctx* ctx, int on);
+tr_status tr_get_merge_duplicates(const tr_ctx* ctx, int* on);
+
 /* Dense TR-ALS (Alg. 1), the comparison method of Sec. 5, with a fixed number of sweeps,
  * synchronous. Core update n solves the full least-squares problem
  * argmin_Z || G_[2]^{!=n} Z - X_[n]^T ||_F over all prod_{j!=n} I_j rows, each with weight 1
@@ -256,6 +290,30 @@ tr_status tr_get_ls_rank(const tr_ctx* ctx, tr_ls_rank* rule);
 tr_status tr_set_sampling(tr_ctx* ctx, tr_sampling sampling);
 tr_status tr_get_sampling(const tr_ctx* ctx, tr_sampling* sampling);
 
+/* Factorisations of the mixed-precision path (TR_PREC_MIXED) in tr_solve and the drivers:
+ * TR_FACTOR_DEFAULT: as TR_PREC_MIXED describes (FP32 normal-matrix factor and double-float
+ *                    leverage factor, each with its FP64 fallback);
+ * TR_FACTOR_FP64   : both factored in FP64 (the normal matrix with the FP64 singular rule,
+ *                    then FP32 triangular solves with one refinement step; the leverage
+ *                    Gram as TR_PREC_FP64 does).
+ * The batched driver and the server keep their own rules. Other values return
+ * TR_ERR_INVALID_ARG. */
+typedef enum tr_factorization { TR_FACTOR_DEFAULT = 0, TR_FACTOR_FP64 = 1 } tr_factorization;
+tr_status tr_set_factorization(tr_ctx* ctx, tr_factorization f);
+tr_status tr_get_factorization(const tr_ctx* ctx, tr_factorization* f);
+
+/* Poll limit of the bounded device waits of this context's tensor-core contraction (rows
+ * a5: the pipeline waits of the FP32 normal-equation kernel used by tr_solve and the drivers
+ * with TR_PREC_MIXED). A context starts with the default (polls < 0), 2^26 polls per wait,
+ * which only a stalled GPU exhausts. When a wait expires the kernel stops issuing, waits for
+ * the MMAs it has already committed (with the default limit), frees its tensor memory and
+ * returns without writing its partial sums; the LS step then leaves the core unchanged and
+ * the next tr_status_sync (or the synchronous driver) returns TR_ERR_TIMEOUT. The context
+ * stays usable. polls = 0 makes every such wait expire at once, a diagnostic setting with
+ * which a caller or a test can exercise the error path. */
+tr_status tr_set_wait_limit(tr_ctx* ctx, int64_t polls);
+tr_status tr_get_wait_limit(const tr_ctx* ctx, int64_t* polls);
+
 /* Launch shapes of the batched driver's kernels, chosen per batch geometry by the
  * project's autotuner (paper_2010_08581_gb300/autotune.py), which times the candidates on
  * scratch copies of a batch. Neither field changes any result: samples are independent,
@@ -279,25 +337,28 @@ tr_status tr_get_batched_tiles(const tr_ctx* ctx, tr_batched_tiles* tiles);
  * Some callers cannot call cudaMalloc: code that issues work while a CUDA graph is being
  * captured in global mode (allocation is not allowed there), latency-critical serving
  * loops where cudaMalloc/cudaFree would synchronise the device, and hosts that have
- * partitioned all device memory up front. tr_solve_noalloc computes exactly what
- * tr_solve computes (same kernels, same arguments, same results) but takes its scratch
- * from one fixed 16 MiB array that the library keeps in device memory; it calls no
+ * partitioned all device memory up front. tr_solve_noalloc computes what tr_solve computes
+ * on a context with the default settings (TR_LS_RANK_STOP, the default wait limit): the
+ * same kernels with the same arguments, so the new core is bit-identical. It takes its
+ * scratch from one fixed 16 MiB array that the library keeps in device memory, calls no
  * cudaMalloc, cudaFree or allocating library routine, and needs no context.
  *
  * - Every GPU on which the library is loaded holds the 16 MiB array until the process
  *   exits.
- * - A problem whose scratch (the split partials of the L x (L+I) contraction plus the
- *   L x I right-hand sides and the factor) exceeds 16 MiB is rejected with
+ * - A problem whose scratch (the split partials of the L x (L+I) contraction, the L x I
+ *   right-hand sides, the factor and its images) exceeds 16 MiB is rejected with
  *   TR_ERR_INVALID_ARG and a message (tr_last_error(NULL)); nothing is launched. For
  *   J = 4000, L = 100, I = 500 about 7 MiB are used.
- * - All calls share the array and it keeps the previous call's contents, so calls that
- *   overlap on the GPU (on different streams, or on several host threads) race and give
- *   wrong results: serialise them on one stream.
+ * - All calls share the array and it keeps the previous call's contents (each call clears
+ *   what must start at zero), so calls that overlap on the GPU (on different streams, or on
+ *   several host threads) race and give wrong results: serialise them on one stream.
  * - The first call on each device (with that device current) resolves the array's
  *   device address and sets kernel attributes; make that first call before any stream
- *   capture begins.
- * - info (device int32, may be NULL) receives 0, or column+1 of the first non-positive
- *   pivot, in which case core_out is left unchanged.
+ *   capture begins. The address is kept for the life of the process: after
+ *   cudaDeviceReset on that device the entry point must not be called again.
+ * - info (device int32, may be NULL) receives 0 on success, column+1 of the first
+ *   non-positive pivot, or -1 when a bounded wait of the tensor-core contraction expired
+ *   (TR_PREC_MIXED); in both failure cases core_out is left unchanged.
  * Arguments otherwise as tr_solve; the current device must be the one holding the data. */
 tr_status tr_solve_noalloc(const void* A, const void* Y, tr_dtype dtype, int64_t J, int Rl,
                            int Rr, int64_t I, tr_precision prec, double* core_out,

@@ -48,6 +48,9 @@ struct tr_ctx {
   tr_batched_tiles tiles{4, 64};    // launch shapes of the batched kernels
   tr_sampling sampling = TR_SAMPLING_LEVERAGE;   // draws of tr_als_sampled / batched
   tr_ls_rank ls_rank = TR_LS_RANK_STOP;          // rule for small pivots of the LS step
+  long long wait_limit = -1;                     // polls per bounded wait (< 0: default)
+  tr_factorization factorization = TR_FACTOR_DEFAULT;  // mixed path's factorisations
+  int merge = 0;                                 // merge repeated draws in the drivers
 };
 
 namespace {
@@ -255,6 +258,13 @@ tr_status leverage_dist(tr_ctx* ctx, char* ws, const double* mat, int64_t I, int
   LevPass p1{}, p2{};
   double* ell;
   leverage_plan(c, I, L, &p1, &p2, &ell);
+  if (I < L && leverage_jacobi_fits(I, L)) {
+    // Wide G_(2) with few rows: one-sided Jacobi in one CTA, the singular-value rank rule
+    if (wait_before_rows) TR_CUDA(cudaStreamWaitEvent(st, wait_before_rows, 0));
+    TR_LAUNCH("leverage_jacobi", launch_leverage_jacobi(mat, I, L, L, ell, p, cdf, skip,
+                                                        ctx->d_err, st));
+    return TR_OK;
+  }
   unsigned* counter = reinterpret_cast<unsigned*>(reinterpret_cast<char*>(ell) +
                                                   ((I * sizeof(double) + 255) & ~size_t(255)));
   const double eps = 2.220446049250313e-16;
@@ -290,7 +300,7 @@ tr_status leverage_run(tr_ctx* ctx, char* ws, const double* core, int64_t I, int
 // ------------------------------------------------------------------------------------
 struct SolvePlan {
   void* partial; double* M; double* BT; double* Lrow; double* Lcol; double* invdiag;
-  int* keep; int* info; void* limg; float* mimg; int splits;
+  int* keep; int* info; void* limg; float* mimg; float* wimg; int splits;
 };
 
 bool use_tensor_cores(bool f64) {
@@ -312,6 +322,7 @@ size_t solve_plan(Carver& c, int64_t J, int L, int64_t I, bool f64, SolvePlan* s
   s->info = c.take<int>(1);
   s->limg = c.take<char>(trsm_image_bytes(L, !f64));
   s->mimg = f64 ? nullptr : reinterpret_cast<float*>(c.take<char>(trsm_image_bytes(L, true)));
+  s->wimg = f64 ? nullptr : reinterpret_cast<float*>(c.take<char>(trsm_image_bytes(L, true)));
   return c.off;
 }
 
@@ -322,15 +333,16 @@ size_t solve_bytes(int64_t J, int L, int64_t I, bool f64) {
 }
 
 tr_status solve_contract(tr_ctx* ctx, const SolvePlan& s, const void* A, const void* Y,
-                         bool f64, int64_t J, int L, int64_t I, cudaStream_t st) {
+                         bool f64, int64_t J, int L, int64_t I, cudaStream_t st,
+                         const int64_t* jdev = nullptr) {
   const int64_t ld = L + I;
   if (use_tensor_cores(f64)) {
     TR_LAUNCH("normal_eq_tc", launch_normal_eq_tc(static_cast<const float*>(A),
                                                   static_cast<const float*>(Y), J, L, I,
                                                   static_cast<float*>(s.partial), s.splits,
-                                                  ctx->d_err, st));
+                                                  ctx->d_err, st, ctx->wait_limit, jdev));
   } else {
-    TR_LAUNCH("normal_eq", launch_normal_eq(A, Y, f64, J, L, I, s.partial, s.splits, st));
+    TR_LAUNCH("normal_eq", launch_normal_eq(A, Y, f64, J, L, I, s.partial, s.splits, st, jdev));
   }
   // mixed: the reduction also writes M's FP32 values in the factorisation's work-array
   // layout (into Lrow, free until an FP64 fallback) and M's FP32 image
@@ -349,6 +361,14 @@ tr_status solve_contract(tr_ctx* ctx, const SolvePlan& s, const void* A, const v
 tr_status solve_cholesky(tr_ctx* ctx, const SolvePlan& s, bool f64, int L, cudaStream_t st) {
   const double eps = 2.220446049250313e-16;
   const int mode = ctx->ls_rank == TR_LS_RANK_DROP ? 1 : 0;
+  if (!f64 && ctx->factorization == TR_FACTOR_FP64) {
+    // FP64 factorisation, FP32 image of the factor for the FP32 solves with refinement
+    TR_LAUNCH("cholesky_solve",
+              launch_cholesky(s.M, L, mode, static_cast<double>(L) * eps, s.Lrow, s.Lcol,
+                              s.invdiag, s.keep, s.info, ctx->d_err, st, nullptr,
+                              static_cast<float*>(s.limg), s.mimg));
+    return TR_OK;
+  }
   if (!f64) {
     const double eps32 = 1.1920928955078125e-07;
     TR_LAUNCH("cholesky_solve",
@@ -370,6 +390,12 @@ tr_status solve_cholesky(tr_ctx* ctx, const SolvePlan& s, bool f64, int L, cudaS
 tr_status solve_rhs(tr_ctx* ctx, const SolvePlan& s, int Rl, int Rr, int64_t I, bool refine,
                     double* core_out, cudaStream_t st) {
   const int L = Rl * Rr;
+  if (refine && solve_inv_fits(L)) {
+    TR_LAUNCH("solve_rhs", launch_solve_inv(L, static_cast<const float*>(s.limg), s.mimg,
+                                            s.invdiag, s.info, I, s.BT, L, Rl, Rr, core_out,
+                                            s.wimg, st));
+    return TR_OK;
+  }
   TR_LAUNCH("solve_rhs", launch_trsm(refine ? 2 : 1, refine, L, s.Lrow, s.Lcol, s.invdiag, s.info,
                                       I, s.BT, L, s.M, Rl, Rr, core_out, nullptr, st, s.limg,
                                       s.mimg));
@@ -399,15 +425,28 @@ tr_status solve_run(tr_ctx* ctx, char* ws, const void* A, const void* Y, bool f6
 // distribution if the solve reported a singular system (the core is then unchanged).
 tr_status update_run(tr_ctx* ctx, char* ws, size_t solve_ws, const void* A, const void* Y,
                      bool f64, int64_t J, int Rl, int Rr, int64_t I, double* core_out, double* p,
-                     double* cdf, cudaStream_t st, cudaStream_t side) {
+                     double* cdf, cudaStream_t st, cudaStream_t side,
+                     const int64_t* jdev = nullptr) {
   const int L = Rl * Rr;
   Carver c(ws);
   SolvePlan s;
   solve_plan(c, J, L, I, f64, &s);
-  TR_TRY(solve_contract(ctx, s, A, Y, f64, J, L, I, st));
+  TR_TRY(solve_contract(ctx, s, A, Y, f64, J, L, I, st, jdev));
   if (!p) {   // uniform sampling: the new core needs no distribution
     TR_TRY(solve_cholesky(ctx, s, f64, L, st));
     return solve_rhs(ctx, s, Rl, Rr, I, !f64, core_out, st);
+  }
+  const bool mixed_lev = !f64 && ctx->factorization != TR_FACTOR_FP64;
+  if (ctx->ls_rank == TR_LS_RANK_DROP) {
+    // A dropped column is only nearly dependent on the kept ones, and its unknowns are set to
+    // zero: the new core's column space is that of the kept columns of B^T, not of B^T. The
+    // distribution is therefore the leverage of the new core itself (Alg. 2, "update n-th
+    // distribution"), formed after the solve. The core's slice-major rows are its G_(2) rows
+    // with the columns permuted, which leaves the leverage scores unchanged.
+    TR_TRY(solve_cholesky(ctx, s, f64, L, st));
+    TR_TRY(solve_rhs(ctx, s, Rl, Rr, I, !f64, core_out, st));
+    return leverage_dist(ctx, ws + solve_ws, core_out, I, L, p, cdf, s.info, st, nullptr,
+                         mixed_lev);
   }
   TR_CUDA(cudaEventRecord(ctx->ev_fork, st));
   TR_CUDA(cudaStreamWaitEvent(side, ctx->ev_fork, 0));
@@ -416,7 +455,8 @@ tr_status update_run(tr_ctx* ctx, char* ws, size_t solve_ws, const void* A, cons
   // keep the old distribution when the core was not updated.
   TR_CUDA(cudaEventRecord(ctx->ev_info, st));
   TR_TRY(solve_rhs(ctx, s, Rl, Rr, I, !f64, core_out, st));
-  TR_TRY(leverage_dist(ctx, ws + solve_ws, s.BT, I, L, p, cdf, s.info, side, ctx->ev_info, !f64));
+  TR_TRY(leverage_dist(ctx, ws + solve_ws, s.BT, I, L, p, cdf, s.info, side, ctx->ev_info,
+                       mixed_lev));
   TR_CUDA(cudaEventRecord(ctx->ev_join, side));
   TR_CUDA(cudaStreamWaitEvent(st, ctx->ev_join, 0));
   return TR_OK;
@@ -465,8 +505,10 @@ struct AlsPlan {
   int sweeps; tr_precision prec; const double* const* init; double* const* cores;
   const int64_t* Js = nullptr;   // per-sweep sample sizes (Sec. 4.2), or null: J for all;
                                  // J is then their maximum (workspace)
+  const int64_t* Jupd = nullptr; // per-update sample sizes [sweeps][N] (Sec. 4.2), or null
   std::vector<double*> p, cdf;
   int32_t* idx; double* w; void* A; void* Y; char* ws;
+  int32_t* idx2 = nullptr; double* w2 = nullptr; int64_t* jm = nullptr;   // merged draws
   size_t solve_ws;   // bytes of the stage region used by the LS step; leverage follows it
 };
 
@@ -489,6 +531,11 @@ tr_status als_plan(tr_ctx* ctx, AlsPlan& P) {
     P.w = c.take<double>(P.J);
     P.A = c.take<char>(static_cast<size_t>(P.J) * Lmax * es);
     P.Y = c.take<char>(static_cast<size_t>(P.J) * Imax * es);
+    if (ctx->merge) {
+      P.idx2 = c.take<int32_t>(static_cast<size_t>(P.J) * (N - 1));
+      P.w2 = c.take<double>(P.J);
+      P.jm = c.take<int64_t>(1);
+    }
   };
   double *pb, *cb;
   Carver dry(nullptr);
@@ -537,7 +584,7 @@ tr_status als_issue(tr_ctx* ctx, const AlsPlan& P, uint64_t seed, const uint64_t
   if (!uni)
     for (int k = 1; k < N; ++k)
       TR_TRY(leverage_run(ctx, P.ws, P.cores[k], dims[k], rl_of(ranks, N, k), ranks[k], P.p[k],
-                          P.cdf[k], st, !f64));
+                          P.cdf[k], st, !f64 && ctx->factorization != TR_FACTOR_FP64));
   int64_t stride[kMaxModes];
   row_major_strides(N, dims, stride);
   const bool x64 = P.xdt == TR_F64;
@@ -562,13 +609,29 @@ tr_status als_issue(tr_ctx* ctx, const AlsPlan& P, uint64_t seed, const uint64_t
       ga.In = dims[n];
       ga.stride_n = stride[n];
       const uint64_t uid = static_cast<uint64_t>(s) * N + n;
-      const int64_t Jn = P.Js ? P.Js[s] : P.J;
-      TR_LAUNCH("sample_chain", launch_sample_chain(sa, ca, Jn, seed, uid, P.idx, P.w, P.A, f64,
-                                                    st));
-      TR_LAUNCH("gather", launch_gather(ga, P.X, x64, P.idx, P.w, Jn, P.Y, f64, ctx->d_err, st));
+      const int64_t Jn = P.Jupd ? P.Jupd[static_cast<int64_t>(s) * N + n]
+                                : (P.Js ? P.Js[s] : P.J);
+      MergeArgs ma{};
+      const bool merge = ctx->merge && P.jm && merge_fits(Jn, N - 1, sa.I, &ma);
+      if (merge) {
+        // Sec. 4.2: draws, then one row per distinct multi-index with weight sqrt(count) w;
+        // the rows, fibres and contraction take the merged count from device memory
+        TR_LAUNCH("sample", launch_sample(sa, Jn, seed, uid, P.idx, P.w, st));
+        TR_LAUNCH("merge", launch_merge(P.idx, P.w, Jn, N - 1, ma, P.idx2, P.w2, P.jm, st));
+        SampleArgs sg = sa;
+        sg.given_idx = P.idx2;
+        sg.given_w = P.w2;
+        sg.jdev = P.jm;
+        TR_LAUNCH("sample_chain", launch_sample_chain(sg, ca, Jn, seed, uid, P.idx, P.w, P.A,
+                                                      f64, st, &ga, P.X, x64, P.Y));
+      } else {
+        TR_LAUNCH("sample_chain", launch_sample_chain(sa, ca, Jn, seed, uid, P.idx, P.w, P.A,
+                                                      f64, st, &ga, P.X, x64, P.Y));
+      }
       const int Rl = rl_of(ranks, N, n), Rr = ranks[n];
       TR_TRY(update_run(ctx, P.ws, P.solve_ws, P.A, P.Y, f64, Jn, Rl, Rr, dims[n], P.cores[n],
-                        uni ? nullptr : P.p[n], uni ? nullptr : P.cdf[n], st, side));
+                        uni ? nullptr : P.p[n], uni ? nullptr : P.cdf[n], st, side,
+                        merge ? P.jm : nullptr));
     }
   }
   return TR_OK;
@@ -589,6 +652,11 @@ std::vector<uint64_t> als_key(const tr_ctx* ctx, const AlsPlan& P) {
   u(static_cast<uint64_t>(P.J));
   if (P.Js)
     for (int s = 0; s < P.sweeps; ++s) u(static_cast<uint64_t>(P.Js[s]));
+  u(P.Jupd ? 1 : 0);
+  if (P.Jupd)
+    for (int64_t e = 0; e < static_cast<int64_t>(P.sweeps) * P.N; ++e)
+      u(static_cast<uint64_t>(P.Jupd[e]));
+  u(static_cast<uint64_t>(ctx->merge));
   u(static_cast<uint64_t>(P.sweeps));
   u(P.prec);
   u(P.init ? 1 : 0);
@@ -596,6 +664,8 @@ std::vector<uint64_t> als_key(const tr_ctx* ctx, const AlsPlan& P) {
   u(ctx->arena_bytes);
   u(static_cast<uint64_t>(ctx->sampling));
   u(static_cast<uint64_t>(ctx->ls_rank));
+  u(static_cast<uint64_t>(ctx->wait_limit));
+  u(static_cast<uint64_t>(ctx->factorization));
   return k;
 }
 
@@ -830,6 +900,32 @@ tr_status tr_get_ls_rank(const tr_ctx* ctx, tr_ls_rank* rule) {
   return TR_OK;
 }
 
+tr_status tr_set_factorization(tr_ctx* ctx, tr_factorization f) {
+  if (!ctx) return TR_ERR_INVALID_ARG;
+  if (f != TR_FACTOR_DEFAULT && f != TR_FACTOR_FP64)
+    return fail(ctx, TR_ERR_INVALID_ARG, "unknown factorization %d", static_cast<int>(f));
+  ctx->factorization = f;
+  return TR_OK;
+}
+
+tr_status tr_get_factorization(const tr_ctx* ctx, tr_factorization* f) {
+  if (!ctx || !f) return TR_ERR_INVALID_ARG;
+  *f = ctx->factorization;
+  return TR_OK;
+}
+
+tr_status tr_set_wait_limit(tr_ctx* ctx, int64_t polls) {
+  if (!ctx) return TR_ERR_INVALID_ARG;
+  ctx->wait_limit = polls < 0 ? -1 : static_cast<long long>(polls);
+  return TR_OK;
+}
+
+tr_status tr_get_wait_limit(const tr_ctx* ctx, int64_t* polls) {
+  if (!ctx || !polls) return TR_ERR_INVALID_ARG;
+  *polls = ctx->wait_limit;
+  return TR_OK;
+}
+
 tr_status tr_get_sampling(const tr_ctx* ctx, tr_sampling* sampling) {
   if (!ctx || !sampling) return TR_ERR_INVALID_ARG;
   *sampling = ctx->sampling;
@@ -980,6 +1076,64 @@ tr_status tr_als_sampled_schedule(tr_ctx* ctx, const void* X, tr_dtype X_dtype, 
   tr_status st = read_device_error(ctx, S(stream));
   TR_TRY(fold_graph_marks(ctx));
   return st;
+}
+
+tr_status tr_als_sampled_adaptive(tr_ctx* ctx, const void* X, tr_dtype X_dtype, int N,
+                                  const int64_t* dims, const int* ranks,
+                                  const int64_t* J_per_update, int sweeps, uint64_t seed,
+                                  tr_precision prec, const double* const* init_cores,
+                                  double* const* cores, tr_stream stream) {
+  TR_TRY(check_ctx(ctx));
+  if (!J_per_update && sweeps > 0) return fail(ctx, TR_ERR_INVALID_ARG, "J_per_update is NULL");
+  TR_TRY(check_shape(ctx, N, dims, ranks));
+  int64_t Jmax = 1;
+  for (int64_t e = 0; e < static_cast<int64_t>(sweeps) * N; ++e) {
+    if (J_per_update[e] < 1 || J_per_update[e] > INT32_MAX)
+      return fail(ctx, TR_ERR_INVALID_ARG, "J_per_update[%lld]=%lld", static_cast<long long>(e),
+                  static_cast<long long>(J_per_update[e]));
+    Jmax = J_per_update[e] > Jmax ? J_per_update[e] : Jmax;
+  }
+  TR_TRY(check_als(ctx, X, X_dtype, N, dims, ranks, Jmax, sweeps, prec, cores, init_cores));
+  DeviceGuard g(ctx->device);
+  AlsPlan P{X, X_dtype, N, dims, ranks, Jmax, sweeps, prec, init_cores, cores};
+  P.Jupd = J_per_update;
+  TR_TRY(als_run(ctx, P, seed, S(stream)));
+  tr_status st = read_device_error(ctx, S(stream));
+  TR_TRY(fold_graph_marks(ctx));
+  return st;
+}
+
+tr_status tr_set_merge_duplicates(tr_ctx* ctx, int on) {
+  if (!ctx) return TR_ERR_INVALID_ARG;
+  ctx->merge = on ? 1 : 0;
+  return TR_OK;
+}
+
+tr_status tr_get_merge_duplicates(const tr_ctx* ctx, int* on) {
+  if (!ctx || !on) return TR_ERR_INVALID_ARG;
+  *on = ctx->merge;
+  return TR_OK;
+}
+
+tr_status tr_merge_samples(tr_ctx* ctx, int N, int k, const int64_t* dims, const int32_t* idx,
+                           const double* w, int64_t J, int32_t* idx_out, double* w_out,
+                           int64_t* J_out, tr_stream stream) {
+  TR_TRY(check_ctx(ctx));
+  TR_TRY(check_shape(ctx, N, dims, nullptr));
+  if (k < 0 || k >= N) return fail(ctx, TR_ERR_INVALID_ARG, "k=%d outside [0, N)", k);
+  if (!idx || !w || !idx_out || !w_out || !J_out)
+    return fail(ctx, TR_ERR_INVALID_ARG, "null pointer");
+  int64_t I[kMaxModes];
+  for (int m = 0; m < N - 1; ++m) I[m] = dims[(k + 1 + m) % N];
+  MergeArgs ma{};
+  if (!merge_fits(J, N - 1, I, &ma))
+    return fail(ctx, TR_ERR_INVALID_ARG,
+                "J=%lld outside [1, %d] or the sampled index space is 2^63 or larger",
+                static_cast<long long>(J), kMergeMaxJ);
+  DeviceGuard g(ctx->device);
+  cudaStream_t st = S(stream);
+  TR_LAUNCH("merge", launch_merge(idx, w, J, N - 1, ma, idx_out, w_out, J_out, st));
+  return TR_OK;
 }
 
 tr_status tr_als(tr_ctx* ctx, const void* X, tr_dtype X_dtype, int N, const int64_t* dims,

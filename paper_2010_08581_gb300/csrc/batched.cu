@@ -193,13 +193,14 @@ __global__ void __launch_bounds__((TILE / 4) * (TILE / 4)) kb_contract(
 // ------------------------------------------------------------------------------------
 // Gram matrices of the leverage passes (FP64, full square, 32 x 32 tiles over all rows).
 //   pass 1, tall (I >= L): G1 = S^T S (L x L); wide: G1 = S S^T (I x I), S = the I x L rows
-//           (the core at initialisation, B^T during the updates);
+//           (the core at initialisation and, under the column-dropping LS rule, after each
+//           update; B^T during the updates otherwise);
 //   pass 2 (wide modes only): G2 = C^T C (I x I), C = the pass-1 factor.
 // ------------------------------------------------------------------------------------
 constexpr int GT = 32, GK = 32, GNT = 256;
 
 __global__ void __launch_bounds__(GNT) kb_gram(const BInst* __restrict__ tab, int step, int init_k,
-                                               int pass) {
+                                               int pass, int from_core) {
   __shared__ double P[GK][GT + 1];
   __shared__ double Q[GK][GT + 1];
   const BInst& d = tab[blockIdx.x];
@@ -207,7 +208,7 @@ __global__ void __launch_bounds__(GNT) kb_gram(const BInst* __restrict__ tab, in
   if (!cu.active) return;
   const bool tall = cu.I >= cu.L;
   if (pass == 2 && tall) return;
-  const double* S = cu.init ? d.cores[cu.n] : d.BT;
+  const double* S = (cu.init || from_core) ? d.cores[cu.n] : d.BT;
   const double* src;
   int64_t K, lda;
   int n;
@@ -298,7 +299,7 @@ cudaError_t bl_gram(const BLaunch& b, int step, int init_k, int pass, cudaStream
   if (nmax <= 0) return cudaSuccess;
   const int nt = (nmax + GT - 1) / GT;
   dim3 grid(b.count, nt * nt);
-  kb_gram<<<grid, GNT, 0, st>>>(b.tab, step, init_k, pass);
+  kb_gram<<<grid, GNT, 0, st>>>(b.tab, step, init_k, pass, b.ls_mode == 1 ? 1 : 0);
   return cudaGetLastError();
 }
 

@@ -27,14 +27,15 @@ __global__ void __launch_bounds__(TW * 32) kb_solve(const BInst* __restrict__ ta
 }
 
 __global__ void __launch_bounds__(TW * 32) kb_rows(const BInst* __restrict__ tab, int step,
-                                                   int init_k, unsigned* err, int smem_bytes) {
+                                                   int init_k, unsigned* err, int smem_bytes,
+                                                   int from_core) {
   extern __shared__ __align__(16) unsigned char sm[];
   const BInst& d = tab[blockIdx.x];
   const Cur cu = current(d, step, init_k, true);
   if (!cu.active) return;
   const bool tall = cu.I >= cu.L;
   const int n = tall ? cu.L : static_cast<int>(cu.I);
-  const double* rhs = tall ? (cu.init ? d.cores[cu.n] : d.BT) : d.L1row;
+  const double* rhs = tall ? ((cu.init || from_core) ? d.cores[cu.n] : d.BT) : d.L1row;
   const int64_t ld = tall ? cu.L : cu.I;
   const double* Lr = tall ? d.L1row : d.L2row;
   const double* Lc = tall ? d.L1col : d.L2col;
@@ -64,7 +65,7 @@ cudaError_t bl_leverage_rows(const BLaunch& b, int step, int init_k, unsigned* e
   const int nmax = b.n1max > b.n2max ? b.n1max : b.n2max;
   const int dyn = solve_smem<double>(nmax, 0);
   dim3 grid(b.count, static_cast<unsigned>((b.Imax + TW - 1) / TW));
-  kb_rows<<<grid, TW * 32, dyn, st>>>(b.tab, step, init_k, err, dyn);
+  kb_rows<<<grid, TW * 32, dyn, st>>>(b.tab, step, init_k, err, dyn, b.ls_mode == 1 ? 1 : 0);
   return cudaGetLastError();
 }
 

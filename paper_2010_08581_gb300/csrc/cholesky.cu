@@ -28,6 +28,12 @@ __global__ void __launch_bounds__(CNT) k_cholesky_mixed(const double* __restrict
                                                         TI* img, float* gimg32,
                                                         const float* pre) {
   extern __shared__ double smem[];
+  // A contraction whose bounded wait expired left no valid normal equations: report
+  // info = -1 so that the solve leaves the core unchanged (the error bit is already set).
+  if (err && (*reinterpret_cast<volatile unsigned*>(err) & kErrTimeout)) {
+    if (threadIdx.x == 0) *info = -1;
+    return;
+  }
   const int64_t nn = static_cast<int64_t>(n) * n;
   float* A32 = nn * 4 <= dyn_bytes ? reinterpret_cast<float*>(smem) : reinterpret_cast<float*>(Lrow);
   double* A64 = nn * 8 <= dyn_bytes ? smem : Lrow;

@@ -54,6 +54,11 @@ struct SampleArgs {
   int npos;                      // N - 1
   const uint64_t* seed_dev;      // if non-null, the Philox key is read from here
   int uniform;                   // uniform sampling (Sec. 5): p and cdf unused
+  // fused kernel only: rows from given (merged) samples instead of drawing them, and a
+  // device-side row count (rows >= *jdev are not touched)
+  const int32_t* given_idx = nullptr;
+  const double* given_w = nullptr;
+  const int64_t* jdev = nullptr;
 };
 cudaError_t launch_sample(const SampleArgs& a, int64_t J, uint64_t seed, uint64_t update_id,
                           int32_t* idx, double* w, cudaStream_t st);
@@ -67,12 +72,6 @@ struct ChainArgs {
 cudaError_t launch_subchain(const ChainArgs& a, const int32_t* idx, const double* w,
                             int64_t J, void* A, bool f64, unsigned* err, cudaStream_t st);
 
-// Fused sampler + subchain (driver): the same draws as launch_sample and the same rows as
-// launch_subchain, in one launch; p and the CDFs are staged in shared memory when they fit.
-cudaError_t launch_sample_chain(const SampleArgs& sa, const ChainArgs& ca, int64_t J,
-                                uint64_t seed, uint64_t update_id, int32_t* idx, double* w,
-                                void* A, bool f64, cudaStream_t st);
-
 struct GatherArgs {
   int64_t stride[kMaxModes];     // element stride of the mode at ring position m
   int64_t I[kMaxModes];
@@ -80,6 +79,16 @@ struct GatherArgs {
   int64_t In;                    // length of the gathered mode
   int64_t stride_n;              // its stride
 };
+
+// Fused sampler + subchain (+ fibres) of the driver: the same draws as launch_sample, the
+// same rows as launch_subchain and, when ga and Y are given, the same fibres as
+// launch_gather (in X's dtype x_f64, Y in the rows' dtype), in one launch; p and the CDFs
+// are staged in shared memory when they fit.
+cudaError_t launch_sample_chain(const SampleArgs& sa, const ChainArgs& ca, int64_t J,
+                                uint64_t seed, uint64_t update_id, int32_t* idx, double* w,
+                                void* A, bool f64, cudaStream_t st,
+                                const GatherArgs* ga = nullptr, const void* X = nullptr,
+                                bool x_f64 = false, void* Y = nullptr);
 cudaError_t launch_gather(const GatherArgs& a, const void* X, bool x_f64, const int32_t* idx,
                           const double* w, int64_t J, void* Y, bool y_f64, unsigned* err,
                           cudaStream_t st);
@@ -101,10 +110,16 @@ size_t normal_eq_workspace(int64_t J, int L, int64_t I, bool f64, int* splits);
 // The same contraction on the tensor cores (tcgen05, TF32 split into hi + lo, FP32
 // accumulation in TMEM) for FP32 inputs; FP32 partials [splits][L][L + I].
 size_t normal_eq_tc_workspace(int64_t J, int L, int64_t I, int* splits);
+// wait_limit: polls per pipeline wait of the main loop (< 0: the default, 2^26); when a
+// wait expires the kernel records kErrTimeout in *err and writes no partials.
+// jdev (optional, device): the number of rows actually present (<= J); rows beyond it are
+// not read and the partials of chunks beyond it are zero.
 cudaError_t launch_normal_eq_tc(const float* A, const float* Y, int64_t J, int L, int64_t I,
-                                float* partial, int splits, unsigned* err, cudaStream_t st);
+                                float* partial, int splits, unsigned* err, cudaStream_t st,
+                                long long wait_limit = -1, const int64_t* jdev = nullptr);
 cudaError_t launch_normal_eq(const void* A, const void* Y, bool f64, int64_t J, int L,
-                             int64_t I, void* partial, int splits, cudaStream_t st);
+                             int64_t I, void* partial, int splits, cudaStream_t st,
+                             const int64_t* jdev = nullptr);
 
 // Gram of a row-major matrix: trans=false: G = A^T A (cols x cols); trans=true:
 // G = A A^T (rows x rows). Partials [splits][n][n] FP64; only tiles on or above the
@@ -191,6 +206,41 @@ cudaError_t launch_trsm(int mode, bool f32, int n, const double* Lrow, const dou
                         double* ell, cudaStream_t st, const void* Limg = nullptr,
                         const float* Mimg = nullptr, const CdfEpilogue* cdf = nullptr);
 size_t trsm_image_bytes(int n, bool f32);
+
+// Leverage scores (and, unless skip && *skip, p and the CDF) of the rows of a wide I x L
+// row-major FP64 matrix (row stride lda) by one-sided Jacobi in one CTA (jacobi.cu): the rank
+// rule of a singular value decomposition, sigma > max(I, L) * eps * sigma_max. For
+// 1 <= I < L with I <= kJacobiMaxI; a zero matrix records kErrSingular and gives the
+// uniform distribution.
+constexpr int kJacobiMaxI = 48;
+constexpr size_t kJacobiSmem = 200 * 1024;
+bool leverage_jacobi_fits(int64_t I, int L);
+cudaError_t launch_leverage_jacobi(const double* A, int64_t I, int L, int64_t lda, double* ell,
+                                   double* p, double* cdf, const int* skip, unsigned* err,
+                                   cudaStream_t st);
+
+// Mixed-precision LS solve for L <= 128 (solve_inv.cu): W = L_f^-1 from the factor's FP32
+// image (into Wimg, trsm_image_bytes(n, true) bytes), then z = W^T W b, r = b - M z,
+// z += W^T W r for every row b of rhs (ld), written as the new core; nothing when *info != 0.
+bool solve_inv_fits(int n);
+cudaError_t launch_solve_inv(int n, const float* Limg, const float* Mimg,
+                             const double* invdiag, const int* info, int64_t nvec,
+                             const double* rhs, int64_t ld, int Rl, int Rr, double* core_out,
+                             float* Wimg, cudaStream_t st);
+
+// Merging repeated draws (merge.cu; Sec. 4.2): idx_out / w_out receive one row per distinct
+// multi-index in the order of first occurrence, weight w * sqrt(count), and *J_out (device)
+// their number. For J <= kMergeMaxJ and prod of the sampled sizes < 2^63 (merge_fits, which
+// also fills the ring linear-index strides).
+constexpr int kMergeMaxJ = 8192;
+struct MergeArgs {
+  uint64_t stride[kMaxModes];
+  int Jpow2;
+};
+bool merge_fits(int64_t J, int npos, const int64_t* I, MergeArgs* a);
+cudaError_t launch_merge(const int32_t* idx, const double* w, int64_t J, int npos,
+                         const MergeArgs& a, int32_t* idx_out, double* w_out, int64_t* J_out,
+                         cudaStream_t st);
 
 // Core initialisation N(0,1) by Philox + Box-Muller.
 cudaError_t launch_init_normal(double* out, int64_t count, uint64_t seed, uint32_t stream_id,

@@ -127,6 +127,9 @@ cudaError_t trsm_attributes();
 cudaError_t normal_eq_tc_attributes();
 cudaError_t sample_chain_attributes();
 cudaError_t batched_attributes();
+cudaError_t jacobi_attributes();
+cudaError_t solve_inv_attributes();
+cudaError_t merge_attributes();
 
 cudaError_t init_kernel_attributes(const char** which) {
   cudaError_t e = cholesky_attributes();
@@ -139,6 +142,12 @@ cudaError_t init_kernel_attributes(const char** which) {
   if (e != cudaSuccess) { *which = "sample_chain"; return e; }
   e = batched_attributes();
   if (e != cudaSuccess) { *which = "batched"; return e; }
+  e = jacobi_attributes();
+  if (e != cudaSuccess) { *which = "jacobi"; return e; }
+  e = solve_inv_attributes();
+  if (e != cudaSuccess) { *which = "solve_inv"; return e; }
+  e = merge_attributes();
+  if (e != cudaSuccess) { *which = "merge"; return e; }
   e = fit_attributes();
   if (e != cudaSuccess) *which = "fit";
   return e;

@@ -139,8 +139,11 @@ inline cudaError_t issue_leverage(const BLaunch& bl, int step, int init_k, unsig
 
 // One lockstep step of every instance: draws, subchain rows and fibres, normal equations,
 // then the LS solve on `main` concurrently with the new distribution (from B^T, which has the
-// column space of the new core) on `side`; both branches are joined on `main`. A batch that
-// samples uniformly throughout has no distribution branch.
+// column space of the new core whenever the normal matrix is nonsingular) on `side`; both
+// branches are joined on `main`. A batch that samples uniformly throughout has no
+// distribution branch. Under the column-dropping rule the new core's column space is that of
+// the kept columns of B^T only, so the distribution is formed from the new core itself,
+// after the solve, on `main`.
 inline cudaError_t issue_step(const BLaunch& bl, int step, unsigned* err, const StepStreams& s) {
   cudaError_t e;
   if ((e = bl_sample_chain_gather(bl, step, s.main)) != cudaSuccess) return e;
@@ -148,6 +151,11 @@ inline cudaError_t issue_step(const BLaunch& bl, int step, unsigned* err, const 
   if (!bl.leverage) {   // uniform sampling only: no distribution branch
     if ((e = bl_cholesky(bl, step, 0, 0, err, s.main)) != cudaSuccess) return e;
     return bl_solve(bl, step, s.main);
+  }
+  if (bl.ls_mode == 1) {
+    if ((e = bl_cholesky(bl, step, 0, 0, err, s.main)) != cudaSuccess) return e;
+    if ((e = bl_solve(bl, step, s.main)) != cudaSuccess) return e;
+    return issue_leverage(bl, step, 0, err, s.main, nullptr);
   }
   if ((e = cudaEventRecord(s.fork, s.main)) != cudaSuccess) return e;
   if ((e = cudaStreamWaitEvent(s.side, s.fork, 0)) != cudaSuccess) return e;

@@ -38,9 +38,13 @@ struct Bump {
 
 struct Layout {
   void* partial; double* M; double* BT; double* Lrow; double* Lcol; double* invdiag;
-  int* keep; int* info; unsigned* err; int splits;
+  int* keep; int* info; void* limg; float* mimg; float* wimg; unsigned* err; int splits;
 };
 
+// The scratch of one call, carved as tr_solve carves its workspace: the contraction's split
+// partials, M, B^T, the factor (row- and column-major), its inverse diagonal and pivot flags,
+// the factor's padded image in the solve's arithmetic type, M's FP32 image and the factor's
+// FP32 inverse (mixed path), and the error word.
 size_t layout(char* base, int64_t J, int L, int64_t I, bool f64, Layout* s) {
   Bump b{base};
   const size_t pbytes = f64 ? normal_eq_workspace(J, L, I, true, &s->splits)
@@ -53,6 +57,9 @@ size_t layout(char* base, int64_t J, int L, int64_t I, bool f64, Layout* s) {
   s->invdiag = b.take<double>(L);
   s->keep = b.take<int>(L);
   s->info = b.take<int>(1);
+  s->limg = b.take<char>(trsm_image_bytes(L, !f64));
+  s->mimg = f64 ? nullptr : reinterpret_cast<float*>(b.take<char>(trsm_image_bytes(L, true)));
+  s->wimg = f64 ? nullptr : reinterpret_cast<float*>(b.take<char>(trsm_image_bytes(L, true)));
   s->err = b.take<unsigned>(1);
   return b.off;
 }
@@ -64,7 +71,8 @@ tr_status fail(tr_status st, const std::string& msg) {
 
 // Once per device, with that device current: resolve the device address of the scratch
 // array (host code may not use the symbol itself) and set the kernels' shared-memory
-// limits.
+// limits. The address is cached per device ordinal for the life of the process; a device
+// reset (cudaDeviceReset) reloads the module and invalidates it (see trals.h).
 tr_status setup(int dev, char** out) {
   std::lock_guard<std::mutex> lock(g_setup_mutex);
   if (g_scratch_dev[dev]) {
@@ -114,21 +122,46 @@ extern "C" tr_status tr_solve_noalloc(const void* A, const void* Y, tr_dtype dty
   layout(base, J, L, I, f64, &s);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int64_t ld = L + I;
-  const double eps = 2.220446049250313e-16;
-  cudaError_t e = cudaSuccess;
-  if (f64)
-    e = launch_normal_eq(A, Y, true, J, L, I, s.partial, s.splits, st);
-  else
-    e = launch_normal_eq_tc(static_cast<const float*>(A), static_cast<const float*>(Y), J, L, I,
-                            static_cast<float*>(s.partial), s.splits, s.err, st);
+  const double eps = 2.220446049250313e-16, eps32 = 1.1920928955078125e-07;
+  // The array keeps the previous call's contents: clear the error word first.
+  cudaError_t e = cudaMemsetAsync(s.err, 0, sizeof(unsigned), st);
+  if (e == cudaSuccess) {
+    if (f64)
+      e = launch_normal_eq(A, Y, true, J, L, I, s.partial, s.splits, st);
+    else
+      e = launch_normal_eq_tc(static_cast<const float*>(A), static_cast<const float*>(Y), J, L,
+                              I, static_cast<float*>(s.partial), s.splits, s.err, st);
+  }
+  // The same reduction, factorisation and solves as tr_solve (stop-on-singular rule): on the
+  // mixed path the reduction also writes M's FP32 work array and image for the FP32 factor.
+  ReduceSplit sp;
+  const bool pre = !f64 && L >= 4 && L <= 160;
+  if (pre) {
+    sp.hi = reinterpret_cast<float*>(s.Lrow);
+    sp.lda = (L + 3) & ~3;
+    sp.img = s.mimg;
+    sp.np = L + 1;
+  }
   if (e == cudaSuccess)
-    e = launch_reduce(s.partial, !f64, s.splits, L * ld, ld, L, ld, L, s.M, L, s.BT, L, st);
-  if (e == cudaSuccess)
-    e = launch_cholesky(s.M, L, 0, static_cast<double>(L) * eps, s.Lrow, s.Lcol, s.invdiag,
-                        s.keep, s.info, s.err, st);
-  if (e == cudaSuccess)
-    e = launch_trsm(f64 ? 1 : 2, !f64, L, s.Lrow, s.Lcol, s.invdiag, s.info, I, s.BT, L, s.M, Rl,
-                    Rr, core_out, nullptr, st);
+    e = launch_reduce(s.partial, !f64, s.splits, L * ld, ld, L, ld, L, s.M, L, s.BT, L, st, sp);
+  if (e == cudaSuccess) {
+    if (f64)
+      e = launch_cholesky(s.M, L, 0, static_cast<double>(L) * eps, s.Lrow, s.Lcol, s.invdiag,
+                          s.keep, s.info, s.err, st, static_cast<double*>(s.limg));
+    else
+      e = launch_cholesky_mixed(s.M, L, 0, static_cast<double>(L) * eps,
+                                static_cast<double>(L) * eps32, s.Lrow, s.Lcol, s.invdiag,
+                                s.keep, s.info, s.err, st, static_cast<float*>(s.limg), s.mimg,
+                                pre ? reinterpret_cast<float*>(s.Lrow) : nullptr);
+  }
+  if (e == cudaSuccess) {
+    if (!f64 && solve_inv_fits(L))
+      e = launch_solve_inv(L, static_cast<const float*>(s.limg), s.mimg, s.invdiag, s.info, I,
+                           s.BT, L, Rl, Rr, core_out, s.wimg, st);
+    else
+      e = launch_trsm(f64 ? 1 : 2, !f64, L, s.Lrow, s.Lcol, s.invdiag, s.info, I, s.BT, L, s.M,
+                      Rl, Rr, core_out, nullptr, st, s.limg, s.mimg);
+  }
   if (e == cudaSuccess && info)
     e = cudaMemcpyAsync(info, s.info, sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) return fail(TR_ERR_CUDA, std::string("launch failed: ") + cudaGetErrorString(e));

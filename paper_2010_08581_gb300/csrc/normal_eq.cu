@@ -17,14 +17,16 @@ template <typename T>
 __global__ void __launch_bounds__(NT) k_normal_eq(const T* __restrict__ A,
                                                   const T* __restrict__ Y, int64_t J, int L,
                                                   int64_t I, int64_t chunk,
-                                                  T* __restrict__ partial) {
+                                                  T* __restrict__ partial,
+                                                  const int64_t* __restrict__ jdev) {
   __shared__ T As[BK][BM];
   __shared__ T Bs[BK][BN];
   const int64_t ldc = L + I;
   const int r0 = blockIdx.y * BM;
   const int64_t c0 = static_cast<int64_t>(blockIdx.x) * BN;
   const int64_t j0 = static_cast<int64_t>(blockIdx.z) * chunk;
-  const int64_t j1 = (j0 + chunk < J) ? j0 + chunk : J;
+  const int64_t Jr = jdev ? (*jdev < J ? *jdev : J) : J;
+  const int64_t j1 = (j0 + chunk < Jr) ? j0 + chunk : Jr;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // 16 x 16 threads
   T acc[4][4];
 #pragma unroll
@@ -99,7 +101,8 @@ size_t normal_eq_workspace(int64_t J, int L, int64_t I, bool f64, int* splits) {
 }
 
 cudaError_t launch_normal_eq(const void* A, const void* Y, bool f64, int64_t J, int L,
-                             int64_t I, void* partial, int splits, cudaStream_t st) {
+                             int64_t I, void* partial, int splits, cudaStream_t st,
+                             const int64_t* jdev) {
   int s;
   int64_t chunk;
   plan(J, L, I, &s, &chunk);
@@ -108,11 +111,11 @@ cudaError_t launch_normal_eq(const void* A, const void* Y, bool f64, int64_t J, 
   if (f64)
     k_normal_eq<double><<<grid, NT, 0, st>>>(static_cast<const double*>(A),
                                              static_cast<const double*>(Y), J, L, I, chunk,
-                                             static_cast<double*>(partial));
+                                             static_cast<double*>(partial), jdev);
   else
     k_normal_eq<float><<<grid, NT, 0, st>>>(static_cast<const float*>(A),
                                             static_cast<const float*>(Y), J, L, I, chunk,
-                                            static_cast<float*>(partial));
+                                            static_cast<float*>(partial), jdev);
   return cudaGetLastError();
 }
 

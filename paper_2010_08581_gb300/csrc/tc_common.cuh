@@ -64,9 +64,11 @@ __device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(mbar), "r"(count) : "memory");
 }
 
-// Bounded wait for the given phase parity; returns false if the limit expired.
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-  for (long long it = 0; it < kTcSpinLimit; ++it) {
+// Bounded wait for the given phase parity: at most `limit` polls (0: the wait expires at
+// once); returns false if the limit expired.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity,
+                                          long long limit = kTcSpinLimit) {
+  for (long long it = 0; it < limit; ++it) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"

@@ -23,6 +23,7 @@ TR_F32, TR_F64 = 0, 1
 TR_PREC_FP64, TR_PREC_MIXED = 0, 1
 TR_SAMPLING_LEVERAGE, TR_SAMPLING_UNIFORM = 0, 1
 TR_LS_RANK_STOP, TR_LS_RANK_DROP = 0, 1
+TR_FACTOR_DEFAULT, TR_FACTOR_FP64 = 0, 1
 
 _STATUS_NAMES = ["TR_OK", "TR_ERR_INVALID_ARG", "TR_ERR_OOM", "TR_ERR_BUDGET",
                  "TR_ERR_SINGULAR", "TR_ERR_TIMEOUT", "TR_ERR_CUDA", "TR_ERR_NOT_CONVERGED"]
@@ -120,6 +121,16 @@ SIGNATURES = {
     "tr_get_ls_rank": (c_int, [c_vp, PI]),
     "tr_set_sampling": (c_int, [c_vp, c_int]),
     "tr_get_sampling": (c_int, [c_vp, PI]),
+    "tr_als_sampled_adaptive": (c_int, [c_vp, c_vp, c_int, c_int, P64, PI, P64, c_int, c_u64,
+                                        c_int, PP, PP, c_vp]),
+    "tr_merge_samples": (c_int, [c_vp, c_int, c_int, P64, c_vp, c_vp, c_i64, c_vp, c_vp, c_vp,
+                                 c_vp]),
+    "tr_set_merge_duplicates": (c_int, [c_vp, c_int]),
+    "tr_get_merge_duplicates": (c_int, [c_vp, PI]),
+    "tr_set_factorization": (c_int, [c_vp, c_int]),
+    "tr_get_factorization": (c_int, [c_vp, PI]),
+    "tr_set_wait_limit": (c_int, [c_vp, c_i64]),
+    "tr_get_wait_limit": (c_int, [c_vp, ctypes.POINTER(c_i64)]),
     "tr_set_batched_tiles": (c_int, [c_vp, ctypes.POINTER(TrBatchedTiles)]),
     "tr_get_batched_tiles": (c_int, [c_vp, ctypes.POINTER(TrBatchedTiles)]),
     "tr_server_create": (c_int, [ctypes.POINTER(TrServerConfig), ctypes.POINTER(c_vp)]),
@@ -282,6 +293,49 @@ def tr_get_sampling(ctx: Context) -> int:
     return int(v.value)
 
 
+def tr_merge_samples(ctx: Context, k: int, dims, idx: torch.Tensor, w: torch.Tensor,
+                     idx_out: torch.Tensor, w_out: torch.Tensor, J_out: torch.Tensor,
+                     stream=None):
+    """Merge repeated draws (Sec. 4.2): J_out is a device int64 tensor of one element."""
+    d, _d = _i64s(list(dims))
+    ctx.check(load().tr_merge_samples(ctx.handle, len(dims), k, d, _ptr(idx), _ptr(w),
+                                      idx.shape[0], _ptr(idx_out), _ptr(w_out), _ptr(J_out),
+                                      _stream(stream)))
+
+
+def tr_set_merge_duplicates(ctx: Context, on: bool):
+    ctx.check(load().tr_set_merge_duplicates(ctx.handle, 1 if on else 0))
+
+
+def tr_get_merge_duplicates(ctx: Context) -> bool:
+    v = c_int()
+    ctx.check(load().tr_get_merge_duplicates(ctx.handle, ctypes.byref(v)))
+    return bool(v.value)
+
+
+def tr_set_factorization(ctx: Context, f: int):
+    """TR_FACTOR_DEFAULT or TR_FACTOR_FP64 for the mixed path's factorisations."""
+    ctx.check(load().tr_set_factorization(ctx.handle, int(f)))
+
+
+def tr_get_factorization(ctx: Context) -> int:
+    v = c_int()
+    ctx.check(load().tr_get_factorization(ctx.handle, ctypes.byref(v)))
+    return int(v.value)
+
+
+def tr_set_wait_limit(ctx: Context, polls: int):
+    """Polls per bounded wait of the tensor-core contraction (< 0: the default; 0: every
+    wait expires at once)."""
+    ctx.check(load().tr_set_wait_limit(ctx.handle, int(polls)))
+
+
+def tr_get_wait_limit(ctx: Context) -> int:
+    v = c_i64()
+    ctx.check(load().tr_get_wait_limit(ctx.handle, ctypes.byref(v)))
+    return int(v.value)
+
+
 def tr_subchain(ctx: Context, k: int, dims, ranks, cores: List[torch.Tensor], idx: torch.Tensor,
                 w: Optional[torch.Tensor], A: torch.Tensor, stream=None):
     N = len(dims)
@@ -331,7 +385,8 @@ def tr_init_cores(ctx: Context, dims, ranks, seed: int, k_begin: int, cores, str
 def tr_als_sampled(ctx: Context, X: torch.Tensor, ranks, J, sweeps: int, seed: int,
                    prec: int, cores: List[torch.Tensor],
                    init_cores: Optional[List[Optional[torch.Tensor]]] = None, stream=None):
-    """J: one sample size, or a list with one per sweep (tr_als_sampled_schedule)."""
+    """J: one sample size, a list with one per sweep (tr_als_sampled_schedule), or a list of
+    per-sweep lists with one per core update (tr_als_sampled_adaptive)."""
     dims = list(X.shape)
     d, _d = _i64s(dims)
     r, _r = _ints(ranks)
@@ -340,6 +395,13 @@ def tr_als_sampled(ctx: Context, X: torch.Tensor, ranks, J, sweeps: int, seed: i
         ip, _i = _ptrs(init_cores)
     else:
         ip = ctypes.cast(c_vp(None), PP)
+    if isinstance(J, (list, tuple)) and J and isinstance(J[0], (list, tuple)):
+        flat = [int(v) for row in J for v in row]
+        js, _j = _i64s(flat)
+        ctx.check(load().tr_als_sampled_adaptive(ctx.handle, _ptr(X), _dt(X), len(dims), d, r,
+                                                 js, sweeps, seed, prec, ip, cp,
+                                                 _stream(stream)))
+        return
     if isinstance(J, (list, tuple)):
         js, _j = _i64s(J)
         ctx.check(load().tr_als_sampled_schedule(ctx.handle, _ptr(X), _dt(X), len(dims), d, r,

@@ -1,9 +1,11 @@
 """The high-order shape of Sec. 5 (10-way 4 x ... x 4 tensors, TR ranks 10): every mode is
-wide (I = 4 < L = 100), so each distribution takes the two-pass Cholesky-QR route. On the
-oscillatory function tensor each stage of an update matches the oracle given the oracle's
-distributions; whole sweeps are compared on a TR + noise tensor of the same shape (the
-oscillatory tensors' fast modes give numerically rank-deficient cores, where the Gram-based
-rank rule and the oracle's SVD rule pick different distributions)."""
+wide (I = 4 < L = 100). On the oscillatory function tensors the fast modes' cores become
+numerically rank-deficient (singular-value ratios down to 1e-12), so their distributions
+depend on resolving singular values far below sqrt(eps); the library takes them by
+one-sided Jacobi with the singular-value rank rule. Whole FP64 driver sweeps on the three
+oscillatory tensors therefore match the oracle (same draws, cores within 1e-8), and so does
+each stage of an update. The mixed path's final error is compared where its LS steps stay
+within FP32 resolution (kappa(M) * eps32 < 1; the Airy tensor and a TR + noise tensor)."""
 
 import numpy as np
 import pytest
@@ -73,9 +75,24 @@ def test_highn_core_update_stages_match_oracle(ctx):
         assert rel(to_paper(out), ref) < 1e-9
 
 
-def test_highn_sweep_matches_oracle_fp64(ctx):
-    """A whole FP64 sweep of the driver (fused sampler, distributions from B^T by the
-    two-pass route) on a 10-way TR + noise tensor of the same shape and ranks."""
+@pytest.mark.parametrize("name", ["linear_growth", "airy", "chirp"])
+def test_highn_sweeps_match_oracle_fp64(ctx, name):
+    """Two whole FP64 sweeps of the driver (fused sampler, distributions of the wide cores by
+    Jacobi) on the oscillatory tensor itself: every core within 1e-8 of the oracle's. One
+    different draw would move a core by far more (about 1e-3)."""
+    X = inputs.oscillatory(name, dtype=torch.float64)
+    init = [c.numpy() for c in inputs.random_cores(DIMS, RANKS, 7)]
+    J = 1500
+    ref = orc.tr_als_sampled(X.numpy(), init, J, 2, 3, solver="normal")
+    out = T.empty_cores(DIMS, RANKS)
+    T.tr_als_sampled(ctx, X.to(DEV), RANKS, J, 2, 3, T.TR_PREC_FP64, out,
+                     init_cores=[to_dev_core(c) for c in init])
+    for k in range(10):
+        assert rel(to_paper(out[k]), ref[k]) < 1e-8, k
+
+
+def test_highn_sweep_matches_oracle_fp64_tr_noise(ctx):
+    """A whole FP64 sweep on a 10-way TR + noise tensor of the same shape and ranks."""
     X, _ = inputs.tr_plus_noise(DIMS, RANKS, seed=6, rel_noise=1e-2, dtype=torch.float64)
     init = [c.numpy() for c in inputs.random_cores(DIMS, RANKS, 7)]
     J = 1500
@@ -85,6 +102,27 @@ def test_highn_sweep_matches_oracle_fp64(ctx):
                      init_cores=[to_dev_core(c) for c in init])
     for k in range(10):
         assert rel(to_paper(out[k]), ref[k]) < 1e-8
+
+
+def test_highn_wide_leverage_of_rank_deficient_cores(ctx):
+    """tr_leverage on the cores one oracle sweep leaves on the linear-growth tensor (4 x 100
+    unfoldings with singular-value ratios down to about 1e-12): p and the CDF equal the
+    oracle's SVD-based distribution."""
+    X = inputs.oscillatory("linear_growth", dtype=torch.float64).numpy()
+    init = [c.numpy() for c in inputs.random_cores(DIMS, RANKS, 7)]
+    cores = orc.tr_als_sampled(X, init, 1500, 1, 3, solver="normal")
+    ratios = []
+    for c in cores:
+        sv = np.linalg.svd(orc.core_unfold2(c), compute_uv=False)
+        ratios.append(sv[-1] / sv[0])
+        p_o, cdf_o = orc.core_distribution(c)
+        p = torch.empty(4, dtype=torch.float64, device=DEV)
+        cdf = torch.empty(4, dtype=torch.float64, device=DEV)
+        T.tr_leverage(ctx, to_dev_core(c), p, cdf)
+        T.tr_status_sync(ctx)
+        np.testing.assert_allclose(p.cpu().numpy(), p_o, rtol=0, atol=1e-14)
+        np.testing.assert_allclose(cdf.cpu().numpy(), cdf_o, rtol=0, atol=1e-14)
+    assert min(ratios) < 1e-9   # the case the Gram-based route cannot resolve
 
 
 def test_highn_mixed_final_error(ctx):
@@ -98,4 +136,19 @@ def test_highn_mixed_final_error(ctx):
     T.tr_als_sampled(ctx, Xd, RANKS, J, sweeps, 4, T.TR_PREC_MIXED, out,
                      init_cores=[to_dev_core(c) for c in init])
     e_gpu = T.tr_rel_error(ctx, Xd, RANKS, out)
+    assert abs(e_gpu - e_ref) < 0.01 * e_ref
+
+
+def test_highn_mixed_final_error_airy(ctx):
+    """The mixed path on an oscillatory tensor whose LS steps it can resolve (Airy: kappa(M)
+    up to about 2e7 along the trajectory): final error within 1% of the oracle's."""
+    X = inputs.oscillatory("airy", dtype=torch.float64)
+    init = [c.numpy() for c in inputs.random_cores(DIMS, RANKS, 7)]
+    ref = orc.tr_als_sampled(X.numpy(), init, 2000, 3, 4)
+    e_ref = orc.rel_error(ref, X.numpy())
+    Xf = X.float().to(DEV)
+    out = T.empty_cores(DIMS, RANKS)
+    T.tr_als_sampled(ctx, Xf, RANKS, 2000, 3, 4, T.TR_PREC_MIXED, out,
+                     init_cores=[to_dev_core(c) for c in init])
+    e_gpu = T.tr_rel_error(ctx, Xf, RANKS, out)
     assert abs(e_gpu - e_ref) < 0.01 * e_ref

@@ -95,3 +95,75 @@ def test_drivers_run_through_rank_deficient_updates():
     e_b = T.tr_rel_error(ctx, X, ranks, probs[0]["cores"])
     assert np.isfinite(e_s) and abs(e_s - e_b) < 0.01 * e_s
     ctx.close()
+
+
+def _zero_slice_ring(noise=0.0):
+    """Noise-free (or noisy) 9 x 8 x 7 ring, ranks 3, whose rank index 2 between cores 0 and
+    1 is unused (core 1's first-row slices and core 0's last-column slices are zero), with a
+    start near the truth that keeps those slices zero: every update of cores 0 and 1 has a
+    design with exactly zero columns."""
+    dims, ranks = (9, 8, 7), (3, 3, 3)
+    true = [c.numpy() for c in inputs.random_cores(dims, ranks, 21)]
+    true[1][2, :, :] = 0.0
+    true[0][:, :, 2] = 0.0
+    X = np.ascontiguousarray(orc.tr_reconstruct(true))
+    if noise:
+        rng = np.random.default_rng(23)
+        X = np.ascontiguousarray(
+            X + noise * np.linalg.norm(X) / np.sqrt(X.size) * rng.standard_normal(X.shape))
+    pert = [c.numpy() for c in inputs.random_cores(dims, ranks, 22)]
+    init = [t + 0.05 * p for t, p in zip(true, pert)]
+    init[1][2, :, :] = 0.0
+    init[0][:, :, 2] = 0.0
+    return dims, ranks, X, init
+
+
+def _dev_cores(cores):
+    return [torch.from_numpy(np.ascontiguousarray(np.transpose(c, (1, 0, 2)))).to(DEV)
+            for c in cores]
+
+
+def test_drop_driver_matches_the_oracle_fp64():
+    """Whole FP64 sweeps under TR_LS_RANK_DROP against the oracle's dropping driver, whose
+    next distribution is the leverage of the new core: same draws, cores within 1e-8."""
+    dims, ranks, X, init = _zero_slice_ring()
+    J, sweeps = 300, 5
+    ref = orc.tr_als_sampled(X, init, J, sweeps, 4, solver="normal_drop")
+    ctx = T.Context(0)
+    try:
+        T.tr_set_ls_rank(ctx, T.TR_LS_RANK_DROP)
+        out = T.empty_cores(dims, ranks)
+        T.tr_als_sampled(ctx, torch.from_numpy(X).to(DEV), ranks, J, sweeps, 4, T.TR_PREC_FP64,
+                         out, init_cores=_dev_cores(init))
+        for k in range(3):
+            assert rel(to_paper(out[k]), ref[k]) < 1e-8, k
+    finally:
+        ctx.close()
+
+
+def test_drop_driver_final_error_mixed():
+    dims, ranks, X, init = _zero_slice_ring(noise=1e-2)
+    J, sweeps = 300, 8
+    ref = orc.tr_als_sampled(X, init, J, sweeps, 4, solver="normal_drop")
+    e_o = orc.rel_error(ref, X)
+    ctx = T.Context(0)
+    try:
+        T.tr_set_ls_rank(ctx, T.TR_LS_RANK_DROP)
+        Xd = torch.from_numpy(X).float().to(DEV)
+        out = T.empty_cores(dims, ranks)
+        T.tr_als_sampled(ctx, Xd, ranks, J, sweeps, 4, T.TR_PREC_MIXED, out,
+                         init_cores=_dev_cores(init))
+        e_g = orc.rel_error([to_paper(c) for c in out], X)
+        assert abs(e_g - e_o) <= 0.01 * e_o, (e_g, e_o)
+        # the batched driver follows the same rule and gives the same cores in FP64
+        T.tr_set_ls_rank(ctx, T.TR_LS_RANK_DROP)
+        single = T.empty_cores(dims, ranks)
+        Xd64 = torch.from_numpy(X).to(DEV)
+        T.tr_als_sampled(ctx, Xd64, ranks, J, 3, 4, T.TR_PREC_FP64, single,
+                         init_cores=_dev_cores(init))
+        probs = [dict(X=Xd64, ranks=ranks, J=J, seed=4, init=True, cores=_dev_cores(init))]
+        T.tr_als_sampled_batched(ctx, probs, 3, T.TR_PREC_FP64)
+        for a, b in zip(single, probs[0]["cores"]):
+            assert rel(b.cpu().numpy(), a.cpu().numpy()) < 1e-10
+    finally:
+        ctx.close()
