@@ -198,9 +198,15 @@ LevPass carve_pass(Carver& c, int64_t rows, int cols, bool trans) {
 // with FP64 fallback.
 tr_status run_pass(tr_ctx* ctx, const LevPass& p, const double* A, int64_t rows, int cols,
                    int64_t lda, bool trans, double tol_scale, cudaStream_t st,
-                   bool mixed = false) {
+                   bool mixed = false, const float* A_hi = nullptr,
+                   const float* A_lo = nullptr) {
   const int n = trans ? static_cast<int>(rows) : cols;
-  TR_LAUNCH("gram_f64", launch_gram(A, rows, cols, lda, trans, p.partial, p.splits, st));
+  if (mixed && !trans && A_hi) {
+    // the mixed drivers' tall Gram in double-float from A's planes (written by the reduction)
+    TR_LAUNCH("gram_f64", launch_gram_ff(A_hi, A_lo, rows, cols, lda, p.partial, p.splits, st));
+  } else {
+    TR_LAUNCH("gram_f64", launch_gram(A, rows, cols, lda, trans, p.partial, p.splits, st));
+  }
   // the mixed tall pass: the reduction also writes the double-float planes of the Gram in
   // the factorisation's work-array layout (into Lrow / Lcol, free until the factor's tail)
   ReduceSplit sp;
@@ -253,7 +259,8 @@ size_t leverage_bytes(int64_t I, int L) {
 // when no pivot is small (about 46 significant bits; rank decisions stay FP64).
 tr_status leverage_dist(tr_ctx* ctx, char* ws, const double* mat, int64_t I, int L, double* p,
                         double* cdf, const int* skip, cudaStream_t st,
-                        cudaEvent_t wait_before_rows = nullptr, bool mixed = false) {
+                        cudaEvent_t wait_before_rows = nullptr, bool mixed = false,
+                        const float* mat_hi = nullptr, const float* mat_lo = nullptr) {
   Carver c(ws);
   LevPass p1{}, p2{};
   double* ell;
@@ -272,7 +279,7 @@ tr_status leverage_dist(tr_ctx* ctx, char* ws, const double* mat, int64_t I, int
   TR_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned), st));
   const CdfEpilogue ep{counter, p, cdf, skip, ctx->d_err};
   if (I >= L) {
-    TR_TRY(run_pass(ctx, p1, mat, I, L, L, false, tol, st, mixed));
+    TR_TRY(run_pass(ctx, p1, mat, I, L, L, false, tol, st, mixed, mat_hi, mat_lo));
     if (wait_before_rows) TR_CUDA(cudaStreamWaitEvent(st, wait_before_rows, 0));
     TR_LAUNCH("leverage_rows", launch_trsm(0, false, L, p1.Lrow, p1.Lcol, p1.invdiag, nullptr, I,
                                            mat, L, nullptr, 1, 1, nullptr, ell, st, p1.img,
@@ -301,6 +308,7 @@ tr_status leverage_run(tr_ctx* ctx, char* ws, const double* core, int64_t I, int
 struct SolvePlan {
   void* partial; double* M; double* BT; double* Lrow; double* Lcol; double* invdiag;
   int* keep; int* info; void* limg; float* mimg; float* wimg; int splits;
+  float* bt_hi = nullptr; float* bt_lo = nullptr;   // double-float planes of B^T (mixed)
 };
 
 bool use_tensor_cores(bool f64) {
@@ -323,6 +331,8 @@ size_t solve_plan(Carver& c, int64_t J, int L, int64_t I, bool f64, SolvePlan* s
   s->limg = c.take<char>(trsm_image_bytes(L, !f64));
   s->mimg = f64 ? nullptr : reinterpret_cast<float*>(c.take<char>(trsm_image_bytes(L, true)));
   s->wimg = f64 ? nullptr : reinterpret_cast<float*>(c.take<char>(trsm_image_bytes(L, true)));
+  s->bt_hi = f64 ? nullptr : c.take<float>(static_cast<size_t>(I) * L);
+  s->bt_lo = f64 ? nullptr : c.take<float>(static_cast<size_t>(I) * L);
   return c.off;
 }
 
@@ -334,7 +344,7 @@ size_t solve_bytes(int64_t J, int L, int64_t I, bool f64) {
 
 tr_status solve_contract(tr_ctx* ctx, const SolvePlan& s, const void* A, const void* Y,
                          bool f64, int64_t J, int L, int64_t I, cudaStream_t st,
-                         const int64_t* jdev = nullptr) {
+                         const int64_t* jdev = nullptr, bool bt_planes = false) {
   const int64_t ld = L + I;
   if (use_tensor_cores(f64)) {
     TR_LAUNCH("normal_eq_tc", launch_normal_eq_tc(static_cast<const float*>(A),
@@ -352,6 +362,10 @@ tr_status solve_contract(tr_ctx* ctx, const SolvePlan& s, const void* A, const v
     sp.lda = (L + 3) & ~3;
     sp.img = s.mimg;
     sp.np = L + 1;
+  }
+  if (bt_planes && s.bt_hi) {
+    sp.t_hi = s.bt_hi;
+    sp.t_lo = s.bt_lo;
   }
   TR_LAUNCH("reduce_MB", launch_reduce(s.partial, !f64, s.splits, L * ld, ld, L, ld, L, s.M, L,
                                        s.BT, L, st, sp));
@@ -431,12 +445,14 @@ tr_status update_run(tr_ctx* ctx, char* ws, size_t solve_ws, const void* A, cons
   Carver c(ws);
   SolvePlan s;
   solve_plan(c, J, L, I, f64, &s);
-  TR_TRY(solve_contract(ctx, s, A, Y, f64, J, L, I, st, jdev));
+  const bool mixed_lev = !f64 && ctx->factorization != TR_FACTOR_FP64;
+  // the distribution branch's tall Gram of B^T runs in double-float from B^T's planes
+  const bool bt_planes = p && mixed_lev && ctx->ls_rank != TR_LS_RANK_DROP && I >= L;
+  TR_TRY(solve_contract(ctx, s, A, Y, f64, J, L, I, st, jdev, bt_planes));
   if (!p) {   // uniform sampling: the new core needs no distribution
     TR_TRY(solve_cholesky(ctx, s, f64, L, st));
     return solve_rhs(ctx, s, Rl, Rr, I, !f64, core_out, st);
   }
-  const bool mixed_lev = !f64 && ctx->factorization != TR_FACTOR_FP64;
   if (ctx->ls_rank == TR_LS_RANK_DROP) {
     // A dropped column is only nearly dependent on the kept ones, and its unknowns are set to
     // zero: the new core's column space is that of the kept columns of B^T, not of B^T. The
@@ -456,7 +472,8 @@ tr_status update_run(tr_ctx* ctx, char* ws, size_t solve_ws, const void* A, cons
   TR_CUDA(cudaEventRecord(ctx->ev_info, st));
   TR_TRY(solve_rhs(ctx, s, Rl, Rr, I, !f64, core_out, st));
   TR_TRY(leverage_dist(ctx, ws + solve_ws, s.BT, I, L, p, cdf, s.info, side, ctx->ev_info,
-                       mixed_lev));
+                       mixed_lev, bt_planes ? s.bt_hi : nullptr,
+                       bt_planes ? s.bt_lo : nullptr));
   TR_CUDA(cudaEventRecord(ctx->ev_join, side));
   TR_CUDA(cudaStreamWaitEvent(st, ctx->ev_join, 0));
   return TR_OK;

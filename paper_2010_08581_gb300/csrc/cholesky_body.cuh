@@ -170,10 +170,12 @@ __device__ __forceinline__ bool cholesky_cta(const double* __restrict__ G, int n
 // numbers, about 46 significant bits: the mixed path's leverage Gram). Panels of Ops::kPB columns:
 // warp 0 factors a panel in registers (lane l holds rows c0 + l + 32q of the panel's
 // columns): per column one shuffle for the pivot, an rsqrt, a scaling and kPB-1 shuffles for
-// the later panel columns, with no barrier. Then every thread applies the panel's rank-kPB
-// update to 4 x 4 tiles of the trailing lower triangle, reading the panel columns as 16-byte
-// vectors from the column-major work array A (Ops::kPlanes planes of lda * n floats, lda a
-// multiple of 4). Two barriers per panel. Every entry receives its updates in column order.
+// the later panel columns, with no barrier. The panel's rank-kPB update is applied to 4 x 4
+// tiles of the trailing lower triangle, reading the panel columns as 16-byte vectors from the
+// column-major work array A (Ops::kPlanes planes of lda * n floats, lda a multiple of 4).
+// With one panel of look-ahead: warp 0 updates and factors the next panel while the other
+// warps update the rest, one barrier per panel. Every entry receives its updates in column
+// order, so the factor does not depend on the schedule.
 // The factor image img (FP32 or FP64, padded column-major) is written once at the end.
 // Returns false (no factor written) when a pivot is <= tol_scale * max diag.
 constexpr int kPanelCholMax = 160;
@@ -343,96 +345,121 @@ __device__ __forceinline__ bool cholesky_panel(const double* __restrict__ G, int
     }
   }
   __syncthreads();
-  for (int c0 = 0; c0 < n; c0 += kPB) {
+  // Panel factorisation of columns [c0, c0 + w) by warp 0, in registers (lane l holds rows
+  // c0 + l + 32q of the panel's columns): per column one shuffle for the pivot, an rsqrt, a
+  // scaling and w - 1 shuffles for the later panel columns, with no barrier.
+  auto factor_panel = [&](int c0) {
     const int w = (n - c0 < kPB) ? n - c0 : kPB;
-    if (warp == 0) {
-      V p[QP][kPB];
+    V p[QP][kPB];
 #pragma unroll
-      for (int q = 0; q < QP; ++q) {
-        const int i = c0 + lane + 32 * q;
+    for (int q = 0; q < QP; ++q) {
+      const int i = c0 + lane + 32 * q;
+#pragma unroll
+      for (int jj = 0; jj < kPB; ++jj)
+        p[q][jj] = (i < n && jj < w && i >= c0 + jj) ? Ops::ld(A, (c0 + jj) * lda + i, ps)
+                                                     : Ops::zero();
+    }
+    const float tol = s_tol;
+    bool ok = true;
+#pragma unroll
+    for (int kk = 0; kk < kPB; ++kk) {
+      if (kk < w) {
+        const V d = Ops::shfl(p[0][kk], kk);                       // row c0+kk: lane kk
+        ok = ok && (Ops::lead(d) > tol);
+        const V inv = ok ? Ops::rsqrt(d) : Ops::zero();
+#pragma unroll
+        for (int q = 0; q < QP; ++q) {
+          const int r = lane + 32 * q;                              // panel row
+          p[q][kk] = (r == kk) ? Ops::mul(d, inv)
+                               : (r > kk ? Ops::mul(p[q][kk], inv) : Ops::zero());
+        }
+#pragma unroll
+        for (int jj = kk + 1; jj < kPB; ++jj) {
+          const V ljk = Ops::shfl(p[0][kk], jj);                    // row c0+jj: lane jj
+#pragma unroll
+          for (int q = 0; q < QP; ++q) p[q][jj] = Ops::fnms(p[q][kk], ljk, p[q][jj]);
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < QP; ++q) {
+      const int i = c0 + lane + 32 * q;
+      if (i < n) {
 #pragma unroll
         for (int jj = 0; jj < kPB; ++jj)
-          p[q][jj] = (i < n && jj < w && i >= c0 + jj) ? Ops::ld(A, (c0 + jj) * lda + i, ps)
-                                                       : Ops::zero();
-      }
-      const float tol = s_tol;
-      bool ok = true;
-#pragma unroll
-      for (int kk = 0; kk < kPB; ++kk) {
-        if (kk < w) {
-          const V d = Ops::shfl(p[0][kk], kk);                       // row c0+kk: lane kk
-          ok = ok && (Ops::lead(d) > tol);
-          const V inv = ok ? Ops::rsqrt(d) : Ops::zero();
-#pragma unroll
-          for (int q = 0; q < QP; ++q) {
-            const int r = lane + 32 * q;                              // panel row
-            p[q][kk] = (r == kk) ? Ops::mul(d, inv)
-                                 : (r > kk ? Ops::mul(p[q][kk], inv) : Ops::zero());
+          if (jj < w && i >= c0 + jj) {
+            Ops::st(A, (c0 + jj) * lda + i, ps, p[q][jj]);
+            if (i == c0 + jj) s_ldiag[i] = p[q][jj];
           }
-#pragma unroll
-          for (int jj = kk + 1; jj < kPB; ++jj) {
-            const V ljk = Ops::shfl(p[0][kk], jj);                    // row c0+jj: lane jj
-#pragma unroll
-            for (int q = 0; q < QP; ++q) p[q][jj] = Ops::fnms(p[q][kk], ljk, p[q][jj]);
-          }
-        }
       }
-#pragma unroll
-      for (int q = 0; q < QP; ++q) {
-        const int i = c0 + lane + 32 * q;
-        if (i < n) {
-#pragma unroll
-          for (int jj = 0; jj < kPB; ++jj)
-            if (jj < w && i >= c0 + jj) {
-              Ops::st(A, (c0 + jj) * lda + i, ps, p[q][jj]);
-              if (i == c0 + jj) s_ldiag[i] = p[q][jj];
-            }
-        }
-      }
-      if (lane == 0 && !ok) s_stop = 1;
     }
-    __syncthreads();
-    if (s_stop) return false;
-    // trailing update of rows/columns [c0 + w, n): 4 x 4 tiles of the lower triangle
+    if (lane == 0 && !ok) s_stop = 1;
+  };
+  // Rank-w update of the 4 x 4 tile (bi, bj) of the trailing triangle at t0 with the panel
+  // [c0, c0 + w): every entry receives the panel's columns in order.
+  auto update_tile = [&](int c0, int w, int t0, int bi, int bj) {
+    const int i0 = t0 + 4 * bi, j0 = t0 + 4 * bj;
+    V acc[4][4];   // acc[c][r]: column j0+c, row i0+r
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {   // columns >= n do not exist (rows up to lda do)
+      if (j0 + c < n) {
+        Ops::ld4(A, (j0 + c) * lda + i0, ps, acc[c]);
+      } else {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) acc[c][r] = Ops::zero();
+      }
+    }
+#pragma unroll
+    for (int kk = 0; kk < kPB; ++kk) {
+      if (kk < w) {
+        V li[4], lj[4];
+        Ops::ld4(A, (c0 + kk) * lda + i0, ps, li);
+        Ops::ld4(A, (c0 + kk) * lda + j0, ps, lj);
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+          for (int r = 0; r < 4; ++r) acc[c][r] = Ops::fnms(li[r], lj[c], acc[c][r]);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+      if (j0 + c < n) Ops::st4(A, (j0 + c) * lda + i0, ps, acc[c]);
+  };
+  // One panel of look-ahead. After panel c0 is final (barrier), warp 0 applies it to the next
+  // panel's columns (tile columns bj < kPB / 4 of the trailing triangle) and factors that panel,
+  // while the other warps apply panel c0 to the rest of the trailing triangle. One barrier per
+  // panel; the next panel's factorisation overlaps the trailing update.
+  if (warp == 0) factor_panel(0);
+  __syncthreads();
+  if (s_stop) return false;
+  constexpr int PB4 = kPB / 4;                      // tile columns of one panel
+  for (int c0 = 0; c0 < n; c0 += kPB) {
+    const int w = (n - c0 < kPB) ? n - c0 : kPB;
     const int t0 = c0 + w;
     const int m = n - t0;
     if (m > 0) {
       const int nb = (m + 3) >> 2;
-      const int ntiles = nb * (nb + 1) / 2;
-      for (int t = tid; t < ntiles; t += CNT) {
-        int bi = static_cast<int>((sqrtf(8.0f * static_cast<float>(t) + 1.0f) - 1.0f) * 0.5f);
-        while (bi * (bi + 1) / 2 > t) --bi;
-        while ((bi + 1) * (bi + 2) / 2 <= t) ++bi;
-        const int bj = t - bi * (bi + 1) / 2;
-        const int i0 = t0 + 4 * bi, j0 = t0 + 4 * bj;
-        V acc[4][4];   // acc[c][r]: column j0+c, row i0+r
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {   // columns >= n do not exist (rows up to lda do)
-          if (j0 + c < n) {
-            Ops::ld4(A, (j0 + c) * lda + i0, ps, acc[c]);
-          } else {
-#pragma unroll
-            for (int r = 0; r < 4; ++r) acc[c][r] = Ops::zero();
-          }
+      const int pb = nb < PB4 ? nb : PB4;
+      if (warp == 0) {
+        for (int bj = 0; bj < pb; ++bj)
+          for (int bi = bj + lane; bi < nb; bi += 32) update_tile(c0, w, t0, bi, bj);
+        __syncwarp();
+        factor_panel(t0);
+      } else {
+        // tiles with bj >= pb: the triangle of size nb - pb starting at (pb, pb)
+        const int mb = nb - pb;
+        const int ntiles = mb * (mb + 1) / 2;
+        for (int t = tid - 32; t < ntiles; t += CNT - 32) {
+          int bi = static_cast<int>((sqrtf(8.0f * static_cast<float>(t) + 1.0f) - 1.0f) * 0.5f);
+          while (bi * (bi + 1) / 2 > t) --bi;
+          while ((bi + 1) * (bi + 2) / 2 <= t) ++bi;
+          const int bj = t - bi * (bi + 1) / 2;
+          update_tile(c0, w, t0, bi + pb, bj + pb);
         }
-#pragma unroll
-        for (int kk = 0; kk < kPB; ++kk) {
-          if (kk < w) {
-            V li[4], lj[4];
-            Ops::ld4(A, (c0 + kk) * lda + i0, ps, li);
-            Ops::ld4(A, (c0 + kk) * lda + j0, ps, lj);
-#pragma unroll
-            for (int c = 0; c < 4; ++c)
-#pragma unroll
-              for (int r = 0; r < 4; ++r) acc[c][r] = Ops::fnms(li[r], lj[c], acc[c][r]);
-          }
-        }
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-          if (j0 + c < n) Ops::st4(A, (j0 + c) * lda + i0, ps, acc[c]);
       }
     }
     __syncthreads();
+    if (s_stop) return false;
   }
   // the factor image, padded column-major: img[c*(n+1) + r] = L[r][c]; or, for a
   // double-float factor with img_hi/img_lo given, its two FP32 planes in that layout (the

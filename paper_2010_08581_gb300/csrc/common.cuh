@@ -127,6 +127,10 @@ cudaError_t launch_normal_eq(const void* A, const void* Y, bool f64, int64_t J, 
 size_t gram_workspace(int64_t rows, int cols, bool trans, int* splits);
 cudaError_t launch_gram(const double* A, int64_t rows, int cols, int64_t lda, bool trans,
                         double* partial, int splits, cudaStream_t st);
+// G = A^T A (trans = false) from double-float planes A = hi + lo (row-major, lda), in
+// compensated FP32 arithmetic; same partial layout and split count as launch_gram.
+cudaError_t launch_gram_ff(const float* Ah, const float* Al, int64_t rows, int cols,
+                           int64_t lda, double* partial, int splits, cudaStream_t st);
 
 // Fixed-order reduction over splits s = 0..splits-1 of an nrows x ncols block of partials
 // (row stride pld, split stride pstride; FP32 or FP64) into FP64. Columns c < c_split go
@@ -141,6 +145,8 @@ struct ReduceSplit {
   int lda = 0;
   float* img = nullptr;
   int np = 0;
+  float* t_hi = nullptr;   // double-float planes of out2 (same layout), for launch_gram_ff
+  float* t_lo = nullptr;
 };
 cudaError_t launch_reduce(const void* partial, bool partial_f32, int splits, int64_t pstride,
                           int64_t pld, int64_t nrows, int64_t ncols, int64_t c_split,

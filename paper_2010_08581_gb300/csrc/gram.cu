@@ -60,6 +60,70 @@ __global__ void __launch_bounds__(GNT) k_gram(const double* __restrict__ A, int6
 }
 
 // ------------------------------------------------------------------------------------
+// The same Gram (trans = false) from double-float input planes X = hi + lo, in compensated
+// FP32 arithmetic on the FP32 pipe (the FP64 pipe runs at about 1/64 of its rate on this GPU):
+// each product's leading part and its exact rounding error (FMA) plus the cross terms, then a
+// two-sum into a (sum, correction) pair per output. About 47 significant bits, as the
+// double-float factorisation that consumes the Gram.
+// ------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(GNT) k_gram_ff(const float* __restrict__ Ah,
+                                                 const float* __restrict__ Al, int64_t K, int n,
+                                                 int64_t lda, int64_t chunk,
+                                                 double* __restrict__ partial) {
+  __shared__ float Ph[GK][GT + 1], Pl[GK][GT + 1];
+  __shared__ float Qh[GK][GT + 1], Ql[GK][GT + 1];
+  const int nt = (n + GT - 1) / GT;
+  int tp = 0, rem = blockIdx.x;
+  while (rem >= nt - tp) { rem -= nt - tp; ++tp; }
+  const int tq = tp + rem;
+  const int p0 = tp * GT, q0 = tq * GT;
+  const int64_t k0 = static_cast<int64_t>(blockIdx.y) * chunk;
+  const int64_t k1 = (k0 + chunk < K) ? k0 + chunk : K;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  float sum[4] = {0.f, 0.f, 0.f, 0.f}, cor[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int64_t kb = k0; kb < k1; kb += GK) {
+#pragma unroll
+    for (int r = 0; r < (GK * GT) / GNT; ++r) {
+      const int e = threadIdx.x + r * GNT;
+      const int kk = e / GT, col = e % GT;
+      const int64_t t = kb + kk;
+      const int p = p0 + col, q = q0 + col;
+      const bool okp = t < k1 && p < n, okq = t < k1 && q < n;
+      Ph[kk][col] = okp ? Ah[t * lda + p] : 0.f;
+      Pl[kk][col] = okp ? Al[t * lda + p] : 0.f;
+      Qh[kk][col] = okq ? Ah[t * lda + q] : 0.f;
+      Ql[kk][col] = okq ? Al[t * lda + q] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < GK; ++kk) {
+      const float yh = Qh[kk][tx], yl = Ql[kk][tx];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float xh = Ph[kk][ty + 8 * u], xl = Pl[kk][ty + 8 * u];
+        const float pr = xh * yh;
+        float er = fmaf(xh, yh, -pr);
+        er = fmaf(xh, yl, er);
+        er = fmaf(xl, yh, er);
+        const float t2 = sum[u] + pr;
+        const float bv = t2 - sum[u];
+        const float ts = (sum[u] - (t2 - bv)) + (pr - bv);
+        sum[u] = t2;
+        cor[u] += ts + er;
+      }
+    }
+    __syncthreads();
+  }
+  double* out = partial + static_cast<int64_t>(blockIdx.y) * n * n;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int p = p0 + ty + 8 * u, q = q0 + tx;
+    if (p < n && q < n)
+      out[static_cast<int64_t>(p) * n + q] = static_cast<double>(sum[u]) + static_cast<double>(cor[u]);
+  }
+}
+
+// ------------------------------------------------------------------------------------
 // Fixed-order reduction of split partials (s = 0, 1, ..., splits-1) into FP64 (FP64
 // partials: FP64 sum; FP32 partials: compensated FP32 sum, then FP64).
 // Columns c < c_split go to out1[r*ld1 + c]; columns c >= c_split go transposed to
@@ -123,8 +187,17 @@ __global__ void __launch_bounds__(256) k_reduce(const TP* __restrict__ partial, 
         if (sp.lo) sp.lo[r * sp.lda + c] = static_cast<float>(s - static_cast<double>(h));
       }
     }
-    if (c < c_split) out1[r * ld1 + c] = s;
-    else out2[(c - c_split) * ld2 + r] = s;
+    if (c < c_split) {
+      out1[r * ld1 + c] = s;
+    } else {
+      const int64_t o = (c - c_split) * ld2 + r;
+      out2[o] = s;
+      if (sp.t_hi) {   // double-float planes of the transposed block (the Gram's input)
+        const float h = static_cast<float>(s);
+        sp.t_hi[o] = h;
+        sp.t_lo[o] = static_cast<float>(s - static_cast<double>(h));
+      }
+    }
   }
 }
 
@@ -162,6 +235,18 @@ cudaError_t launch_gram(const double* A, int64_t rows, int cols, int64_t lda, bo
   if (s != splits) return cudaErrorInvalidValue;
   dim3 grid(nt * (nt + 1) / 2, s);
   k_gram<<<grid, GNT, 0, st>>>(A, K, n, lda, trans, chunk, partial);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gram_ff(const float* Ah, const float* Al, int64_t rows, int cols,
+                           int64_t lda, double* partial, int splits, cudaStream_t st) {
+  const int n = cols;
+  const int nt = (n + GT - 1) / GT;
+  int64_t chunk;
+  const int s = plan_splits(rows, nt * (nt + 1) / 2, GK, &chunk);
+  if (s != splits) return cudaErrorInvalidValue;
+  dim3 grid(nt * (nt + 1) / 2, s);
+  k_gram_ff<<<grid, GNT, 0, st>>>(Ah, Al, rows, n, lda, chunk, partial);
   return cudaGetLastError();
 }
 

@@ -25,6 +25,8 @@ constexpr int TM = 128;          // UMMA M
 constexpr int TN = 128;          // UMMA N (output columns per CTA)
 constexpr int TK = 32;           // samples per pipeline stage (one 128-byte swizzle row)
 constexpr int NT = 256;
+static_assert(TK == 32 && TM == 4 * (NT / 32) * 4,
+              "operand loader: one sample per lane, 4 groups of 4 rows per warp");
 constexpr int STAGES = 2;
 constexpr int A_BYTES = TM * TK * 4;   // 16 KB
 constexpr int B_BYTES = TN * TK * 4;   // 16 KB
@@ -80,15 +82,15 @@ __global__ void __launch_bounds__(NT, 1) k_normal_eq_tc(const float* __restrict_
   const bool vec = (L % 4) == 0 && (I % 4) == 0 &&
                    (reinterpret_cast<uintptr_t>(A) % 16) == 0 &&
                    (reinterpret_cast<uintptr_t>(Y) % 16) == 0;
-  // group q (0..3) of thread t: unit v = t + NT q of the TK x (TM / 4) grid:
-  // sample k = v / (TM / 4), tile rows 4 (v % (TM / 4)) .. + 3
+  // group q (0..3) of thread t: sample k = lane, tile rows 4 g .. 4 g + 3 with
+  // g = warp + 8 q. Lanes cover consecutive samples, so the stores into the K-major swizzled
+  // tile below hit 32 different banks (consecutive k of one row span the whole 128-byte line).
   auto load_chunk = [&](int c, float (&ra)[TK / 2], float (&rb)[TK / 2]) {
     const int64_t jb = j0 + static_cast<int64_t>(c) * TK;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const int v = tid + NT * q;
-      const int64_t j = jb + v / (TM / 4);
-      const int r4 = 4 * (v % (TM / 4));
+      const int64_t j = jb + lane;
+      const int r4 = 4 * (warp + (NT / 32) * q);
       const int am = m0 + r4;
       const int64_t bn = n0 + r4;
       float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
@@ -130,9 +132,8 @@ __global__ void __launch_bounds__(NT, 1) k_normal_eq_tc(const float* __restrict_
     if (s_abort) break;
 #pragma unroll
     for (int u = 0; u < TK / 2; ++u) {
-      const int v = tid + NT * (u / 4);
-      const int k = v / (TM / 4);
-      const int row = 4 * (v % (TM / 4)) + (u % 4);
+      const int k = lane;
+      const int row = 4 * (warp + (NT / 32) * (u / 4)) + (u % 4);
       const float a = ca[u], b = cb[u];
       const float ah = tf32_rna(a), bh = tf32_rna(b);
       const float al = tf32_rna(a - ah), bl = tf32_rna(b - bh);
