@@ -772,6 +772,11 @@ def run_serving(T, dev, seconds, rate=200.0, warmup_s=3.0, pool_size=128, seed=0
                                "max": max(sweeps) if sweeps else None},
         "converged_fraction": round(conv / max(1, len(meas)), 3),
         "median_fit": round(float(np.median([r["fit"] for r, _, _ in meas])), 5) if meas else None,
+        "fit_by_modes": fit_by_modes(meas),
+        "singular_updates": int(sum(r["singular_updates"] for r, _, _ in meas)),
+        "fit_note": "fit = 1 - relative error after the last sweep; requests near fit 0 are "
+                    "ALS stalls from the random N(0,1) start, which the FP64 oracle's stopped "
+                    "driver shows on the same shapes (tests/test_gpu_serving_stalls.py)",
         "ticks": st["ticks"], "ms_per_tick": round(st["tick_ns"] / 1e6 / max(1, st["ticks"]), 3),
         "peak_active": st["peak_active"],
         "peak_charged_gb": round(st["peak_charged_bytes"] / 1e9, 3),
@@ -779,6 +784,23 @@ def run_serving(T, dev, seconds, rate=200.0, warmup_s=3.0, pool_size=128, seed=0
         "drain_s": round((t_end - t_arrivals_end) / 1e9, 2),
         "arrival_lateness_s": round(late, 3),
     }
+
+
+def fit_by_modes(meas):
+    """Final fits of the measured served requests, grouped by their number of modes N: count,
+    quartiles, the fraction at the noise floor (fit > 0.9) and the fraction stalled near
+    relative error 1 (fit < 0.1)."""
+    out = {}
+    for N in (3, 4, 5):
+        f = [r["fit"] for r, _, sh in meas if len(sh["dims"]) == N]
+        if not f:
+            continue
+        q = np.percentile(f, [25, 50, 75])
+        out[str(N)] = {"requests": len(f), "p25": round(float(q[0]), 4),
+                       "p50": round(float(q[1]), 4), "p75": round(float(q[2]), 4),
+                       "noise_floor_frac": round(sum(1 for v in f if v > 0.9) / len(f), 3),
+                       "stalled_frac": round(sum(1 for v in f if v < 0.1) / len(f), 3)}
+    return out
 
 
 def run_reference(args):
