@@ -183,6 +183,7 @@ def algorithmic_cost(kernel, wl):
       gram_f64        : 2*I*L^2 FP64 flops
       leverage_rows   : I*L^2 FP64 flops
       sample          : J*(N-1) * (4 + 8*log2 I) bytes (index writes + CDF probes) + J*8
+      sample_chain    : sample + subchain + gather (draws, rows and fibres in one kernel)
     """
     dims, ranks, J = wl["dims"], wl["ranks"], wl["J"]
     N = len(dims)
@@ -200,6 +201,8 @@ def algorithmic_cost(kernel, wl):
         "gram_f64": ("flops_f64", 2.0 * I * L * L),
         "leverage_rows": ("flops_f64", I * L * L),
         "sample": ("hbm", J * (N - 1) * (4 + 8 * math.log2(max(I, 2))) + J * 8),
+        "sample_chain": ("hbm", J * (N - 1) * (4 + 8 * math.log2(max(I, 2))) + J * 8
+                         + J * (N - 1) * L * 8.0 + J * L * s + 2.0 * J * I * s),
         "reduce_MB": ("hbm", L * (L + I) * 8.0),
         "reduce_gram": ("hbm", L * L * 8.0),
         "cdf": ("hbm", I * 8.0 * 3),
