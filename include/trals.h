@@ -107,6 +107,24 @@ tr_status tr_status_sync(tr_ctx* ctx, tr_stream stream);
 tr_status tr_leverage(tr_ctx* ctx, const double* core, int64_t I, int Rl, int Rr,
                       double* p, double* cdf, tr_stream stream);
 
+/* Row a1 as the mixed-precision drivers compute it after each update (Def. 4; eq. for
+ * p^(n); Alg. 2, "update n-th distribution"): the distribution of a tall matrix A
+ * (I >= L, 4 <= L <= 128) given as two FP32 planes, A = A_hi + A_lo (row-major I x L), the
+ * form in which the drivers hold B^T. K = A^T A is formed in double-float; an FP32 Cholesky
+ * factor of K and its inverse X precondition it, C = X K X^T = I + E is formed in
+ * double-float, and ell_i = w_i^T (I + E)^-1 w_i with w_i = X a_i by the series
+ * sum_k (-E)^k, taken through E^4 (||E||_F <= 1e-3) or E^6 (||E||_F <= 1e-2). If the FP32
+ * factorisation meets a pivot <= L*eps32*max diag or ||E||_F > 1e-2, the double-float
+ * factorisation of K with FP64 fallback and FP64 row solves is used instead (the rank rule of
+ * TR_PREC_MIXED above). Both branches run on the device with no host round trip.
+ * A_hi, A_lo : device FP32 [I][L] (16-byte aligned).
+ * p, cdf     : device FP64 [I] out, as tr_leverage.
+ * branch     : optional device int out: 0 when the preconditioned form was used, 1 when
+ *              the factorisation fallback was.
+ * Other shapes return TR_ERR_INVALID_ARG. */
+tr_status tr_leverage_planes(tr_ctx* ctx, const float* A_hi, const float* A_lo, int64_t I,
+                             int L, double* p, double* cdf, int* branch, tr_stream stream);
+
 /* Row a2 -- J i.i.d. draws from q^{!=k} = prod_{j!=k} p^(j) (Alg. 3; Def. 5).
  * p, cdf   : host arrays of N device pointers (entry k unused), FP64 [dims[j]].
  * seed, update_id : Philox4x32-10 key and counter words: the uniform for sample j at ring

@@ -177,6 +177,7 @@ struct LevPass {  // one Cholesky-QR pass over an m x n row-major matrix (n = Gr
   double* partial; double* G; double* Lrow; double* Lcol; double* invdiag; int* keep; int* info;
   double* img;     // padded FP64 image of the factor for the row solves
   int splits;
+  LevPrecond pre;  // the mixed drivers' preconditioned form (tall passes only)
 };
 
 LevPass carve_pass(Carver& c, int64_t rows, int cols, bool trans) {
@@ -191,6 +192,21 @@ LevPass carve_pass(Carver& c, int64_t rows, int cols, bool trans) {
   p.keep = c.take<int>(n);
   p.info = c.take<int>(1);
   p.img = reinterpret_cast<double*>(c.take<char>(trsm_image_bytes(n, false)));
+  if (!trans && lev_precond_fits(rows, cols)) {
+    p.pre.Limg = reinterpret_cast<float*>(c.take<char>(trsm_image_bytes(n, true)));
+    p.pre.Ximg = reinterpret_cast<float*>(c.take<char>(trsm_image_bytes(n, true)));
+    p.pre.invdiag = c.take<double>(n);
+    p.pre.keep = c.take<int>(n);
+    const size_t ld4 = static_cast<size_t>((n + 3) & ~3);
+    p.pre.Uh = c.take<float>(n * ld4);
+    p.pre.Ul = c.take<float>(n * ld4);
+    p.pre.E = c.take<float>(n * ld4);
+    p.pre.esq = c.take<float>(lev_precond_ctas(n));
+    p.pre.state = c.take<int>(1);
+    p.pre.lda_k = (n + 3) & ~3;
+    p.pre.K_hi = reinterpret_cast<const float*>(p.Lrow);
+    p.pre.K_lo = reinterpret_cast<const float*>(p.Lcol);
+  }
   return p;
 }
 
@@ -253,6 +269,13 @@ size_t leverage_bytes(int64_t I, int L) {
   return leverage_plan(c, I, L, &a, &b, &e);
 }
 
+// The preconditioned form of the mixed drivers' tall leverage scores (on unless
+// TRALS_LEV_PRECOND=0, which keeps the double-float factorisation for every update).
+bool precond_enabled() {
+  const char* e = getenv("TRALS_LEV_PRECOND");
+  return !(e && e[0] == '0');
+}
+
 // Leverage scores of the rows of the I x L row-major matrix `mat` (a core's G_(2), or any
 // matrix with the same column space) and, from them, p and the CDF (unless *skip != 0).
 // `mixed` (the mixed-precision drivers): a tall matrix's Gram is factored in double-float
@@ -278,7 +301,37 @@ tr_status leverage_dist(tr_ctx* ctx, char* ws, const double* mat, int64_t I, int
   const double tol = static_cast<double>(I > L ? I : L) * eps;
   TR_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned), st));
   const CdfEpilogue ep{counter, p, cdf, skip, ctx->d_err};
-  if (I >= L) {
+  if (I >= L && mixed && mat_hi && p1.pre.state && precond_enabled()) {
+    // FP32 preconditioner and a short series (lev_precond.cu); the double-float
+    // factorisation, its image and the FP64 row solves run only when its device flag says so
+    const int n = L;
+    TR_LAUNCH("gram_f64", launch_gram_ff(mat_hi, mat_lo, I, n, n, p1.partial, p1.splits, st));
+    ReduceSplit sp;
+    sp.hi = reinterpret_cast<float*>(p1.Lrow);
+    sp.lo = reinterpret_cast<float*>(p1.Lcol);
+    sp.lda = (n + 3) & ~3;
+    TR_LAUNCH("reduce_gram", launch_reduce(p1.partial, false, p1.splits,
+                                           static_cast<int64_t>(n) * n, n, n, n, n, p1.G, n,
+                                           nullptr, 0, st, sp));
+    TR_LAUNCH("lev_factor", launch_lev_precond(0, p1.pre, n, I, mat_hi, mat_lo, L, ell, ep, st));
+    TR_LAUNCH("lev_inverse", launch_lev_precond(1, p1.pre, n, I, mat_hi, mat_lo, L, ell, ep, st));
+    TR_LAUNCH("lev_u", launch_lev_precond(2, p1.pre, n, I, mat_hi, mat_lo, L, ell, ep, st));
+    TR_LAUNCH("lev_e", launch_lev_precond(3, p1.pre, n, I, mat_hi, mat_lo, L, ell, ep, st));
+    if (wait_before_rows) TR_CUDA(cudaStreamWaitEvent(st, wait_before_rows, 0));
+    TR_LAUNCH("lev_rows", launch_lev_precond(4, p1.pre, n, I, mat_hi, mat_lo, L, ell, ep, st));
+    const int* gate = p1.pre.state;
+    const double eps_ff = 9.094947017729282e-13;   // 2^-40
+    TR_LAUNCH("cholesky_leverage",
+              launch_cholesky_lev_mixed(p1.G, n, tol, tol / eps * eps_ff, p1.Lrow, p1.Lcol,
+                                        p1.invdiag, p1.keep, p1.info, ctx->d_err, st, p1.img,
+                                        sp.hi, sp.lo, gate));
+    TR_LAUNCH("ff_image", launch_ff_image(p1.Lrow, p1.Lcol, n, p1.info, p1.img, st, gate));
+    CdfEpilogue ep2 = ep;
+    ep2.run_if = gate;
+    TR_LAUNCH("leverage_rows", launch_trsm(0, false, L, p1.Lrow, p1.Lcol, p1.invdiag, nullptr, I,
+                                           mat, L, nullptr, 1, 1, nullptr, ell, st, p1.img,
+                                           nullptr, &ep2));
+  } else if (I >= L) {
     TR_TRY(run_pass(ctx, p1, mat, I, L, L, false, tol, st, mixed, mat_hi, mat_lo));
     if (wait_before_rows) TR_CUDA(cudaStreamWaitEvent(st, wait_before_rows, 0));
     TR_LAUNCH("leverage_rows", launch_trsm(0, false, L, p1.Lrow, p1.Lcol, p1.invdiag, nullptr, I,
@@ -683,6 +736,7 @@ std::vector<uint64_t> als_key(const tr_ctx* ctx, const AlsPlan& P) {
   u(static_cast<uint64_t>(ctx->ls_rank));
   u(static_cast<uint64_t>(ctx->wait_limit));
   u(static_cast<uint64_t>(ctx->factorization));
+  u(precond_enabled() ? 1 : 0);
   return k;
 }
 
@@ -838,6 +892,34 @@ tr_status tr_status_sync(tr_ctx* ctx, tr_stream stream) {
   TR_TRY(check_ctx(ctx));
   DeviceGuard g(ctx->device);
   return read_device_error(ctx, S(stream));
+}
+
+tr_status tr_leverage_planes(tr_ctx* ctx, const float* A_hi, const float* A_lo, int64_t I,
+                             int L, double* p, double* cdf, int* branch, tr_stream stream) {
+  TR_TRY(check_ctx(ctx));
+  if (!A_hi || !A_lo || !p || !cdf) return fail(ctx, TR_ERR_INVALID_ARG, "null pointer");
+  if (!lev_precond_fits(I, L))
+    return fail(ctx, TR_ERR_INVALID_ARG, "tr_leverage_planes needs I >= L, 4 <= L <= 128 "
+                "(I=%lld L=%d)", static_cast<long long>(I), L);
+  if ((reinterpret_cast<uintptr_t>(A_hi) | reinterpret_cast<uintptr_t>(A_lo)) & 15)
+    return fail(ctx, TR_ERR_INVALID_ARG, "A_hi and A_lo must be 16-byte aligned");
+  DeviceGuard g(ctx->device);
+  const size_t need = leverage_bytes(I, L) + static_cast<size_t>(I) * L * sizeof(double) + 256;
+  TR_TRY(ensure_ws(ctx, need));
+  cudaStream_t st = S(stream);
+  // the FP64 matrix (hi + lo) for the fallback's row solves, after the leverage workspace
+  double* mat = reinterpret_cast<double*>(ctx->arena + ((leverage_bytes(I, L) + 255) & ~size_t(255)));
+  TR_CUDA(launch_planes_sum(A_hi, A_lo, static_cast<int64_t>(I) * L, mat, st));
+  TR_TRY(leverage_dist(ctx, ctx->arena, mat, I, L, p, cdf, nullptr, st, nullptr, true, A_hi,
+                       A_lo));
+  if (branch) {
+    Carver c(ctx->arena);
+    LevPass p1{}, p2{};
+    double* ell;
+    leverage_plan(c, I, L, &p1, &p2, &ell);
+    TR_CUDA(launch_copy_int(precond_enabled() ? p1.pre.state : nullptr, 1, branch, st));
+  }
+  return TR_OK;
 }
 
 tr_status tr_leverage(tr_ctx* ctx, const double* core, int64_t I, int Rl, int Rr, double* p,

@@ -49,8 +49,10 @@ __global__ void __launch_bounds__(CNT) k_cholesky_lev_mixed(const double* __rest
                                                             int* info, unsigned* err,
                                                             int dyn_bytes, double* img64,
                                                             const float* pre_hi,
-                                                            const float* pre_lo) {
+                                                            const float* pre_lo,
+                                                            const int* run_if) {
   extern __shared__ double smem[];
+  if (run_if && *run_if == 0) return;
   const int64_t nn = static_cast<int64_t>(n) * n;
   float* Aff = panel_floats<FFOps>(n) * 4 <= dyn_bytes ? reinterpret_cast<float*>(smem) : nullptr;
   double* A64 = nn * 8 <= dyn_bytes ? smem : Lrow;
@@ -62,8 +64,9 @@ __global__ void __launch_bounds__(CNT) k_cholesky_lev_mixed(const double* __rest
 __global__ void __launch_bounds__(256) k_ff_image(const float* __restrict__ hi,
                                                   const float* __restrict__ lo, int64_t count,
                                                   const int* __restrict__ info,
-                                                  double* __restrict__ img64) {
-  if (*info != 2) return;
+                                                  double* __restrict__ img64,
+                                                  const int* __restrict__ run_if) {
+  if ((run_if && *run_if == 0) || *info != 2) return;
   for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < count;
        e += static_cast<int64_t>(gridDim.x) * blockDim.x)
     img64[e] = static_cast<double>(hi[e]) + static_cast<double>(lo[e]);
@@ -72,24 +75,27 @@ __global__ void __launch_bounds__(256) k_ff_image(const float* __restrict__ hi,
 }  // namespace
 
 cudaError_t launch_ff_image(const double* Lrow, const double* Lcol, int n, const int* info,
-                            double* img64, cudaStream_t st) {
+                            double* img64, cudaStream_t st, const int* run_if) {
   const int64_t count = static_cast<int64_t>(n) * (n + 1);
   const unsigned blocks = static_cast<unsigned>((count + 255) / 256 < sm_count() ? (count + 255) / 256 : sm_count());
   k_ff_image<<<blocks, 256, 0, st>>>(reinterpret_cast<const float*>(Lrow),
-                                     reinterpret_cast<const float*>(Lcol), count, info, img64);
+                                     reinterpret_cast<const float*>(Lcol), count, info, img64,
+                                     run_if);
   return cudaGetLastError();
 }
 
 cudaError_t launch_cholesky_lev_mixed(const double* G, int n, double tol64, double tolff,
                                       double* Lrow, double* Lcol, double* invdiag, int* keep,
                                       int* info, unsigned* err, cudaStream_t st, double* img64,
-                                      const float* pre_hi, const float* pre_lo) {
+                                      const float* pre_hi, const float* pre_lo,
+                                      const int* run_if) {
   const size_t nn = static_cast<size_t>(n) * n;
   const size_t ff = static_cast<size_t>(panel_floats<FFOps>(n)) * 4;
   const size_t want = nn * 8 > ff ? nn * 8 : ff;
   const size_t dyn = want <= kCholDyn ? want : (nn * 8 <= kCholDyn ? nn * 8 : 0);
   k_cholesky_lev_mixed<<<1, CNT, dyn, st>>>(G, n, tol64, tolff, Lrow, Lcol, invdiag, keep, info,
-                                            err, static_cast<int>(dyn), img64, pre_hi, pre_lo);
+                                            err, static_cast<int>(dyn), img64, pre_hi, pre_lo,
+                                            run_if);
   return cudaGetLastError();
 }
 

@@ -175,13 +175,15 @@ cudaError_t launch_cholesky_lev_mixed(const double* G, int n, double tol64, doub
                                       double* Lrow, double* Lcol, double* invdiag, int* keep,
                                       int* info, unsigned* err, cudaStream_t st, double* img64,
                                       const float* pre_hi = nullptr,
-                                      const float* pre_lo = nullptr);
+                                      const float* pre_lo = nullptr,
+                                      const int* run_if = nullptr);
 // pre / pre_hi, pre_lo: the work array's planes already written by launch_reduce (a
 // ReduceSplit with lda = (n + 3) & ~3), or null to convert from G.
 // After launch_cholesky_lev_mixed: img64 = hi + lo of the FP32 planes it left in Lrow / Lcol
 // when its double-float branch succeeded (*info == 2); otherwise nothing.
+// run_if (both launches, optional): nothing is done unless *run_if != 0.
 cudaError_t launch_ff_image(const double* Lrow, const double* Lcol, int n, const int* info,
-                            double* img64, cudaStream_t st);
+                            double* img64, cudaStream_t st, const int* run_if = nullptr);
 cudaError_t launch_cholesky(const double* G, int n, int mode, double tol_scale, double* Lrow,
                             double* Lcol, double* invdiag, int* keep, int* info,
                             unsigned* err, cudaStream_t st, double* img64 = nullptr,
@@ -205,6 +207,7 @@ struct CdfEpilogue {
   double* cdf;
   const int* skip;
   unsigned* err;
+  const int* run_if = nullptr;   // when given, the launch does nothing unless *run_if != 0
 };
 cudaError_t launch_trsm(int mode, bool f32, int n, const double* Lrow, const double* Lcol,
                         const double* invdiag, const int* info, int64_t nvec, const double* rhs,
@@ -233,6 +236,43 @@ cudaError_t launch_solve_inv(int n, const float* Limg, const float* Mimg,
                              const double* invdiag, const int* info, int64_t nvec,
                              const double* rhs, int64_t ld, int Rl, int Rr, double* core_out,
                              float* Wimg, cudaStream_t st);
+
+// The mixed drivers' leverage scores of a tall I x n row-major matrix A given as double-float
+// planes (Ah + Al, row stride lda), 4 <= n <= 128 (lev_precond.cu): an FP32 Cholesky factor of
+// K = A^T A (from the reduction's FP32 work array K_hi, row stride lda_k) and its inverse X
+// as preconditioner, C = X K X^T = I + E in double-float from K's planes, and
+// ell_i = w_i^T (I + E)^-1 w_i with w_i = X a_i by a short series; then, from the last CTA,
+// p and the CDF as launch_trsm's epilogue (ep.counter 0 before the launch). When the FP32
+// factorisation fails or ||E||_F is too large for the series, nothing is written and
+// *state = 1 (0 otherwise): the caller's fallback launches are gated on it (run_if).
+// Five launches, issued in order by stage = 0 (FP32 factor; sets *state), 1 (inverse),
+// 2 (U = X K), 3 (E = U X^T - I), 4 (rows, p and the CDF; reads ep.skip); lda_k must be
+// (n + 3) & ~3.
+struct LevPrecond {
+  const float* K_hi;
+  const float* K_lo;
+  int lda_k;
+  float* Limg;       // FP32 factor image (trsm_image_bytes(n, true) bytes)
+  float* Ximg;       // its inverse, same layout
+  double* invdiag;   // n
+  int* keep;         // n
+  float* Uh;         // U = X K as double-float planes, n x lda_k each
+  float* Ul;
+  float* E;          // n x lda_k
+  float* esq;        // lev_precond_ctas(n)
+  int* state;
+};
+bool lev_precond_fits(int64_t I, int n);
+int lev_precond_ctas(int n);
+cudaError_t launch_lev_precond(int stage, const LevPrecond& lp, int n, int64_t I,
+                               const float* Ah, const float* Al, int64_t lda, double* ell,
+                               const CdfEpilogue& ep, cudaStream_t st);
+
+// dst[e] = hi[e] + lo[e] in FP64 (lev_precond.cu).
+cudaError_t launch_planes_sum(const float* hi, const float* lo, int64_t count, double* dst,
+                              cudaStream_t st);
+// *dst = src ? *src : v, on the stream (lev_precond.cu).
+cudaError_t launch_copy_int(const int* src, int v, int* dst, cudaStream_t st);
 
 // Merging repeated draws (merge.cu; Sec. 4.2): idx_out / w_out receive one row per distinct
 // multi-index in the order of first occurrence, weight w * sqrt(count), and *J_out (device)

@@ -130,6 +130,7 @@ cudaError_t batched_attributes();
 cudaError_t jacobi_attributes();
 cudaError_t solve_inv_attributes();
 cudaError_t merge_attributes();
+cudaError_t lev_precond_attributes();
 
 cudaError_t init_kernel_attributes(const char** which) {
   cudaError_t e = cholesky_attributes();
@@ -148,6 +149,8 @@ cudaError_t init_kernel_attributes(const char** which) {
   if (e != cudaSuccess) { *which = "solve_inv"; return e; }
   e = merge_attributes();
   if (e != cudaSuccess) { *which = "merge"; return e; }
+  e = lev_precond_attributes();
+  if (e != cudaSuccess) { *which = "lev_precond"; return e; }
   e = fit_attributes();
   if (e != cudaSuccess) *which = "fit";
   return e;

@@ -204,6 +204,21 @@ cudaError_t launch_solve_inv(int n, const float* Limg, const float* Mimg,
   return cudaGetLastError();
 }
 
+// The inverse alone (the preconditioner of the mixed drivers' leverage scores): W = L_f^-1
+// into Wimg; nothing when *info != 0.
+cudaError_t launch_tri_inv(int n, const float* Limg, const double* invdiag, const int* info,
+                           float* Wimg, cudaStream_t st) {
+  if (!solve_inv_fits(n)) return cudaErrorInvalidValue;
+  const unsigned ib = static_cast<unsigned>((n + IW - 1) / IW);
+  switch ((n + 31) / 32) {
+    case 1: k_tri_inv<1><<<ib, IW * 32, inv_smem(n), st>>>(n, Limg, invdiag, info, Wimg); break;
+    case 2: k_tri_inv<2><<<ib, IW * 32, inv_smem(n), st>>>(n, Limg, invdiag, info, Wimg); break;
+    case 3: k_tri_inv<3><<<ib, IW * 32, inv_smem(n), st>>>(n, Limg, invdiag, info, Wimg); break;
+    default: k_tri_inv<4><<<ib, IW * 32, inv_smem(n), st>>>(n, Limg, invdiag, info, Wimg); break;
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t solve_inv_attributes() {
   const int di = static_cast<int>(inv_smem(128)), ds = static_cast<int>(solve_smem_bytes(128));
   cudaError_t e = cudaFuncSetAttribute(k_tri_inv<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, di);

@@ -150,8 +150,9 @@ __device__ __forceinline__ void stage_async(void* dst, const void* src, int byte
   asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
 
-// Block-wide exclusive scan (fixed order) of one double per thread for TW warps.
-__device__ __forceinline__ double block_scan_tw(double v, double* wt, double* total) {
+// Block-wide exclusive scan (fixed order) of one double per thread for NW warps.
+template <int NW>
+__device__ __forceinline__ double block_scan_nw(double v, double* wt, double* total) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double inc = v;
 #pragma unroll
@@ -163,7 +164,7 @@ __device__ __forceinline__ double block_scan_tw(double v, double* wt, double* to
   __syncthreads();
   if (threadIdx.x == 0) {
     double run = 0.0;
-    for (int q = 0; q < TW; ++q) { const double t = wt[q]; wt[q] = run; run += t; }
+    for (int q = 0; q < NW; ++q) { const double t = wt[q]; wt[q] = run; run += t; }
     *total = run;
   }
   __syncthreads();
@@ -172,17 +173,23 @@ __device__ __forceinline__ double block_scan_tw(double v, double* wt, double* to
   return r;
 }
 
-// p = ell / sum(ell) and its prefix sum, by the CTA that finishes last (mode 0 only).
-__device__ inline void cdf_epilogue(const CdfEpilogue& ep, const double* ell, int64_t I) {
-  __shared__ double wt[TW];
+__device__ __forceinline__ double block_scan_tw(double v, double* wt, double* total) {
+  return block_scan_nw<TW>(v, wt, total);
+}
+
+// p = ell / sum(ell) and its prefix sum, by the CTA that finishes last (mode 0 only), whose
+// NW warps all take part.
+template <int NW>
+__device__ inline void cdf_epilogue_nw(const CdfEpilogue& ep, const double* ell, int64_t I) {
+  __shared__ double wt[NW];
   __shared__ double s_total;
   if (ep.skip && *ep.skip) return;
   const int t = threadIdx.x;
-  const int64_t chunk = (I + TW * 32 - 1) / (TW * 32);
+  const int64_t chunk = (I + NW * 32 - 1) / (NW * 32);
   const int64_t b = t * chunk, e = (b + chunk < I) ? b + chunk : I;
   double s = 0.0;
   for (int64_t i = b; i < e; ++i) s += __ldcg(ell + i);
-  block_scan_tw(s, wt, &s_total);
+  block_scan_nw<NW>(s, wt, &s_total);
   const double total = s_total;
   if (!(total > 0.0) || !isfinite(total)) {
     for (int64_t i = b; i < e; ++i) {
@@ -192,15 +199,22 @@ __device__ inline void cdf_epilogue(const CdfEpilogue& ep, const double* ell, in
     if (t == 0) atomicOr(ep.err, kErrSingular);
     return;
   }
+  // one division: p_i = ell_i * (1 / total) (within an ulp of ell_i / total; an FP64 division
+  // per entry costs far more than the multiply on this GPU's FP64 pipe)
+  const double rt = 1.0 / total;
   double sp = 0.0;
-  for (int64_t i = b; i < e; ++i) sp += __ldcg(ell + i) / total;
-  double run = block_scan_tw(sp, wt, &s_total);
+  for (int64_t i = b; i < e; ++i) sp += __ldcg(ell + i) * rt;
+  double run = block_scan_nw<NW>(sp, wt, &s_total);
   for (int64_t i = b; i < e; ++i) {
-    const double pi = __ldcg(ell + i) / total;
+    const double pi = __ldcg(ell + i) * rt;
     ep.p[i] = pi;
     run += pi;
     ep.cdf[i] = run;
   }
+}
+
+__device__ inline void cdf_epilogue(const CdfEpilogue& ep, const double* ell, int64_t I) {
+  cdf_epilogue_nw<TW>(ep, ell, I);
 }
 
 template <typename T, int QN, int NB, bool SMEM, bool PACK = false>
@@ -216,7 +230,7 @@ __device__ __forceinline__ void trsm_cta(unsigned char* trsm_smem, int64_t cta, 
                                                   double* __restrict__ core_out,
                                                   double* __restrict__ ell, CdfEpilogue ep,
                                                   int nctas) {
-  if (info && *info) return;
+  if ((info && *info) || (ep.run_if && *ep.run_if == 0)) return;
   const int np = n + 1;
   const int img_elems = ((n * np * static_cast<int>(sizeof(T)) + 15) / 16) * 16 /
                         static_cast<int>(sizeof(T));

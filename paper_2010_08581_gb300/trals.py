@@ -93,6 +93,7 @@ SIGNATURES = {
     "tr_last_error": (ctypes.c_char_p, [c_vp]),
     "tr_status_sync": (c_int, [c_vp, c_vp]),
     "tr_leverage": (c_int, [c_vp, c_vp, c_i64, c_int, c_int, c_vp, c_vp, c_vp]),
+    "tr_leverage_planes": (c_int, [c_vp, c_vp, c_vp, c_i64, c_int, c_vp, c_vp, c_vp, c_vp]),
     "tr_sample": (c_int, [c_vp, c_int, c_int, P64, PP, PP, c_i64, c_u64, c_u64, c_vp, c_vp,
                           c_vp]),
     "tr_sample_uniform": (c_int, [c_vp, c_int, c_int, P64, c_i64, c_u64, c_u64, c_vp, c_vp,
@@ -250,6 +251,16 @@ def tr_leverage(ctx: Context, core: torch.Tensor, p: torch.Tensor, cdf: torch.Te
     I, Rl, Rr = core.shape
     ctx.check(load().tr_leverage(ctx.handle, _ptr(core), I, Rl, Rr, _ptr(p), _ptr(cdf),
                                  _stream(stream)))
+
+
+def tr_leverage_planes(ctx: Context, A_hi: torch.Tensor, A_lo: torch.Tensor, p: torch.Tensor,
+                       cdf: torch.Tensor, branch: Optional[torch.Tensor] = None, stream=None):
+    """A_hi, A_lo: float32 (I, L) row-major on the device (A = A_hi + A_lo); p, cdf: float64
+    (I,); branch (optional): int32 (1,) receiving 0 (preconditioned form) or 1 (fallback)."""
+    I, L = A_hi.shape
+    ctx.check(load().tr_leverage_planes(ctx.handle, _ptr(A_hi), _ptr(A_lo), I, L, _ptr(p),
+                                        _ptr(cdf), _ptr(branch) if branch is not None else None,
+                                        _stream(stream)))
 
 
 def tr_sample(ctx: Context, k: int, dims, ps: List[torch.Tensor], cdfs: List[torch.Tensor],
