@@ -173,6 +173,8 @@ void drop_graph(tr_ctx* ctx) {
 // ------------------------------------------------------------------------------------
 // Row a1: leverage-score distribution of one core.
 // ------------------------------------------------------------------------------------
+constexpr int kGramTiles = 64;   // Gram tile counters of launch_gram_dd (n <= 128: 10 tiles)
+
 struct LevPass {  // one Cholesky-QR pass over an m x n row-major matrix (n = Gram size)
   double* partial; double* G; double* Lrow; double* Lcol; double* invdiag; int* keep; int* info;
   double* img;     // padded FP64 image of the factor for the row solves
@@ -206,6 +208,8 @@ LevPass carve_pass(Carver& c, int64_t rows, int cols, bool trans) {
     p.pre.lda_k = (n + 3) & ~3;
     p.pre.K_hi = reinterpret_cast<const float*>(p.Lrow);
     p.pre.K_lo = reinterpret_cast<const float*>(p.Lcol);
+    p.pre.gph = c.take<float>(gram_dd_partial_floats(rows, cols));
+    p.pre.gpl = c.take<float>(gram_dd_partial_floats(rows, cols));
   }
   return p;
 }
@@ -258,7 +262,7 @@ size_t leverage_plan(Carver& c, int64_t I, int L, LevPass* p1, LevPass* p2, doub
     *p2 = carve_pass(c, I, static_cast<int>(I), false);  // Gram of C (I x I)
   }
   *ell = c.take<double>(I);
-  c.take<unsigned>(1);   // completion counter of the fused CDF step
+  c.take<unsigned>(1 + kGramTiles);   // completion counters: the CDF step, then the Gram tiles
   return c.off;
 }
 
@@ -299,20 +303,18 @@ tr_status leverage_dist(tr_ctx* ctx, char* ws, const double* mat, int64_t I, int
                                                   ((I * sizeof(double) + 255) & ~size_t(255)));
   const double eps = 2.220446049250313e-16;
   const double tol = static_cast<double>(I > L ? I : L) * eps;
-  TR_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned), st));
+  TR_CUDA(cudaMemsetAsync(counter, 0, (1 + kGramTiles) * sizeof(unsigned), st));
   const CdfEpilogue ep{counter, p, cdf, skip, ctx->d_err};
   if (I >= L && mixed && mat_hi && p1.pre.state && precond_enabled()) {
     // FP32 preconditioner and a short series (lev_precond.cu); the double-float
     // factorisation, its image and the FP64 row solves run only when its device flag says so
     const int n = L;
-    TR_LAUNCH("gram_f64", launch_gram_ff(mat_hi, mat_lo, I, n, n, p1.partial, p1.splits, st));
     ReduceSplit sp;
     sp.hi = reinterpret_cast<float*>(p1.Lrow);
     sp.lo = reinterpret_cast<float*>(p1.Lcol);
     sp.lda = (n + 3) & ~3;
-    TR_LAUNCH("reduce_gram", launch_reduce(p1.partial, false, p1.splits,
-                                           static_cast<int64_t>(n) * n, n, n, n, n, p1.G, n,
-                                           nullptr, 0, st, sp));
+    TR_LAUNCH("gram_dd", launch_gram_dd(mat_hi, mat_lo, I, n, n, p1.pre.gph, p1.pre.gpl,
+                                        counter + 1, sp.hi, sp.lo, sp.lda, p1.G, st));
     TR_LAUNCH("lev_factor", launch_lev_precond(0, p1.pre, n, I, mat_hi, mat_lo, L, ell, ep, st));
     TR_LAUNCH("lev_inverse", launch_lev_precond(1, p1.pre, n, I, mat_hi, mat_lo, L, ell, ep, st));
     TR_LAUNCH("lev_u", launch_lev_precond(2, p1.pre, n, I, mat_hi, mat_lo, L, ell, ep, st));

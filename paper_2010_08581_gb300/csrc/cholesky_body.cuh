@@ -23,6 +23,8 @@
 // img[c*(n+1) + r] = L[r][c] in FP64 and/or FP32, and the FP32 image of the symmetric input.
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace trk {
@@ -346,13 +348,15 @@ __device__ __forceinline__ bool cholesky_panel(const double* __restrict__ G, int
   }
   __syncthreads();
   // Panel factorisation of columns [c0, c0 + w) by warp 0, in registers (lane l holds rows
-  // c0 + l + 32q of the panel's columns): per column one shuffle for the pivot, an rsqrt, a
-  // scaling and w - 1 shuffles for the later panel columns, with no barrier.
-  auto factor_panel = [&](int c0) {
+  // c0 + l + 32q, q < QPD, of the panel's columns): per column one shuffle for the pivot, an
+  // rsqrt, a scaling and w - 1 shuffles for the later panel columns, with no barrier. QPD is
+  // the number of 32-row slots the panel's rows need (instantiated per count).
+  auto factor_panel_q = [&](auto qc, int c0) {
+    constexpr int QPD = decltype(qc)::value;
     const int w = (n - c0 < kPB) ? n - c0 : kPB;
-    V p[QP][kPB];
+    V p[QPD][kPB];
 #pragma unroll
-    for (int q = 0; q < QP; ++q) {
+    for (int q = 0; q < QPD; ++q) {
       const int i = c0 + lane + 32 * q;
 #pragma unroll
       for (int jj = 0; jj < kPB; ++jj)
@@ -368,7 +372,7 @@ __device__ __forceinline__ bool cholesky_panel(const double* __restrict__ G, int
         ok = ok && (Ops::lead(d) > tol);
         const V inv = ok ? Ops::rsqrt(d) : Ops::zero();
 #pragma unroll
-        for (int q = 0; q < QP; ++q) {
+        for (int q = 0; q < QPD; ++q) {
           const int r = lane + 32 * q;                              // panel row
           p[q][kk] = (r == kk) ? Ops::mul(d, inv)
                                : (r > kk ? Ops::mul(p[q][kk], inv) : Ops::zero());
@@ -377,12 +381,12 @@ __device__ __forceinline__ bool cholesky_panel(const double* __restrict__ G, int
         for (int jj = kk + 1; jj < kPB; ++jj) {
           const V ljk = Ops::shfl(p[0][kk], jj);                    // row c0+jj: lane jj
 #pragma unroll
-          for (int q = 0; q < QP; ++q) p[q][jj] = Ops::fnms(p[q][kk], ljk, p[q][jj]);
+          for (int q = 0; q < QPD; ++q) p[q][jj] = Ops::fnms(p[q][kk], ljk, p[q][jj]);
         }
       }
     }
 #pragma unroll
-    for (int q = 0; q < QP; ++q) {
+    for (int q = 0; q < QPD; ++q) {
       const int i = c0 + lane + 32 * q;
       if (i < n) {
 #pragma unroll
@@ -394,6 +398,14 @@ __device__ __forceinline__ bool cholesky_panel(const double* __restrict__ G, int
       }
     }
     if (lane == 0 && !ok) s_stop = 1;
+  };
+  auto factor_panel = [&](int c0) {
+    const int slots = (n - c0 + 31) >> 5;
+    if (slots <= 1) factor_panel_q(std::integral_constant<int, 1>{}, c0);
+    else if (slots == 2) factor_panel_q(std::integral_constant<int, 2>{}, c0);
+    else if (slots == 3) factor_panel_q(std::integral_constant<int, 3>{}, c0);
+    else if (slots == 4) factor_panel_q(std::integral_constant<int, 4>{}, c0);
+    else factor_panel_q(std::integral_constant<int, QP>{}, c0);
   };
   // Rank-w update of the 4 x 4 tile (bi, bj) of the trailing triangle at t0 with the panel
   // [c0, c0 + w): every entry receives the panel's columns in order.
@@ -487,6 +499,155 @@ __device__ __forceinline__ bool cholesky_panel(const double* __restrict__ G, int
   return true;
 }
 
+// Blocked right-looking FP32 Cholesky without look-ahead, for any block size (blockDim.x a
+// multiple of 32, at least 64): per panel of kP32 columns, warp 0 factors the panel in
+// registers (as cholesky_panel, with QPD 32-row slots sized to the rows left), one barrier,
+// then every thread takes 4 x 4 tiles of the rank-kP32 update of the trailing triangle, one
+// barrier. At n = 100 this measured 31 us with 256 threads against 39 us for cholesky_panel
+// with one panel of look-ahead and 512 threads: the look-ahead kept warp 0 busy with tile
+// updates on the critical path, and a 512-thread barrier costs more. A: the work array (as
+// cholesky_panel, FP32, lda = panel_lda(n)), filled from pre (the reduction's FP32 work array).
+// Writes the padded factor image img (FP32), invdiag (FP64), keep (all 1) and *info = 0;
+// returns false (nothing written) when a pivot is <= tol_scale * max diag.
+constexpr int kP32 = 8;
+
+template <int QPD>
+__device__ __forceinline__ bool factor_panel_p32(float* A, int lda, int n, int c0, float tol,
+                                                 float* ldiag) {
+  const int lane = threadIdx.x & 31;
+  const int w = (n - c0 < kP32) ? n - c0 : kP32;
+  float p[QPD][kP32];
+#pragma unroll
+  for (int q = 0; q < QPD; ++q) {
+    const int i = c0 + lane + 32 * q;
+#pragma unroll
+    for (int jj = 0; jj < kP32; ++jj)
+      p[q][jj] = (i < n && jj < w && i >= c0 + jj) ? A[(c0 + jj) * lda + i] : 0.f;
+  }
+  bool ok = true;
+#pragma unroll
+  for (int kk = 0; kk < kP32; ++kk) {
+    if (kk < w) {
+      const float d = __shfl_sync(0xffffffffu, p[0][kk], kk);
+      ok = ok && (d > tol);
+      const float inv = ok ? rsqrtf(d) : 0.f;
+#pragma unroll
+      for (int q = 0; q < QPD; ++q) {
+        const int r = lane + 32 * q;
+        p[q][kk] = (r == kk) ? d * inv : (r > kk ? p[q][kk] * inv : 0.f);
+      }
+#pragma unroll
+      for (int jj = kk + 1; jj < kP32; ++jj) {
+        const float ljk = __shfl_sync(0xffffffffu, p[0][kk], jj);
+#pragma unroll
+        for (int q = 0; q < QPD; ++q) p[q][jj] = fmaf(-p[q][kk], ljk, p[q][jj]);
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < QPD; ++q) {
+    const int i = c0 + lane + 32 * q;
+#pragma unroll
+    for (int jj = 0; jj < kP32; ++jj)
+      if (i < n && jj < w && i >= c0 + jj) {
+        A[(c0 + jj) * lda + i] = p[q][jj];
+        if (i == c0 + jj) ldiag[i] = p[q][jj];
+      }
+  }
+  return ok;
+}
+
+__device__ __forceinline__ bool cholesky_panel_f32(int n, double tol_scale, float* A,
+                                                   const float* __restrict__ pre, float* img,
+                                                   double* invdiag, int* keep_out, int* info) {
+  __shared__ float ldiag[kPanelCholMax];
+  __shared__ float s_tol;
+  __shared__ int s_bad;
+  const int nt = blockDim.x;
+  const int lda = panel_lda(n);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int e = tid * 4; e < lda * n; e += nt * 4)
+    *reinterpret_cast<float4*>(A + e) = *reinterpret_cast<const float4*>(pre + e);
+  if (warp == 0) {
+    float md = 0.f;
+    for (int i = lane; i < n; i += 32) md = fmaxf(md, pre[i * lda + i]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) md = fmaxf(md, __shfl_xor_sync(0xffffffffu, md, o));
+    if (lane == 0) {
+      s_tol = static_cast<float>(tol_scale) * md;
+      s_bad = 0;
+    }
+  }
+  __syncthreads();
+  for (int c0 = 0; c0 < n; c0 += kP32) {
+    if (warp == 0) {
+      const int slots = (n - c0 + 31) >> 5;
+      bool ok;
+      if (slots <= 1) ok = factor_panel_p32<1>(A, lda, n, c0, s_tol, ldiag);
+      else if (slots == 2) ok = factor_panel_p32<2>(A, lda, n, c0, s_tol, ldiag);
+      else if (slots == 3) ok = factor_panel_p32<3>(A, lda, n, c0, s_tol, ldiag);
+      else if (slots == 4) ok = factor_panel_p32<4>(A, lda, n, c0, s_tol, ldiag);
+      else ok = factor_panel_p32<(kPanelCholMax + 31) / 32>(A, lda, n, c0, s_tol, ldiag);
+      if (!ok && lane == 0) s_bad = 1;
+    }
+    __syncthreads();
+    if (s_bad) return false;
+    // rank-w update of the trailing triangle (rows i >= j >= t0), 4 x 4 tiles; rows up to
+    // lda exist in every column (lda = panel_lda(n)), columns >= n are skipped
+    const int w = (n - c0 < kP32) ? n - c0 : kP32;
+    const int t0 = c0 + w, m = n - t0;
+    if (m > 0) {
+      const int nb = (m + 3) >> 2;
+      const int ntiles = nb * (nb + 1) / 2;
+      for (int t = tid; t < ntiles; t += nt) {
+        int bi = static_cast<int>((sqrtf(8.0f * static_cast<float>(t) + 1.0f) - 1.0f) * 0.5f);
+        while (bi * (bi + 1) / 2 > t) --bi;
+        while ((bi + 1) * (bi + 2) / 2 <= t) ++bi;
+        const int bj = t - bi * (bi + 1) / 2;
+        const int i0 = t0 + 4 * bi, j0 = t0 + 4 * bj;
+        float acc[4][4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          if (j0 + c < n) {
+            const float4 v = *reinterpret_cast<const float4*>(A + (j0 + c) * lda + i0);
+            acc[c][0] = v.x; acc[c][1] = v.y; acc[c][2] = v.z; acc[c][3] = v.w;
+          } else {
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc[c][r] = 0.f;
+          }
+        }
+#pragma unroll
+        for (int kk = 0; kk < kP32; ++kk) {
+          if (kk < w) {
+            const float4 li = *reinterpret_cast<const float4*>(A + (c0 + kk) * lda + i0);
+            const float4 lj = *reinterpret_cast<const float4*>(A + (c0 + kk) * lda + j0);
+            const float a4[4] = {li.x, li.y, li.z, li.w}, b4[4] = {lj.x, lj.y, lj.z, lj.w};
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+#pragma unroll
+              for (int r = 0; r < 4; ++r) acc[c][r] = fmaf(-a4[r], b4[c], acc[c][r]);
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          if (j0 + c < n)
+            *reinterpret_cast<float4*>(A + (j0 + c) * lda + i0) =
+                make_float4(acc[c][0], acc[c][1], acc[c][2], acc[c][3]);
+      }
+    }
+    __syncthreads();
+  }
+  const int np = n + 1;
+  for (int j = warp; j < n; j += nt / 32)
+    for (int i = lane; i < n; i += 32) img[j * np + i] = (i >= j) ? A[j * lda + i] : 0.f;
+  for (int k = tid; k < n; k += nt) {
+    keep_out[k] = 1;
+    invdiag[k] = 1.0 / static_cast<double>(ldiag[k]);
+  }
+  if (tid == 0) *info = 0;
+  return true;
+}
+
 // FP32 first, FP64 if needed: the factorisation of the mixed-precision LS step's normal
 // matrix (mode 0, image TI = float). The FP32 attempt accepts the factor only if every pivot
 // exceeds tol32 * max diag (so it never drops a column); otherwise the same matrix is factored
@@ -505,7 +666,11 @@ __device__ __forceinline__ void cholesky_cta_mixed(const double* __restrict__ G,
   constexpr bool f32img = sizeof(TI) == 4;
   double* img64 = f32img ? nullptr : reinterpret_cast<double*>(img);
   float* img32 = f32img ? reinterpret_cast<float*>(img) : nullptr;
-  if (n >= 4 && n <= kPanelCholMax && img) {
+  if (n >= 4 && n <= kPanelCholMax && img && pre && f32img) {   // (gimg32: written by the reduction)
+    if (cholesky_panel_f32(n, tol32, A32, pre, reinterpret_cast<float*>(img), invdiag,
+                           keep_out, info))
+      return;
+  } else if (n >= 4 && n <= kPanelCholMax && img) {
     if (cholesky_panel<F32Ops, TI>(G, n, tol32, A32, invdiag, keep_out, info, img, gimg32,
                                    nullptr, nullptr, pre))
       return;

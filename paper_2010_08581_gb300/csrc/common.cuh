@@ -261,8 +261,17 @@ struct LevPrecond {
   float* E;          // n x lda_k
   float* esq;        // lev_precond_ctas(n)
   int* state;
+  float* gph;        // launch_gram_dd scratch (gram_dd_partial_floats each)
+  float* gpl;
 };
 bool lev_precond_fits(int64_t I, int n);
+// K = A^T A of the tall I x n double-float planes (row stride lda_a) in one launch: K's
+// double-float planes kh/kl[r*lda + c] (c >= r) and K in FP64 (k64, n x n). Scratch: ph and pl
+// of gram_dd_partial_floats(I, n) floats each, and cnt[ntiles] zero on entry (left zero).
+size_t gram_dd_partial_floats(int64_t I, int n);
+cudaError_t launch_gram_dd(const float* Ah, const float* Al, int64_t I, int n, int64_t lda_a,
+                           float* ph, float* pl, unsigned* cnt, float* kh, float* kl, int lda,
+                           double* k64, cudaStream_t st);
 int lev_precond_ctas(int n);
 cudaError_t launch_lev_precond(int stage, const LevPrecond& lp, int n, int64_t I,
                                const float* Ah, const float* Al, int64_t lda, double* ell,

@@ -35,6 +35,7 @@ constexpr float kTauF = 1e-2f;         // largest ||E||_F of the fast form
 constexpr float kTauF4 = 1e-3f;        // up to this, terms through E^4 suffice
 constexpr int LT = 16;                 // tile edge of the products U = X K and C = U X^T
 constexpr int kMaxPre = 128;           // largest n of the preconditioned form
+constexpr int kCholPreNT = 256;        // threads of the FP32 factorisation
 
 __host__ __device__ inline int pad4(int v) { return (v + 3) & ~3; }
 
@@ -74,15 +75,113 @@ __device__ __forceinline__ void renorm(float s, float c, float& h, float& l) {
   l = c - (h - s);
 }
 
+// K = A^T A of a tall I x n matrix given as double-float planes, in one launch: CTA (tile,
+// split) forms the split's 32 x 32 tile sum in compensated FP32 (each product's leading part
+// and its exact error by a fused multiply-add, plus the cross terms, then a two-sum), writes
+// it as an FP32 pair, and the CTA that finishes a tile last adds the splits' pairs in split
+// order by two-sums. It writes K's double-float planes in the reduction's work-array layout
+// (kh/kl[r*lda + c], c >= r) and K in FP64 (k64[r*n + c]) for the factorisation fallback.
+constexpr int GD = 32, GDK = 32, GDNT = 256;
+
+__global__ void __launch_bounds__(GDNT) k_gram_dd(const float* __restrict__ Ah,
+                                                  const float* __restrict__ Al, int64_t K, int n,
+                                                  int64_t lda_a, int64_t chunk, int splits,
+                                                  float* __restrict__ ph, float* __restrict__ pl,
+                                                  unsigned* __restrict__ cnt,
+                                                  float* __restrict__ kh, float* __restrict__ kl,
+                                                  int lda, double* __restrict__ k64) {
+  __shared__ float Ph[GDK][GD + 1], Pl[GDK][GD + 1];
+  __shared__ float Qh[GDK][GD + 1], Ql[GDK][GD + 1];
+  __shared__ int s_last;
+  const int nt = (n + GD - 1) / GD;
+  int tp = 0, rem = blockIdx.x;
+  while (rem >= nt - tp) { rem -= nt - tp; ++tp; }
+  const int tq = tp + rem;
+  const int p0 = tp * GD, q0 = tq * GD;
+  const int64_t k0 = static_cast<int64_t>(blockIdx.y) * chunk;
+  const int64_t k1 = (k0 + chunk < K) ? k0 + chunk : K;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  float sum[4] = {0.f, 0.f, 0.f, 0.f}, cor[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int64_t kb = k0; kb < k1; kb += GDK) {
+#pragma unroll
+    for (int r = 0; r < (GDK * GD) / GDNT; ++r) {
+      const int e = threadIdx.x + r * GDNT;
+      const int kk = e / GD, col = e % GD;
+      const int64_t t = kb + kk;
+      const int p = p0 + col, q = q0 + col;
+      const bool okp = t < k1 && p < n, okq = t < k1 && q < n;
+      Ph[kk][col] = okp ? Ah[t * lda_a + p] : 0.f;
+      Pl[kk][col] = okp ? Al[t * lda_a + p] : 0.f;
+      Qh[kk][col] = okq ? Ah[t * lda_a + q] : 0.f;
+      Ql[kk][col] = okq ? Al[t * lda_a + q] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < GDK; ++kk) {
+      const float yh = Qh[kk][tx], yl = Ql[kk][tx];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float xh = Ph[kk][ty + 8 * u], xl = Pl[kk][ty + 8 * u];
+        const float pr = xh * yh;
+        float er = fmaf(xh, yh, -pr);
+        er = fmaf(xh, yl, er);
+        er = fmaf(xl, yh, er);
+        float t2, ts;
+        two_sum(sum[u], pr, t2, ts);
+        sum[u] = t2;
+        cor[u] += ts + er;
+      }
+    }
+    __syncthreads();
+  }
+  // this split's tile as FP32 pairs: [split][tile][32 x 32]
+  const int64_t tb = (static_cast<int64_t>(blockIdx.y) * gridDim.x + blockIdx.x) * GD * GD;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int e = (ty + 8 * u) * GD + tx;
+    ph[tb + e] = sum[u];
+    pl[tb + e] = cor[u];
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0)
+    s_last = (atomicAdd(cnt + blockIdx.x, 1u) == static_cast<unsigned>(splits) - 1) ? 1 : 0;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int e = (ty + 8 * u) * GD + tx;
+    float hs = 0.f, hc = 0.f;
+    for (int sp = 0; sp < splits; ++sp) {
+      const int64_t o = (static_cast<int64_t>(sp) * gridDim.x + blockIdx.x) * GD * GD + e;
+      float t2, ts;
+      two_sum(hs, __ldcg(ph + o), t2, ts);
+      hs = t2;
+      hc += __ldcg(pl + o) + ts;
+    }
+    float h, l;
+    renorm(hs, hc, h, l);
+    const int p = p0 + ty + 8 * u, q = q0 + tx;
+    if (p < n && q < n) {
+      k64[static_cast<int64_t>(p) * n + q] = static_cast<double>(h) + static_cast<double>(l);
+      if (q >= p) {
+        kh[p * lda + q] = h;
+        kl[p * lda + q] = l;
+      }
+    }
+  }
+  if (threadIdx.x == 0) cnt[blockIdx.x] = 0u;
+}
+
 // The FP32 factor of the preconditioner (one CTA): K's FP32 values from the reduction's work
 // array; on success the factor's padded image, 1/diag and *state = 0, otherwise *state = 1.
-__global__ void __launch_bounds__(CNT) k_chol_pre(int n, double tol32, const float* __restrict__ pre,
+__global__ void __launch_bounds__(kCholPreNT) k_chol_pre(int n, double tol32, const float* __restrict__ pre,
                                                   float* __restrict__ Limg,
                                                   double* __restrict__ invdiag,
                                                   int* __restrict__ keep, int* state) {
   extern __shared__ __align__(16) float csm[];
-  const bool ok = cholesky_panel<F32Ops, float>(nullptr, n, tol32, csm, invdiag, keep, state,
-                                                Limg, nullptr, nullptr, nullptr, pre, nullptr);
+  const bool ok = cholesky_panel_f32(n, tol32, csm, pre, Limg, invdiag, keep, state);
   if (!ok && threadIdx.x == 0) *state = 1;
 }
 
@@ -419,6 +518,30 @@ cudaError_t launch_copy_int(const int* src, int v, int* dst, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+int gram_dd_splits(int64_t I, int64_t* chunk) {
+  int64_t c = (I + 7) / 8;                      // about 8 splits of at least 32 rows
+  c = (c + GDK - 1) / GDK * GDK;
+  *chunk = c;
+  return static_cast<int>((I + c - 1) / c);
+}
+
+size_t gram_dd_partial_floats(int64_t I, int n) {
+  int64_t chunk;
+  const int nt = (n + GD - 1) / GD;
+  return static_cast<size_t>(gram_dd_splits(I, &chunk)) * (nt * (nt + 1) / 2) * GD * GD;
+}
+
+cudaError_t launch_gram_dd(const float* Ah, const float* Al, int64_t I, int n, int64_t lda_a,
+                           float* ph, float* pl, unsigned* cnt, float* kh, float* kl, int lda,
+                           double* k64, cudaStream_t st) {
+  int64_t chunk;
+  const int splits = gram_dd_splits(I, &chunk);
+  const int nt = (n + GD - 1) / GD;
+  k_gram_dd<<<dim3(nt * (nt + 1) / 2, splits), GDNT, 0, st>>>(Ah, Al, I, n, lda_a, chunk, splits,
+                                                              ph, pl, cnt, kh, kl, lda, k64);
+  return cudaGetLastError();
+}
+
 bool lev_precond_fits(int64_t I, int n) { return n >= 4 && n <= kMaxPre && I >= n; }
 
 int lev_precond_ctas(int n) {
@@ -435,7 +558,7 @@ cudaError_t launch_lev_precond(int stage, const LevPrecond& lp, int n, int64_t I
   switch (stage) {
     case 0: {
       const double eps32 = 1.1920928955078125e-07;
-      k_chol_pre<<<1, CNT, chol_pre_smem(n), st>>>(n, static_cast<double>(n) * eps32, lp.K_hi,
+      k_chol_pre<<<1, kCholPreNT, chol_pre_smem(n), st>>>(n, static_cast<double>(n) * eps32, lp.K_hi,
                                                    lp.Limg, lp.invdiag, lp.keep, lp.state);
       return cudaGetLastError();
     }
