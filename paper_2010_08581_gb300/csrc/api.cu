@@ -582,7 +582,36 @@ struct AlsPlan {
   int32_t* idx; double* w; void* A; void* Y; char* ws;
   int32_t* idx2 = nullptr; double* w2 = nullptr; int64_t* jm = nullptr;   // merged draws
   size_t solve_ws;   // bytes of the stage region used by the LS step; leverage follows it
+  // per mode: a copy of X with that mode last (contiguous fibres), or null; and the element
+  // strides of every mode in that copy
+  void* Xm[kMaxModes] = {};
+  int64_t mstride[kMaxModes][kMaxModes] = {};
+  unsigned copy_mask = 0;
 };
+
+// A copy of X with mode n last is made for a strided mode when the decomposition's scattered
+// fibre reads would move more DRAM bytes than the copy: each scattered element costs about
+// 64 bytes (measured: ncu showed about 100 bytes of DRAM reads per 4-byte element of the
+// strided modes of the 500^3 tensor), the copy 2 |X| (read and write). TRALS_PERMUTE=0 turns
+// the copies off.
+bool permute_enabled() {
+  const char* e = getenv("TRALS_PERMUTE");
+  return !(e && e[0] == '0');
+}
+
+unsigned choose_copies(const AlsPlan& P, size_t xbytes) {
+  if (!permute_enabled()) return 0;
+  int64_t stride[kMaxModes];
+  row_major_strides(P.N, P.dims, stride);
+  unsigned mask = 0;
+  for (int n = 0; n < P.N; ++n) {
+    if (stride[n] < 8) continue;
+    const double scattered = static_cast<double>(P.sweeps) * static_cast<double>(P.J) *
+                             static_cast<double>(P.dims[n]) * 64.0;
+    if (scattered >= 2.0 * static_cast<double>(xbytes)) mask |= 1u << n;
+  }
+  return mask;
+}
 
 tr_status als_plan(tr_ctx* ctx, AlsPlan& P) {
   const int N = P.N;
@@ -625,10 +654,45 @@ tr_status als_plan(tr_ctx* ctx, AlsPlan& P) {
     stage = solve_max + a > stage ? solve_max + a : stage;
   }
   P.solve_ws = solve_max;
-  TR_TRY(ensure_ws(ctx, persist + stage));
+  // contiguous copies of X for strided modes, when they pay and memory allows
+  int64_t numel = 1;
+  for (int k = 0; k < N; ++k) numel *= P.dims[k];
+  const size_t xbytes = (static_cast<size_t>(numel) * (P.xdt == TR_F64 ? 8 : 4) + 255) & ~size_t(255);
+  P.copy_mask = choose_copies(P, xbytes);
+  size_t ncopy = 0;
+  for (int n = 0; n < N; ++n) ncopy += (P.copy_mask >> n) & 1u;
+  if (ncopy) {
+    const size_t need = persist + stage + ncopy * xbytes;
+    size_t free_b = 0, total_b = 0;
+    bool fits = need <= ctx->arena_bytes;
+    if (!fits && cudaMemGetInfo(&free_b, &total_b) == cudaSuccess)
+      fits = need + need / 4 <= free_b + ctx->arena_bytes;
+    cudaGetLastError();
+    if (ctx->budget && need + ctx->host_stage_bytes > ctx->budget) fits = false;
+    if (!fits) {
+      P.copy_mask = 0;
+      ncopy = 0;
+    }
+  }
+  TR_TRY(ensure_ws(ctx, persist + ncopy * xbytes + stage));
   Carver c(ctx->arena);
   carve(c, &pb, &cb);
-  P.ws = ctx->arena + persist;
+  char* copies = ctx->arena + persist;
+  for (int n = 0; n < N; ++n) {
+    P.Xm[n] = nullptr;
+    if (!((P.copy_mask >> n) & 1u)) continue;
+    P.Xm[n] = copies;
+    copies += xbytes;
+    // strides in the copy: the other modes in their order, then mode n
+    int64_t run = P.dims[n];
+    P.mstride[n][n] = 1;
+    for (int k = N - 1; k >= 0; --k) {
+      if (k == n) continue;
+      P.mstride[n][k] = run;
+      run *= P.dims[k];
+    }
+  }
+  P.ws = ctx->arena + persist + ncopy * xbytes;
   P.p.resize(N);
   P.cdf.resize(N);
   int64_t off = 0;
@@ -651,6 +715,15 @@ tr_status als_issue(tr_ctx* ctx, const AlsPlan& P, uint64_t seed, const uint64_t
       TR_LAUNCH("init_normal", launch_init_normal(P.cores[k], static_cast<int64_t>(count), seed,
                                                   static_cast<uint32_t>(k), seed_dev, st));
     }
+  }
+  // contiguous copies of X for the strided modes (made every call: X may change)
+  for (int n = 0; n < N; ++n) {
+    if (!P.Xm[n]) continue;
+    int64_t pre = 1, post = 1;
+    for (int k = 0; k < n; ++k) pre *= dims[k];
+    for (int k = n + 1; k < N; ++k) post *= dims[k];
+    TR_LAUNCH("mode_last", launch_mode_last(P.X, P.xdt == TR_F64, pre, dims[n], post, P.Xm[n],
+                                            st));
   }
   const bool uni = ctx->sampling == TR_SAMPLING_UNIFORM;
   if (!uni)
@@ -680,6 +753,12 @@ tr_status als_issue(tr_ctx* ctx, const AlsPlan& P, uint64_t seed, const uint64_t
       }
       ga.In = dims[n];
       ga.stride_n = stride[n];
+      const void* Xn = P.X;
+      if (P.Xm[n]) {   // the copy with mode n last: contiguous fibres
+        for (int m = 0; m < N - 1; ++m) ga.stride[m] = P.mstride[n][(n + 1 + m) % N];
+        ga.stride_n = 1;
+        Xn = P.Xm[n];
+      }
       const uint64_t uid = static_cast<uint64_t>(s) * N + n;
       const int64_t Jn = P.Jupd ? P.Jupd[static_cast<int64_t>(s) * N + n]
                                 : (P.Js ? P.Js[s] : P.J);
@@ -695,10 +774,10 @@ tr_status als_issue(tr_ctx* ctx, const AlsPlan& P, uint64_t seed, const uint64_t
         sg.given_w = P.w2;
         sg.jdev = P.jm;
         TR_LAUNCH("sample_chain", launch_sample_chain(sg, ca, Jn, seed, uid, P.idx, P.w, P.A,
-                                                      f64, st, &ga, P.X, x64, P.Y));
+                                                      f64, st, &ga, Xn, x64, P.Y));
       } else {
         TR_LAUNCH("sample_chain", launch_sample_chain(sa, ca, Jn, seed, uid, P.idx, P.w, P.A,
-                                                      f64, st, &ga, P.X, x64, P.Y));
+                                                      f64, st, &ga, Xn, x64, P.Y));
       }
       const int Rl = rl_of(ranks, N, n), Rr = ranks[n];
       TR_TRY(update_run(ctx, P.ws, P.solve_ws, P.A, P.Y, f64, Jn, Rl, Rr, dims[n], P.cores[n],
@@ -739,6 +818,7 @@ std::vector<uint64_t> als_key(const tr_ctx* ctx, const AlsPlan& P) {
   u(static_cast<uint64_t>(ctx->wait_limit));
   u(static_cast<uint64_t>(ctx->factorization));
   u(precond_enabled() ? 1 : 0);
+  u(P.copy_mask);
   return k;
 }
 

@@ -89,6 +89,11 @@ cudaError_t launch_sample_chain(const SampleArgs& sa, const ChainArgs& ca, int64
                                 void* A, bool f64, cudaStream_t st,
                                 const GatherArgs* ga = nullptr, const void* X = nullptr,
                                 bool x_f64 = false, void* Y = nullptr);
+// out = X viewed as [pre][In][post] (row-major) with the middle mode moved last:
+// out[a][q][i] = X[a][i][q] (gather.cu). The drivers use it to give a strided mode contiguous
+// fibres.
+cudaError_t launch_mode_last(const void* X, bool x_f64, int64_t pre, int64_t In, int64_t post,
+                             void* out, cudaStream_t st);
 cudaError_t launch_gather(const GatherArgs& a, const void* X, bool x_f64, const int32_t* idx,
                           const double* w, int64_t J, void* Y, bool y_f64, unsigned* err,
                           cudaStream_t st);

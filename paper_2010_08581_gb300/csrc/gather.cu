@@ -74,7 +74,102 @@ cudaError_t run(const GatherArgs& a, const void* X, const int32_t* idx, const do
   return cudaGetLastError();
 }
 
+// X viewed as [P_pre][I_n][P_post] (row-major) copied to [P_pre][P_post][I_n]: mode n moved
+// last, so that its fibres are contiguous. 32 x 32 tiles through shared memory (padded against
+// bank conflicts): reads coalesced along P_post, writes along I_n.
+constexpr int TT = 32, TR = 8;
+
+template <typename TX>
+__global__ void __launch_bounds__(TT * TR) k_mode_last(const TX* __restrict__ X, int64_t In,
+                                                       int64_t Post, int64_t tiles_n,
+                                                       int64_t tiles_p, TX* __restrict__ out) {
+  __shared__ TX tile[TT][TT + 1];
+  const int64_t b = blockIdx.x;
+  const int64_t per = tiles_n * tiles_p;
+  const int64_t pre = b / per;
+  const int64_t r = b - pre * per;
+  const int64_t tn = r / tiles_p, tp = r - tn * tiles_p;
+  const int64_t i0 = tn * TT, q0 = tp * TT;
+  const TX* src = X + pre * In * Post;
+  TX* dst = out + pre * In * Post;
+  const int tx = threadIdx.x & (TT - 1), ty = threadIdx.x / TT;
+#pragma unroll
+  for (int k = 0; k < TT; k += TR) {
+    const int64_t i = i0 + ty + k, q = q0 + tx;
+    if (i < In && q < Post) tile[ty + k][tx] = src[i * Post + q];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < TT; k += TR) {
+    const int64_t q = q0 + ty + k, i = i0 + tx;
+    if (i < In && q < Post) dst[q * In + i] = tile[tx][ty + k];
+  }
+}
+
+// FP32 with 16-byte accesses: 64 x 64 tiles, 256 threads; float4 loads along P_post and
+// float4 stores along I_n when both extents are multiples of 4 (else the kernel above).
+constexpr int T4 = 64;
+
+__global__ void __launch_bounds__(256) k_mode_last4(const float* __restrict__ X, int64_t In,
+                                                    int64_t Post, int64_t tiles_n,
+                                                    int64_t tiles_p, float* __restrict__ out) {
+  __shared__ float tile[T4][T4 + 1];
+  const int64_t b = blockIdx.x;
+  const int64_t per = tiles_n * tiles_p;
+  const int64_t pre = b / per;
+  const int64_t r = b - pre * per;
+  const int64_t tn = r / tiles_p, tp = r - tn * tiles_p;
+  const int64_t i0 = tn * T4, q0 = tp * T4;
+  const float* src = X + pre * In * Post;
+  float* dst = out + pre * In * Post;
+  const int t = threadIdx.x, c4 = 4 * (t & 15), r0 = t >> 4;
+#pragma unroll
+  for (int k = 0; k < T4; k += 16) {
+    const int64_t i = i0 + r0 + k, q = q0 + c4;
+    if (i < In && q < Post) {   // Post % 4 == 0: the whole vector is in range
+      const float4 v = __ldg(reinterpret_cast<const float4*>(src + i * Post + q));
+      tile[r0 + k][c4] = v.x; tile[r0 + k][c4 + 1] = v.y;
+      tile[r0 + k][c4 + 2] = v.z; tile[r0 + k][c4 + 3] = v.w;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < T4; k += 16) {
+    const int64_t q = q0 + r0 + k, i = i0 + c4;
+    if (i < In && q < Post) {   // In % 4 == 0
+      const int qq = r0 + k;
+      *reinterpret_cast<float4*>(dst + q * In + i) =
+          make_float4(tile[c4][qq], tile[c4 + 1][qq], tile[c4 + 2][qq], tile[c4 + 3][qq]);
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_mode_last(const void* X, bool x_f64, int64_t pre, int64_t In, int64_t post,
+                             void* out, cudaStream_t st) {
+  if (pre <= 0 || In <= 0 || post <= 0) return cudaSuccess;
+  if (!x_f64 && In % 4 == 0 && post % 4 == 0 &&
+      reinterpret_cast<uintptr_t>(X) % 16 == 0 && reinterpret_cast<uintptr_t>(out) % 16 == 0) {
+    const int64_t tn4 = (In + T4 - 1) / T4, tp4 = (post + T4 - 1) / T4;
+    const int64_t b4 = pre * tn4 * tp4;
+    if (b4 > 0x7fffffffLL) return cudaErrorInvalidValue;
+    k_mode_last4<<<static_cast<unsigned>(b4), 256, 0, st>>>(static_cast<const float*>(X), In,
+                                                            post, tn4, tp4,
+                                                            static_cast<float*>(out));
+    return cudaGetLastError();
+  }
+  const int64_t tn = (In + TT - 1) / TT, tp = (post + TT - 1) / TT;
+  const int64_t blocks = pre * tn * tp;
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+  if (x_f64)
+    k_mode_last<double><<<static_cast<unsigned>(blocks), TT * TR, 0, st>>>(
+        static_cast<const double*>(X), In, post, tn, tp, static_cast<double*>(out));
+  else
+    k_mode_last<float><<<static_cast<unsigned>(blocks), TT * TR, 0, st>>>(
+        static_cast<const float*>(X), In, post, tn, tp, static_cast<float*>(out));
+  return cudaGetLastError();
+}
 
 cudaError_t launch_gather(const GatherArgs& a, const void* X, bool x_f64, const int32_t* idx,
                           const double* w, int64_t J, void* Y, bool y_f64, unsigned* err,

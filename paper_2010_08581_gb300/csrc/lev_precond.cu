@@ -82,6 +82,7 @@ __device__ __forceinline__ void renorm(float s, float c, float& h, float& l) {
 // order by two-sums. It writes K's double-float planes in the reduction's work-array layout
 // (kh/kl[r*lda + c], c >= r) and K in FP64 (k64[r*n + c]) for the factorisation fallback.
 constexpr int GD = 32, GDK = 32, GDNT = 256;
+constexpr int kGramDdMaxSplits = 8;   // gram_dd_splits gives at most 8
 
 __global__ void __launch_bounds__(GDNT) k_gram_dd(const float* __restrict__ Ah,
                                                   const float* __restrict__ Al, int64_t K, int n,
@@ -153,12 +154,22 @@ __global__ void __launch_bounds__(GDNT) k_gram_dd(const float* __restrict__ Ah,
   for (int u = 0; u < 4; ++u) {
     const int e = (ty + 8 * u) * GD + tx;
     float hs = 0.f, hc = 0.f;
-    for (int sp = 0; sp < splits; ++sp) {
-      const int64_t o = (static_cast<int64_t>(sp) * gridDim.x + blockIdx.x) * GD * GD + e;
-      float t2, ts;
-      two_sum(hs, __ldcg(ph + o), t2, ts);
-      hs = t2;
-      hc += __ldcg(pl + o) + ts;
+    for (int sp0 = 0; sp0 < splits; sp0 += kGramDdMaxSplits) {
+      float vh[kGramDdMaxSplits], vl[kGramDdMaxSplits];   // all loads first, then the sums
+#pragma unroll
+      for (int k = 0; k < kGramDdMaxSplits; ++k) {
+        const int sp = sp0 + k;
+        const int64_t o = (static_cast<int64_t>(sp) * gridDim.x + blockIdx.x) * GD * GD + e;
+        vh[k] = sp < splits ? __ldcg(ph + o) : 0.f;
+        vl[k] = sp < splits ? __ldcg(pl + o) : 0.f;
+      }
+#pragma unroll
+      for (int k = 0; k < kGramDdMaxSplits; ++k) {
+        float t2, ts;
+        two_sum(hs, vh[k], t2, ts);
+        hs = t2;
+        hc += vl[k] + ts;
+      }
     }
     float h, l;
     renorm(hs, hc, h, l);
