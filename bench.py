@@ -53,9 +53,11 @@ def workload_config(wl):
                     "step (one whole decomposition), mixed precision: FP32 design rows and "
                     "fibres; TF32x3 tensor-core normal equations with FP32 accumulation; "
                     "normal matrix factored in FP32 (FP64 if a pivot is small) with FP32 "
-                    "triangular solves and one refinement step; leverage Gram formed in FP64 "
-                    "and factored in double-float (FP64 if a pivot is small), FP64 leverage "
-                    "rows",
+                    "triangular solves and one refinement step; leverage scores from the "
+                    "double-float Gram through an FP32 Cholesky preconditioner and a "
+                    "double-float series (the double-float factorisation with FP64 fallback "
+                    "when the preconditioner is poor); strided modes read from contiguous "
+                    "copies of X made in every step",
         "dims": list(wl["dims"]), "ranks": list(wl["ranks"]), "J": wl["J"],
         "sweeps_per_step": wl["sweeps"],
         "l2": "inputs larger than L2: X is 500 MB (> 129 MB L2); samples are redrawn every "
@@ -184,6 +186,12 @@ def algorithmic_cost(kernel, wl):
       leverage_rows   : I*L^2 FP64 flops
       sample          : J*(N-1) * (4 + 8*log2 I) bytes (index writes + CDF probes) + J*8
       sample_chain    : sample + subchain + gather (draws, rows and fibres in one kernel)
+      lev_factor      : L^3/3 FP32 flops (one CTA: the preconditioner's Cholesky factor)
+      lev_inverse     : L^3/3 FP32 flops (its inverse X, one warp per column)
+      gram_dd         : I*L^2 double-float flops (Gram of B^T, upper tiles)
+      lev_u, lev_e    : L^3 and L^3/3 double-float flops (U = X K, E = U X^T - I)
+      lev_rows        : I*L^2 double-float flops (w = X b per row; the FP32 series is smaller)
+      mode_last       : 2 * |X| * 4 bytes (X read and its copy written, once per strided mode)
     """
     dims, ranks, J = wl["dims"], wl["ranks"], wl["J"]
     N = len(dims)
@@ -207,6 +215,13 @@ def algorithmic_cost(kernel, wl):
         "reduce_gram": ("hbm", L * L * 8.0),
         "cdf": ("hbm", I * 8.0 * 3),
         "init_normal": ("hbm", I * L * 8.0),
+        "lev_factor": ("flops_f32", L ** 3 / 3.0),
+        "lev_inverse": ("flops_f32", L ** 3 / 3.0),
+        "gram_dd": ("flops_ff", I * L * L),
+        "lev_u": ("flops_ff", float(L) ** 3),
+        "lev_e": ("flops_ff", L ** 3 / 3.0),
+        "lev_rows": ("flops_ff", I * L * L),
+        "mode_last": ("hbm", 2.0 * math.prod(dims) * s),
     }
     return table.get(kernel)
 
@@ -230,74 +245,95 @@ def traffic_for(kernel):
 
 
 def roofline(prof, wl, peaks):
-    ranked = sorted(prof.items(), key=lambda kv: -kv[1][0])
-    for name, (ms, n) in ranked:
-        cost = algorithmic_cost(name, wl)
-        if cost is None:
+    """The roofline object of the kernel with the largest share of the timed kernel time
+    (among those with a stated algorithmic cost)."""
+    top = rooflines(prof, wl, peaks, 1)
+    return top[0] if top else None
+
+
+def rooflines(prof, wl, peaks, k):
+    """Roofline objects of the k kernels with the largest shares of the timed kernel time."""
+    tot_ms = sum(v[0] for v in prof.values())
+    out = []
+    for name, (ms, n) in sorted(prof.items(), key=lambda kv: -kv[1][0]):
+        e = roofline_entry(name, ms, n, wl, peaks)
+        if e is None:
             continue
-        kind, amount = cost
-        avg_s = ms / 1e3 / n
-        if kind == "hbm":
-            peak, src = _peak_hbm(peaks)
-            ach = amount / avg_s / 1e9
-            return {"kernel": name, "bound": "hbm", "achieved": round(ach, 3), "peak": peak,
-                    "unit": "GB/s", "frac": round(ach / peak, 5),
-                    "traffic": traffic_for(name), "peak_source": f"{src} HBM copy",
-                    "avg_launch_us": round(avg_s * 1e6, 3), "launches": n,
-                    "share_of_timed": None}
-        if kind == "flops_f64":
-            # FP64 ALU: nominal GB300 FP64 rate (no measured FP64 peak is provided); an FMA
-            # microbenchmark on this GPU measured 1.20 TFLOP/s, about 2 DFMA/clk/SM.
-            peak = NOMINAL_FP64_TFLOPS
-            ach = amount / avg_s / 1e12
-            return {"kernel": name, "bound": "alu", "achieved": round(ach, 6), "peak": peak,
-                    "unit": "TFLOP/s", "frac": round(ach / peak, 5),
-                    "frac_of_one_sm": round(ach / (peak / 152), 4),
-                    "traffic": traffic_for(name),
-                    "peak_source": "nominal FP64 1.25 TFLOP/s for 152 SMs (one-CTA kernels are "
-                                   "bounded by one SM: see frac_of_one_sm)",
-                    "avg_launch_us": round(avg_s * 1e6, 3), "launches": n,
-                    "share_of_timed": None}
-        if kind == "flops_f32":
-            # SIMT FP32: 152 SMs * 128 FMA/clk * 2 * 2.07 GHz
-            peak = 152 * 128 * 2 * 2.07e9 / 1e12
-            ach = amount / avg_s / 1e12
-            return {"kernel": name, "bound": "alu", "achieved": round(ach, 4), "peak": round(peak, 2),
-                    "unit": "TFLOP/s", "frac": round(ach / peak, 5),
-                    "frac_of_one_sm": round(ach / (peak / 152), 4),
-                    "traffic": traffic_for(name),
-                    "peak_source": "FP32 SIMT: 152 SMs x 128 FMA/clk x 2 x 2.07 GHz",
-                    "avg_launch_us": round(avg_s * 1e6, 3), "launches": n,
-                    "share_of_timed": None}
-        if kind == "flops_ff":
-            # double-float on the FP32 pipe: one multiply-add a - x*y is 15 FP32 instructions
-            # (Dekker's product via FMA, then a two-sum); 128 lanes/clk/SM at 2.07 GHz
-            per_sm = 128 * 2.07e9 * 2 / 15 / 1e12
-            peak = 152 * per_sm
-            ach = amount / avg_s / 1e12
-            return {"kernel": name, "bound": "alu", "achieved": round(ach, 6),
-                    "peak": round(peak, 3), "unit": "TFLOP/s", "frac": round(ach / peak, 5),
-                    "frac_of_one_sm": round(ach / per_sm, 4),
-                    "frac_of_one_sm_fp64": round(ach / (NOMINAL_FP64_TFLOPS / 152), 4),
-                    "traffic": traffic_for(name),
-                    "peak_source": "double-float on FP32 SIMT: 152 SMs x 128 lanes x 2.07 GHz x "
-                                   "2 flops / 15 instructions per multiply-add (one-CTA kernel: "
-                                   "see frac_of_one_sm; frac_of_one_sm_fp64 compares with one "
-                                   "SM's nominal FP64 rate)",
-                    "avg_launch_us": round(avg_s * 1e6, 3), "launches": n,
-                    "share_of_timed": None}
-        if kind == "flops_tf32":
-            bf16, src = (peaks or {}).get("bf16_tflops"), "measured"
-            if not isinstance(bf16, (int, float)):
-                bf16, src = FALLBACK_BF16_TFLOPS, "fallback"
-            peak = bf16 * 0.5          # dense TF32 = half the dense BF16 rate (nominal ratio)
-            ach = amount / avg_s / 1e12
-            return {"kernel": name, "bound": "tensor", "achieved": round(ach, 3),
-                    "peak": round(peak, 1), "unit": "TFLOP/s", "frac": round(ach / peak, 5),
-                    "traffic": traffic_for(name),
-                    "peak_source": f"{src} BF16 x 0.5 (TF32/BF16 nominal ratio)",
-                    "avg_launch_us": round(avg_s * 1e6, 3), "launches": n,
-                    "share_of_timed": None}
+        e["share_of_timed"] = round(ms / max(tot_ms, 1e-9), 4)
+        out.append(e)
+        if len(out) == k:
+            break
+    return out
+
+
+def roofline_entry(name, ms, n, wl, peaks):
+    """Roofline object of one kernel: algorithmic work per launch over its average launch time."""
+    cost = algorithmic_cost(name, wl)
+    if cost is None:
+        return None
+    kind, amount = cost
+    avg_s = ms / 1e3 / n
+    if kind == "hbm":
+        peak, src = _peak_hbm(peaks)
+        ach = amount / avg_s / 1e9
+        return {"kernel": name, "bound": "hbm", "achieved": round(ach, 3), "peak": peak,
+                "unit": "GB/s", "frac": round(ach / peak, 5),
+                "traffic": traffic_for(name), "peak_source": f"{src} HBM copy",
+                "avg_launch_us": round(avg_s * 1e6, 3), "launches": n,
+                "share_of_timed": None}
+    if kind == "flops_f64":
+        # FP64 ALU: nominal GB300 FP64 rate (no measured FP64 peak is provided); an FMA
+        # microbenchmark on this GPU measured 1.20 TFLOP/s, about 2 DFMA/clk/SM.
+        peak = NOMINAL_FP64_TFLOPS
+        ach = amount / avg_s / 1e12
+        return {"kernel": name, "bound": "alu", "achieved": round(ach, 6), "peak": peak,
+                "unit": "TFLOP/s", "frac": round(ach / peak, 5),
+                "frac_of_one_sm": round(ach / (peak / 152), 4),
+                "traffic": traffic_for(name),
+                "peak_source": "nominal FP64 1.25 TFLOP/s for 152 SMs (one-CTA kernels are "
+                               "bounded by one SM: see frac_of_one_sm)",
+                "avg_launch_us": round(avg_s * 1e6, 3), "launches": n,
+                "share_of_timed": None}
+    if kind == "flops_f32":
+        # SIMT FP32: 152 SMs * 128 FMA/clk * 2 * 2.07 GHz
+        peak = 152 * 128 * 2 * 2.07e9 / 1e12
+        ach = amount / avg_s / 1e12
+        return {"kernel": name, "bound": "alu", "achieved": round(ach, 4), "peak": round(peak, 2),
+                "unit": "TFLOP/s", "frac": round(ach / peak, 5),
+                "frac_of_one_sm": round(ach / (peak / 152), 4),
+                "traffic": traffic_for(name),
+                "peak_source": "FP32 SIMT: 152 SMs x 128 FMA/clk x 2 x 2.07 GHz",
+                "avg_launch_us": round(avg_s * 1e6, 3), "launches": n,
+                "share_of_timed": None}
+    if kind == "flops_ff":
+        # double-float on the FP32 pipe: one multiply-add a - x*y is 15 FP32 instructions
+        # (Dekker's product via FMA, then a two-sum); 128 lanes/clk/SM at 2.07 GHz
+        per_sm = 128 * 2.07e9 * 2 / 15 / 1e12
+        peak = 152 * per_sm
+        ach = amount / avg_s / 1e12
+        return {"kernel": name, "bound": "alu", "achieved": round(ach, 6),
+                "peak": round(peak, 3), "unit": "TFLOP/s", "frac": round(ach / peak, 5),
+                "frac_of_one_sm": round(ach / per_sm, 4),
+                "frac_of_one_sm_fp64": round(ach / (NOMINAL_FP64_TFLOPS / 152), 4),
+                "traffic": traffic_for(name),
+                "peak_source": "double-float on FP32 SIMT: 152 SMs x 128 lanes x 2.07 GHz x "
+                               "2 flops / 15 instructions per multiply-add (one-CTA kernel: "
+                               "see frac_of_one_sm; frac_of_one_sm_fp64 compares with one "
+                               "SM's nominal FP64 rate)",
+                "avg_launch_us": round(avg_s * 1e6, 3), "launches": n,
+                "share_of_timed": None}
+    if kind == "flops_tf32":
+        bf16, src = (peaks or {}).get("bf16_tflops"), "measured"
+        if not isinstance(bf16, (int, float)):
+            bf16, src = FALLBACK_BF16_TFLOPS, "fallback"
+        peak = bf16 * 0.5          # dense TF32 = half the dense BF16 rate (nominal ratio)
+        ach = amount / avg_s / 1e12
+        return {"kernel": name, "bound": "tensor", "achieved": round(ach, 3),
+                "peak": round(peak, 1), "unit": "TFLOP/s", "frac": round(ach / peak, 5),
+                "traffic": traffic_for(name),
+                "peak_source": f"{src} BF16 x 0.5 (TF32/BF16 nominal ratio)",
+                "avg_launch_us": round(avg_s * 1e6, 3), "launches": n,
+                "share_of_timed": None}
     return None
 
 
@@ -1018,9 +1054,7 @@ def run_ours(args):
         serving = run_serving(T, dev, args.serve_seconds)
 
     roof = roofline(prof, wl, peaks)
-    tot_ms = sum(v[0] for v in prof.values())
-    if roof:
-        roof["share_of_timed"] = round(prof[roof["kernel"]][0] / max(tot_ms, 1e-9), 4)
+    roof_top = rooflines(prof, wl, peaks, 6)
     launches = int(sum(v[1] for v in prof.values()))
     lat = sorted(step_ms)
 
@@ -1043,6 +1077,7 @@ def run_ours(args):
             "gpu_launches_note": "kernels of this library launched in the profiled repeat of "
                                  "the timed steps (same work as the timed region)",
             "roofline": roof,
+            "rooflines_top": roof_top,
             "profiled_pass": {"value": round(profiled_value, 3), "unit": "sweeps/s",
                               "what": "the timed steps repeated with CUDA events around every "
                                       "kernel; source of kernels_ms and roofline"},

@@ -56,11 +56,17 @@ typedef enum tr_dtype { TR_F32 = 0, TR_F64 = 1 } tr_dtype;
  *                The normal matrix is factored in FP32 when every pivot exceeds
  *                L*eps32*max diag, else in FP64 (same singular rule as TR_PREC_FP64);
  *                FP32 triangular solves and one step of iterative refinement against the
- *                FP32-accurate normal-equation residual. In the drivers, the leverage Gram
- *                of a tall matrix (I >= L) is factored in double-float (pairs of FP32,
- *                about 46 significant bits) when every pivot exceeds
- *                max(I,L)*2^-40*max diag, else in FP64 with column dropping; all other
- *                leverage arithmetic, and tr_leverage, is FP64. */
+ *                FP32-accurate normal-equation residual. In the drivers, the leverage
+ *                scores of a tall matrix (I >= L, 4 <= L <= 128) are those of
+ *                tr_leverage_planes: an FP32 Cholesky preconditioner of the double-float
+ *                Gram and a double-float series, or, when that preconditioner is poor, the
+ *                Gram factored in double-float (pairs of FP32, about 46 significant bits)
+ *                when every pivot exceeds max(I,L)*2^-40*max diag, else in FP64 with column
+ *                dropping. All other leverage arithmetic, and tr_leverage, is FP64.
+ *                The drivers (both precisions) read the fibres of a strided mode from a
+ *                copy of X with that mode last, made at the start of each call, when the
+ *                scattered reads would move more bytes than the copy and memory allows;
+ *                results are bitwise the same as reading X itself. */
 typedef enum tr_precision { TR_PREC_FP64 = 0, TR_PREC_MIXED = 1 } tr_precision;
 
 /* How tr_als_sampled, tr_als_sampled_host and tr_als_sampled_batched draw their samples.

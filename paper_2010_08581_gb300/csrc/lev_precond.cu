@@ -16,8 +16,9 @@
 // are the FP32 factorisation and the columns of its inverse.
 //
 // The fast form is taken only when the FP32 factorisation succeeds (every pivot above
-// n * eps32 * max diag) and ||E||_F <= kTauF; the series then stops at E^4 (||E||_F <= 1e-3)
-// or E^6, leaving a truncation error below 1e-14 relative. Otherwise the device flag
+// n * eps32 * max diag) and ||E||_F <= kTauF; the series then stops at E^2 (||E||_F <= 1e-5),
+// E^4 (<= 1e-3) or E^6, leaving a truncation error below 1e-14 relative. The Gram K comes
+// from one launch (k_gram_dd) in double-float. Otherwise the device flag
 // `state` is set and the double-float factorisation with FP64 fallback (the rank rule of the
 // FP64 path) runs instead, gated on the same flag, so both outcomes are decided on the device
 // without a host round trip.

@@ -39,8 +39,9 @@ def test_kernels_without_a_cost_are_skipped_and_kinds_map_to_bounds():
 
 def test_traffic_is_reported_only_for_the_measured_source(tmp_path, monkeypatch):
     table = json.load(open(os.path.join(bench.ROOT, "profiles", "traffic.json")))
-    assert bench.traffic_for("cholesky_leverage") in (table["cholesky_leverage"]["bytes_per_launch"],
-                                                      None)
+    for kernel, entry in table.items():
+        assert bench.traffic_for(kernel) in (entry["bytes_per_launch"], None)
+        assert bench.algorithmic_cost(kernel, WL) is not None
     fake = tmp_path / "repo"
     (fake / "profiles").mkdir(parents=True)
     (fake / "paper_2010_08581_gb300" / "csrc").mkdir(parents=True)
