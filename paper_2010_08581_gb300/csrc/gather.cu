@@ -41,7 +41,23 @@ __global__ void __launch_bounds__(kWarps * 32) k_gather(GatherArgs a,
         (reinterpret_cast<uintptr_t>(src) % 16 == 0) &&
         (reinterpret_cast<uintptr_t>(out) % 16 == 0)) {
       const int64_t nv = In / V;
-      for (int64_t v = lane; v < nv; v += 32) {
+      int64_t v = lane;
+      if constexpr (sizeof(TX) == 4) {
+        // four 16-byte loads in flight per lane before their stores
+        for (; v + 96 < nv; v += 128) {
+          float4 x[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) x[u] = __ldg(reinterpret_cast<const float4*>(src) + v + 32 * u);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            float4 y;
+            y.x = static_cast<float>(x[u].x * s); y.y = static_cast<float>(x[u].y * s);
+            y.z = static_cast<float>(x[u].z * s); y.w = static_cast<float>(x[u].w * s);
+            reinterpret_cast<float4*>(out)[v + 32 * u] = y;
+          }
+        }
+      }
+      for (; v < nv; v += 32) {
         if constexpr (sizeof(TX) == 4) {
           float4 x = __ldg(reinterpret_cast<const float4*>(src) + v);
           float4 y;
