@@ -273,6 +273,15 @@ size_t leverage_bytes(int64_t I, int L) {
   return leverage_plan(c, I, L, &a, &b, &e);
 }
 
+// Largest ||E||_F of the preconditioned series (TRALS_LEV_TAU, default 1e-2; 0 sends every
+// distribution to the factorisation fallback, which the tests use to run it in a graph).
+float lev_tau() {
+  const char* e = getenv("TRALS_LEV_TAU");
+  if (!e || !*e) return 1e-2f;
+  const float v = strtof(e, nullptr);
+  return v >= 0.f && v <= 1e-2f ? v : 1e-2f;
+}
+
 // The preconditioned form of the mixed drivers' tall leverage scores (on unless
 // TRALS_LEV_PRECOND=0, which keeps the double-float factorisation for every update).
 bool precond_enabled() {
@@ -320,7 +329,11 @@ tr_status leverage_dist(tr_ctx* ctx, char* ws, const double* mat, int64_t I, int
     TR_LAUNCH("lev_u", launch_lev_precond(2, p1.pre, n, I, mat_hi, mat_lo, L, ell, ep, st));
     TR_LAUNCH("lev_e", launch_lev_precond(3, p1.pre, n, I, mat_hi, mat_lo, L, ell, ep, st));
     if (wait_before_rows) TR_CUDA(cudaStreamWaitEvent(st, wait_before_rows, 0));
-    TR_LAUNCH("lev_rows", launch_lev_precond(4, p1.pre, n, I, mat_hi, mat_lo, L, ell, ep, st));
+    LevPrecond lp = p1.pre;
+    lp.tau = lev_tau();
+    TR_LAUNCH("lev_rows", launch_lev_precond(4, lp, n, I, mat_hi, mat_lo, L, ell, ep, st));
+    // the fallback: issued always, each launch exits at once unless the device flag asks for
+    // it (a conditional graph node measured slower than these three launches)
     const int* gate = p1.pre.state;
     const double eps_ff = 9.094947017729282e-13;   // 2^-40
     TR_LAUNCH("cholesky_leverage",
@@ -818,6 +831,12 @@ std::vector<uint64_t> als_key(const tr_ctx* ctx, const AlsPlan& P) {
   u(static_cast<uint64_t>(ctx->wait_limit));
   u(static_cast<uint64_t>(ctx->factorization));
   u(precond_enabled() ? 1 : 0);
+  {
+    const float t = lev_tau();
+    uint32_t b;
+    memcpy(&b, &t, sizeof b);
+    u(b);
+  }
   u(P.copy_mask);
   return k;
 }

@@ -268,6 +268,7 @@ struct LevPrecond {
   int* state;
   float* gph;        // launch_gram_dd scratch (gram_dd_partial_floats each)
   float* gpl;
+  float tau = 1e-2f; // largest ||E||_F of the series (above it: the fallback)
 };
 bool lev_precond_fits(int64_t I, int n);
 // K = A^T A of the tall I x n double-float planes (row stride lda_a) in one launch: K's

@@ -16,7 +16,7 @@
 // are the FP32 factorisation and the columns of its inverse.
 //
 // The fast form is taken only when the FP32 factorisation succeeds (every pivot above
-// n * eps32 * max diag) and ||E||_F <= kTauF; the series then stops at E^2 (||E||_F <= 1e-5),
+// n * eps32 * max diag) and ||E||_F <= tau (1e-2); the series then stops at E^2 (||E||_F <= 1e-5),
 // E^4 (<= 1e-3) or E^6, leaving a truncation error below 1e-14 relative. The Gram K comes
 // from one launch (k_gram_dd) in double-float. Otherwise the device flag
 // `state` is set and the double-float factorisation with FP64 fallback (the rank rule of the
@@ -32,7 +32,6 @@ cudaError_t launch_tri_inv(int n, const float* Limg, const double* invdiag, cons
 
 namespace {
 
-constexpr float kTauF = 1e-2f;         // largest ||E||_F of the fast form
 constexpr float kTauF4 = 1e-3f;        // up to this, terms through E^4 suffice
 constexpr int LT = 16;                 // tile edge of the products U = X K and C = U X^T
 constexpr int kMaxPre = 128;           // largest n of the preconditioned form
@@ -323,7 +322,7 @@ constexpr int LR_NT = 512;
 
 // LR_ROWS rows of A per CTA: w = X a in double-float, ell = w.w - w.v1 + v1.v1 - ..., then
 // (last CTA) p and the CDF. Every CTA reads the same ||E||_F^2 (fixed-order sum of esq); when
-// it exceeds kTauF^2 no CTA computes anything and CTA 0 sets *state = 1 for the fallback.
+// it exceeds tau^2 no CTA computes anything and CTA 0 sets *state = 1 for the fallback.
 // The series is cut where the next term is below 1e-15 relative: through E^2 for
 // ||E||_F <= 1e-5, E^4 for <= 1e-3, E^6 otherwise.
 // w: thread t serves rows 2h, 2h+1 (h = t / 64 % 2), the columns u and n-1-u (u = t % 64),
@@ -337,16 +336,16 @@ __global__ void __launch_bounds__(LR_NT) k_lev_rows(int n, int64_t I, const floa
                                                     const float* __restrict__ E, int lde,
                                                     const float* __restrict__ esq, int nesq,
                                                     int* state, double* __restrict__ ell,
-                                                    CdfEpilogue ep) {
+                                                    CdfEpilogue ep, float tau) {
   extern __shared__ __align__(16) float lrs[];  // X image, then E (row stride lde)
   __shared__ float2 as[LR_ROWS][kMaxPre];     // (a_hi, a_lo)
   __shared__ float wv[LR_ROWS][kMaxPre];      // w (FP32), then v1, v2
   __shared__ float part[LR_KS][128][8];       // quarter sums: (s, c) per row-column pair
   __shared__ float red[LR_NT / 32][8];
-  if (*reinterpret_cast<volatile int*>(state) != 0) return;
+  if (*reinterpret_cast<volatile int*>(state) != 0) return;   // the FP32 factor failed
   float f2 = 0.f;
   for (int b = 0; b < nesq; ++b) f2 += esq[b];
-  if (!(f2 <= kTauF * kTauF)) {
+  if (!(f2 <= tau * tau)) {
     if (blockIdx.x == 0 && threadIdx.x == 0) *state = 1;
     return;
   }
@@ -588,7 +587,7 @@ cudaError_t launch_lev_precond(int stage, const LevPrecond& lp, int n, int64_t I
       const unsigned rb = static_cast<unsigned>((I + LR_ROWS - 1) / LR_ROWS);
       k_lev_rows<<<rb, LR_NT, lev_rows_smem(n), st>>>(n, I, Ah, Al, lda, lp.Ximg, lp.E, ld,
                                                         lp.esq, lev_precond_ctas(n), lp.state,
-                                                        ell, ep);
+                                                        ell, ep, lp.tau);
       return cudaGetLastError();
     }
     default:

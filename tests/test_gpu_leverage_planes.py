@@ -153,3 +153,31 @@ def test_rejects_unsupported_shapes(ctx):
         with pytest.raises(T.TrError) as e:
             T.tr_leverage_planes(ctx, z, z, p, p)
         assert e.value.status == T.TR_ERR_INVALID_ARG
+
+
+def test_driver_runs_the_fallback_inside_its_graph(ctx, monkeypatch):
+    """The mixed driver's graph holds the factorisation fallback as launches gated by a
+    device flag. TRALS_LEV_TAU=0 makes every distribution take it; the decomposition must
+    then follow the factorisation form (TRALS_LEV_PRECOND=0) draw for draw. A fallback that
+    did not run would leave stale distributions and different draws."""
+    from paper_2010_08581_gb300 import inputs
+    dims, ranks, J, sweeps = (120, 110, 100), (6, 6, 6), 1000, 4
+    X, _ = inputs.tr_plus_noise(dims, ranks, seed=12, rel_noise=1e-2, dtype=torch.float32)
+    Xd = X.to(DEV)
+    init = [inputs.slice_major(c).to(DEV) for c in inputs.random_cores(dims, ranks, 13)]
+
+    def run_driver():
+        out = T.empty_cores(dims, ranks)
+        T.tr_als_sampled(ctx, Xd, ranks, J, sweeps, 5, T.TR_PREC_MIXED, out, init_cores=init)
+        T.tr_status_sync(ctx)
+        return [o.cpu().numpy() for o in out], T.tr_rel_error(ctx, Xd, ranks, out)
+
+    fast, e_fast = run_driver()
+    monkeypatch.setenv("TRALS_LEV_TAU", "0")
+    forced, _ = run_driver()
+    monkeypatch.delenv("TRALS_LEV_TAU")
+    monkeypatch.setenv("TRALS_LEV_PRECOND", "0")
+    fact, e_fact = run_driver()
+    for a, b in zip(forced, fact):
+        assert np.linalg.norm(a - b) <= 1e-8 * np.linalg.norm(b)
+    assert abs(e_fast - e_fact) <= 0.01 * e_fact
