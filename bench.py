@@ -186,8 +186,8 @@ def algorithmic_cost(kernel, wl):
       leverage_rows   : I*L^2 FP64 flops
       sample          : J*(N-1) * (4 + 8*log2 I) bytes (index writes + CDF probes) + J*8
       sample_chain    : sample + subchain + gather (draws, rows and fibres in one kernel)
-      lev_factor      : L^3/3 FP32 flops (one CTA: the preconditioner's Cholesky factor)
-      lev_inverse     : L^3/3 FP32 flops (its inverse X, one warp per column)
+      lev_factor      : 2*L^3/3 FP32 flops (one CTA: the preconditioner's Cholesky factor
+                        and its inverse X in one pass)
       gram_dd         : I*L^2 double-float flops (Gram of B^T, upper tiles)
       lev_u, lev_e    : L^3 and L^3/3 double-float flops (U = X K, E = U X^T - I)
       lev_rows        : I*L^2 double-float flops (w = X b per row; the FP32 series is smaller)
@@ -215,8 +215,7 @@ def algorithmic_cost(kernel, wl):
         "reduce_gram": ("hbm", L * L * 8.0),
         "cdf": ("hbm", I * 8.0 * 3),
         "init_normal": ("hbm", I * L * 8.0),
-        "lev_factor": ("flops_f32", L ** 3 / 3.0),
-        "lev_inverse": ("flops_f32", L ** 3 / 3.0),
+        "lev_factor": ("flops_f32", 2.0 * L ** 3 / 3.0),
         "gram_dd": ("flops_ff", I * L * L),
         "lev_u": ("flops_ff", float(L) ** 3),
         "lev_e": ("flops_ff", L ** 3 / 3.0),

@@ -358,9 +358,9 @@ tr_status tr_get_batched_tiles(const tr_ctx* ctx, tr_batched_tiles* tiles);
 /* Least-squares step without any device allocation (the paper has no counterpart; this
  * is a deployment variant of tr_solve).
  *
- * Some callers cannot call cudaMalloc: code that issues work while a CUDA graph is being
- * captured in global mode (allocation is not allowed there), latency-critical serving
- * loops where cudaMalloc/cudaFree would synchronise the device, and hosts that have
+ * Some callers cannot call cudaMalloc: plug-ins and callbacks that run inside a host
+ * framework which owns the device memory and forbids them to allocate, latency-critical
+ * serving loops where cudaMalloc/cudaFree would synchronise the device, and hosts that have
  * partitioned all device memory up front. tr_solve_noalloc computes what tr_solve computes
  * on a context with the default settings (TR_LS_RANK_STOP, the default wait limit): the
  * same kernels with the same arguments, so the new core is bit-identical. It takes its

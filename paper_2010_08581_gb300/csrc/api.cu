@@ -195,10 +195,7 @@ LevPass carve_pass(Carver& c, int64_t rows, int cols, bool trans) {
   p.info = c.take<int>(1);
   p.img = reinterpret_cast<double*>(c.take<char>(trsm_image_bytes(n, false)));
   if (!trans && lev_precond_fits(rows, cols)) {
-    p.pre.Limg = reinterpret_cast<float*>(c.take<char>(trsm_image_bytes(n, true)));
     p.pre.Ximg = reinterpret_cast<float*>(c.take<char>(trsm_image_bytes(n, true)));
-    p.pre.invdiag = c.take<double>(n);
-    p.pre.keep = c.take<int>(n);
     const size_t ld4 = static_cast<size_t>((n + 3) & ~3);
     p.pre.Uh = c.take<float>(n * ld4);
     p.pre.Ul = c.take<float>(n * ld4);
@@ -325,13 +322,12 @@ tr_status leverage_dist(tr_ctx* ctx, char* ws, const double* mat, int64_t I, int
     TR_LAUNCH("gram_dd", launch_gram_dd(mat_hi, mat_lo, I, n, n, p1.pre.gph, p1.pre.gpl,
                                         counter + 1, sp.hi, sp.lo, sp.lda, p1.G, st));
     TR_LAUNCH("lev_factor", launch_lev_precond(0, p1.pre, n, I, mat_hi, mat_lo, L, ell, ep, st));
-    TR_LAUNCH("lev_inverse", launch_lev_precond(1, p1.pre, n, I, mat_hi, mat_lo, L, ell, ep, st));
-    TR_LAUNCH("lev_u", launch_lev_precond(2, p1.pre, n, I, mat_hi, mat_lo, L, ell, ep, st));
-    TR_LAUNCH("lev_e", launch_lev_precond(3, p1.pre, n, I, mat_hi, mat_lo, L, ell, ep, st));
+    TR_LAUNCH("lev_u", launch_lev_precond(1, p1.pre, n, I, mat_hi, mat_lo, L, ell, ep, st));
+    TR_LAUNCH("lev_e", launch_lev_precond(2, p1.pre, n, I, mat_hi, mat_lo, L, ell, ep, st));
     if (wait_before_rows) TR_CUDA(cudaStreamWaitEvent(st, wait_before_rows, 0));
     LevPrecond lp = p1.pre;
     lp.tau = lev_tau();
-    TR_LAUNCH("lev_rows", launch_lev_precond(4, lp, n, I, mat_hi, mat_lo, L, ell, ep, st));
+    TR_LAUNCH("lev_rows", launch_lev_precond(3, lp, n, I, mat_hi, mat_lo, L, ell, ep, st));
     // the fallback: issued always, each launch exits at once unless the device flag asks for
     // it (a conditional graph node measured slower than these three launches)
     const int* gate = p1.pre.state;
@@ -377,6 +373,7 @@ struct SolvePlan {
   void* partial; double* M; double* BT; double* Lrow; double* Lcol; double* invdiag;
   int* keep; int* info; void* limg; float* mimg; float* wimg; int splits;
   float* bt_hi = nullptr; float* bt_lo = nullptr;   // double-float planes of B^T (mixed)
+  int* fast = nullptr;   // the one-CTA FP32 factor-and-inverse succeeded (mixed, L <= 128)
 };
 
 bool use_tensor_cores(bool f64) {
@@ -401,6 +398,7 @@ size_t solve_plan(Carver& c, int64_t J, int L, int64_t I, bool f64, SolvePlan* s
   s->wimg = f64 ? nullptr : reinterpret_cast<float*>(c.take<char>(trsm_image_bytes(L, true)));
   s->bt_hi = f64 ? nullptr : c.take<float>(static_cast<size_t>(I) * L);
   s->bt_lo = f64 ? nullptr : c.take<float>(static_cast<size_t>(I) * L);
+  s->fast = f64 ? nullptr : c.take<int>(1);
   return c.off;
 }
 
@@ -440,6 +438,12 @@ tr_status solve_contract(tr_ctx* ctx, const SolvePlan& s, const void* A, const v
   return TR_OK;
 }
 
+// The flag of the mixed LS step's one-CTA FP32 factor-and-inverse (launch_cholesky_mixed),
+// or nullptr where that form does not apply (FP64 arithmetic or factorisations, L > 128).
+int* tiles_flag(const tr_ctx* ctx, const SolvePlan& s, bool f64, int L) {
+  return (!f64 && ctx->factorization != TR_FACTOR_FP64 && L >= 4 && L <= 128) ? s.fast : nullptr;
+}
+
 tr_status solve_cholesky(tr_ctx* ctx, const SolvePlan& s, bool f64, int L, cudaStream_t st) {
   const double eps = 2.220446049250313e-16;
   const int mode = ctx->ls_rank == TR_LS_RANK_DROP ? 1 : 0;
@@ -459,7 +463,8 @@ tr_status solve_cholesky(tr_ctx* ctx, const SolvePlan& s, bool f64, int L, cudaS
                                     s.keep, s.info, ctx->d_err, st, static_cast<float*>(s.limg),
                                     s.mimg,
                                     L >= 4 && L <= 160 ? reinterpret_cast<float*>(s.Lrow)
-                                                       : nullptr));
+                                                       : nullptr,
+                                    s.wimg, tiles_flag(ctx, s, f64, L)));
     return TR_OK;
   }
   TR_LAUNCH("cholesky_solve",
@@ -475,7 +480,7 @@ tr_status solve_rhs(tr_ctx* ctx, const SolvePlan& s, int Rl, int Rr, int64_t I, 
   if (refine && solve_inv_fits(L)) {
     TR_LAUNCH("solve_rhs", launch_solve_inv(L, static_cast<const float*>(s.limg), s.mimg,
                                             s.invdiag, s.info, I, s.BT, L, Rl, Rr, core_out,
-                                            s.wimg, st));
+                                            s.wimg, st, tiles_flag(ctx, s, !refine, L)));
     return TR_OK;
   }
   TR_LAUNCH("solve_rhs", launch_trsm(refine ? 2 : 1, refine, L, s.Lrow, s.Lcol, s.invdiag, s.info,

@@ -1,6 +1,7 @@
 // Single-problem launches of the one-CTA Cholesky factorisation (cholesky_body.cuh) for
 // the leverage scores of Def. 4 (row a1) and the LS step of Alg. 2 (row a6): FP64, the
 // mixed LS step's FP32-then-FP64 form, and the double-float leverage form.
+#include "chol_inv.cuh"
 #include "cholesky_body.cuh"
 
 namespace trk {
@@ -26,8 +27,10 @@ __global__ void __launch_bounds__(CNT) k_cholesky_mixed(const double* __restrict
                                                         double* invdiag, int* keep_out,
                                                         int* info, unsigned* err, int dyn_bytes,
                                                         TI* img, float* gimg32,
-                                                        const float* pre) {
+                                                        const float* pre,
+                                                        const int* __restrict__ skip_if) {
   extern __shared__ double smem[];
+  if (skip_if && *skip_if) return;   // the factor and its inverse are formed already
   // A contraction whose bounded wait expired left no valid normal equations: report
   // info = -1 so that the solve leaves the core unchanged (the error bit is already set).
   if (err && (*reinterpret_cast<volatile unsigned*>(err) & kErrTimeout)) {
@@ -39,6 +42,34 @@ __global__ void __launch_bounds__(CNT) k_cholesky_mixed(const double* __restrict
   double* A64 = nn * 8 <= dyn_bytes ? smem : Lrow;
   cholesky_cta_mixed<TI>(G, n, mode, tol64, tol32, A32, A64, Lrow, Lcol, invdiag, keep_out, info,
                          err, img, gimg32, A32 == reinterpret_cast<float*>(smem) ? pre : nullptr);
+}
+
+// The mixed-precision LS step's FP32 factor and its inverse in one CTA (chol_inv_tiles) from
+// the reduction's FP32 work array pre; on success wimg, keep, *info = 0 and *fast = 1,
+// otherwise *fast = 0 and nothing else (k_cholesky_mixed then runs). A contraction whose
+// bounded wait expired gives *info = -1 and *fast = 1 (nothing to factor).
+__global__ void __launch_bounds__(kCiMaxThreads) k_chol_inv_solve(int n, float tol_scale,
+                                                                  const float* __restrict__ pre,
+                                                                  int lda, float* __restrict__ wimg,
+                                                                  int* __restrict__ keep,
+                                                                  int* __restrict__ info,
+                                                                  const unsigned* err,
+                                                                  int* __restrict__ fast) {
+  __shared__ CiShared cs;
+  if (err && (*reinterpret_cast<const volatile unsigned*>(err) & kErrTimeout)) {
+    if (threadIdx.x == 0) {
+      *info = -1;
+      *fast = 1;
+    }
+    return;
+  }
+  const bool ok = chol_inv_tiles(n, tol_scale, pre, lda, wimg, cs);
+  if (ok)
+    for (int k = threadIdx.x; k < n; k += blockDim.x) keep[k] = 1;
+  if (threadIdx.x == 0) {
+    if (ok) *info = 0;
+    *fast = ok ? 1 : 0;
+  }
 }
 
 // The mixed-precision drivers' leverage Gram (tall, mode 1): double-float, FP64 if needed.
@@ -102,12 +133,19 @@ cudaError_t launch_cholesky_lev_mixed(const double* G, int n, double tol64, doub
 cudaError_t launch_cholesky_mixed(const double* G, int n, int mode, double tol64, double tol32,
                                   double* Lrow, double* Lcol, double* invdiag, int* keep,
                                   int* info, unsigned* err, cudaStream_t st, float* img32,
-                                  float* gimg32, const float* pre) {
+                                  float* gimg32, const float* pre, float* wimg, int* fast) {
   const size_t nn = static_cast<size_t>(n) * n;
   const size_t dyn = nn * 8 <= kCholDyn ? nn * 8 : (nn * 4 <= kCholDyn ? nn * 4 : 0);
+  const bool tiles = wimg && fast && pre && n >= 4 && n <= kCiMaxN;
+  if (tiles) {
+    k_chol_inv_solve<<<1, chol_inv_threads(n), 0, st>>>(n, static_cast<float>(tol32), pre,
+                                                        (n + 3) & ~3, wimg, keep, info, err, fast);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   k_cholesky_mixed<float><<<1, CNT, dyn, st>>>(G, n, mode, tol64, tol32, Lrow, Lcol, invdiag, keep,
                                                info, err, static_cast<int>(dyn), img32, gimg32,
-                                               pre);
+                                               pre, tiles ? fast : nullptr);
   return cudaGetLastError();
 }
 

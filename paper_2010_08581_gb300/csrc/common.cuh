@@ -169,10 +169,15 @@ cudaError_t launch_reduce(const void* partial, bool partial_f32, int splits, int
 // Mixed-precision LS step: an FP32 factor when every pivot > tol32 * max diag, written as the
 // FP32 image img32 + invdiag + keep + info; otherwise the FP64 factorisation with tol64
 // and the mode's rule (as launch_cholesky: 0 stops, 1 drops the column).
+// With wimg and fast (and pre, 4 <= n <= 128) an FP32 factor and its inverse are first formed
+// together in one CTA (chol_inv.cuh): on success W = L_f^-1 goes to wimg (the image
+// launch_solve_inv reads), keep = 1, *info = 0 and *fast = 1, and the launches above exit at
+// once; otherwise *fast = 0 and they run as described. Pass the same fast to launch_solve_inv.
 cudaError_t launch_cholesky_mixed(const double* G, int n, int mode, double tol64, double tol32,
                                   double* Lrow, double* Lcol, double* invdiag, int* keep,
                                   int* info, unsigned* err, cudaStream_t st, float* img32,
-                                  float* gimg32, const float* pre = nullptr);
+                                  float* gimg32, const float* pre = nullptr,
+                                  float* wimg = nullptr, int* fast = nullptr);
 // Mixed-precision drivers' leverage Gram of a tall matrix (mode 1): double-float factor when
 // every pivot > tolff * max diag (FP64 image img64 + invdiag + keep + info), otherwise the FP64
 // factorisation with tol64 and column dropping (as launch_cholesky, mode 1).
@@ -236,11 +241,12 @@ cudaError_t launch_leverage_jacobi(const double* A, int64_t I, int L, int64_t ld
 // Mixed-precision LS solve for L <= 128 (solve_inv.cu): W = L_f^-1 from the factor's FP32
 // image (into Wimg, trsm_image_bytes(n, true) bytes), then z = W^T W b, r = b - M z,
 // z += W^T W r for every row b of rhs (ld), written as the new core; nothing when *info != 0.
+// With fast (launch_cholesky_mixed's flag) W is not formed when *fast != 0: it is already in Wimg.
 bool solve_inv_fits(int n);
 cudaError_t launch_solve_inv(int n, const float* Limg, const float* Mimg,
                              const double* invdiag, const int* info, int64_t nvec,
                              const double* rhs, int64_t ld, int Rl, int Rr, double* core_out,
-                             float* Wimg, cudaStream_t st);
+                             float* Wimg, cudaStream_t st, const int* fast = nullptr);
 
 // The mixed drivers' leverage scores of a tall I x n row-major matrix A given as double-float
 // planes (Ah + Al, row stride lda), 4 <= n <= 128 (lev_precond.cu): an FP32 Cholesky factor of
@@ -250,17 +256,14 @@ cudaError_t launch_solve_inv(int n, const float* Limg, const float* Mimg,
 // p and the CDF as launch_trsm's epilogue (ep.counter 0 before the launch). When the FP32
 // factorisation fails or ||E||_F is too large for the series, nothing is written and
 // *state = 1 (0 otherwise): the caller's fallback launches are gated on it (run_if).
-// Five launches, issued in order by stage = 0 (FP32 factor; sets *state), 1 (inverse),
-// 2 (U = X K), 3 (E = U X^T - I), 4 (rows, p and the CDF; reads ep.skip); lda_k must be
-// (n + 3) & ~3.
+// Four launches, issued in order by stage = 0 (FP32 factor and its inverse X in one CTA;
+// sets *state), 1 (U = X K), 2 (E = U X^T - I), 3 (rows, p and the CDF; reads ep.skip);
+// lda_k must be (n + 3) & ~3.
 struct LevPrecond {
   const float* K_hi;
   const float* K_lo;
   int lda_k;
-  float* Limg;       // FP32 factor image (trsm_image_bytes(n, true) bytes)
-  float* Ximg;       // its inverse, same layout
-  double* invdiag;   // n
-  int* keep;         // n
+  float* Ximg;       // X = L^-1, padded FP32 image (trsm_image_bytes(n, true) bytes)
   float* Uh;         // U = X K as double-float planes, n x lda_k each
   float* Ul;
   float* E;          // n x lda_k

@@ -4,16 +4,16 @@
 //
 // For any nonsingular X, K^-1 = X^T (X K X^T)^-1 X, so with w_i = X a_i and C = X K X^T,
 //   ell_i = w_i^T C^-1 w_i.
-// X = L^-1 from the FP32 Cholesky factor of K (one CTA, then one warp per column of the
-// inverse) makes C = I + E with E small (of order n * eps32 * cond(K)). Then
+// X = L^-1 from the FP32 Cholesky factor of K (factor and inverse in one CTA, k_chol_inv)
+// makes C = I + E with E small (of order n * eps32 * cond(K)). Then
 //   C^-1 = I - E + E^2 - ...,   ell_i = w.w - w.v1 + v1.v1 - v1.v2 + v2.v2 - v2.v3 + v3.v3 - ...
 // with v1 = E w, v2 = E v1, v3 = E v2. X only has to be a good preconditioner: C and w are
 // formed from the same X, so the identity holds for the X actually computed. The products
 // that carry the leading digits (C = X K X^T, w = X a, w.w) run in double-float (hi + lo FP32
 // pairs, compensated dot products after Ogita, Rump and Oishi, SIAM J. Sci. Comput. 2005);
 // E is then rounded to FP32 and the corrections, which are smaller than ell_i by the factor
-// ||E||, run in FP32. All of this is parallel work over many CTAs; the only serial chains
-// are the FP32 factorisation and the columns of its inverse.
+// ||E||, run in FP32. All of this is parallel work over many CTAs; the only serial chain
+// is the one-CTA pass that forms the FP32 factor and its inverse.
 //
 // The fast form is taken only when the FP32 factorisation succeeds (every pivot above
 // n * eps32 * max diag) and ||E||_F <= tau (1e-2); the series then stops at E^2 (||E||_F <= 1e-5),
@@ -22,20 +22,17 @@
 // `state` is set and the double-float factorisation with FP64 fallback (the rank rule of the
 // FP64 path) runs instead, gated on the same flag, so both outcomes are decided on the device
 // without a host round trip.
+#include "chol_inv.cuh"
 #include "cholesky_body.cuh"
 #include "trsm_body.cuh"
 
 namespace trk {
-
-cudaError_t launch_tri_inv(int n, const float* Limg, const double* invdiag, const int* info,
-                           float* Wimg, cudaStream_t st);
 
 namespace {
 
 constexpr float kTauF4 = 1e-3f;        // up to this, terms through E^4 suffice
 constexpr int LT = 16;                 // tile edge of the products U = X K and C = U X^T
 constexpr int kMaxPre = 128;           // largest n of the preconditioned form
-constexpr int kCholPreNT = 256;        // threads of the FP32 factorisation
 
 __host__ __device__ inline int pad4(int v) { return (v + 3) & ~3; }
 
@@ -185,18 +182,18 @@ __global__ void __launch_bounds__(GDNT) k_gram_dd(const float* __restrict__ Ah,
   if (threadIdx.x == 0) cnt[blockIdx.x] = 0u;
 }
 
-// The FP32 factor of the preconditioner (one CTA): K's FP32 values from the reduction's work
-// array; on success the factor's padded image, 1/diag and *state = 0, otherwise *state = 1.
-__global__ void __launch_bounds__(kCholPreNT) k_chol_pre(int n, double tol32, const float* __restrict__ pre,
-                                                  float* __restrict__ Limg,
-                                                  double* __restrict__ invdiag,
-                                                  int* __restrict__ keep, int* state) {
-  extern __shared__ __align__(16) float csm[];
-  const bool ok = cholesky_panel_f32(n, tol32, csm, pre, Limg, invdiag, keep, state);
-  if (!ok && threadIdx.x == 0) *state = 1;
+// The preconditioner X = L^-1 of K = L L^T in FP32, factor and inverse in one CTA
+// (chol_inv_tiles). K comes from the reduction's FP32 work array. On success: the padded
+// column-major image of X and *state = 0; when a pivot is <= tol_scale * max diag K:
+// *state = 1 and nothing else.
+__global__ void __launch_bounds__(kCiMaxThreads) k_chol_inv(int n, float tol_scale,
+                                                            const float* __restrict__ pre,
+                                                            int lda, float* __restrict__ Ximg,
+                                                            int* __restrict__ state) {
+  __shared__ CiShared cs;
+  const bool ok = chol_inv_tiles(n, tol_scale, pre, lda, Ximg, cs);
+  if (threadIdx.x == 0) *state = ok ? 0 : 1;
 }
-
-size_t chol_pre_smem(int n) { return static_cast<size_t>(panel_floats<F32Ops>(n)) * 4; }
 
 // The symmetric K[k][c] from its double-float planes, which hold the entries c >= r of row r
 // (row stride lda).
@@ -569,21 +566,19 @@ cudaError_t launch_lev_precond(int stage, const LevPrecond& lp, int n, int64_t I
   switch (stage) {
     case 0: {
       const double eps32 = 1.1920928955078125e-07;
-      k_chol_pre<<<1, kCholPreNT, chol_pre_smem(n), st>>>(n, static_cast<double>(n) * eps32, lp.K_hi,
-                                                   lp.Limg, lp.invdiag, lp.keep, lp.state);
+      k_chol_inv<<<1, chol_inv_threads(n), 0, st>>>(n, static_cast<float>(n * eps32), lp.K_hi,
+                                                    lp.lda_k, lp.Ximg, lp.state);
       return cudaGetLastError();
     }
     case 1:
-      return launch_tri_inv(n, lp.Limg, lp.invdiag, lp.state, lp.Ximg, st);
-    case 2:
       k_lev_u<<<dim3(nt, nt), dim3(LT, LT), 0, st>>>(n, lp.K_hi, lp.K_lo, lp.lda_k, lp.Ximg,
                                                      lp.state, lp.Uh, lp.Ul, ld);
       return cudaGetLastError();
-    case 3:
+    case 2:
       k_lev_e<<<lev_precond_ctas(n), dim3(LT, LT), 0, st>>>(n, lp.Uh, lp.Ul, ld, lp.Ximg,
                                                            lp.state, lp.E, ld, lp.esq);
       return cudaGetLastError();
-    case 4: {
+    case 3: {
       const unsigned rb = static_cast<unsigned>((I + LR_ROWS - 1) / LR_ROWS);
       k_lev_rows<<<rb, LR_NT, lev_rows_smem(n), st>>>(n, I, Ah, Al, lda, lp.Ximg, lp.E, ld,
                                                         lp.esq, lev_precond_ctas(n), lp.state,
@@ -596,12 +591,8 @@ cudaError_t launch_lev_precond(int stage, const LevPrecond& lp, int n, int64_t I
 }
 
 cudaError_t lev_precond_attributes() {
-  cudaError_t e = cudaFuncSetAttribute(k_chol_pre, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(chol_pre_smem(kMaxPre)));
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_lev_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(lev_rows_smem(kMaxPre)));
-  return e;
+  return cudaFuncSetAttribute(k_lev_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              static_cast<int>(lev_rows_smem(kMaxPre)));
 }
 
 }  // namespace trk

@@ -38,13 +38,14 @@ struct Bump {
 
 struct Layout {
   void* partial; double* M; double* BT; double* Lrow; double* Lcol; double* invdiag;
-  int* keep; int* info; void* limg; float* mimg; float* wimg; unsigned* err; int splits;
+  int* keep; int* info; void* limg; float* mimg; float* wimg; unsigned* err; int* fast;
+  int splits;
 };
 
 // The scratch of one call, carved as tr_solve carves its workspace: the contraction's split
 // partials, M, B^T, the factor (row- and column-major), its inverse diagonal and pivot flags,
 // the factor's padded image in the solve's arithmetic type, M's FP32 image and the factor's
-// FP32 inverse (mixed path), and the error word.
+// FP32 inverse (mixed path), the error word and the flag of the one-CTA factor-and-inverse.
 size_t layout(char* base, int64_t J, int L, int64_t I, bool f64, Layout* s) {
   Bump b{base};
   const size_t pbytes = f64 ? normal_eq_workspace(J, L, I, true, &s->splits)
@@ -61,6 +62,7 @@ size_t layout(char* base, int64_t J, int L, int64_t I, bool f64, Layout* s) {
   s->mimg = f64 ? nullptr : reinterpret_cast<float*>(b.take<char>(trsm_image_bytes(L, true)));
   s->wimg = f64 ? nullptr : reinterpret_cast<float*>(b.take<char>(trsm_image_bytes(L, true)));
   s->err = b.take<unsigned>(1);
+  s->fast = f64 ? nullptr : b.take<int>(1);
   return b.off;
 }
 
@@ -136,6 +138,7 @@ extern "C" tr_status tr_solve_noalloc(const void* A, const void* Y, tr_dtype dty
   // mixed path the reduction also writes M's FP32 work array and image for the FP32 factor.
   ReduceSplit sp;
   const bool pre = !f64 && L >= 4 && L <= 160;
+  const bool tiles = !f64 && L >= 4 && L <= 128;   // as tr_solve's default factorisation
   if (pre) {
     sp.hi = reinterpret_cast<float*>(s.Lrow);
     sp.lda = (L + 3) & ~3;
@@ -152,12 +155,13 @@ extern "C" tr_status tr_solve_noalloc(const void* A, const void* Y, tr_dtype dty
       e = launch_cholesky_mixed(s.M, L, 0, static_cast<double>(L) * eps,
                                 static_cast<double>(L) * eps32, s.Lrow, s.Lcol, s.invdiag,
                                 s.keep, s.info, s.err, st, static_cast<float*>(s.limg), s.mimg,
-                                pre ? reinterpret_cast<float*>(s.Lrow) : nullptr);
+                                pre ? reinterpret_cast<float*>(s.Lrow) : nullptr, s.wimg,
+                                tiles ? s.fast : nullptr);
   }
   if (e == cudaSuccess) {
     if (!f64 && solve_inv_fits(L))
       e = launch_solve_inv(L, static_cast<const float*>(s.limg), s.mimg, s.invdiag, s.info, I,
-                           s.BT, L, Rl, Rr, core_out, s.wimg, st);
+                           s.BT, L, Rl, Rr, core_out, s.wimg, st, tiles ? s.fast : nullptr);
     else
       e = launch_trsm(f64 ? 1 : 2, !f64, L, s.Lrow, s.Lcol, s.invdiag, s.info, I, s.BT, L, s.M,
                       Rl, Rr, core_out, nullptr, st, s.limg, s.mimg);

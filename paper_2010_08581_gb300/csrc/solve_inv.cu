@@ -33,9 +33,10 @@ template <int QN>
 __global__ void __launch_bounds__(IW * 32) k_tri_inv(int n, const float* __restrict__ Limg,
                                                      const double* __restrict__ invdiag,
                                                      const int* __restrict__ info,
-                                                     float* __restrict__ Wimg) {
+                                                     float* __restrict__ Wimg,
+                                                     const int* __restrict__ skip_if) {
   extern __shared__ __align__(16) unsigned char ism[];
-  if (*info != 0) return;
+  if (*info != 0 || (skip_if && *skip_if)) return;
   const int np = n + 1;
   float* inv = reinterpret_cast<float*>(ism);
   float* Ls = inv + kMaxL;
@@ -186,36 +187,21 @@ size_t solve_inv_workspace(int n) { return img_bytes32(n); }
 cudaError_t launch_solve_inv(int n, const float* Limg, const float* Mimg,
                              const double* invdiag, const int* info, int64_t nvec,
                              const double* rhs, int64_t ld, int Rl, int Rr, double* core_out,
-                             float* Wimg, cudaStream_t st) {
+                             float* Wimg, cudaStream_t st, const int* fast) {
   if (!solve_inv_fits(n)) return cudaErrorInvalidValue;
   if (nvec <= 0) return cudaSuccess;
   const unsigned ib = static_cast<unsigned>((n + IW - 1) / IW);
   switch ((n + 31) / 32) {
-    case 1: k_tri_inv<1><<<ib, IW * 32, inv_smem(n), st>>>(n, Limg, invdiag, info, Wimg); break;
-    case 2: k_tri_inv<2><<<ib, IW * 32, inv_smem(n), st>>>(n, Limg, invdiag, info, Wimg); break;
-    case 3: k_tri_inv<3><<<ib, IW * 32, inv_smem(n), st>>>(n, Limg, invdiag, info, Wimg); break;
-    default: k_tri_inv<4><<<ib, IW * 32, inv_smem(n), st>>>(n, Limg, invdiag, info, Wimg); break;
+    case 1: k_tri_inv<1><<<ib, IW * 32, inv_smem(n), st>>>(n, Limg, invdiag, info, Wimg, fast); break;
+    case 2: k_tri_inv<2><<<ib, IW * 32, inv_smem(n), st>>>(n, Limg, invdiag, info, Wimg, fast); break;
+    case 3: k_tri_inv<3><<<ib, IW * 32, inv_smem(n), st>>>(n, Limg, invdiag, info, Wimg, fast); break;
+    default: k_tri_inv<4><<<ib, IW * 32, inv_smem(n), st>>>(n, Limg, invdiag, info, Wimg, fast); break;
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const unsigned sb = static_cast<unsigned>((nvec + SNR - 1) / SNR);
   k_solve_inv<<<sb, SNT, solve_smem_bytes(n), st>>>(n, Wimg, Mimg, info, nvec, rhs, ld, Rl, Rr,
                                                      core_out);
-  return cudaGetLastError();
-}
-
-// The inverse alone (the preconditioner of the mixed drivers' leverage scores): W = L_f^-1
-// into Wimg; nothing when *info != 0.
-cudaError_t launch_tri_inv(int n, const float* Limg, const double* invdiag, const int* info,
-                           float* Wimg, cudaStream_t st) {
-  if (!solve_inv_fits(n)) return cudaErrorInvalidValue;
-  const unsigned ib = static_cast<unsigned>((n + IW - 1) / IW);
-  switch ((n + 31) / 32) {
-    case 1: k_tri_inv<1><<<ib, IW * 32, inv_smem(n), st>>>(n, Limg, invdiag, info, Wimg); break;
-    case 2: k_tri_inv<2><<<ib, IW * 32, inv_smem(n), st>>>(n, Limg, invdiag, info, Wimg); break;
-    case 3: k_tri_inv<3><<<ib, IW * 32, inv_smem(n), st>>>(n, Limg, invdiag, info, Wimg); break;
-    default: k_tri_inv<4><<<ib, IW * 32, inv_smem(n), st>>>(n, Limg, invdiag, info, Wimg); break;
-  }
   return cudaGetLastError();
 }
 

@@ -1,5 +1,5 @@
 """tr_solve_noalloc: the least-squares step for callers that cannot allocate device memory
-(for example code running while a CUDA graph is captured in global mode, or serving loops
+(for example plug-ins inside a host framework that owns all device memory, or serving loops
 that must not synchronise the device through cudaMalloc/cudaFree). It runs the same kernels
 with the same arguments as tr_solve on a default context, so it must give the same new
 core bit for bit, call after call, although every call reuses one fixed scratch array; and
