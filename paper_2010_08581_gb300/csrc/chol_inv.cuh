@@ -126,9 +126,16 @@ __device__ __forceinline__ bool chol_inv_tiles(int n, float tol_scale,
       a[r][c] = (act && col < n && i < n && i >= col) ? xr[r] : 0.f;
     }
   }
-  if (t < 32) {
+  if (t < 32) {   // the largest diagonal entry: all loads issued before the first use
+    float dv[kCiMaxN / 32];
+#pragma unroll
+    for (int q = 0; q < kCiMaxN / 32; ++q) {
+      const int i = t + 32 * q;
+      dv[q] = i < n ? pre[static_cast<int64_t>(i) * lda + i] : 0.f;
+    }
     float md = 0.f;
-    for (int i = t; i < n; i += 32) md = fmaxf(md, pre[static_cast<int64_t>(i) * lda + i]);
+#pragma unroll
+    for (int q = 0; q < kCiMaxN / 32; ++q) md = fmaxf(md, dv[q]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) md = fmaxf(md, __shfl_xor_sync(0xffffffffu, md, o));
     if (t == 0) s.tol = tol_scale * md;

@@ -3,8 +3,9 @@
 //   W = L_f^-1 (explicit, FP32);  z = W^T W b;  r = b - M z;  z += W^T W r,
 // the same arithmetic structure as the substitution kernel's mode 2 (two substitutions, the
 // residual against M's FP32 image, two more substitutions), with each substitution turned
-// into a product by W. The inverse costs one triangular solve per column, done once per
-// factor by many warps in parallel (k_tri_inv); the solves of the I right-hand sides are then
+// into a product by W. W normally comes with the factor from the one-CTA factor-and-inverse
+// pass (chol_inv.cuh); after its fallback factorisation, k_tri_inv forms it with one
+// triangular solve per column, many warps in parallel. The solves of the I right-hand sides are then
 // small dense products (k_solve_inv), which spread over the GPU instead of running one
 // 100-step dependent chain per warp. A dropped column (inverse pivot 0) gives a zero row and
 // column of W, so its unknown is 0 and it updates nothing, as in the substitutions.
