@@ -265,6 +265,26 @@ def rooflines(prof, wl, peaks, k):
     return out
 
 
+_SM_COUNT = []
+
+
+def alu_basis(peaks):
+    """SM count and SM clock (GHz) behind the ALU peaks: the count queried from the device
+    (152 on GB300 when no device is visible), the clock from the measured peaks' sm_max_mhz
+    (GB300's 2070 MHz maximum otherwise)."""
+    if not _SM_COUNT:
+        sms = 152
+        try:
+            if torch.cuda.is_available():
+                sms = int(torch.cuda.get_device_properties(0).multi_processor_count)
+        except Exception:
+            pass
+        _SM_COUNT.append(sms)
+    mhz = (peaks or {}).get("sm_max_mhz")
+    ghz = float(mhz) / 1e3 if isinstance(mhz, (int, float)) and mhz > 0 else 2.07
+    return _SM_COUNT[0], ghz
+
+
 def roofline_entry(name, ms, n, wl, peaks):
     """Roofline object of one kernel: algorithmic work per launch over its average launch time."""
     cost = algorithmic_cost(name, wl)
@@ -272,6 +292,7 @@ def roofline_entry(name, ms, n, wl, peaks):
         return None
     kind, amount = cost
     avg_s = ms / 1e3 / n
+    sms, ghz = alu_basis(peaks)
     if kind == "hbm":
         peak, src = _peak_hbm(peaks)
         ach = amount / avg_s / 1e9
@@ -287,35 +308,35 @@ def roofline_entry(name, ms, n, wl, peaks):
         ach = amount / avg_s / 1e12
         return {"kernel": name, "bound": "alu", "achieved": round(ach, 6), "peak": peak,
                 "unit": "TFLOP/s", "frac": round(ach / peak, 5),
-                "frac_of_one_sm": round(ach / (peak / 152), 4),
+                "frac_of_one_sm": round(ach / (peak / sms), 4),
                 "traffic": traffic_for(name),
-                "peak_source": "nominal FP64 1.25 TFLOP/s for 152 SMs (one-CTA kernels are "
+                "peak_source": f"nominal FP64 1.25 TFLOP/s for {sms} SMs (one-CTA kernels are "
                                "bounded by one SM: see frac_of_one_sm)",
                 "avg_launch_us": round(avg_s * 1e6, 3), "launches": n,
                 "share_of_timed": None}
     if kind == "flops_f32":
-        # SIMT FP32: 152 SMs * 128 FMA/clk * 2 * 2.07 GHz
-        peak = 152 * 128 * 2 * 2.07e9 / 1e12
+        # SIMT FP32: SMs * 128 FMA/clk * 2 * SM clock
+        peak = sms * 128 * 2 * ghz * 1e9 / 1e12
         ach = amount / avg_s / 1e12
         return {"kernel": name, "bound": "alu", "achieved": round(ach, 4), "peak": round(peak, 2),
                 "unit": "TFLOP/s", "frac": round(ach / peak, 5),
-                "frac_of_one_sm": round(ach / (peak / 152), 4),
+                "frac_of_one_sm": round(ach / (peak / sms), 4),
                 "traffic": traffic_for(name),
-                "peak_source": "FP32 SIMT: 152 SMs x 128 FMA/clk x 2 x 2.07 GHz",
+                "peak_source": f"FP32 SIMT: {sms} SMs x 128 FMA/clk x 2 x {ghz:.2f} GHz",
                 "avg_launch_us": round(avg_s * 1e6, 3), "launches": n,
                 "share_of_timed": None}
     if kind == "flops_ff":
         # double-float on the FP32 pipe: one multiply-add a - x*y is 15 FP32 instructions
-        # (Dekker's product via FMA, then a two-sum); 128 lanes/clk/SM at 2.07 GHz
-        per_sm = 128 * 2.07e9 * 2 / 15 / 1e12
-        peak = 152 * per_sm
+        # (Dekker's product via FMA, then a two-sum); 128 lanes/clk/SM at the SM clock
+        per_sm = 128 * ghz * 1e9 * 2 / 15 / 1e12
+        peak = sms * per_sm
         ach = amount / avg_s / 1e12
         return {"kernel": name, "bound": "alu", "achieved": round(ach, 6),
                 "peak": round(peak, 3), "unit": "TFLOP/s", "frac": round(ach / peak, 5),
                 "frac_of_one_sm": round(ach / per_sm, 4),
-                "frac_of_one_sm_fp64": round(ach / (NOMINAL_FP64_TFLOPS / 152), 4),
+                "frac_of_one_sm_fp64": round(ach / (NOMINAL_FP64_TFLOPS / sms), 4),
                 "traffic": traffic_for(name),
-                "peak_source": "double-float on FP32 SIMT: 152 SMs x 128 lanes x 2.07 GHz x "
+                "peak_source": f"double-float on FP32 SIMT: {sms} SMs x 128 lanes x {ghz:.2f} GHz x "
                                "2 flops / 15 instructions per multiply-add (one-CTA kernel: "
                                "see frac_of_one_sm; frac_of_one_sm_fp64 compares with one "
                                "SM's nominal FP64 rate)",

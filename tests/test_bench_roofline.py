@@ -56,3 +56,12 @@ def test_traffic_is_reported_only_for_the_measured_source(tmp_path, monkeypatch)
     src.write_text("kernel v2")
     assert bench.traffic_for("k") is None
     assert bench.traffic_for("absent") is None
+
+
+def test_alu_peaks_follow_the_sm_count_and_the_measured_clock():
+    sms, ghz = bench.alu_basis({"sm_max_mhz": 1000.0})
+    assert ghz == pytest.approx(1.0)
+    r = bench.roofline({"cholesky_solve": [4.0, 100]}, WL, {"sm_max_mhz": 1000.0})
+    assert r["peak"] == pytest.approx(sms * 128 * 2 * 1.0e9 / 1e12, rel=1e-3)
+    assert f"{sms} SMs" in r["peak_source"]
+    assert bench.alu_basis(None)[1] == pytest.approx(2.07)
