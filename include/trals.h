@@ -55,7 +55,9 @@ typedef enum tr_dtype { TR_F32 = 0, TR_F64 = 1 } tr_dtype;
  * TR_PREC_MIXED: design rows and fibres in FP32, contractions with FP32 accumulation.
  *                The normal matrix is factored in FP32 when every pivot exceeds
  *                L*eps32*max diag, else in FP64 (same singular rule as TR_PREC_FP64);
- *                FP32 triangular solves and one step of iterative refinement against the
+ *                FP32 solves (for L <= 128 products by the factor's FP32 inverse, formed
+ *                together with the FP32 factor in one pass; triangular substitutions
+ *                otherwise) and one step of iterative refinement against the
  *                FP32-accurate normal-equation residual. In the drivers, the leverage
  *                scores of a tall matrix (I >= L, 4 <= L <= 128) are those of
  *                tr_leverage_planes: an FP32 Cholesky preconditioner of the double-float
