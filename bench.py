@@ -52,8 +52,9 @@ def workload_config(wl):
                     f"Gaussian noise; target ranks 10, J={wl['J']}, {wl['sweeps']} sweeps per "
                     "step (one whole decomposition), mixed precision: FP32 design rows and "
                     "fibres; TF32x3 tensor-core normal equations with FP32 accumulation; "
-                    "normal matrix factored in FP32 (FP64 if a pivot is small) with FP32 "
-                    "triangular solves and one refinement step; leverage scores from the "
+                    "normal matrix factored in FP32 together with the factor's FP32 "
+                    "inverse (FP64 factorisation if a pivot is small), FP32 solves by "
+                    "that inverse and one refinement step; leverage scores from the "
                     "double-float Gram through an FP32 Cholesky preconditioner and a "
                     "double-float series (the double-float factorisation with FP64 fallback "
                     "when the preconditioner is poor); strided modes read from contiguous "
