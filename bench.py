@@ -181,7 +181,9 @@ def algorithmic_cost(kernel, wl):
       subchain        : J*(N-1)*L*8 slice bytes read + J*L*4 written
       normal_eq_tc    : 2*J*L*(L + I) useful flops (TF32 tensor cores)
       cholesky_leverage: L^3/3 flops in double-float (FP32 pairs; one CTA, mixed path)
-      cholesky_solve  : L^3/3 flops in FP32 (one CTA, mixed path)
+      cholesky_solve  : L^3/3 flops in FP32 (one CTA, mixed path: the factor; the inverse
+                        formed in the same pass replaces the substitutions of solve_rhs,
+                        whose flops are counted there)
       solve_rhs       : 6*L^2*I FP32 flops (two triangular solve pairs + residual)
       gram_f64        : 2*I*L^2 FP64 flops
       leverage_rows   : I*L^2 FP64 flops
